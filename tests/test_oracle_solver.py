@@ -1,0 +1,192 @@
+"""Pins for the oracle's proximity operators, CG and SDMM (Algorithm 1)."""
+import math
+
+import numpy as np
+import pytest
+from scipy.optimize import minimize, minimize_scalar
+
+from oracle import prox, sara
+from oracle import sdmm as S
+from oracle.cg import cg
+from tests._tiny import tiny_problem
+
+
+# ---------------------------------------------------------------- proxes (7)
+@pytest.mark.parametrize("seed", range(5))
+def test_soft_threshold_solves_eq7(seed):
+    rng = np.random.default_rng(seed)
+    for v, tau in zip(rng.normal(0, 2, 20), rng.uniform(0, 2, 20)):
+        r = minimize_scalar(lambda z: tau * abs(z) + 0.5 * (v - z) ** 2,
+                            bounds=(-10, 10), method="bounded", options={"xatol": 1e-12})
+        assert prox.soft_threshold(np.array(v), tau) == pytest.approx(r.x, abs=1e-7)
+    assert prox.soft_threshold(np.array([2.0, -2.0]), 2.0).tolist() == [0.0, 0.0]
+
+
+def test_positive_projection_solves_eq7():
+    rng = np.random.default_rng(1)
+    for v in rng.normal(0, 2, 20):
+        r = minimize_scalar(lambda z: 0.5 * (v - z) ** 2, bounds=(0, 10), method="bounded",
+                            options={"xatol": 1e-12})
+        assert prox.proj_positive(np.array(v)) == pytest.approx(r.x, abs=1e-7)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_ball_projection_solves_eq7(seed):
+    rng = np.random.default_rng(seed)
+    y = rng.standard_normal(3) + 1j * rng.standard_normal(3)
+    v = y + rng.standard_normal(3) * 2 + 1j * rng.standard_normal(3)
+    eps = 0.7
+    to_c = lambda z: z[:3] + 1j * z[3:]
+    res = minimize(lambda z: 0.5 * np.sum(np.abs(v - to_c(z)) ** 2),
+                   np.concatenate([y.real, y.imag]), method="SLSQP",
+                   constraints=[{"type": "ineq", "fun": lambda z: eps ** 2 - np.sum(np.abs(to_c(z) - y) ** 2)}],
+                   options={"ftol": 1e-14, "maxiter": 500})
+    p = prox.proj_l2_ball(v, y, eps)
+    assert np.max(np.abs(p - to_c(res.x))) < 1e-5
+    inside = y + 0.1 * (v - y) / np.linalg.norm(v - y)
+    assert np.array_equal(prox.proj_l2_ball(inside, y, eps), inside)
+
+
+def test_projections_firmly_nonexpansive():
+    rng = np.random.default_rng(7)
+    y = rng.standard_normal(50) + 1j * rng.standard_normal(50)
+    for _ in range(20):
+        a = rng.standard_normal(50) * 3 + 1j * rng.standard_normal(50)
+        b = rng.standard_normal(50) * 3 + 1j * rng.standard_normal(50)
+        for P in (lambda v: prox.proj_l2_ball(v, y, 2.0),):
+            pa, pb = P(a), P(b)
+            lhs = np.sum(np.abs(pa - pb) ** 2)
+            rhs = np.real(np.vdot(pa - pb, a - b))
+            assert lhs <= rhs + 1e-12
+        ra, rb = a.real, b.real
+        for P in (prox.proj_positive, lambda v: prox.soft_threshold(v, 0.3)):
+            pa, pb = P(ra), P(rb)
+            assert np.sum((pa - pb) ** 2) <= np.sum((pa - pb) * (ra - rb)) + 1e-12
+
+
+# ---------------------------------------------------------------- CG (step 5)
+def test_cg_matches_dense_solve():
+    T = tiny_problem()
+    dop, nu = T["dop"], T["nu"]
+    n = T["n"]
+    A = nu * nu * np.real(T["Phi"].conj().T @ T["Phi"]) + 2.0 * np.eye(n * n)
+    b = np.random.default_rng(0).standard_normal(n * n)
+    ref = np.linalg.solve(A, b).reshape(n, n)
+    Q = lambda v: nu * nu * dop.gram_real(v) + 2.0 * v
+    x = cg(Q, b.reshape(n, n), np.zeros((n, n)), 60)
+    assert np.max(np.abs(x - ref)) < 1e-10 * np.max(np.abs(ref))
+    # warm start at the solution stays there
+    x2 = cg(Q, b.reshape(n, n), ref, 5)
+    assert np.max(np.abs(x2 - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+# ---------------------------------------------------------------- SDMM
+def test_composite_operator_identity():
+    """sum_i L_i^H L_i = Psi Psi^H + I + Phi^H Phi = Phi^H Phi + 2I (Section 3)."""
+    T = tiny_problem()
+    x = np.random.default_rng(2).standard_normal((8, 8))
+    lhs = T["dpsi"].synthesis(T["dpsi"].analysis(x)) + x + T["dop"].gram_real(x)
+    rhs = T["dop"].gram_real(x) + 2.0 * x
+    assert np.max(np.abs(lhs - rhs)) < 1e-12 * np.max(np.abs(rhs))
+
+
+def test_feasible_zero_gives_zero():
+    """eps >= ||y||: x = 0 is feasible and minimal, and SDMM never leaves it."""
+    T = tiny_problem()
+    w = np.ones(9 * 64)
+    st = S.sdmm(T["dop"], T["dpsi"], T["y"], 1.01 * np.linalg.norm(T["y"]), 1e-3, w, 50, 10, T["nu"])
+    assert np.all(st.x == 0.0)
+
+
+def test_init_with_x0_is_a_fixed_point_of_the_first_update():
+    """Steps 1-3 with z = 0 give sum_i x_i = Q x0, so step 5 returns x0."""
+    T = tiny_problem()
+    x0 = np.abs(np.random.default_rng(5).standard_normal((8, 8)))
+    st = S.sdmm_init(T["dop"], T["dpsi"], x0, T["nu"])
+    nu = T["nu"]
+    Q = lambda v: nu * nu * T["dop"].gram_real(v) + 2.0 * v
+    assert np.max(np.abs(st.xs - Q(x0))) < 1e-12 * np.max(np.abs(st.xs))
+
+
+def _duality_gap(T, st, w, gamma):
+    """Fenchel dual of problem (3) with the scaled ball (centre nu y, radius
+    nu eps): maximise -Re<u3, nu y> - nu eps ||u3|| subject to |u1| <= w,
+    u2 <= 0 and Psi u1 + u2 + nu Re Phi^H u3 = 0.  SDMM's scaled duals
+    z_i / gamma give the candidate (u1 clipped to its box, u2 the nonpositive
+    part of the balance); returns (relative gap, balance residual)."""
+    nu = T["nu"]
+    u1 = np.clip(st.z1 / gamma, -w, w)
+    u3 = st.z3 / gamma
+    s = T["dpsi"].synthesis(u1) + nu * T["dop"].phi_adj_real(u3)
+    u2 = np.minimum(-s, 0.0)
+    resid = np.linalg.norm(s + u2) / np.linalg.norm(T["dpsi"].synthesis(u1))
+    dual = -np.real(np.vdot(u3, nu * T["y"])) - nu * T["eps"] * np.linalg.norm(u3)
+    primal = float(np.sum(w * np.abs(T["dpsi"].analysis(st.x))))
+    return (primal - dual) / primal, resid
+
+
+@pytest.mark.slow
+def test_sdmm_reaches_the_optimum_of_problem_3():
+    """Algorithm 1 (oracle) closes the convex duality gap of problem (3):
+    a certificate of optimality that does not rely on SDMM's own steps."""
+    T = tiny_problem()
+    w = np.random.default_rng(1).uniform(0.5, 1.5, 9 * 64)
+    gamma = 10.0 * S.default_gamma(T["dop"], T["dpsi"], T["y"], T["nu"])
+    st = S.sdmm(T["dop"], T["dpsi"], T["y"], T["eps"], gamma, w, 1500, 20, T["nu"])
+    gap, resid = _duality_gap(T, st, w, gamma)
+    assert 0.0 <= gap < 1e-6
+    assert resid < 1e-4
+    assert np.linalg.norm(T["y"] - T["dop"].phi(st.x)) <= T["eps"] * (1 + 1e-6)
+    assert st.x.min() >= -1e-6 * st.x.max()
+    # fixed point of Algorithm 1: sum_i L_i^H z_i -> 0
+    nu = T["nu"]
+    bal = T["dpsi"].synthesis(st.z1) + st.z2 + nu * T["dop"].phi_adj_real(st.z3)
+    assert np.linalg.norm(bal) < 1e-5 * np.linalg.norm(T["dpsi"].synthesis(st.z1))
+
+
+def test_planted_sdmm_mistake_is_caught():
+    """Dropping the dual update's sign (z <- z - (Lx - r)) stops SDMM reaching
+    the optimum that the correct iteration reaches."""
+    T = tiny_problem()
+    w = np.ones(9 * 64)
+    gamma = 10.0 * S.default_gamma(T["dop"], T["dpsi"], T["y"], T["nu"])
+    good = S.sdmm(T["dop"], T["dpsi"], T["y"], T["eps"], gamma, w, 400, 20, T["nu"])
+    st = S.sdmm_init(T["dop"], T["dpsi"], np.zeros((8, 8)), T["nu"])
+    nu = T["nu"]
+    Q = lambda v: nu * nu * T["dop"].gram_real(v) + 2.0 * v
+    for _ in range(400):
+        st.x = cg(Q, st.xs, st.x, 20)
+        a1 = T["dpsi"].analysis(st.x)
+        r1 = prox.soft_threshold(a1 + st.z1, gamma * w)
+        st.z1 = st.z1 - (a1 - r1)  # planted sign error
+        v2 = st.x + st.z2
+        r2 = prox.proj_positive(v2)
+        st.z2 = v2 - r2
+        v3 = nu * T["dop"].phi(st.x) + st.z3
+        r3 = prox.proj_l2_ball(v3, nu * T["y"], nu * T["eps"])
+        st.z3 = v3 - r3
+        st.xs = T["dpsi"].synthesis(r1 - st.z1) + (r2 - st.z2) + nu * T["dop"].phi_adj_real(r3 - st.z3)
+    f_good = np.sum(np.abs(T["dpsi"].analysis(good.x)))
+    f_bad = np.sum(np.abs(T["dpsi"].analysis(st.x)))
+    feas_bad = np.linalg.norm(T["y"] - T["dop"].phi(st.x)) <= T["eps"] * 1.01
+    assert not (feas_bad and abs(f_bad - f_good) < 1e-3 * f_good)
+
+
+def test_reweighting_rule():
+    alpha = np.array([0.0, 1.0, -3.0, 1e-9])
+    d = S.delta_schedule(alpha, 1)
+    assert d == pytest.approx(np.std(alpha))
+    assert S.delta_schedule(alpha, 3) == pytest.approx(0.01 * np.std(alpha))
+    assert S.delta_schedule(np.zeros(4), 1) == 1.0
+    w = S.reweight(alpha, 0.5)
+    assert w[0] == 1.0 and np.all((w > 0) & (w <= 1.0))
+    assert w[2] == pytest.approx(0.5 / 3.5)
+
+
+def test_sara_outer_loop_runs_and_is_feasible():
+    T = tiny_problem()
+    gamma = 10.0 * S.default_gamma(T["dop"], T["dpsi"], T["y"], T["nu"])
+    x, rounds = S.sara_solve(T["dop"], T["dpsi"], T["y"], T["eps"], gamma, 300, 20, T["nu"], 2)
+    assert len(rounds) == 3
+    assert np.linalg.norm(T["y"] - T["dop"].phi(x)) <= T["eps"] * 1.01
+    assert x.min() >= -1e-6
