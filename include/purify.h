@@ -1,0 +1,181 @@
+/*
+ * purify.h -- C-ABI of the GB300 SARA-SDMM imaging library (libpurify_gb300.so).
+ *
+ * The library solves the reweighted analysis problem of the paper's
+ * Section 2.2, Eq. 3,
+ *     min_{x in R_+^N} || W Psi^H x ||_1   subject to   || y - Phi x ||_2 <= eps,
+ * by SDMM (Section 3, Algorithm 1) on one GPU, with SARA's reweighting as an
+ * outer loop (Section 2.2).  It exposes the two operator pairs the method is
+ * built from -- the measurement operator Phi (a Kaiser-Bessel NUFFT, Section 4)
+ * with its adjoint, and the SARA dictionary Psi (Section 2.2) with its
+ * adjoint -- and the solver.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Return value: 0 (PURIFY_OK) on success, a negative purify_status otherwise.
+ *   No entry point aborts the process.  purify_strerror() names a code.
+ * - Pointers marked "device" are CUDA device pointers on the current device;
+ *   the caller owns them and keeps them alive until the call has completed on
+ *   `stream`.  The library never frees caller memory.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Operator calls are asynchronous on that stream; purify_sdmm_solve blocks
+ *   until the solve has finished (its stats are then valid).
+ * - Real arrays are float (precision PURIFY_FP32) or double (PURIFY_FP64),
+ *   fixed when the operator is created.  Complex arrays are interleaved
+ *   (re, im) pairs of that type.
+ * - Images are n x n, row-major; pixel (i1, i2) sits at p = (i1 - n/2, i2 - n/2).
+ *   Visibility m is y_m = sum_p x_p exp(-i (u_m p1 + v_m p2)) up to the
+ *   NUFFT's approximation error (unnormalised; u pairs with rows).
+ * - Visibility vectors passed across the ABI are in the caller's uv order;
+ *   the library permutes internally.
+ */
+#ifndef PURIFY_H
+#define PURIFY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct purify_op purify_op;
+
+enum purify_precision { PURIFY_FP32 = 0, PURIFY_FP64 = 1 };
+
+enum purify_status {
+  PURIFY_OK = 0,
+  PURIFY_ERR_INVALID = -1,       /* bad argument: null pointer, size, unsupported option */
+  PURIFY_ERR_NOMEM = -2,         /* device allocation failed */
+  PURIFY_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+  PURIFY_ERR_TIMEOUT = -4,       /* a bounded device-side wait gave up */
+  PURIFY_ERR_NOT_CONVERGED = -5, /* halting rule not met within t_max (x is still valid) */
+  PURIFY_ERR_BUDGET = -6         /* request exceeds the configured device-memory budget */
+};
+
+/*
+ * purify_op_create -- build the measurement operator Phi = G F Z S for a
+ * fixed uv coverage (Section 4: a non-uniform FFT from the discrete image to
+ * continuous visibilities) and the SARA dictionary for `dwt_levels` levels.
+ *   uv          device, double[M][2]: (u_m, v_m) in radians per pixel, any
+ *               real values (taken modulo 2 pi onto [-pi, pi)).
+ *   M           number of visibilities, 1 <= M < 2^31.
+ *   n           image side; a power of two, 16 <= n <= 2048.
+ *   oversample  grid oversampling alpha; must be 2 (grid side K = 2n).
+ *   J           Kaiser-Bessel support in grid cells; must be 8.
+ *   dwt_levels  wavelet levels L, 1 <= L, with n / 2^L >= 2.
+ *   precision   PURIFY_FP32 (float storage, FP64 reductions) or PURIFY_FP64.
+ *   stream      stream for the set-up kernels (uv binning, tables).
+ *   out         receives the new operator; untouched on error.
+ * The operator owns device copies of the sorted uv tiles and tables and is
+ * released by purify_op_destroy.  Synchronises `stream` before returning.
+ */
+int purify_op_create(const double* uv, int64_t M, int n, int oversample, int J,
+                     int dwt_levels, int precision, void* stream, purify_op** out);
+
+/* purify_op_destroy -- free everything the operator owns (NULL is a no-op). */
+int purify_op_destroy(purify_op* op);
+
+/*
+ * purify_op_info -- report sizes fixed at creation (any pointer may be NULL):
+ * image side, visibility count, grid side K, uv tile side, work items,
+ * precision, and device bytes owned by the operator.
+ */
+int purify_op_info(const purify_op* op, int* n, int64_t* M, int* K, int* tile,
+                   int* n_items, int* precision, int64_t* device_bytes);
+
+/*
+ * purify_phi -- y = Phi x (Section 4 NUFFT: deapodise S, zero-pad Z,
+ * 2D FFT F, Kaiser-Bessel degridding G).
+ *   x  device, real[n][n];   y  device, complex[M] (caller's uv order).
+ */
+int purify_phi(purify_op* op, const void* x, void* y, void* stream);
+
+/*
+ * purify_phi_adj -- x = Re(Phi^H y): gridding G^H, inverse FFT, crop Z^T and
+ * deapodise S.  This is the adjoint of Phi restricted to real images (the
+ * problem is posed on R_+^N, Eq. 2-3), so <Phi x, y> = <x, Phi^H y> in the
+ * real inner product.
+ *   y  device, complex[M] (caller's uv order);   x  device, real[n][n].
+ */
+int purify_phi_adj(purify_op* op, const void* y, void* x, void* stream);
+
+/*
+ * purify_sara_fwd -- c = Psi^H x (Section 2.2): the Dirac basis and the
+ * Daubechies Db1..Db8 periodic orthonormal wavelet bases with `dwt_levels`
+ * levels, each scaled by 1/sqrt(9) so that Psi Psi^H = I.
+ *   x  device, real[n][n];   c  device, real[9][n][n], basis-major (block 0
+ *   Dirac, block b the Db_b coefficients in Mallat layout).
+ */
+int purify_sara_fwd(purify_op* op, const void* x, void* c, void* stream);
+
+/* purify_sara_adj -- x = Psi c, the adjoint (and left inverse) of purify_sara_fwd. */
+int purify_sara_adj(purify_op* op, const void* c, void* x, void* stream);
+
+/* Solver parameters (Algorithm 1 and the SARA loop). */
+typedef struct {
+  double eps;         /* l2 bound on the noise, Eq. 2-3 (> 0) */
+  double gamma;       /* SDMM step gamma > 0; <= 0 selects 1e-3 ||Psi^H (nu^2 Phi^H y)||_inf */
+  double nu;          /* scale applied to Phi inside SDMM (problem unchanged); <= 0 selects 1/||Phi||_2 */
+  int t_max;          /* SDMM iterations per reweighting round (>= 1) */
+  int cg_iters;       /* conjugate-gradient steps per global update (>= 1) */
+  double xi;          /* relative objective change for halting; 0 runs exactly t_max iterations */
+  int n_reweight;     /* reweighted solves after the first, unweighted one (>= 0) */
+  double delta0;      /* first reweighting delta; <= 0 selects std of the round-0 coefficients */
+  double delta_min;   /* lower bound on delta; <= 0 selects 1e-4 * delta_1 */
+  double delta_decay; /* delta_k = max(decay^(k-1) delta_1, delta_min); <= 0 selects 0.1 */
+  int warm_start;     /* non-zero: each reweighted round starts from the previous solution */
+  int power_iters;    /* power-iteration steps used when nu <= 0 (>= 1) */
+  int use_graph;      /* non-zero: replay one SDMM iteration as a captured CUDA graph */
+} purify_params;
+
+/* Solver statistics, filled by purify_sdmm_solve. */
+typedef struct {
+  int iterations;       /* SDMM iterations run, all rounds */
+  int rounds;           /* SARA rounds run (1 + reweighted) */
+  int converged;        /* halting rule met in the last round (always 0 when xi == 0) */
+  double objective;     /* ||W Psi^H x||_1 at the returned x, last round's W */
+  double residual;      /* ||y - Phi x||_2 at the returned x */
+  double nu;            /* scale used for Phi inside SDMM */
+  double gamma;         /* gamma used */
+  double elapsed_ms;    /* wall time of the solve on the device stream */
+} purify_stats;
+
+/*
+ * purify_sdmm_solve -- SARA: solve Eq. 3 with W = I by SDMM (Algorithm 1),
+ * then `n_reweight` times update W from the last solution and solve again.
+ *   y      device, complex[M], caller's uv order (the measured visibilities).
+ *   params host, read only.
+ *   x_out  device, real[n][n]: the last round's x_hat.
+ *   stats  host, may be NULL.
+ * Blocks until the solve has finished on `stream`.  Returns
+ * PURIFY_ERR_NOT_CONVERGED (with a valid x_out) when xi > 0 and the halting
+ * rule was not met within t_max in the last round.
+ */
+int purify_sdmm_solve(purify_op* op, const void* y, const purify_params* params,
+                      void* x_out, purify_stats* stats, void* stream);
+
+/*
+ * Kernel timing (instrumentation; the paper has no counterpart).  While
+ * enabled, every kernel the operator launches is bracketed by CUDA events on
+ * its stream and the solver runs without graph replay; purify_profile_read
+ * returns, per kernel kind, the summed device time and launch count since
+ * profiling was enabled.  Kinds: 0 row_fwd, 1 col_fwd, 2 degrid, 3 grid,
+ * 4 gram, 5 col_inv, 6 row_inv, 7 sara_analysis, 8 sara_synthesis,
+ * 9 vector (CG updates and scalar finalisation), 10 memset.
+ */
+enum { PURIFY_NUM_KERNEL_KINDS = 11 };
+int purify_profile(purify_op* op, int enable);
+int purify_profile_read(purify_op* op, int kind, double* total_ms, int64_t* launches);
+const char* purify_kernel_name(int kind);
+
+/* purify_default_params -- the defaults described in purify_params. */
+void purify_default_params(purify_params* p);
+
+/* purify_strerror -- static description of a status code. */
+const char* purify_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PURIFY_H */

@@ -1,0 +1,276 @@
+"""Thin ctypes binding of libpurify_gb300.so (C-ABI in include/purify.h).
+
+Argument marshalling only: every step of the imaging path runs in the
+library's CUDA kernels.  PyTorch supplies device memory and the current
+stream.  The module-level functions carry the C entry points' names; the
+``Operator`` class wraps one ``purify_op`` handle.
+
+Raises ``RuntimeError`` when the library has not been built (there is no
+fallback path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpurify_gb300.so")
+
+PURIFY_FP32, PURIFY_FP64 = 0, 1
+_STATUS = {0: "ok", -1: "invalid argument", -2: "device allocation failed", -3: "CUDA runtime error",
+           -4: "bounded device wait timed out", -5: "halting rule not met within t_max",
+           -6: "device memory budget exceeded"}
+
+
+class PurifyError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {_STATUS.get(code, 'unknown')} ({code})")
+        self.code = code
+
+
+class purify_params(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("gamma", ctypes.c_double), ("nu", ctypes.c_double),
+                ("t_max", ctypes.c_int), ("cg_iters", ctypes.c_int), ("xi", ctypes.c_double),
+                ("n_reweight", ctypes.c_int), ("delta0", ctypes.c_double), ("delta_min", ctypes.c_double),
+                ("delta_decay", ctypes.c_double), ("warm_start", ctypes.c_int), ("power_iters", ctypes.c_int),
+                ("use_graph", ctypes.c_int)]
+
+
+class purify_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("rounds", ctypes.c_int), ("converged", ctypes.c_int),
+                ("objective", ctypes.c_double), ("residual", ctypes.c_double), ("nu", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("elapsed_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["purify_op_create", "purify_op_destroy", "purify_op_info", "purify_phi", "purify_phi_adj",
+           "purify_sara_fwd", "purify_sara_adj", "purify_sdmm_solve", "purify_default_params",
+           "purify_strerror", "purify_profile", "purify_profile_read", "purify_kernel_name"]
+KERNEL_KINDS = ["row_fwd", "col_fwd", "degrid", "grid", "gram", "col_inv", "row_inv", "sara_analysis",
+                "sara_synthesis", "vector", "memset"]
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the CUDA library (once).  Fails loudly if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1406_0359_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.purify_op_create.argtypes = [vp, i64, ci, ci, ci, ci, ci, vp, ctypes.POINTER(vp)]
+    L.purify_op_destroy.argtypes = [vp]
+    L.purify_op_info.argtypes = [vp] + [ctypes.POINTER(ci), ctypes.POINTER(i64), ctypes.POINTER(ci),
+                                        ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci),
+                                        ctypes.POINTER(i64)]
+    for f in ("purify_phi", "purify_phi_adj", "purify_sara_fwd", "purify_sara_adj"):
+        getattr(L, f).argtypes = [vp, vp, vp, vp]
+    L.purify_sdmm_solve.argtypes = [vp, vp, ctypes.POINTER(purify_params), vp, ctypes.POINTER(purify_stats), vp]
+    L.purify_default_params.argtypes = [ctypes.POINTER(purify_params)]
+    L.purify_default_params.restype = None
+    L.purify_strerror.argtypes = [ci]
+    L.purify_strerror.restype = ctypes.c_char_p
+    L.purify_profile.argtypes = [vp, ci]
+    L.purify_profile_read.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+    L.purify_kernel_name.argtypes = [ci]
+    L.purify_kernel_name.restype = ctypes.c_char_p
+    for f in EXPORTS:
+        if f not in ("purify_default_params", "purify_strerror", "purify_kernel_name"):
+            getattr(L, f).restype = ci
+    _lib = L
+    return L
+
+
+def _check(rc: int, where: str, allow=()) -> int:
+    if rc != 0 and rc not in allow:
+        raise PurifyError(rc, where)
+    return rc
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t: torch.Tensor, dtype: torch.dtype, shape=None) -> ctypes.c_void_p:
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous CUDA {dtype} tensor, got {t.dtype} on {t.device}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------- C entry points
+def purify_op_create(uv: torch.Tensor, n: int, dwt_levels: int, precision: int = PURIFY_FP32,
+                     oversample: int = 2, J: int = 8, stream=None) -> ctypes.c_void_p:
+    """uv: CUDA float64 tensor (M, 2) in radians.  Returns the opaque handle."""
+    h = ctypes.c_void_p()
+    _check(lib().purify_op_create(_dptr(uv, torch.float64), uv.shape[0], n, oversample, J, dwt_levels,
+                                  precision, _stream(stream), ctypes.byref(h)), "purify_op_create")
+    return h
+
+
+def purify_op_destroy(h) -> None:
+    if h:
+        lib().purify_op_destroy(h)
+
+
+def purify_op_info(h) -> dict:
+    n, K, tile, ni, prec = (ctypes.c_int() for _ in range(5))
+    M, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().purify_op_info(h, ctypes.byref(n), ctypes.byref(M), ctypes.byref(K), ctypes.byref(tile),
+                                ctypes.byref(ni), ctypes.byref(prec), ctypes.byref(b)), "purify_op_info")
+    return dict(n=n.value, M=M.value, K=K.value, tile=tile.value, n_items=ni.value, precision=prec.value,
+                device_bytes=b.value)
+
+
+def purify_phi(h, x_ptr, y_ptr, stream=None) -> None:
+    _check(lib().purify_phi(h, x_ptr, y_ptr, _stream(stream)), "purify_phi")
+
+
+def purify_phi_adj(h, y_ptr, x_ptr, stream=None) -> None:
+    _check(lib().purify_phi_adj(h, y_ptr, x_ptr, _stream(stream)), "purify_phi_adj")
+
+
+def purify_sara_fwd(h, x_ptr, c_ptr, stream=None) -> None:
+    _check(lib().purify_sara_fwd(h, x_ptr, c_ptr, _stream(stream)), "purify_sara_fwd")
+
+
+def purify_sara_adj(h, c_ptr, x_ptr, stream=None) -> None:
+    _check(lib().purify_sara_adj(h, c_ptr, x_ptr, _stream(stream)), "purify_sara_adj")
+
+
+def purify_default_params() -> purify_params:
+    p = purify_params()
+    lib().purify_default_params(ctypes.byref(p))
+    return p
+
+
+def purify_sdmm_solve(h, y_ptr, params: purify_params, x_ptr, stream=None) -> tuple[int, purify_stats]:
+    st = purify_stats()
+    rc = lib().purify_sdmm_solve(h, y_ptr, ctypes.byref(params), x_ptr, ctypes.byref(st), _stream(stream))
+    _check(rc, "purify_sdmm_solve", allow=(-5,))
+    return rc, st
+
+
+def purify_strerror(code: int) -> str:
+    return lib().purify_strerror(code).decode()
+
+
+def purify_profile(h, enable: bool) -> None:
+    _check(lib().purify_profile(h, int(enable)), "purify_profile")
+
+
+def purify_profile_read(h, kind: int) -> tuple[float, int]:
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(lib().purify_profile_read(h, kind, ctypes.byref(ms), ctypes.byref(n)), "purify_profile_read")
+    return ms.value, n.value
+
+
+def purify_kernel_name(kind: int) -> str:
+    return lib().purify_kernel_name(kind).decode()
+
+
+# ------------------------------------------------------------- convenience
+@dataclass
+class SolveResult:
+    x: torch.Tensor
+    stats: dict
+    status: int
+
+
+class Operator:
+    """One measurement operator + SARA dictionary on the current CUDA device."""
+
+    def __init__(self, uv, n: int, levels: int, precision: str = "fp32", stream=None):
+        self.n, self.levels = n, levels
+        self.prec = PURIFY_FP32 if precision == "fp32" else PURIFY_FP64
+        self.rdtype = torch.float32 if self.prec == PURIFY_FP32 else torch.float64
+        self.cdtype = torch.complex64 if self.prec == PURIFY_FP32 else torch.complex128
+        uv_t = torch.as_tensor(uv, dtype=torch.float64)
+        if not uv_t.is_cuda:
+            uv_t = uv_t.cuda()
+        self.M = uv_t.shape[0]
+        self.h = purify_op_create(uv_t.contiguous(), n, levels, self.prec, stream=stream)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            purify_op_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        return purify_op_info(self.h)
+
+    def profile(self, enable: bool) -> None:
+        purify_profile(self.h, enable)
+
+    def kernel_times(self) -> dict:
+        """{kind: (total_ms, launches)} accumulated since profiling was enabled."""
+        return {KERNEL_KINDS[k]: purify_profile_read(self.h, k) for k in range(len(KERNEL_KINDS))}
+
+    def phi(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        n = self.n
+        y = out if out is not None else torch.empty(self.M, dtype=self.cdtype, device=x.device)
+        purify_phi(self.h, _dptr(x, self.rdtype, (n, n)), _dptr(y, self.cdtype, (self.M,)), stream)
+        return y
+
+    def phi_adj(self, y: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        n = self.n
+        x = out if out is not None else torch.empty(n, n, dtype=self.rdtype, device=y.device)
+        purify_phi_adj(self.h, _dptr(y, self.cdtype, (self.M,)), _dptr(x, self.rdtype, (n, n)), stream)
+        return x
+
+    def sara_fwd(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        n = self.n
+        c = out if out is not None else torch.empty(9, n, n, dtype=self.rdtype, device=x.device)
+        purify_sara_fwd(self.h, _dptr(x, self.rdtype, (n, n)), _dptr(c, self.rdtype, (9, n, n)), stream)
+        return c
+
+    def sara_adj(self, c: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        n = self.n
+        x = out if out is not None else torch.empty(n, n, dtype=self.rdtype, device=c.device)
+        purify_sara_adj(self.h, _dptr(c, self.rdtype, (9, n, n)), _dptr(x, self.rdtype, (n, n)), stream)
+        return x
+
+    def solve(self, y: torch.Tensor, eps: float, t_max: int = 200, cg_iters: int = 10, n_reweight: int = 0,
+              gamma: float = 0.0, nu: float = 0.0, xi: float = 0.0, delta0: float = 0.0,
+              delta_min: float = 0.0, delta_decay: float = 0.1, warm_start: bool = True,
+              power_iters: int = 30, use_graph: bool = True, out: torch.Tensor | None = None,
+              stream=None) -> SolveResult:
+        p = purify_default_params()
+        p.eps, p.gamma, p.nu, p.t_max, p.cg_iters = eps, gamma, nu, t_max, cg_iters
+        p.xi, p.n_reweight, p.delta0, p.delta_min = xi, n_reweight, delta0, delta_min
+        p.delta_decay, p.warm_start, p.power_iters, p.use_graph = delta_decay, int(warm_start), power_iters, int(use_graph)
+        n = self.n
+        x = out if out is not None else torch.empty(n, n, dtype=self.rdtype, device=y.device)
+        rc, st = purify_sdmm_solve(self.h, _dptr(y, self.cdtype, (self.M,)), p, _dptr(x, self.rdtype, (n, n)),
+                                   stream)
+        return SolveResult(x, st.as_dict(), rc)
+
+
+def solve_from_host(uv_host, y_host, n: int, levels: int, eps: float, precision: str = "fp32",
+                    **kw) -> SolveResult:
+    """End-to-end call on host arrays: copy uv and y to the device, build the
+    operator, solve, and copy the image back to host memory."""
+    dev = torch.device("cuda")
+    uv = torch.as_tensor(uv_host, dtype=torch.float64).to(dev, non_blocking=True)
+    op = Operator(uv, n, levels, precision)
+    y = torch.as_tensor(y_host).to(dev, dtype=op.cdtype, non_blocking=True)
+    res = op.solve(y, eps, **kw)
+    x_host = res.x.cpu()
+    op.close()
+    return SolveResult(x_host, res.stats, res.status)

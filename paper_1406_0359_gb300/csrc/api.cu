@@ -1,0 +1,754 @@
+// C-ABI of libpurify_gb300 (include/purify.h): operator set-up, the operator
+// pairs Phi / Phi^H and Psi^H / Psi, and the SDMM solver with the SARA
+// reweighting loop (Section 2.2, Section 3 Algorithm 1) driven from the host,
+// all compute in this library's kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <initializer_list>
+#include <new>
+#include <vector>
+
+#include "../../include/purify.h"
+#include "host_math.h"
+#include "internal.h"
+#include "solver_kernels.h"
+
+struct purify_op {
+  virtual ~purify_op() {}
+  virtual int phi(const void* x, void* y, cudaStream_t s) = 0;
+  virtual int phi_adj(const void* y, void* x, cudaStream_t s) = 0;
+  virtual int sara_fwd(const void* x, void* c, cudaStream_t s) = 0;
+  virtual int sara_adj(const void* c, void* x, cudaStream_t s) = 0;
+  virtual int solve(const void* y, const purify_params* p, void* x, purify_stats* st, cudaStream_t s) = 0;
+  virtual void info(int* n, int64_t* M, int* K, int* tile, int* n_items, int* precision, int64_t* bytes) const = 0;
+
+  // ---- kernel timing (instrumentation)
+  enum Kind { KK_ROW_FWD = 0, KK_COL_FWD, KK_DEGRID, KK_GRID, KK_GRAM, KK_COL_INV, KK_ROW_INV, KK_SARA_ANA,
+              KK_SARA_SYN, KK_VEC, KK_MEMSET, KK_COUNT };
+  bool prof = false;
+  struct Pending { int kind; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[KK_COUNT] = {0};
+  int64_t prof_n[KK_COUNT] = {0};
+  cudaStream_t prof_stream = nullptr;
+  int prof_kind = -1;
+  cudaEvent_t ev() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void prof_begin(int kind, cudaStream_t s) {
+    if (!prof) return;
+    Pending p{kind, ev(), ev()};
+    cudaEventRecord(p.a, s);
+    pending.push_back(p);
+  }
+  void prof_end(cudaStream_t s) {
+    if (!prof || pending.empty()) return;
+    cudaEventRecord(pending.back().b, s);
+  }
+  void prof_collect() {
+    for (auto& p : pending) {
+      float ms = 0.f;
+      if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        prof_ms[p.kind] += ms;
+        prof_n[p.kind] += 1;
+      }
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+  void prof_reset() {
+    prof_collect();
+    for (int k = 0; k < KK_COUNT; ++k) {
+      prof_ms[k] = 0;
+      prof_n[k] = 0;
+    }
+  }
+  void prof_release() {
+    prof_collect();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+  }
+};
+
+#define PROF(kind, stream, stmt) \
+  do {                           \
+    prof_begin(kind, stream);    \
+    stmt;                        \
+    prof_end(stream);            \
+  } while (0)
+
+namespace purify {
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+int map_err(cudaError_t e) {
+  if (e == cudaSuccess) return PURIFY_OK;
+  if (e == cudaErrorMemoryAllocation) return PURIFY_ERR_NOMEM;
+  return PURIFY_ERR_CUDA;
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return map_err(e_);     \
+  } while (0)
+
+template <typename T> class OpImpl : public purify_op {
+  typedef typename cplx_t<T>::type C;
+
+ public:
+  Geometry g{};
+  int levels = 0, chunk = 0, n_items = 0;
+  Pos<T>* pos = nullptr;
+  int* perm = nullptr;
+  WorkItem* items = nullptr;
+  T* deapod = nullptr;
+  C* tw = nullptr;
+  C* gridA = nullptr;
+  C* gridP = nullptr;
+  C* gridQ = nullptr;
+  CUtensorMap tmap;
+  KbPoly<T> kb;
+  SaraPlan<T> sara{};
+  double* partials = nullptr;
+  double* sc = nullptr;
+  double* h_sc = nullptr;
+  int* err = nullptr;
+  // solver state
+  T *xh = nullptr, *xs = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr;
+  T *z1 = nullptr, *z2 = nullptr, *w = nullptr;
+  C *z3 = nullptr, *ys = nullptr;
+  int64_t bytes = 0;
+  std::vector<void*> allocs;
+
+  ~OpImpl() override {
+    prof_release();
+    for (void* a : allocs) cudaFree(a);
+    if (h_sc) cudaFreeHost(h_sc);
+  }
+
+  template <typename U> int alloc(U** ptr, size_t count) {
+    void* a = nullptr;
+    const size_t b = count * sizeof(U) > 0 ? count * sizeof(U) : 16;
+    CK(cudaMalloc(&a, b));
+    allocs.push_back(a);
+    bytes += int64_t(b);
+    *ptr = static_cast<U*>(a);
+    return PURIFY_OK;
+  }
+
+  size_t N() const { return size_t(g.n) * g.n; }
+  size_t grid_bytes() const { return size_t(g.KP) * g.KP * sizeof(C); }
+
+  int create(const double* uv, int64_t M, int n, int L, cudaStream_t s) {
+    g.n = n;
+    g.K = 2 * n;
+    g.KP = g.K + kJ;
+    g.pad_lo = kJ / 2 - 1;
+    g.TB = g.K >= 1024 ? 32 : 16;
+    if (g.TB > g.K) g.TB = g.K;
+    g.ntile1d = g.K / g.TB;
+    g.M = M;
+    levels = L;
+    chunk = 1024;
+    CK(configure_fft<T>());
+    CK(configure_nufft<T>());
+    CK(configure_sara<T>());
+    // tables: deapodisation, twiddles, kernel polynomial, filters (host, double)
+    const double beta = kb_beta(kJ, 2.0);
+    std::vector<T> hs(n);
+    for (int i = 0; i < n; ++i) hs[i] = T(1.0 / kb_fourier(double(i - n / 2) / g.K, kJ, beta));
+    std::vector<C> htw(g.K);
+    for (int m = 0; m < g.K; ++m) {
+      const double a = -2.0 * M_PI * double(m) / g.K;
+      htw[m].x = T(std::cos(a));
+      htw[m].y = T(std::sin(a));
+    }
+    std::vector<double> coef;
+    constexpr int D = KbDeg<T>::value;
+    kb_poly_fit(kJ, beta, D, coef);
+    for (int a = 0; a < kJ; ++a)
+      for (int d = 0; d <= D; ++d) kb.c[a][d] = T(coef[size_t(a) * (D + 1) + d]);
+    std::memset(&sara.f, 0, sizeof(sara.f));
+    for (int k = 1; k <= kMaxDb; ++k) {
+      const std::vector<double> h = daubechies_lowpass(k);
+      const int F = 2 * k;
+      for (int m = 0; m < F; ++m) {
+        sara.f.h[k - 1][m] = T(h[m]);
+        sara.f.g[k - 1][m] = T(((m & 1) ? -1.0 : 1.0) * h[F - 1 - m]);
+      }
+    }
+    int rc;
+    if ((rc = alloc(&deapod, n))) return rc;
+    if ((rc = alloc(&tw, g.K))) return rc;
+    if ((rc = alloc(&pos, M))) return rc;
+    if ((rc = alloc(&perm, M))) return rc;
+    if ((rc = alloc(&gridA, size_t(n) * g.K))) return rc;
+    if ((rc = alloc(&gridP, size_t(g.KP) * g.KP))) return rc;
+    if ((rc = alloc(&gridQ, size_t(g.KP) * g.KP))) return rc;
+    if ((rc = alloc(&sc, kNumScalars))) return rc;
+    if ((rc = alloc(&err, 1))) return rc;
+    sara.n = n;
+    sara.levels = L;
+    if ((rc = alloc(&sara.s0, 8 * N() / 4))) return rc;
+    if ((rc = alloc(&sara.s1, 8 * N() / 4))) return rc;
+    if ((rc = alloc(&sara.cs, 9 * N()))) return rc;
+    CK(cudaMallocHost(&h_sc, kNumScalars * sizeof(double)));
+    CK(cudaMemcpyAsync(deapod, hs.data(), n * sizeof(T), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(tw, htw.data(), g.K * sizeof(C), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(sc, 0, kNumScalars * sizeof(double), s));
+    CK(cudaMemsetAsync(gridP, 0, grid_bytes(), s));
+    rc = build_bins<T>(uv, M, g, chunk, pos, perm, &items, &n_items, s);
+    if (rc) return rc;
+    allocs.push_back(items);
+    bytes += int64_t(n_items) * sizeof(WorkItem);
+    const int np = std::max({2 * n_items, row_inv_blocks(g), sara_partials_capacity(n, L), vec_blocks(9 * N()), 1});
+    if ((rc = alloc(&partials, np))) return rc;
+    // TMA descriptor of the padded forward grid, 8-byte elements
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return PURIFY_ERR_CUDA;
+    const int cw = int(sizeof(C) / 8);
+    const int PW = g.TB + kJ;
+    cuuint64_t dims[2] = {cuuint64_t(g.KP) * cw, cuuint64_t(g.KP)};
+    cuuint64_t strides[1] = {cuuint64_t(g.KP) * sizeof(C)};
+    cuuint32_t box[2] = {cuuint32_t(PW * cw), cuuint32_t(PW)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult cr = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, gridP, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return PURIFY_ERR_CUDA;
+    CK(cudaStreamSynchronize(s));
+    return PURIFY_OK;
+  }
+
+  void info(int* n, int64_t* M, int* K, int* tile, int* ni, int* prec, int64_t* b) const override {
+    if (n) *n = g.n;
+    if (M) *M = g.M;
+    if (K) *K = g.K;
+    if (tile) *tile = g.TB;
+    if (ni) *ni = n_items;
+    if (prec) *prec = sizeof(T) == 4 ? PURIFY_FP32 : PURIFY_FP64;
+    if (b) *b = bytes;
+  }
+
+  // ---- operator building blocks (enqueue only)
+  void fwd_grid(const RowPro<T>& pro, cudaStream_t s) {
+    PROF(KK_ROW_FWD, s, launch_row_fwd<T>(g, pro, deapod, gridA, tw, s));
+    PROF(KK_COL_FWD, s, launch_col_fwd<T>(g, gridA, gridP, tw, s));
+  }
+  void zero_q(cudaStream_t s) { PROF(KK_MEMSET, s, cudaMemsetAsync(gridQ, 0, grid_bytes(), s)); }
+  void col_inv(cudaStream_t s) { PROF(KK_COL_INV, s, launch_col_inv<T>(g, gridQ, gridA, tw, s)); }
+  void degrid(const DegridEp<C>& ep, cudaStream_t s) {
+    PROF(KK_DEGRID, s, launch_degrid<T>(g, tmap, items, n_items, pos, perm, kb, ep, err, s));
+  }
+  void grid(const GridPro<C>& pro, cudaStream_t s) {
+    PROF(KK_GRID, s, launch_grid<T>(g, items, n_items, pos, perm, kb, pro, gridQ, s));
+  }
+  void fin(const double* pa, int na, const double* pb, int nb, int op, double arg, cudaStream_t s) {
+    PROF(KK_VEC, s, launch_finalize(pa, na, pb, nb, op, arg, sc, s));
+  }
+  RowPro<T> plain(const T* x) const {
+    RowPro<T> pro{};
+    pro.mode = PRO_PLAIN;
+    pro.x = x;
+    return pro;
+  }
+  // Re(Phi^H Phi) up to the row epilogue: forward passes, gram, inverse column pass.
+  void gram_front(const RowPro<T>& pro, cudaStream_t s) {
+    fwd_grid(pro, s);
+    zero_q(s);
+    PROF(KK_GRAM, s, launch_gram<T>(g, tmap, items, n_items, pos, kb, gridQ, err, s));
+    col_inv(s);
+  }
+  int row_ep(const RowEp<T>& ep, cudaStream_t s) {
+    int np = 0;
+    PROF(KK_ROW_INV, s, np = launch_row_inv<T>(g, gridA, deapod, ep, tw, s));
+    return np;
+  }
+
+  int check(cudaStream_t s, bool sync) {
+    CK(cudaGetLastError());
+    if (sync) {
+      CK(cudaStreamSynchronize(s));
+      int h = 0;
+      CK(cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (h) {
+        cudaMemset(err, 0, sizeof(int));
+        return PURIFY_ERR_TIMEOUT;
+      }
+    }
+    return PURIFY_OK;
+  }
+
+  // ---- public operators
+  int phi(const void* x, void* y, cudaStream_t s) override {
+    fwd_grid(plain(static_cast<const T*>(x)), s);
+    DegridEp<C> ep{};
+    ep.mode = DG_STORE_PERM;
+    ep.y = static_cast<C*>(y);
+    degrid(ep, s);
+    return check(s, false);
+  }
+
+  int phi_adj(const void* y, void* x, cudaStream_t s) override {
+    zero_q(s);
+    GridPro<C> pro{};
+    pro.mode = GP_PERM;
+    pro.y = static_cast<const C*>(y);
+    grid(pro, s);
+    col_inv(s);
+    RowEp<T> ep{};
+    ep.mode = EP_STORE;
+    ep.out = static_cast<T*>(x);
+    row_ep(ep, s);
+    return check(s, false);
+  }
+
+  int sara_fwd(const void* x, void* c, cudaStream_t s) override {
+    PROF(KK_SARA_ANA, s, sara_analysis<T>(sara, static_cast<const T*>(x), static_cast<T*>(c), s));
+    return check(s, false);
+  }
+  int sara_adj(const void* c, void* x, cudaStream_t s) override {
+    PROF(KK_SARA_SYN, s, sara_synthesis<T>(sara, static_cast<const T*>(c), static_cast<T*>(x), s));
+    return check(s, false);
+  }
+
+  // ---- solver
+  int ensure_solver() {
+    if (xh) return PURIFY_OK;
+    int rc;
+    const size_t n2 = N();
+    if ((rc = alloc(&xh, n2)) || (rc = alloc(&xs, n2)) || (rc = alloc(&r, n2)) || (rc = alloc(&p, n2)) ||
+        (rc = alloc(&Ap, n2)) || (rc = alloc(&z1, 9 * n2)) || (rc = alloc(&z2, n2)) || (rc = alloc(&w, 9 * n2)) ||
+        (rc = alloc(&z3, size_t(g.M))) || (rc = alloc(&ys, size_t(g.M))))
+      return rc;
+    return PURIFY_OK;
+  }
+
+  int read_scalars(cudaStream_t s) {
+    CK(cudaMemcpyAsync(h_sc, sc, kNumScalars * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return PURIFY_OK;
+  }
+
+  // ||Phi||^2 by power iteration on Re(Phi^H Phi) from the all-ones image / n.
+  int power_norm_sq(int iters, double* lam, cudaStream_t s) {
+    launch_fill<T>(p, N(), T(1.0 / g.n), s);
+    for (int it = 0; it < iters; ++it) {
+      RowPro<T> pro{};
+      if (it == 0) {
+        pro = plain(p);
+      } else {
+        pro.mode = PRO_SCALE;
+        pro.x = Ap;
+        pro.scalars = sc;
+        pro.idx = S_INVNORM;
+      }
+      gram_front(pro, s);
+      RowEp<T> ep{};
+      ep.mode = EP_POWER;
+      ep.out = Ap;
+      ep.partials = partials;
+      const int np = row_ep(ep, s);
+      fin(partials, np, nullptr, 0, FIN_NORM, 0.0, s);
+    }
+    int rc = check(s, true);
+    if (rc) return rc;
+    if ((rc = read_scalars(s))) return rc;
+    *lam = h_sc[S_LAMBDA];
+    return PURIFY_OK;
+  }
+
+  // 1e-3 ||Psi^H (nu^2 Re Phi^H y)||_inf with y the sorted visibilities.
+  int default_gamma(double nu, double* gamma, cudaStream_t s) {
+    zero_q(s);
+    GridPro<C> pro{};
+    pro.mode = GP_SORTED;
+    pro.y = ys;
+    grid(pro, s);
+    col_inv(s);
+    RowEp<T> ep{};
+    ep.mode = EP_STORE;
+    ep.out = Ap;
+    row_ep(ep, s);
+    sara_analysis<T>(sara, Ap, z1, s);
+    const int np = launch_reduce<T>(z1, 9 * N(), RED_MAXABS, sc, partials, s);
+    launch_max_partials(partials, np, sc, s);
+    int rc = check(s, true);
+    if (rc) return rc;
+    if ((rc = read_scalars(s))) return rc;
+    *gamma = 1e-3 * nu * nu * h_sc[S_MAXABS];
+    return PURIFY_OK;
+  }
+
+  // Population standard deviation of Psi^H x_hat (reweighting delta_1).
+  int coef_std(double* out, cudaStream_t s) {
+    sara_analysis<T>(sara, xh, z1, s);
+    const size_t D = 9 * N();
+    int np = launch_reduce<T>(z1, D, RED_SUM, sc, partials, s);
+    launch_finalize(partials, np, nullptr, 0, FIN_MEAN, double(D), sc, s);
+    np = launch_reduce<T>(z1, D, RED_VAR, sc, partials, s);
+    launch_finalize(partials, np, nullptr, 0, FIN_VAR, double(D), sc, s);
+    int rc = check(s, true);
+    if (rc) return rc;
+    if ((rc = read_scalars(s))) return rc;
+    *out = h_sc[S_STD];
+    return PURIFY_OK;
+  }
+
+  // One SDMM iteration (Algorithm 1, steps 5-10), enqueue only.
+  void iteration(double nu, double gamma, double eps, int cg_iters, cudaStream_t s) {
+    const double nu2 = nu * nu;
+    const size_t n2 = N();
+    // step 5: x_hat = (Phi^H Phi + 2I)^-1 sum_i x_i by CG, warm-started at x_hat
+    gram_front(plain(xh), s);
+    {
+      RowEp<T> ep{};
+      ep.mode = EP_CG_R0;
+      ep.out = r;
+      ep.out2 = p;
+      ep.p = xh;
+      ep.b = xs;
+      ep.nu2 = nu2;
+      ep.partials = partials;
+      const int np = row_ep(ep, s);
+      fin(partials, np, nullptr, 0, FIN_RR0, 0.0, s);
+    }
+    for (int it = 0; it < cg_iters; ++it) {
+      RowPro<T> pro = plain(p);
+      if (it > 0) {
+        pro.mode = PRO_CG_P;
+        pro.p = p;
+        pro.r = r;
+        pro.scalars = sc;
+        pro.idx = S_BETA;
+      }
+      gram_front(pro, s);
+      RowEp<T> ep{};
+      ep.mode = EP_CG_AP;
+      ep.out = Ap;
+      ep.p = p;
+      ep.nu2 = nu2;
+      ep.partials = partials;
+      int np = row_ep(ep, s);
+      fin(partials, np, nullptr, 0, FIN_ALPHA, 0.0, s);
+      PROF(KK_VEC, s, np = launch_cg_xr<T>(xh, r, p, Ap, sc, n2, partials, s));
+      fin(partials, np, nullptr, 0, FIN_BETA, 0.0, s);
+    }
+    // block 1 (l1 on Psi^H x_hat) fused into the analysis, block 2 (positivity)
+    // fused into the synthesis: xs = x_1 + x_2
+    L1Block<T> b1{};
+    b1.z1 = z1;
+    b1.w = w;
+    b1.gamma = gamma;
+    b1.partials = partials;
+    int npo = 0;
+    PROF(KK_SARA_ANA, s, npo = sara_analysis_prox<T>(sara, xh, b1, s));
+    fin(partials, npo, nullptr, 0, FIN_OBJ, 0.0, s);
+    PROF(KK_SARA_SYN, s, sara_synthesis_pos<T>(sara, xh, z2, xs, s));
+    // block 3 (data fidelity): v = nu Phi x_hat + z_3, project on the ball,
+    // xs += nu Re Phi^H (2r - v)
+    fwd_grid(plain(xh), s);
+    DegridEp<C> dep{};
+    dep.mode = DG_BALL;
+    dep.z = z3;
+    dep.ys = ys;
+    dep.nu = nu;
+    dep.part0 = partials;
+    dep.part1 = partials + n_items;
+    degrid(dep, s);
+    fin(partials, n_items, partials + n_items, n_items, FIN_BALL, nu * eps, s);
+    zero_q(s);
+    GridPro<C> gp{};
+    gp.mode = GP_BALL;
+    gp.z = z3;
+    gp.ys = ys;
+    gp.nu = nu;
+    gp.scalars = sc;
+    gp.scale_idx = S_BALLSCALE;
+    grid(gp, s);
+    col_inv(s);
+    RowEp<T> ep{};
+    ep.mode = EP_XS_ADD;
+    ep.out = xs;
+    ep.b = xs;
+    ep.nu = nu;
+    row_ep(ep, s);
+  }
+
+  int solve(const void* y, const purify_params* P, void* x_out, purify_stats* st, cudaStream_t s) override {
+    if (!(P->eps > 0) || P->t_max < 1 || P->cg_iters < 1 || P->n_reweight < 0 || P->xi < 0 ||
+        (P->nu <= 0 && P->power_iters < 1))
+      return PURIFY_ERR_INVALID;
+    int rc = ensure_solver();
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+    const size_t n2 = N(), M = size_t(g.M);
+    launch_gather<C>(static_cast<const C*>(y), perm, M, ys, s);
+    double nu = P->nu;
+    if (!(nu > 0)) {
+      double lam = 0;
+      if ((rc = power_norm_sq(P->power_iters, &lam, s))) return rc;
+      nu = lam > 0 ? 1.0 / std::sqrt(lam) : 1.0;
+    }
+    double gamma = P->gamma;
+    if (!(gamma > 0)) {
+      if ((rc = default_gamma(nu, &gamma, s))) return rc;
+      if (!(gamma > 0)) gamma = 1e-12;
+    }
+    const double decay = P->delta_decay > 0 ? P->delta_decay : 0.1;
+    double delta1 = 0.0;
+    int total_iters = 0, converged = 0;
+    double obj = 0.0, resid = 0.0;
+    cudaGraphExec_t gexec = nullptr;
+    if (P->use_graph && !prof) {
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      iteration(nu, gamma, P->eps, P->cg_iters, s);
+      cudaError_t ce = cudaStreamEndCapture(s, &graph);
+      if (ce != cudaSuccess) return map_err(ce);
+      ce = cudaGraphInstantiate(&gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) return map_err(ce);
+    }
+    launch_fill<T>(w, 9 * n2, T(1), s);
+    CK(cudaMemsetAsync(xh, 0, n2 * sizeof(T), s));
+    for (int round = 0; round <= P->n_reweight; ++round) {
+      if (round > 0) {
+        if (round == 1) {
+          if (P->delta0 > 0) {
+            delta1 = P->delta0;
+          } else {
+            if ((rc = coef_std(&delta1, s))) break;
+          }
+          if (!(delta1 > 0)) delta1 = 1.0;
+        }
+        const double dmin = P->delta_min > 0 ? P->delta_min : 1e-4 * delta1;
+        const double delta = std::max(std::pow(decay, round - 1) * delta1, dmin);
+        sara_analysis<T>(sara, xh, w, s);
+        launch_reweight<T>(w, 9 * n2, delta, s);
+      }
+      cudaMemsetAsync(z1, 0, 9 * n2 * sizeof(T), s);
+      cudaMemsetAsync(z2, 0, n2 * sizeof(T), s);
+      cudaMemsetAsync(z3, 0, M * sizeof(C), s);
+      if (round > 0 && P->warm_start) {
+        // steps 1-3 with x_hat^(0) = previous solution: sum_i x_i = (Phi^H Phi + 2I) x_hat^(0)
+        gram_front(plain(xh), s);
+        RowEp<T> ep{};
+        ep.mode = EP_QX;
+        ep.out = xs;
+        ep.p = xh;
+        ep.nu2 = nu * nu;
+        row_ep(ep, s);
+      } else {
+        cudaMemsetAsync(xh, 0, n2 * sizeof(T), s);
+        cudaMemsetAsync(xs, 0, n2 * sizeof(T), s);
+      }
+      if ((rc = check(s, false))) break;
+      double prev = -1.0;
+      converged = 0;
+      for (int t = 0; t < P->t_max; ++t) {
+        if (gexec) {
+          CK(cudaGraphLaunch(gexec, s));
+        } else {
+          iteration(nu, gamma, P->eps, P->cg_iters, s);
+        }
+        ++total_iters;
+        if (P->xi > 0) {
+          if ((rc = check(s, true)) || (rc = read_scalars(s))) break;
+          const double f = h_sc[S_OBJ], res = h_sc[S_RESID];
+          if (prev >= 0 && std::fabs(f - prev) / std::max(prev, 1e-300) < P->xi && res <= P->eps * (1 + 1e-3)) {
+            converged = 1;
+            break;
+          }
+          prev = f;
+        }
+      }
+      if (rc) break;
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(x_out, xh, n2 * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    CK(cudaEventRecord(e1, s));
+    if ((rc = check(s, true))) return rc;
+    if ((rc = read_scalars(s))) return rc;
+    prof_collect();
+    obj = h_sc[S_OBJ];
+    resid = h_sc[S_RESID];
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) {
+      st->iterations = total_iters;
+      st->rounds = P->n_reweight + 1;
+      st->converged = converged;
+      st->objective = obj;
+      st->residual = resid;
+      st->nu = nu;
+      st->gamma = gamma;
+      st->elapsed_ms = ms;
+    }
+    if (P->xi > 0 && !converged) return PURIFY_ERR_NOT_CONVERGED;
+    return PURIFY_OK;
+  }
+};
+
+}  // namespace
+}  // namespace purify
+
+using purify::OpImpl;
+
+extern "C" {
+
+int purify_op_create(const double* uv, int64_t M, int n, int oversample, int J, int dwt_levels, int precision,
+                     void* stream, purify_op** out) {
+  if (!uv || !out || M < 1 || M >= (int64_t(1) << 31) || n < 16 || n > 2048 || (n & (n - 1)) ||
+      oversample != 2 || J != purify::kJ || dwt_levels < 1 || (n >> dwt_levels) < 2 ||
+      (precision != PURIFY_FP32 && precision != PURIFY_FP64))
+    return PURIFY_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  purify_op* op = nullptr;
+  int rc;
+  if (precision == PURIFY_FP32) {
+    OpImpl<float>* o = new (std::nothrow) OpImpl<float>();
+    if (!o) return PURIFY_ERR_NOMEM;
+    rc = o->create(uv, M, n, dwt_levels, s);
+    op = o;
+  } else {
+    OpImpl<double>* o = new (std::nothrow) OpImpl<double>();
+    if (!o) return PURIFY_ERR_NOMEM;
+    rc = o->create(uv, M, n, dwt_levels, s);
+    op = o;
+  }
+  if (rc) {
+    delete op;
+    return rc;
+  }
+  *out = op;
+  return PURIFY_OK;
+}
+
+int purify_op_destroy(purify_op* op) {
+  delete op;
+  return PURIFY_OK;
+}
+
+int purify_op_info(const purify_op* op, int* n, int64_t* M, int* K, int* tile, int* n_items, int* precision,
+                   int64_t* device_bytes) {
+  if (!op) return PURIFY_ERR_INVALID;
+  op->info(n, M, K, tile, n_items, precision, device_bytes);
+  return PURIFY_OK;
+}
+
+int purify_phi(purify_op* op, const void* x, void* y, void* stream) {
+  if (!op || !x || !y) return PURIFY_ERR_INVALID;
+  return op->phi(x, y, static_cast<cudaStream_t>(stream));
+}
+
+int purify_phi_adj(purify_op* op, const void* y, void* x, void* stream) {
+  if (!op || !x || !y) return PURIFY_ERR_INVALID;
+  return op->phi_adj(y, x, static_cast<cudaStream_t>(stream));
+}
+
+int purify_sara_fwd(purify_op* op, const void* x, void* c, void* stream) {
+  if (!op || !x || !c) return PURIFY_ERR_INVALID;
+  return op->sara_fwd(x, c, static_cast<cudaStream_t>(stream));
+}
+
+int purify_sara_adj(purify_op* op, const void* c, void* x, void* stream) {
+  if (!op || !x || !c) return PURIFY_ERR_INVALID;
+  return op->sara_adj(c, x, static_cast<cudaStream_t>(stream));
+}
+
+int purify_profile(purify_op* op, int enable) {
+  if (!op) return PURIFY_ERR_INVALID;
+  op->prof_reset();
+  op->prof = enable != 0;
+  return PURIFY_OK;
+}
+
+int purify_profile_read(purify_op* op, int kind, double* total_ms, int64_t* launches) {
+  if (!op || kind < 0 || kind >= PURIFY_NUM_KERNEL_KINDS) return PURIFY_ERR_INVALID;
+  op->prof_collect();
+  if (total_ms) *total_ms = op->prof_ms[kind];
+  if (launches) *launches = op->prof_n[kind];
+  return PURIFY_OK;
+}
+
+const char* purify_kernel_name(int kind) {
+  static const char* names[] = {"row_fwd", "col_fwd", "degrid", "grid", "gram", "col_inv",
+                                "row_inv", "sara_analysis", "sara_synthesis", "vector", "memset"};
+  if (kind < 0 || kind >= PURIFY_NUM_KERNEL_KINDS) return "unknown";
+  return names[kind];
+}
+
+void purify_default_params(purify_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->eps = 0.0;
+  p->gamma = 0.0;
+  p->nu = 0.0;
+  p->t_max = 200;
+  p->cg_iters = 10;
+  p->xi = 0.0;
+  p->n_reweight = 0;
+  p->delta0 = 0.0;
+  p->delta_min = 0.0;
+  p->delta_decay = 0.1;
+  p->warm_start = 1;
+  p->power_iters = 30;
+  p->use_graph = 1;
+}
+
+int purify_sdmm_solve(purify_op* op, const void* y, const purify_params* params, void* x_out, purify_stats* stats,
+                      void* stream) {
+  if (!op || !y || !params || !x_out) return PURIFY_ERR_INVALID;
+  return op->solve(y, params, x_out, stats, static_cast<cudaStream_t>(stream));
+}
+
+const char* purify_strerror(int status) {
+  switch (status) {
+    case PURIFY_OK: return "ok";
+    case PURIFY_ERR_INVALID: return "invalid argument";
+    case PURIFY_ERR_NOMEM: return "device allocation failed";
+    case PURIFY_ERR_CUDA: return "CUDA runtime error";
+    case PURIFY_ERR_TIMEOUT: return "bounded device wait timed out";
+    case PURIFY_ERR_NOT_CONVERGED: return "halting rule not met within t_max";
+    case PURIFY_ERR_BUDGET: return "device memory budget exceeded";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+// Shared device helpers for the GB300 SARA-SDMM kernels: complex arithmetic,
+// FP64 block reductions, bounded mbarrier waits and TMA copies (sm_103a).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define PD __device__ __forceinline__
+
+namespace purify {
+
+template <typename T> struct cplx_t;
+template <> struct cplx_t<float> { typedef float2 type; };
+template <> struct cplx_t<double> { typedef double2 type; };
+
+template <typename C> PD C cz() { C r; r.x = 0; r.y = 0; return r; }
+template <typename C, typename T> PD C cmk(T a, T b) { C r; r.x = a; r.y = b; return r; }
+template <typename C> PD C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> PD C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> PD C cmul(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+template <typename C, typename T> PD C cscale(C a, T s) { a.x *= s; a.y *= s; return a; }
+template <typename C> PD C cmul_i(C a) { C r; r.x = -a.y; r.y = a.x; return r; }  // i * a
+
+// Device error flag values (first writer wins).
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1 };
+
+// Bounded spin budget for mbarrier waits: far beyond any TMA latency, short
+// enough that a lost transaction surfaces as an error instead of a hang.
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+PD void set_error(int* err, int code) {
+  if (err) atomicCAS(err, DEV_OK, code);
+}
+
+// ---------------------------------------------------------------- reductions
+PD double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+PD double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Deterministic block sum (fixed tree order); result valid in thread 0.
+template <int NT> __device__ double block_sum(double v, double* sh /*[32]*/) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = (lane < NT / 32) ? sh[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  __syncthreads();
+  return r;
+}
+template <int NT> __device__ double block_max(double v, double* sh) {
+  v = warp_max(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = (lane < NT / 32) ? sh[lane] : 0.0;
+    r = warp_max(r);
+  }
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------- mbarrier + TMA
+PD uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+PD void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+PD void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+PD void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+PD void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+PD bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+// Wait for `phase` of `bar` with a bounded spin; on timeout flag the error,
+// keep waiting (bounded again) so the copy in flight lands before the CTA
+// can exit, and return false.
+PD bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, int* err) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, phase)) return true;
+  set_error(err, DEV_TIMEOUT);
+  for (uint32_t i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, phase)) break;
+  return false;
+}
+PD void tma_load_2d(void* smem_dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(smem_dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+}  // namespace purify

@@ -1,0 +1,189 @@
+// Internal data layout and kernel launchers of the GB300 SARA-SDMM path.
+//
+// HBM layout of one operator (T = float or double, C = complex<T>):
+//   pos    [M]        visibility positions in uv-tile order (Pos<T>)
+//   perm   [M]        sorted slot -> caller's visibility index
+//   items  [n_items]  work items: (tile, first slot, end slot), <= chunk slots each
+//   gridA  [n][K]     compact rows: image rows after the row FFT (forward) or
+//                     before the inverse row FFT (adjoint)
+//   gridP  [KP][KP]   forward oversampled grid with a J-wide periodic halo,
+//                     read in (TB+J)^2 patches by TMA for degridding
+//   gridQ  [KP][KP]   gridding accumulator with the same halo (folded on read)
+// with K = 2n the oversampled grid side and KP = K + J its padded side.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace purify {
+
+constexpr int kJ = 8;           // Kaiser-Bessel support (taps per axis)
+constexpr int kDegF = 10;       // kernel polynomial degree, FP32 path
+constexpr int kDegD = 16;       // kernel polynomial degree, FP64 path
+constexpr int kMaxDb = 8;       // Db1..Db8
+constexpr int kMaxTaps = 16;    // Db8 length
+
+template <typename T> struct KbDeg;
+template <> struct KbDeg<float> { static constexpr int value = kDegF; };
+template <> struct KbDeg<double> { static constexpr int value = kDegD; };
+
+// Kernel polynomial coefficients, tap-major: c[a][d] for x = 2f - 1.
+template <typename T> struct KbPoly { T c[kJ][KbDeg<T>::value + 1]; };
+
+// Encoded grid position of one visibility inside its uv tile.
+// FP32: 8 integer bits of cell + 24 fraction bits per axis (6e-8 cell resolution).
+// FP64: the tile-local coordinate itself.
+template <typename T> struct Pos;
+template <> struct Pos<float> { uint32_t u, v; };
+template <> struct Pos<double> { double u, v; };
+
+struct WorkItem { int tile, begin, end, pad; };
+
+struct Geometry {
+  int n, K, KP, pad_lo, TB, ntile1d;
+  int64_t M;
+};
+
+// Daubechies analysis filters h (low) and g (high), zero-padded to 16 taps.
+template <typename T> struct DbFilters { T h[kMaxDb][kMaxTaps]; T g[kMaxDb][kMaxTaps]; };
+
+// Row-pass epilogues (inverse row FFT -> image): val = Re(.) * s[i1] s[i2].
+enum RowEpMode : int {
+  EP_STORE = 0,     // out = val
+  EP_CG_AP = 1,     // out = nu2 val + 2 p;           partial += p * out
+  EP_CG_R0 = 2,     // out = b - (nu2 val + 2 p); out2 = out; partial += out^2
+  EP_POWER = 3,     // out = val;                      partial += val^2
+  EP_XS_ADD = 4,    // out = b + nu val   (b may alias out)
+  EP_QX = 5         // out = nu2 val + 2 p
+};
+template <typename T> struct RowEp {
+  int mode;
+  T* out;
+  T* out2;
+  const T* p;
+  const T* b;
+  double nu, nu2;
+  double* partials;
+};
+
+// Forward row-pass prologues (image -> row FFT input).
+enum RowProMode : int {
+  PRO_PLAIN = 0,    // src = x
+  PRO_CG_P = 1,     // p = r + beta p (beta = scalars[beta_idx]); write p; src = p
+  PRO_SCALE = 2     // src = x * scalars[scale_idx]   (power iteration normalisation)
+};
+template <typename T> struct RowPro {
+  int mode;
+  const T* x;
+  T* p;
+  const T* r;
+  const double* scalars;
+  int idx;
+};
+
+// Degridding epilogues (per visibility slot i, value acc = (G F Z S x)_i).
+enum DegridMode : int {
+  DG_STORE_PERM = 0,  // y[perm[i]] = acc
+  DG_STORE_SORTED = 1,// y[i] = acc
+  DG_BALL = 2         // v = nu acc + z[i]; z[i] = v; partials: |v - nu y_i|^2, |acc - y_i|^2
+};
+template <typename C> struct DegridEp {
+  int mode;
+  C* y;
+  C* z;
+  const C* ys;
+  double nu;
+  double* part0;
+  double* part1;
+};
+
+// Gridding prologues (value u scattered for slot i).
+enum GridMode : int {
+  GP_PERM = 0,        // u = y[perm[i]]
+  GP_SORTED = 1,      // u = y[i]
+  GP_BALL = 2         // v = z[i], c = nu ys[i]; r = c + (v - c) * scale; z[i] = v - r; u = 2r - v
+};
+template <typename C> struct GridPro {
+  int mode;
+  const C* y;
+  C* z;
+  const C* ys;
+  double nu;
+  const double* scalars;
+  int scale_idx;
+};
+
+// ----------------------------------------------------------------- launchers
+// Raise the dynamic shared-memory limit of every kernel (once per operator,
+// outside any stream capture).
+template <typename T> cudaError_t configure_fft();
+template <typename T> cudaError_t configure_nufft();
+template <typename T> cudaError_t configure_sara();
+
+template <typename T>
+void launch_row_fwd(const Geometry& g, const RowPro<T>& pro, const T* deapod, typename cplx_t<T>::type* A,
+                    const typename cplx_t<T>::type* tw, cudaStream_t s);
+template <typename T>
+void launch_col_fwd(const Geometry& g, const typename cplx_t<T>::type* A, typename cplx_t<T>::type* P,
+                    const typename cplx_t<T>::type* tw, cudaStream_t s);
+template <typename T>
+void launch_col_inv(const Geometry& g, const typename cplx_t<T>::type* Q, typename cplx_t<T>::type* A,
+                    const typename cplx_t<T>::type* tw, cudaStream_t s);
+// Returns the number of partial sums written (one per CTA).
+template <typename T>
+int launch_row_inv(const Geometry& g, const typename cplx_t<T>::type* A, const T* deapod, const RowEp<T>& ep,
+                   const typename cplx_t<T>::type* tw, cudaStream_t s);
+int row_inv_blocks(const Geometry& g);
+
+template <typename T>
+void launch_degrid(const Geometry& g, const CUtensorMap& map, const WorkItem* items, int n_items,
+                   const Pos<T>* pos, const int* perm, const KbPoly<T>& kb, const DegridEp<typename cplx_t<T>::type>& ep,
+                   int* err, cudaStream_t s);
+template <typename T>
+void launch_grid(const Geometry& g, const WorkItem* items, int n_items, const Pos<T>* pos, const int* perm,
+                 const KbPoly<T>& kb, const GridPro<typename cplx_t<T>::type>& pro, typename cplx_t<T>::type* Q,
+                 cudaStream_t s);
+template <typename T>
+void launch_gram(const Geometry& g, const CUtensorMap& map, const WorkItem* items, int n_items, const Pos<T>* pos,
+                 const KbPoly<T>& kb, typename cplx_t<T>::type* Q, int* err, cudaStream_t s);
+
+// uv binning (once per operator).  Fills pos/perm and returns the work list.
+template <typename T>
+int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>* pos, int* perm,
+               WorkItem** items_out, int* n_items_out, cudaStream_t s);
+
+// SARA dictionary.
+template <typename T>
+struct SaraPlan {
+  int n, levels;
+  T* s0;   // [8][(n/2)^2] scratch bands
+  T* s1;
+  T* cs;   // [9][n][n] scratch coefficients (prox output)
+  DbFilters<T> f;
+};
+// Psi^H x (plain), c is [9][n][n].
+template <typename T> void sara_analysis(const SaraPlan<T>& P, const T* x, T* c, cudaStream_t s);
+// Psi c (plain).
+template <typename T> void sara_synthesis(const SaraPlan<T>& P, const T* c, T* x, cudaStream_t s);
+
+// SDMM l1 block fused with the analysis: v = Psi^H xh + z1; r = soft(v, gamma w);
+// z1 = v - r; cs = 2r - v; objective partials sum w |Psi^H xh|.
+template <typename T>
+struct L1Block {
+  T* z1;
+  const T* w;      // may be null (w = 1)
+  double gamma;
+  double* partials;  // per-CTA partial objective, laid out by launch
+};
+// Returns number of objective partials written.
+template <typename T>
+int sara_analysis_prox(const SaraPlan<T>& P, const T* xh, const L1Block<T>& b, cudaStream_t s);
+// x1 = Psi cs, then positivity block fused in the final level:
+// v2 = xh + z2; r2 = max(v2, 0); z2 = v2 - r2; xs = x1 + 2 r2 - v2.
+template <typename T>
+void sara_synthesis_pos(const SaraPlan<T>& P, const T* xh, T* z2, T* xs, cudaStream_t s);
+int sara_partials_capacity(int n, int levels);
+
+}  // namespace purify

@@ -1,0 +1,430 @@
+// SARA dictionary Psi = [Dirac, Db1, ..., Db8] / 3 (Section 2.2) on the GPU.
+//
+// Analysis (Psi^H): one launch per wavelet level covers all eight Daubechies
+// filters (blockIdx.z = filter).  A CTA stages its periodic input tile once in
+// shared memory, filters the rows (axis 1) into low/high halves, then the
+// columns (axis 0), and writes the three detail sub-bands of the level to their
+// Mallat positions; the low-low band goes to a scratch band for the next level
+// (or to its final place at the last level).  Convention, per axis:
+//     lo[k] = sum_m h[m] x[(2k + m) mod L],   hi[k] = sum_m g[m] x[(2k + m) mod L].
+// Synthesis (Psi) is the exact adjoint, one launch per level from the coarsest;
+// the finest level is fused across all eight filters and the Dirac block, so
+// the image is written once.
+//
+// SDMM fusions (Algorithm 1, blocks i = 1, 2): the analysis epilogue applies
+// the l1 proximity operator to v = Psi^H x_hat + z_1 (soft threshold at
+// gamma w), updates z_1 and emits 2 r_1 - v_1 for the synthesis, plus FP64
+// partial sums of the objective ||W Psi^H x_hat||_1; the final synthesis
+// epilogue applies the positivity block and writes x_1 + x_2.
+#include "internal.h"
+
+namespace purify {
+
+namespace {
+
+constexpr int kTH = 16;  // analysis: output coefficients per tile side
+constexpr int kTO = 32;  // synthesis: output samples per tile side
+constexpr int kThr = 256;
+
+template <typename T> PD T third() { return T(1) / T(3); }
+
+PD int wrap(int i, int L) {
+  i %= L;
+  return i < 0 ? i + L : i;
+}
+
+// Final coefficient epilogue: plain store or fused l1 prox.
+template <typename T> struct CoefOut {
+  T* c;           // plain: Psi^H x [9][n][n]
+  int prox;       // 0: plain, 1: l1 block
+  T* z1;
+  const T* w;
+  T* cs;          // prox output 2r - v
+  T gamma;
+};
+
+template <typename T> PD void emit(const CoefOut<T>& o, size_t idx, T alpha, double& part) {
+  if (!o.prox) {
+    o.c[idx] = alpha;
+    return;
+  }
+  const T wj = o.w ? o.w[idx] : T(1);
+  const T v = alpha + o.z1[idx];
+  const T thr = o.gamma * wj;
+  const T av = fabs(v);
+  const T r = av > thr ? copysign(av - thr, v) : T(0);
+  o.z1[idx] = v - r;
+  o.cs[idx] = T(2) * r - v;
+  part += double(wj) * fabs(double(alpha));
+}
+
+template <typename T> struct AnaArgs {
+  const T* in;
+  size_t in_stride;  // elements between filters' input bands (0: shared input)
+  int L;             // input band side
+  int n;
+  T* s_out;          // LL scratch [8][H*H]
+  int last;          // LL band is final
+  CoefOut<T> out;
+  double* partials;  // per-CTA objective partials (prox only)
+};
+
+template <typename T, int F>
+__device__ void ana_body(const AnaArgs<T>& A, const T* __restrict__ h, const T* __restrict__ g, int k, T* sm,
+                         double* red) {
+  constexpr int W = 2 * kTH + F - 2;
+  T* X = sm;
+  T* lo = X + W * W;
+  T* hi = lo + W * kTH;
+  const int L = A.L, H = L / 2, n = A.n;
+  const int r0 = blockIdx.y * kTH, c0 = blockIdx.x * kTH;
+  const T* in = A.in + size_t(k) * A.in_stride;
+  for (int e = threadIdx.x; e < W * W; e += kThr) {
+    const int ir = e / W, ic = e - ir * W;
+    X[e] = in[size_t(wrap(2 * r0 + ir, L)) * L + wrap(2 * c0 + ic, L)];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < W * kTH; e += kThr) {
+    const int ir = e / kTH, c = e - ir * kTH;
+    const T* xr = X + ir * W + 2 * c;
+    T sl = 0, sh = 0;
+#pragma unroll
+    for (int m = 0; m < F; ++m) {
+      sl = fma(h[m], xr[m], sl);
+      sh = fma(g[m], xr[m], sh);
+    }
+    lo[e] = sl;
+    hi[e] = sh;
+  }
+  __syncthreads();
+  double part = 0.0;
+  const int r = threadIdx.x / kTH, c = threadIdx.x - r * kTH;
+  const int R = r0 + r, Cc = c0 + c;
+  if (R < H && Cc < H) {
+    T ll = 0, lh = 0, hl = 0, hh = 0;
+#pragma unroll
+    for (int m = 0; m < F; ++m) {
+      const T a = lo[(2 * r + m) * kTH + c], b = hi[(2 * r + m) * kTH + c];
+      ll = fma(h[m], a, ll);
+      lh = fma(h[m], b, lh);
+      hl = fma(g[m], a, hl);
+      hh = fma(g[m], b, hh);
+    }
+    const size_t base = size_t(k + 1) * n * n;
+    const T t3 = third<T>();
+    emit(A.out, base + size_t(R) * n + (H + Cc), lh * t3, part);
+    emit(A.out, base + size_t(H + R) * n + Cc, hl * t3, part);
+    emit(A.out, base + size_t(H + R) * n + (H + Cc), hh * t3, part);
+    if (A.last)
+      emit(A.out, base + size_t(R) * n + Cc, ll * t3, part);
+    else
+      A.s_out[size_t(k) * H * H + size_t(R) * H + Cc] = ll;
+  }
+  if (A.partials) {
+    const double t = block_sum<kThr>(part, red);
+    if (threadIdx.x == 0)
+      A.partials[(size_t(blockIdx.z) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThr) k_ana_level(AnaArgs<T> A, DbFilters<T> f) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __shared__ double red[32];
+  T* sm = reinterpret_cast<T*>(sm_raw);
+  const int k = blockIdx.z;
+  const T* h = f.h[k];
+  const T* g = f.g[k];
+  switch (k) {
+    case 0: ana_body<T, 2>(A, h, g, k, sm, red); break;
+    case 1: ana_body<T, 4>(A, h, g, k, sm, red); break;
+    case 2: ana_body<T, 6>(A, h, g, k, sm, red); break;
+    case 3: ana_body<T, 8>(A, h, g, k, sm, red); break;
+    case 4: ana_body<T, 10>(A, h, g, k, sm, red); break;
+    case 5: ana_body<T, 12>(A, h, g, k, sm, red); break;
+    case 6: ana_body<T, 14>(A, h, g, k, sm, red); break;
+    default: ana_body<T, 16>(A, h, g, k, sm, red); break;
+  }
+}
+
+// Dirac block: c_0 = x / 3 (with the prox epilogue when fused).
+template <typename T>
+__global__ void __launch_bounds__(kThr) k_dirac(const T* __restrict__ x, size_t N, CoefOut<T> out,
+                                                double* partials) {
+  __shared__ double red[32];
+  double part = 0.0;
+  const size_t i = size_t(blockIdx.x) * kThr + threadIdx.x;
+  if (i < N) emit(out, i, x[i] * third<T>(), part);
+  if (partials) {
+    const double t = block_sum<kThr>(part, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  }
+}
+
+template <typename T> struct SynArgs {
+  const T* c;       // final coefficients [9][n][n] (plain Psi^H layout)
+  const T* s_in;    // LL band from the coarser synthesis level, or null (LL is final in c)
+  int H;            // coefficient band side; output side L = 2H
+  int n;
+  T* s_out;         // [8][L*L] (intermediate levels)
+  // finest level (fused over filters):
+  int fused;
+  int pos_block;    // apply the positivity block
+  T* x_out;
+  const T* xh;
+  T* z2;
+};
+
+// One filter's level synthesis of the output tile (i0, j0) into Xo[kTO][kTO].
+template <typename T, int F>
+__device__ void syn_body(const SynArgs<T>& S, const T* __restrict__ h, const T* __restrict__ g, int k, T* sm,
+                         int i0, int j0, T (&acc)[kTO * kTO / kThr], bool accumulate) {
+  constexpr int CT = kTO / 2 + F / 2;
+  T* LLt = sm;
+  T* LHt = LLt + CT * CT;
+  T* HLt = LHt + CT * CT;
+  T* HHt = HLt + CT * CT;
+  T* Ulo = HHt + CT * CT;      // [kTO][CT]
+  T* Uhi = Ulo + kTO * CT;
+  const int H = S.H, n = S.n, L = 2 * H;
+  const T* cb = S.c + size_t(k + 1) * n * n;
+  const T t3 = third<T>();
+  const int rb = i0 / 2 - F / 2, cbase = j0 / 2 - F / 2;
+  for (int e = threadIdx.x; e < CT * CT; e += kThr) {
+    const int lr = e / CT, lc = e - lr * CT;
+    const int r = wrap(rb + lr, H), c = wrap(cbase + lc, H);
+    LLt[e] = S.s_in ? S.s_in[size_t(k) * H * H + size_t(r) * H + c] : cb[size_t(r) * n + c] * t3;
+    LHt[e] = cb[size_t(r) * n + (H + c)] * t3;
+    HLt[e] = cb[size_t(H + r) * n + c] * t3;
+    HHt[e] = cb[size_t(H + r) * n + (H + c)] * t3;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kTO * CT; e += kThr) {
+    const int il = e / CT, lc = e - il * CT;
+    T ul = 0, uh = 0;
+    const int par = il & 1;
+#pragma unroll
+    for (int t = 0; t < F / 2; ++t) {
+      const int m = par + 2 * t;
+      const int lr = (il - m) / 2 + F / 2;
+      ul = fma(h[m], LLt[lr * CT + lc], ul);
+      ul = fma(g[m], HLt[lr * CT + lc], ul);
+      uh = fma(h[m], LHt[lr * CT + lc], uh);
+      uh = fma(g[m], HHt[lr * CT + lc], uh);
+    }
+    Ulo[e] = ul;
+    Uhi[e] = uh;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < kTO * kTO / kThr; ++q) {
+    const int e = threadIdx.x + q * kThr;
+    const int il = e / kTO, jl = e - il * kTO;
+    T v = 0;
+    const int par = jl & 1;
+#pragma unroll
+    for (int t = 0; t < F / 2; ++t) {
+      const int m = par + 2 * t;
+      const int lc = (jl - m) / 2 + F / 2;
+      v = fma(h[m], Ulo[il * CT + lc], v);
+      v = fma(g[m], Uhi[il * CT + lc], v);
+    }
+    if (accumulate) {
+      acc[q] += v;
+    } else if (i0 + il < L && j0 + jl < L) {
+      S.s_out[size_t(k) * L * L + size_t(i0 + il) * L + (j0 + jl)] = v;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void syn_dispatch(const SynArgs<T>& S, const DbFilters<T>& f, int k, T* sm, int i0, int j0,
+                             T (&acc)[kTO * kTO / kThr], bool accumulate) {
+  const T* h = f.h[k];
+  const T* g = f.g[k];
+  switch (k) {
+    case 0: syn_body<T, 2>(S, h, g, k, sm, i0, j0, acc, accumulate); break;
+    case 1: syn_body<T, 4>(S, h, g, k, sm, i0, j0, acc, accumulate); break;
+    case 2: syn_body<T, 6>(S, h, g, k, sm, i0, j0, acc, accumulate); break;
+    case 3: syn_body<T, 8>(S, h, g, k, sm, i0, j0, acc, accumulate); break;
+    case 4: syn_body<T, 10>(S, h, g, k, sm, i0, j0, acc, accumulate); break;
+    case 5: syn_body<T, 12>(S, h, g, k, sm, i0, j0, acc, accumulate); break;
+    case 6: syn_body<T, 14>(S, h, g, k, sm, i0, j0, acc, accumulate); break;
+    default: syn_body<T, 16>(S, h, g, k, sm, i0, j0, acc, accumulate); break;
+  }
+}
+
+// Intermediate synthesis level: blockIdx.z = filter, output band -> scratch.
+template <typename T>
+__global__ void __launch_bounds__(kThr) k_syn_level(SynArgs<T> S, DbFilters<T> f) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sm = reinterpret_cast<T*>(sm_raw);
+  T acc[kTO * kTO / kThr];
+  syn_dispatch(S, f, blockIdx.z, sm, blockIdx.y * kTO, blockIdx.x * kTO, acc, false);
+}
+
+// Finest level: all eight filters and the Dirac block summed into the image.
+template <typename T>
+__global__ void __launch_bounds__(kThr) k_syn_final(SynArgs<T> S, DbFilters<T> f) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sm = reinterpret_cast<T*>(sm_raw);
+  const int i0 = blockIdx.y * kTO, j0 = blockIdx.x * kTO;
+  T acc[kTO * kTO / kThr];
+#pragma unroll
+  for (int q = 0; q < kTO * kTO / kThr; ++q) acc[q] = 0;
+  for (int k = 0; k < kMaxDb; ++k) syn_dispatch(S, f, k, sm, i0, j0, acc, true);
+  const int n = S.n;
+  const T t3 = third<T>();
+#pragma unroll
+  for (int q = 0; q < kTO * kTO / kThr; ++q) {
+    const int e = threadIdx.x + q * kThr;
+    const int il = e / kTO, jl = e - il * kTO;
+    if (i0 + il >= n || j0 + jl >= n) continue;
+    const size_t idx = size_t(i0 + il) * n + (j0 + jl);
+    const T x1 = acc[q] + S.c[idx] * t3;  // Dirac block
+    if (S.pos_block) {
+      const T v2 = S.xh[idx] + S.z2[idx];
+      const T r2 = v2 > T(0) ? v2 : T(0);
+      S.z2[idx] = v2 - r2;
+      S.x_out[idx] = x1 + (T(2) * r2 - v2);
+    } else {
+      S.x_out[idx] = x1;
+    }
+  }
+}
+
+template <typename T> size_t ana_smem(int F) {
+  const int W = 2 * kTH + F - 2;
+  return size_t(W * W + 2 * W * kTH) * sizeof(T);
+}
+template <typename T> size_t syn_smem(int F) {
+  const int CT = kTO / 2 + F / 2;
+  return size_t(4 * CT * CT + 2 * kTO * CT) * sizeof(T);
+}
+
+inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// Runs the analysis levels; returns partial sums written (prox mode).
+template <typename T>
+int run_analysis(const SaraPlan<T>& P, const T* x, const CoefOut<T>& out, double* partials, cudaStream_t s) {
+  const int n = P.n;
+  const size_t N = size_t(n) * n;
+  int np = 0;
+  const int nb0 = int((N + kThr - 1) / kThr);
+  k_dirac<T><<<nb0, kThr, 0, s>>>(x, N, out, partials ? partials : nullptr);
+  if (partials) np += nb0;
+  const size_t sm = ana_smem<T>(16);
+  const T* in = x;
+  size_t in_stride = 0;
+  T* bufs[2] = {P.s0, P.s1};
+  for (int lev = 1; lev <= P.levels; ++lev) {
+    const int L = n >> (lev - 1), H = L / 2;
+    AnaArgs<T> A;
+    A.in = in;
+    A.in_stride = in_stride;
+    A.L = L;
+    A.n = n;
+    A.s_out = bufs[lev & 1];
+    A.last = lev == P.levels;
+    A.out = out;
+    A.partials = partials ? partials + np : nullptr;
+    dim3 grid(cdiv(H, kTH), cdiv(H, kTH), kMaxDb);
+    k_ana_level<T><<<grid, kThr, sm, s>>>(A, P.f);
+    if (partials) np += int(grid.x * grid.y * grid.z);
+    in = A.s_out;
+    in_stride = size_t(H) * H;
+  }
+  return np;
+}
+
+template <typename T>
+void run_synthesis(const SaraPlan<T>& P, const T* c, T* x, int pos_block, const T* xh, T* z2, cudaStream_t s) {
+  const int n = P.n;
+  const size_t sm = syn_smem<T>(16);
+  T* bufs[2] = {P.s0, P.s1};
+  const T* s_in = nullptr;
+  for (int lev = P.levels; lev >= 2; --lev) {
+    const int H = n >> lev, L = 2 * H;
+    SynArgs<T> S{};
+    S.c = c;
+    S.s_in = s_in;
+    S.H = H;
+    S.n = n;
+    S.s_out = bufs[lev & 1];
+    dim3 grid(cdiv(L, kTO), cdiv(L, kTO), kMaxDb);
+    k_syn_level<T><<<grid, kThr, sm, s>>>(S, P.f);
+    s_in = S.s_out;
+  }
+  SynArgs<T> S{};
+  S.c = c;
+  S.s_in = s_in;
+  S.H = n / 2;
+  S.n = n;
+  S.fused = 1;
+  S.pos_block = pos_block;
+  S.x_out = x;
+  S.xh = xh;
+  S.z2 = z2;
+  dim3 grid(cdiv(n, kTO), cdiv(n, kTO), 1);
+  k_syn_final<T><<<grid, kThr, sm, s>>>(S, P.f);
+}
+
+}  // namespace
+
+template <typename T> cudaError_t configure_sara() {
+  const int mx = 227 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_ana_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_syn_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_syn_final<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  return e;
+}
+template cudaError_t configure_sara<float>();
+template cudaError_t configure_sara<double>();
+
+int sara_partials_capacity(int n, int levels) {
+  int np = (n * n + kThr - 1) / kThr;
+  for (int lev = 1; lev <= levels; ++lev) {
+    const int H = n >> lev;
+    np += cdiv(H, kTH) * cdiv(H, kTH) * kMaxDb;
+  }
+  return np;
+}
+
+template <typename T> void sara_analysis(const SaraPlan<T>& P, const T* x, T* c, cudaStream_t s) {
+  CoefOut<T> out{};
+  out.c = c;
+  out.prox = 0;
+  run_analysis<T>(P, x, out, nullptr, s);
+}
+
+template <typename T> void sara_synthesis(const SaraPlan<T>& P, const T* c, T* x, cudaStream_t s) {
+  run_synthesis<T>(P, c, x, 0, nullptr, nullptr, s);
+}
+
+template <typename T>
+int sara_analysis_prox(const SaraPlan<T>& P, const T* xh, const L1Block<T>& b, cudaStream_t s) {
+  CoefOut<T> out{};
+  out.prox = 1;
+  out.z1 = b.z1;
+  out.w = b.w;
+  out.cs = P.cs;
+  out.gamma = T(b.gamma);
+  return run_analysis(P, xh, out, b.partials, s);
+}
+
+template <typename T>
+void sara_synthesis_pos(const SaraPlan<T>& P, const T* xh, T* z2, T* xs, cudaStream_t s) {
+  run_synthesis<T>(P, P.cs, xs, 1, xh, z2, s);
+}
+
+#define INST(T)                                                                                 \
+  template void sara_analysis<T>(const SaraPlan<T>&, const T*, T*, cudaStream_t);                 \
+  template void sara_synthesis<T>(const SaraPlan<T>&, const T*, T*, cudaStream_t);                \
+  template int sara_analysis_prox<T>(const SaraPlan<T>&, const T*, const L1Block<T>&, cudaStream_t); \
+  template void sara_synthesis_pos<T>(const SaraPlan<T>&, const T*, T*, T*, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace purify

@@ -1,0 +1,185 @@
+// Small vector kernels of the SDMM solver (Algorithm 1) and the SARA
+// reweighting: CG vector updates with FP64 partial sums, deterministic
+// finalisation of device scalars (CG alpha/beta, the l2-ball scale, the
+// objective, norms), visibility permutation and the reweighting rule.
+#include "solver_kernels.h"
+
+namespace purify {
+
+namespace {
+constexpr int kT = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kT) k_cg_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                                              const T* __restrict__ Ap, const double* __restrict__ sc, size_t N,
+                                              double* __restrict__ partials) {
+  __shared__ double red[32];
+  const T alpha = T(sc[S_ALPHA]);
+  double part = 0.0;
+  for (size_t i = size_t(blockIdx.x) * kT + threadIdx.x; i < N; i += size_t(gridDim.x) * kT) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const T rv = fma(-alpha, Ap[i], r[i]);
+    r[i] = rv;
+    part += double(rv) * double(rv);
+  }
+  const double t = block_sum<kT>(part, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+// One block: sum partials in a fixed order, then apply `op`.
+__global__ void __launch_bounds__(kT) k_finalize(const double* __restrict__ pa, int na,
+                                                 const double* __restrict__ pb, int nb, int op, double arg,
+                                                 double* __restrict__ sc) {
+  __shared__ double red[32];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < na; i += kT) a += pa[i];
+  for (int i = threadIdx.x; i < nb; i += kT) b += pb[i];
+  a = block_sum<kT>(a, red);
+  b = block_sum<kT>(b, red);
+  if (threadIdx.x != 0) return;
+  switch (op) {
+    case FIN_RR0:
+      sc[S_RR] = a;
+      break;
+    case FIN_ALPHA:
+      sc[S_PAP] = a;
+      sc[S_ALPHA] = a > 0.0 ? sc[S_RR] / a : 0.0;
+      break;
+    case FIN_BETA: {
+      const double rr = sc[S_RR];
+      sc[S_BETA] = rr > 0.0 ? a / rr : 0.0;
+      sc[S_RR] = a;
+    } break;
+    case FIN_BALL: {  // arg = nu * eps
+      const double s = sqrt(a);
+      sc[S_BALLNORM] = s;
+      sc[S_BALLSCALE] = (s <= arg) ? 1.0 : arg / s;
+      sc[S_RESID] = sqrt(b);
+    } break;
+    case FIN_OBJ:
+      sc[S_OBJ] = a;
+      break;
+    case FIN_NORM: {
+      const double l = sqrt(a);
+      sc[S_LAMBDA] = l;
+      sc[S_INVNORM] = l > 0.0 ? 1.0 / l : 0.0;
+    } break;
+    case FIN_MEAN:  // arg = element count
+      sc[S_MEAN] = a / arg;
+      break;
+    case FIN_VAR:
+      sc[S_STD] = sqrt(a / arg);
+      break;
+    case FIN_MAX:
+      sc[S_MAXABS] = a;
+      break;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kT) k_sum_partials(const T* __restrict__ v, size_t N, int op,
+                                                     const double* __restrict__ sc, double* __restrict__ partials) {
+  __shared__ double red[32];
+  double part = 0.0;
+  const double mean = op == RED_VAR ? sc[S_MEAN] : 0.0;
+  for (size_t i = size_t(blockIdx.x) * kT + threadIdx.x; i < N; i += size_t(gridDim.x) * kT) {
+    const double x = double(v[i]);
+    if (op == RED_SUM) part += x;
+    else if (op == RED_VAR) part += (x - mean) * (x - mean);
+    else if (op == RED_MAXABS) part = fmax(part, fabs(x));
+    else part += x * x;
+  }
+  double t;
+  if (op == RED_MAXABS) t = block_max<kT>(part, red);
+  else t = block_sum<kT>(part, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kT) k_max_partials(const double* __restrict__ p, int np, double* __restrict__ sc) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < np; i += kT) m = fmax(m, p[i]);
+  m = block_max<kT>(m, red);
+  if (threadIdx.x == 0) sc[S_MAXABS] = m;
+}
+
+template <typename T>
+__global__ void k_reweight(T* __restrict__ w, size_t N, double delta) {
+  for (size_t i = size_t(blockIdx.x) * kT + threadIdx.x; i < N; i += size_t(gridDim.x) * kT)
+    w[i] = T(delta / (delta + fabs(double(w[i]))));
+}
+
+template <typename T>
+__global__ void k_fill(T* __restrict__ v, size_t N, T val) {
+  for (size_t i = size_t(blockIdx.x) * kT + threadIdx.x; i < N; i += size_t(gridDim.x) * kT) v[i] = val;
+}
+
+template <typename T>
+__global__ void k_scale(T* __restrict__ v, size_t N, const double* __restrict__ sc, int idx, double mul) {
+  const T s = T(sc[idx] * mul);
+  for (size_t i = size_t(blockIdx.x) * kT + threadIdx.x; i < N; i += size_t(gridDim.x) * kT) v[i] *= s;
+}
+
+template <typename C>
+__global__ void k_gather(const C* __restrict__ src, const int* __restrict__ perm, size_t M, C* __restrict__ dst) {
+  for (size_t i = size_t(blockIdx.x) * kT + threadIdx.x; i < M; i += size_t(gridDim.x) * kT) dst[i] = src[perm[i]];
+}
+
+inline int nblk(size_t N) {
+  size_t b = (N + kT - 1) / kT;
+  if (b > 4096) b = 4096;
+  return int(b > 0 ? b : 1);
+}
+}  // namespace
+
+int vec_blocks(size_t N) { return nblk(N); }
+
+template <typename T>
+int launch_cg_xr(T* x, T* r, const T* p, const T* Ap, const double* sc, size_t N, double* partials, cudaStream_t s) {
+  const int b = nblk(N);
+  k_cg_xr<T><<<b, kT, 0, s>>>(x, r, p, Ap, sc, N, partials);
+  return b;
+}
+
+void launch_finalize(const double* pa, int na, const double* pb, int nb, int op, double arg, double* sc,
+                     cudaStream_t s) {
+  k_finalize<<<1, kT, 0, s>>>(pa, na, pb, nb, op, arg, sc);
+}
+
+template <typename T>
+int launch_reduce(const T* v, size_t N, int op, const double* sc, double* partials, cudaStream_t s) {
+  const int b = nblk(N);
+  k_sum_partials<T><<<b, kT, 0, s>>>(v, N, op, sc, partials);
+  return b;
+}
+
+void launch_max_partials(const double* p, int np, double* sc, cudaStream_t s) {
+  k_max_partials<<<1, kT, 0, s>>>(p, np, sc);
+}
+
+template <typename T> void launch_reweight(T* w, size_t N, double delta, cudaStream_t s) {
+  k_reweight<T><<<nblk(N), kT, 0, s>>>(w, N, delta);
+}
+template <typename T> void launch_fill(T* v, size_t N, T val, cudaStream_t s) {
+  k_fill<T><<<nblk(N), kT, 0, s>>>(v, N, val);
+}
+template <typename T> void launch_scale(T* v, size_t N, const double* sc, int idx, double mul, cudaStream_t s) {
+  k_scale<T><<<nblk(N), kT, 0, s>>>(v, N, sc, idx, mul);
+}
+template <typename C> void launch_gather(const C* src, const int* perm, size_t M, C* dst, cudaStream_t s) {
+  k_gather<C><<<nblk(M), kT, 0, s>>>(src, perm, M, dst);
+}
+
+#define INST(T)                                                                                       \
+  template int launch_cg_xr<T>(T*, T*, const T*, const T*, const double*, size_t, double*, cudaStream_t); \
+  template int launch_reduce<T>(const T*, size_t, int, const double*, double*, cudaStream_t);           \
+  template void launch_reweight<T>(T*, size_t, double, cudaStream_t);                                   \
+  template void launch_fill<T>(T*, size_t, T, cudaStream_t);                                            \
+  template void launch_scale<T>(T*, size_t, const double*, int, double, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+template void launch_gather<float2>(const float2*, const int*, size_t, float2*, cudaStream_t);
+template void launch_gather<double2>(const double2*, const int*, size_t, double2*, cudaStream_t);
+
+}  // namespace purify

@@ -1,0 +1,31 @@
+// Vector kernels and device scalars of the SDMM solver.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "common.cuh"
+
+namespace purify {
+
+// Device scalar slots (double[kNumScalars]).
+enum ScalarSlot : int {
+  S_RR = 0, S_ALPHA, S_BETA, S_PAP, S_BALLSCALE, S_BALLNORM, S_RESID, S_OBJ,
+  S_LAMBDA, S_INVNORM, S_MEAN, S_STD, S_MAXABS, kNumScalars
+};
+enum FinOp : int { FIN_RR0 = 0, FIN_ALPHA, FIN_BETA, FIN_BALL, FIN_OBJ, FIN_NORM, FIN_MEAN, FIN_VAR, FIN_MAX };
+enum RedOp : int { RED_SQ = 0, RED_SUM, RED_VAR, RED_MAXABS };
+
+int vec_blocks(size_t N);
+template <typename T>
+int launch_cg_xr(T* x, T* r, const T* p, const T* Ap, const double* sc, size_t N, double* partials, cudaStream_t s);
+void launch_finalize(const double* pa, int na, const double* pb, int nb, int op, double arg, double* sc,
+                     cudaStream_t s);
+template <typename T>
+int launch_reduce(const T* v, size_t N, int op, const double* sc, double* partials, cudaStream_t s);
+void launch_max_partials(const double* p, int np, double* sc, cudaStream_t s);
+template <typename T> void launch_reweight(T* w, size_t N, double delta, cudaStream_t s);
+template <typename T> void launch_fill(T* v, size_t N, T val, cudaStream_t s);
+template <typename T> void launch_scale(T* v, size_t N, const double* sc, int idx, double mul, cudaStream_t s);
+template <typename C> void launch_gather(const C* src, const int* perm, size_t M, C* dst, cudaStream_t s);
+
+}  // namespace purify

@@ -1,0 +1,113 @@
+"""GPU parity of Phi, Phi^H and Psi^H, Psi against the FP64 oracle, through the C-ABI."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import sara as osara
+from oracle.nufft import NUFFT
+from paper_1406_0359_gb300 import synth
+from tests._gpu import TOL, host, need_gpu, rel, to_dev
+
+pytestmark = pytest.mark.gpu
+
+CASES = [(16, 97, 1), (64, 4096, 1), (256, 131072, 2), (128, 5000, 9)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    need_gpu()
+
+
+def make_op(uv, n, levels, prec):
+    from paper_1406_0359_gb300.binding import Operator
+
+    return Operator(torch.as_tensor(uv).cuda(), n, levels, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("n,M,seed", CASES)
+def test_phi_and_adjoint_match_oracle(prec, n, M, seed):
+    uv = synth.uv_coverage(M, n, seed)
+    ref = NUFFT(uv, n)
+    op = make_op(uv, n, 2, prec)
+    x = synth.random_image(n, seed + 10)
+    y = synth.random_vis(M, seed + 20)
+    yg = host(op.phi(to_dev(x, prec)))
+    assert rel(yg, ref.phi(x)) < TOL[prec]
+    xg = host(op.phi_adj(to_dev(y, prec)))
+    assert rel(xg, ref.phi_adj_real(y)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_edge_coverages(prec):
+    n = 32
+    K = 2 * n
+    cell = 2 * math.pi / K
+    uv = np.array([[-math.pi, -math.pi], [0.0, 0.0], [math.pi - 1e-13, math.pi - 1e-13],
+                   [3 * cell, -5 * cell], [0.5 * cell, 0.25 * cell], [-math.pi, 0.3],
+                   [7.0, -9.0]])  # last point outside [-pi, pi): wrapped
+    ref = NUFFT(np.mod(uv + math.pi, 2 * math.pi) - math.pi, n)
+    op = make_op(uv, n, 1, prec)
+    x = synth.random_image(n, 3)
+    assert rel(host(op.phi(to_dev(x, prec))), ref.phi(x)) < TOL[prec]
+    y = synth.random_vis(uv.shape[0], 4)
+    assert rel(host(op.phi_adj(to_dev(y, prec))), ref.phi_adj_real(y)) < TOL[prec]
+    # every point in one tile; a single point
+    uv1 = np.full((300, 2), 0.01) + 1e-3 * np.random.default_rng(0).standard_normal((300, 2))
+    ref1 = NUFFT(uv1, n)
+    op1 = make_op(uv1, n, 1, prec)
+    assert rel(host(op1.phi(to_dev(x, prec))), ref1.phi(x)) < TOL[prec]
+    y1 = synth.random_vis(300, 5)
+    assert rel(host(op1.phi_adj(to_dev(y1, prec))), ref1.phi_adj_real(y1)) < TOL[prec]
+    op2 = make_op(uv1[:1], n, 1, prec)
+    assert rel(host(op2.phi(to_dev(x, prec))), NUFFT(uv1[:1], n).phi(x)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("n,levels", [(16, 3), (64, 3), (256, 4), (32, 4)])
+def test_sara_matches_oracle(prec, n, levels):
+    uv = synth.uv_coverage(64, n, 1)
+    op = make_op(uv, n, levels, prec)
+    x = synth.random_image(n, n)
+    c = host(op.sara_fwd(to_dev(x, prec)))
+    cref = osara.analysis(x, levels)
+    assert rel(c, cref) < TOL[prec]
+    d = np.random.default_rng(n).standard_normal((9, n, n))
+    xa = host(op.sara_adj(to_dev(d, prec)))
+    assert rel(xa, osara.synthesis(d, levels)) < TOL[prec]
+    # tight frame on the GPU
+    back = host(op.sara_adj(op.sara_fwd(to_dev(x, prec))))
+    assert rel(back, x) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_adjoint_identity_on_gpu(prec):
+    n, M = 256, 131072
+    uv = synth.uv_coverage(M, n, 2)
+    op = make_op(uv, n, 4, prec)
+    x = synth.random_image(n, 1)
+    y = synth.random_vis(M, 2)
+    lhs = float(np.real(np.vdot(y, host(op.phi(to_dev(x, prec))))))
+    rhs = float(np.sum(x * host(op.phi_adj(to_dev(y, prec)))))
+    assert abs(lhs - rhs) / abs(lhs) < (1e-5 if prec == "fp32" else 1e-12)
+
+
+def test_full_size_phi_sampled_and_adjoint_identity():
+    """1024^2 image, 4,194,304 uv points, 2048^2 grid, FP32 (the bench
+    configuration): sampled visibilities against the oracle computed one by
+    one, and the adjoint identity over all of them."""
+    n, M = 1024, 4194304
+    uv = synth.uv_coverage(M, n, 3)
+    op = make_op(uv, n, 4, "fp32")
+    x = synth.sky(n, 3, 12, 160)
+    yg = host(op.phi(to_dev(x, "fp32")))
+    idx = np.random.default_rng(0).choice(M, 2000, replace=False)
+    ref = NUFFT(uv[idx], n).phi(x)
+    assert rel(yg[idx], ref) < TOL["fp32"]
+    y = synth.random_vis(M, 4)
+    xg = host(op.phi_adj(to_dev(y, "fp32")))
+    lhs = float(np.real(np.vdot(y, yg)))
+    rhs = float(np.sum(x * xg))
+    assert abs(lhs - rhs) / abs(lhs) < 1e-5
