@@ -174,6 +174,11 @@ void purify_default_params(purify_params* p);
 /* purify_strerror -- static description of a status code. */
 const char* purify_strerror(int status);
 
+/* purify_last_error -- detail of the calling thread's last failure (which
+ * call, where, the CUDA error name); empty if none.  Valid until the next
+ * failing call on this thread. */
+const char* purify_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

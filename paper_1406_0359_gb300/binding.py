@@ -26,8 +26,8 @@ _STATUS = {0: "ok", -1: "invalid argument", -2: "device allocation failed", -3: 
 
 
 class PurifyError(RuntimeError):
-    def __init__(self, code: int, where: str):
-        super().__init__(f"{where}: {_STATUS.get(code, 'unknown')} ({code})")
+    def __init__(self, code: int, where: str, detail: str = ""):
+        super().__init__(f"{where}: {_STATUS.get(code, 'unknown')} ({code}) {detail}".rstrip())
         self.code = code
 
 
@@ -50,7 +50,8 @@ class purify_stats(ctypes.Structure):
 
 EXPORTS = ["purify_op_create", "purify_op_destroy", "purify_op_info", "purify_phi", "purify_phi_adj",
            "purify_sara_fwd", "purify_sara_adj", "purify_sdmm_solve", "purify_default_params",
-           "purify_strerror", "purify_profile", "purify_profile_read", "purify_kernel_name"]
+           "purify_strerror", "purify_profile", "purify_profile_read", "purify_kernel_name",
+           "purify_last_error"]
 KERNEL_KINDS = ["row_fwd", "col_fwd", "degrid", "grid", "gram", "col_inv", "row_inv", "sara_analysis",
                 "sara_synthesis", "vector", "memset"]
 
@@ -82,8 +83,10 @@ def lib() -> ctypes.CDLL:
     L.purify_profile_read.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
     L.purify_kernel_name.argtypes = [ci]
     L.purify_kernel_name.restype = ctypes.c_char_p
+    L.purify_last_error.argtypes = []
+    L.purify_last_error.restype = ctypes.c_char_p
     for f in EXPORTS:
-        if f not in ("purify_default_params", "purify_strerror", "purify_kernel_name"):
+        if f not in ("purify_default_params", "purify_strerror", "purify_kernel_name", "purify_last_error"):
             getattr(L, f).restype = ci
     _lib = L
     return L
@@ -91,7 +94,7 @@ def lib() -> ctypes.CDLL:
 
 def _check(rc: int, where: str, allow=()) -> int:
     if rc != 0 and rc not in allow:
-        raise PurifyError(rc, where)
+        raise PurifyError(rc, where, lib().purify_last_error().decode(errors="replace"))
     return rc
 
 

@@ -108,16 +108,23 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-int map_err(cudaError_t e) {
+thread_local char g_last_error[256] = "";
+
+void note_error(const char* what, int line, const char* detail) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s (api.cu:%d): %s", what, line, detail);
+}
+
+int map_err(cudaError_t e, int line = 0) {
   if (e == cudaSuccess) return PURIFY_OK;
+  note_error("CUDA call failed", line, cudaGetErrorName(e));
   if (e == cudaErrorMemoryAllocation) return PURIFY_ERR_NOMEM;
   return PURIFY_ERR_CUDA;
 }
 
-#define CK(call)                                   \
-  do {                                             \
-    cudaError_t e_ = (call);                       \
-    if (e_ != cudaSuccess) return map_err(e_);     \
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return map_err(e_, __LINE__);  \
   } while (0)
 
 template <typename T> class OpImpl : public purify_op {
@@ -147,10 +154,16 @@ template <typename T> class OpImpl : public purify_op {
   C *z3 = nullptr, *ys = nullptr;
   int64_t bytes = 0;
   std::vector<void*> allocs;
+  cudaStream_t own = nullptr;  // solver stream (capturable, non-blocking)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 
   ~OpImpl() override {
     prof_release();
+    if (own) cudaStreamSynchronize(own);
     for (void* a : allocs) cudaFree(a);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (own) cudaStreamDestroy(own);
     if (h_sc) cudaFreeHost(h_sc);
   }
 
@@ -172,12 +185,15 @@ template <typename T> class OpImpl : public purify_op {
     g.K = 2 * n;
     g.KP = g.K + kJ;
     g.pad_lo = kJ / 2 - 1;
-    g.TB = g.K >= 1024 ? 32 : 16;
+    g.TB = 16;
     if (g.TB > g.K) g.TB = g.K;
     g.ntile1d = g.K / g.TB;
     g.M = M;
     levels = L;
     chunk = 1024;
+    CK(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
     CK(configure_fft<T>());
     CK(configure_nufft<T>());
     CK(configure_sara<T>());
@@ -227,14 +243,20 @@ template <typename T> class OpImpl : public purify_op {
     CK(cudaMemsetAsync(sc, 0, kNumScalars * sizeof(double), s));
     CK(cudaMemsetAsync(gridP, 0, grid_bytes(), s));
     rc = build_bins<T>(uv, M, g, chunk, pos, perm, &items, &n_items, s);
-    if (rc) return rc;
+    if (rc) {
+      note_error("uv binning failed", __LINE__, cudaGetErrorName(cudaGetLastError()));
+      return rc;
+    }
     allocs.push_back(items);
     bytes += int64_t(n_items) * sizeof(WorkItem);
     const int np = std::max({2 * n_items, row_inv_blocks(g), sara_partials_capacity(n, L), vec_blocks(9 * N()), 1});
     if ((rc = alloc(&partials, np))) return rc;
     // TMA descriptor of the padded forward grid, 8-byte elements
     EncodeTiledFn enc = encode_fn();
-    if (!enc) return PURIFY_ERR_CUDA;
+    if (!enc) {
+      note_error("cuTensorMapEncodeTiled unavailable", __LINE__, "driver entry point not found");
+      return PURIFY_ERR_CUDA;
+    }
     const int cw = int(sizeof(C) / 8);
     const int PW = g.TB + kJ;
     cuuint64_t dims[2] = {cuuint64_t(g.KP) * cw, cuuint64_t(g.KP)};
@@ -244,7 +266,12 @@ template <typename T> class OpImpl : public purify_op {
     CUresult cr = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, gridP, dims, strides, box, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) return PURIFY_ERR_CUDA;
+    if (cr != CUDA_SUCCESS) {
+      char buf[64];
+      std::snprintf(buf, sizeof(buf), "CUresult %d", int(cr));
+      note_error("cuTensorMapEncodeTiled failed", __LINE__, buf);
+      return PURIFY_ERR_CUDA;
+    }
     CK(cudaStreamSynchronize(s));
     return PURIFY_OK;
   }
@@ -504,12 +531,25 @@ template <typename T> class OpImpl : public purify_op {
     row_ep(ep, s);
   }
 
-  int solve(const void* y, const purify_params* P, void* x_out, purify_stats* st, cudaStream_t s) override {
+  // The solve runs on the operator's own stream (the caller's stream may be the
+  // legacy default stream, which cannot be captured into a graph), ordered
+  // after the caller's prior work and before its later work by events.
+  int solve(const void* y, const purify_params* P, void* x_out, purify_stats* st, cudaStream_t user) override {
     if (!(P->eps > 0) || P->t_max < 1 || P->cg_iters < 1 || P->n_reweight < 0 || P->xi < 0 ||
         (P->nu <= 0 && P->power_iters < 1))
       return PURIFY_ERR_INVALID;
     int rc = ensure_solver();
     if (rc) return rc;
+    CK(cudaEventRecord(ev_in, user));
+    CK(cudaStreamWaitEvent(own, ev_in, 0));
+    rc = solve_on(y, P, x_out, st, own);
+    cudaEventRecord(ev_out, own);
+    cudaStreamWaitEvent(user, ev_out, 0);
+    return rc;
+  }
+
+  int solve_on(const void* y, const purify_params* P, void* x_out, purify_stats* st, cudaStream_t s) {
+    int rc = PURIFY_OK;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -537,10 +577,10 @@ template <typename T> class OpImpl : public purify_op {
       CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
       iteration(nu, gamma, P->eps, P->cg_iters, s);
       cudaError_t ce = cudaStreamEndCapture(s, &graph);
-      if (ce != cudaSuccess) return map_err(ce);
+      if (ce != cudaSuccess) return map_err(ce, __LINE__);
       ce = cudaGraphInstantiate(&gexec, graph, 0);
       cudaGraphDestroy(graph);
-      if (ce != cudaSuccess) return map_err(ce);
+      if (ce != cudaSuccess) return map_err(ce, __LINE__);
     }
     launch_fill<T>(w, 9 * n2, T(1), s);
     CK(cudaMemsetAsync(xh, 0, n2 * sizeof(T), s));
@@ -737,6 +777,8 @@ int purify_sdmm_solve(purify_op* op, const void* y, const purify_params* params,
   if (!op || !y || !params || !x_out) return PURIFY_ERR_INVALID;
   return op->solve(y, params, x_out, stats, static_cast<cudaStream_t>(stream));
 }
+
+const char* purify_last_error(void) { return purify::g_last_error; }
 
 const char* purify_strerror(int status) {
   switch (status) {

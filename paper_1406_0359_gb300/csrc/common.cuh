@@ -37,6 +37,19 @@ PD void set_error(int* err, int code) {
   if (err) atomicCAS(err, DEV_OK, code);
 }
 
+// Raise a kernel's dynamic shared-memory limit to what the device allows
+// next to the kernel's static shared memory (host).
+template <typename K> inline cudaError_t raise_smem_limit(K kernel) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes a;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, kernel);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - int(a.sharedSizeBytes));
+  return e;
+}
+
 // ---------------------------------------------------------------- reductions
 PD double warp_sum(double v) {
 #pragma unroll

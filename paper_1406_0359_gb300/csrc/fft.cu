@@ -1,14 +1,21 @@
-// Oversampled 2D FFT passes of the NUFFT (operator F of Phi = G F Z S, Section 4)
-// as shared-memory Stockham transforms: one radix-8 stage when log2 K is odd,
-// then radix-4 stages, each butterfly held in registers between two barriers.
+// Oversampled 2D FFT passes of the NUFFT (operator F of Phi = G F Z S, Section 4).
+//
+// Each length-K transform (K = 2n, a power of two) is a Stockham sequence of
+// register radix-16 stages (one radix-8/4/2 stage last when log2 K is not a
+// multiple of 4).  A thread always holds the 16 elements t + m K/16 of its
+// sequence: the first stage reads them straight from global memory, the last
+// writes its outputs straight to global memory, and the stages in between
+// exchange through shared memory (padded every 16 elements against bank
+// conflicts) -- two shared round trips for K = 2048.
 //
 // Forward (Phi):   row pass over the n non-zero image rows, fused with the
-//                  deapodisation S and zero-padding Z; column pass over all K
-//                  columns, writing the padded grid (periodic J-wide halo) that
-//                  the degridding kernels stage by TMA.
-// Adjoint (Phi^H): column pass reading the padded gridding accumulator and
-//                  folding its halo back onto the torus, keeping only the n rows
-//                  the crop Z^T retains; row pass fused with the crop, the
+//                  deapodisation S and zero-padding Z (only the n non-zero
+//                  inputs are read); column pass over all K columns, reading
+//                  only the n non-zero rows and writing the padded grid (with
+//                  its periodic J-wide halo) that degridding stages by TMA.
+// Adjoint (Phi^H): column pass reading the padded gridding accumulator, folding
+//                  its halo back onto the torus, writing only the n rows the
+//                  crop Z^T keeps; row pass fused with the crop, the
 //                  deapodisation and the solver epilogues.
 #include "internal.h"
 
@@ -16,251 +23,299 @@ namespace purify {
 
 namespace {
 
-template <typename C> PD void dft4(C (&a)[4], int dir) {
-  // X_k = sum_r a_r exp(dir * 2 pi i r k / 4), dir = -1 forward, +1 inverse
-  const C s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
-  const C s13 = cadd(a[1], a[3]), d13 = csub(a[1], a[3]);
+template <typename C> PD C cneg(C a) { a.x = -a.x; a.y = -a.y; return a; }
+
+template <typename C> PD void dft2(C& a, C& b) {
+  const C t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+// X_k = sum_r a_r exp(dir 2 pi i r k / 4), dir = -1 forward, +1 inverse
+template <typename C> PD void dft4(C& a0, C& a1, C& a2, C& a3, int dir) {
+  const C s02 = cadd(a0, a2), d02 = csub(a0, a2);
+  const C s13 = cadd(a1, a3), d13 = csub(a1, a3);
   C j13 = cmul_i(d13);
-  if (dir < 0) { j13.x = -j13.x; j13.y = -j13.y; }
-  a[0] = cadd(s02, s13);
-  a[2] = csub(s02, s13);
-  a[1] = cadd(d02, j13);
-  a[3] = csub(d02, j13);
+  if (dir < 0) j13 = cneg(j13);
+  a0 = cadd(s02, s13);
+  a2 = csub(s02, s13);
+  a1 = cadd(d02, j13);
+  a3 = csub(d02, j13);
 }
 
-template <typename C> PD void dft8(C (&a)[8], int dir) {
-  typedef decltype(a[0].x) T;
-  C e[4] = {a[0], a[2], a[4], a[6]};
-  C o[4] = {a[1], a[3], a[5], a[7]};
-  dft4(e, dir);
-  dft4(o, dir);
-  const T h = T(0.70710678118654752440084436210485);
-  const T sg = dir < 0 ? T(-1) : T(1);
-  C w1 = cmk<C>(h, sg * h), w3 = cmk<C>(-h, sg * h);
-  C t1 = cmul(o[1], w1);
-  C t2 = cmul_i(o[2]);
-  if (dir < 0) { t2.x = -t2.x; t2.y = -t2.y; }
-  C t3 = cmul(o[3], w3);
-  a[0] = cadd(e[0], o[0]);
-  a[4] = csub(e[0], o[0]);
-  a[1] = cadd(e[1], t1);
-  a[5] = csub(e[1], t1);
-  a[2] = cadd(e[2], t2);
-  a[6] = csub(e[2], t2);
-  a[3] = cadd(e[3], t3);
-  a[7] = csub(e[3], t3);
+// exp(dir 2 pi i m / 16) for the fixed m used by the radix-16/8 butterflies
+template <typename C> PD C w16(int m, int dir) {
+  typedef decltype(C().x) T;
+  const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173);
+  const T h = T(0.70710678118654752440);
+  T re = 1, im = 0;
+  switch (m) {
+    case 1: re = c1; im = s1; break;
+    case 2: re = h; im = h; break;
+    case 3: re = s1; im = c1; break;
+    case 4: re = 0; im = 1; break;
+    case 6: re = -h; im = h; break;
+    case 9: re = -c1; im = -s1; break;
+    default: break;
+  }
+  return cmk<C>(re, dir < 0 ? -im : im);
 }
 
-template <int R, typename C> PD void dftR(C (&a)[R], int dir);
-template <> PD void dftR<4, float2>(float2 (&a)[4], int dir) { dft4(a, dir); }
-template <> PD void dftR<4, double2>(double2 (&a)[4], int dir) { dft4(a, dir); }
-template <> PD void dftR<8, float2>(float2 (&a)[8], int dir) { dft8(a, dir); }
-template <> PD void dftR<8, double2>(double2 (&a)[8], int dir) { dft8(a, dir); }
+// In-register DFT of a[o], a[o+st], ..., R points (Cooley-Tukey, natural order out).
+template <int R, typename C> struct Dft;
+template <typename C> struct Dft<2, C> {
+  static PD void run(C* a, int o, int st, int) { dft2(a[o], a[o + st]); }
+};
+template <typename C> struct Dft<4, C> {
+  static PD void run(C* a, int o, int st, int dir) { dft4(a[o], a[o + st], a[o + 2 * st], a[o + 3 * st], dir); }
+};
+template <typename C> struct Dft<8, C> {
+  // 8 = 2 x 4: 2-point DFTs on (n2, n2+4), twiddle W8^(n2 k1), 4-point DFTs over n2
+  static PD void run(C* a, int o, int st, int dir) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft2(a[o + n2 * st], a[o + (n2 + 4) * st]);
+    a[o + 5 * st] = cmul(a[o + 5 * st], w16<C>(2, dir));
+    a[o + 6 * st] = cmul(a[o + 6 * st], w16<C>(4, dir));
+    a[o + 7 * st] = cmul(a[o + 7 * st], w16<C>(6, dir));
+    dft4(a[o], a[o + st], a[o + 2 * st], a[o + 3 * st], dir);
+    dft4(a[o + 4 * st], a[o + 5 * st], a[o + 6 * st], a[o + 7 * st], dir);
+    C t[8];  // X[k1 + 2 k2] = a[4 k1 + k2]
+#pragma unroll
+    for (int k1 = 0; k1 < 2; ++k1)
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) t[k1 + 2 * k2] = a[o + (k1 * 4 + k2) * st];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[o + k * st] = t[k];
+  }
+};
+template <typename C> struct Dft<16, C> {
+  // 16 = 4 x 4: 4-point DFTs on (n2, n2+4, n2+8, n2+12), twiddle W16^(n2 k1), 4-point DFTs
+  static PD void run(C* a, int o, int st, int dir) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2)
+      dft4(a[o + n2 * st], a[o + (n2 + 4) * st], a[o + (n2 + 8) * st], a[o + (n2 + 12) * st], dir);
+#pragma unroll
+    for (int n2 = 1; n2 < 4; ++n2)
+#pragma unroll
+      for (int k1 = 1; k1 < 4; ++k1)
+        a[o + (n2 + 4 * k1) * st] = cmul(a[o + (n2 + 4 * k1) * st], w16<C>(n2 * k1, dir));
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+      dft4(a[o + 4 * k1 * st], a[o + (4 * k1 + 1) * st], a[o + (4 * k1 + 2) * st], a[o + (4 * k1 + 3) * st], dir);
+    C t[16];  // X[k1 + 4 k2] = a[4 k1 + k2]
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) t[k1 + 4 * k2] = a[o + (4 * k1 + k2) * st];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[o + k * st] = t[k];
+  }
+};
 
-// One Stockham radix-R stage over nseq sequences of length N (pitch apart),
-// sub-transform length Ns.  Every thread holds at most MAXB butterflies.
-template <int R, int MAXB, typename C>
-__device__ void fft_stage(C* s, int N, int Ns, int nseq, int pitch, const C* __restrict__ tw, int dir) {
-  const int nbs = N / R;
-  const int nb = nseq * nbs;
+PD int sidx(int e) { return e + (e >> 4); }  // padded shared index
+
+// Compile-time plan of a length-2^LOGN transform: radix-16 stages, then one
+// radix-2^(LOGN mod 4) stage; T = N/16 threads per sequence.
+template <int LOGN> struct Plan {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int T = N / 16;
+  static constexpr int NST = (LOGN + 3) / 4;
+  __host__ __device__ static constexpr int radix(int st) { return (st + 1 < NST || LOGN % 4 == 0) ? 16 : (1 << (LOGN % 4)); }
+};
+
+// One Stockham stage on the registers: v[m] holds element t + m T of the
+// stage input.  Thread t owns butterflies j = t + q T (q < 16/R); input r of
+// butterfly j is element j + r N/R, i.e. register q + r 16/R.  After the
+// twiddles and the DFT, register q + r 16/R is output (j - k) R + k + r Ns
+// with k = j mod Ns; sink(position, value) receives every output.
+template <int R, int N, int T, typename C, typename Sink>
+PD void stage(C (&v)[16], int t, int Ns, const C* __restrict__ tw, int dir, Sink sink) {
+  constexpr int Q = 16 / R;
   const int tstride = N / (Ns * R);
-  C a[MAXB][R];
 #pragma unroll
-  for (int b = 0; b < MAXB; ++b) {
-    const int j = threadIdx.x + b * blockDim.x;
-    if (j < nb) {
-      const int seq = j / nbs, jj = j - seq * nbs;
-      const int k = jj & (Ns - 1);
-      const C* src = s + seq * pitch + jj;
+  for (int q = 0; q < Q; ++q) {
+    const int j = t + q * T;
+    const int k = j & (Ns - 1);
+    if (k) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        C v = src[r * nbs];
-        if (r > 0 && k > 0) {
-          C t = tw[r * k * tstride];
-          if (dir > 0) t.y = -t.y;
-          v = cmul(v, t);
-        }
-        a[b][r] = v;
+      for (int r = 1; r < R; ++r) {
+        C w = tw[r * k * tstride];
+        if (dir > 0) w.y = -w.y;
+        v[q + r * Q] = cmul(v[q + r * Q], w);
       }
     }
+    Dft<R, C>::run(v, q, Q, dir);
   }
-  __syncthreads();
 #pragma unroll
-  for (int b = 0; b < MAXB; ++b) {
-    const int j = threadIdx.x + b * blockDim.x;
-    if (j < nb) {
-      const int seq = j / nbs, jj = j - seq * nbs;
-      const int k = jj & (Ns - 1);
-      dftR<R>(a[b], dir);
-      C* dst = s + seq * pitch + (jj - k) * R + k;
+  for (int q = 0; q < Q; ++q) {
+    const int j = t + q * T;
+    const int k = j & (Ns - 1);
+    const int base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) dst[r * Ns] = a[b][r];
-    }
-  }
-  __syncthreads();
-}
-
-constexpr int kMaxB = 8;
-
-template <typename C>
-__device__ void fft_smem(C* s, int N, int logN, int nseq, int pitch, const C* __restrict__ tw, int dir) {
-  int Ns = 1;
-  if (logN & 1) {
-    fft_stage<8, kMaxB / 2>(s, N, 1, nseq, pitch, tw, dir);
-    Ns = 8;
-  }
-  while (Ns < N) {
-    fft_stage<4, kMaxB>(s, N, Ns, nseq, pitch, tw, dir);
-    Ns *= 4;
+    for (int r = 0; r < R; ++r) sink(base + r * Ns, v[q + r * Q]);
   }
 }
 
-constexpr int kRowThreads = 128;
-
-inline int ilog2(int v) {
-  int l = 0;
-  while ((1 << l) < v) ++l;
-  return l;
+template <int LOGN, int ST, typename C, typename Store>
+PD void run_stages(C (&v)[16], int t, int Ns, C* s, const C* tw, int dir, Store store) {
+  typedef Plan<LOGN> P;
+  constexpr int R = P::radix(ST);
+  if constexpr (ST + 1 == P::NST) {
+    stage<R, P::N, P::T>(v, t, Ns, tw, dir, store);
+  } else {
+    stage<R, P::N, P::T>(v, t, Ns, tw, dir, [&](int q, C x) { s[sidx(q)] = x; });
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = s[sidx(t + m * P::T)];
+    __syncthreads();
+    run_stages<LOGN, ST + 1>(v, t, Ns * R, s, tw, dir, store);
+  }
 }
+
+// All stages of one sequence: load(m) supplies input element t + m T,
+// store(q, value) receives output q.  s is this sequence's padded shared buffer.
+template <int LOGN, typename C, typename Load, typename Store>
+PD void fft_seq(int t, C* s, const C* tw, int dir, Load load, Store store) {
+  C v[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) v[m] = load(m);
+  run_stages<LOGN, 0>(v, t, 1, s, tw, dir, store);
+}
+
+constexpr int kRowCta = 256;
+
 inline int row_nseq(const Geometry& g) {
-  int s = 512 / g.K;
+  int s = kRowCta / (g.K / 16);
   if (s < 1) s = 1;
-  if (s > 4) s = 4;
+  if (s > g.n) s = g.n;
   return s;
 }
 template <typename T> inline int col_width() { return 32 / int(sizeof(typename cplx_t<T>::type)); }
-inline int col_threads(int cw, int K) {
-  int t = cw * K / 4 / kMaxB;
-  if (t < 128) t = 128;
-  if (t > 1024) t = 1024;
-  return t;
-}
+__host__ __device__ inline size_t padded(int N) { return size_t(N) + size_t(N) / 16 + 1; }
 
 // ----------------------------------------------------------------- kernels
-template <typename T>
-__global__ void __launch_bounds__(kRowThreads) k_row_fwd(Geometry g, RowPro<T> pro, const T* __restrict__ deapod,
-                                                          typename cplx_t<T>::type* __restrict__ A,
-                                                          const typename cplx_t<T>::type* __restrict__ tw, int nseq,
-                                                          int logK) {
+template <typename T, int LOGN> struct ColThreads {
+  static constexpr int value = (32 / int(sizeof(typename cplx_t<T>::type))) * ((1 << LOGN) / 16);
+};
+
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(kRowCta) k_row_fwd(Geometry g, RowPro<T> pro, const T* __restrict__ deapod,
+                                                  typename cplx_t<T>::type* __restrict__ A,
+                                                  const typename cplx_t<T>::type* __restrict__ tw, int nseq) {
   typedef typename cplx_t<T>::type C;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  C* s = reinterpret_cast<C*>(sm_raw);
   const int K = g.K, n = g.n, half = n / 2;
-  const int row0 = blockIdx.x * nseq;
-  for (int e = threadIdx.x; e < nseq * K; e += blockDim.x) s[e] = cz<C>();
-  __syncthreads();
-  for (int e = threadIdx.x; e < nseq * n; e += blockDim.x) {
-    const int r = e / n, i2 = e - r * n, i1 = row0 + r;
+  const int seq = threadIdx.x / Plan<LOGN>::T, t = threadIdx.x - seq * Plan<LOGN>::T;
+  const int i1 = blockIdx.x * nseq + seq;
+  C* s = reinterpret_cast<C*>(sm_raw) + seq * padded(K);
+  const T s1 = deapod[i1];
+  const T beta = pro.mode == PRO_CG_P ? T(pro.scalars[pro.idx]) : T(0);
+  const T scl = pro.mode == PRO_SCALE ? T(pro.scalars[pro.idx]) : T(1);
+  auto load = [&](int m) -> C {
+    const int q = t + m * Plan<LOGN>::T;            // grid column
+    const int i2 = (q + half) & (K - 1);  // image column when q is a padded position
+    if (i2 >= n) return cz<C>();
     const size_t idx = size_t(i1) * n + i2;
     T v;
     if (pro.mode == PRO_CG_P) {
-      const T beta = T(pro.scalars[pro.idx]);
       v = pro.r[idx] + beta * pro.p[idx];
       pro.p[idx] = v;
-    } else if (pro.mode == PRO_SCALE) {
-      v = pro.x[idx] * T(pro.scalars[pro.idx]);
     } else {
-      v = pro.x[idx];
+      v = pro.x[idx] * scl;
     }
-    const int q2 = (i2 - half) & (K - 1);
-    s[r * K + q2] = cmk<C>(v * deapod[i1] * deapod[i2], T(0));
-  }
-  __syncthreads();
-  fft_smem(s, K, logK, nseq, K, tw, -1);
-  for (int e = threadIdx.x; e < nseq * K; e += blockDim.x) A[size_t(row0) * K + e] = s[e];
+    return cmk<C>(v * s1 * deapod[i2], T(0));
+  };
+  C* out = A + size_t(i1) * K;
+  auto store = [&](int q, C v) { out[q] = v; };
+  fft_seq<LOGN>(t, s, tw, -1, load, store);
 }
 
-template <typename T>
-__global__ void k_col_fwd(Geometry g, const typename cplx_t<T>::type* __restrict__ A,
-                          typename cplx_t<T>::type* __restrict__ P, const typename cplx_t<T>::type* __restrict__ tw,
-                          int cw, int logK) {
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN>::value <= 512 ? 2 : 1) k_col_fwd(Geometry g, const typename cplx_t<T>::type* __restrict__ A,
+                                                  typename cplx_t<T>::type* __restrict__ Pg,
+                                                  const typename cplx_t<T>::type* __restrict__ tw, int cw) {
   typedef typename cplx_t<T>::type C;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  C* s = reinterpret_cast<C*>(sm_raw);
   const int K = g.K, n = g.n, half = n / 2, pl = g.pad_lo, KP = g.KP;
-  const int pitch = K + 1;
-  const int c0 = blockIdx.x * cw;
-  for (int e = threadIdx.x; e < cw * pitch; e += blockDim.x) s[e] = cz<C>();
-  __syncthreads();
-  for (int e = threadIdx.x; e < n * cw; e += blockDim.x) {
-    const int i1 = e / cw, cc = e - i1 * cw;
-    const int q1 = (i1 - half) & (K - 1);
-    s[cc * pitch + q1] = A[size_t(i1) * K + c0 + cc];
-  }
-  __syncthreads();
-  fft_smem(s, K, logK, cw, pitch, tw, -1);
-  const int jhi = kJ - pl;  // grid indices < jhi are repeated past the end
-  for (int e = threadIdx.x; e < K * cw; e += blockDim.x) {
-    const int q = e / cw, cc = e - q * cw, c = c0 + cc;
-    const C v = s[cc * pitch + q];
-    int rows[2] = {q + pl, -1}, cols[2] = {c + pl, -1};
+  const int cc = threadIdx.x % cw, t = threadIdx.x / cw;
+  const int c = blockIdx.x * cw + cc;
+  C* s = reinterpret_cast<C*>(sm_raw) + cc * padded(K);
+  auto load = [&](int m) -> C {
+    const int q = t + m * Plan<LOGN>::T;  // grid row
+    const int i1 = (q + half) & (K - 1);
+    return i1 < n ? A[size_t(i1) * K + c] : cz<C>();
+  };
+  const int jhi = kJ - pl;  // grid indices < jhi repeat past the end
+  int cols[2] = {c + pl, -1};
+  if (c >= K - pl) cols[1] = c + pl - K;
+  else if (c < jhi) cols[1] = c + pl + K;
+  auto store = [&](int q, C v) {
+    int rows[2] = {q + pl, -1};
     if (q >= K - pl) rows[1] = q + pl - K;
     else if (q < jhi) rows[1] = q + pl + K;
-    if (c >= K - pl) cols[1] = c + pl - K;
-    else if (c < jhi) cols[1] = c + pl + K;
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
       for (int b = 0; b < 2; ++b)
-        if (rows[a] >= 0 && cols[b] >= 0) P[size_t(rows[a]) * KP + cols[b]] = v;
-  }
+        if (rows[a] >= 0 && cols[b] >= 0) Pg[size_t(rows[a]) * KP + cols[b]] = v;
+  };
+  fft_seq<LOGN>(t, s, tw, -1, load, store);
 }
 
-template <typename T>
-__global__ void k_col_inv(Geometry g, const typename cplx_t<T>::type* __restrict__ Q,
-                          typename cplx_t<T>::type* __restrict__ A, const typename cplx_t<T>::type* __restrict__ tw,
-                          int cw, int logK) {
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN>::value <= 512 ? 2 : 1) k_col_inv(Geometry g, const typename cplx_t<T>::type* __restrict__ Q,
+                                                  typename cplx_t<T>::type* __restrict__ A,
+                                                  const typename cplx_t<T>::type* __restrict__ tw, int cw) {
   typedef typename cplx_t<T>::type C;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  C* s = reinterpret_cast<C*>(sm_raw);
   const int K = g.K, n = g.n, half = n / 2, pl = g.pad_lo, KP = g.KP;
-  const int pitch = K + 1;
-  const int c0 = blockIdx.x * cw;
+  const int cc = threadIdx.x % cw, t = threadIdx.x / cw;
+  const int c = blockIdx.x * cw + cc;
+  C* s = reinterpret_cast<C*>(sm_raw) + cc * padded(K);
   const int jhi = kJ - pl;
-  for (int e = threadIdx.x; e < K * cw; e += blockDim.x) {
-    const int q = e / cw, cc = e - q * cw, c = c0 + cc;
-    int rows[2] = {q + pl, -1}, cols[2] = {c + pl, -1};
+  int cols[2] = {c + pl, -1};
+  if (c >= K - pl) cols[1] = c + pl - K;
+  else if (c < jhi) cols[1] = c + pl + K;
+  auto load = [&](int m) -> C {
+    const int q = t + m * Plan<LOGN>::T;
+    int rows[2] = {q + pl, -1};
     if (q >= K - pl) rows[1] = q + pl - K;
     else if (q < jhi) rows[1] = q + pl + K;
-    if (c >= K - pl) cols[1] = c + pl - K;
-    else if (c < jhi) cols[1] = c + pl + K;
     C v = cz<C>();
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
       for (int b = 0; b < 2; ++b)
         if (rows[a] >= 0 && cols[b] >= 0) v = cadd(v, Q[size_t(rows[a]) * KP + cols[b]]);
-    s[cc * pitch + q] = v;
-  }
-  __syncthreads();
-  fft_smem(s, K, logK, cw, pitch, tw, +1);
-  for (int e = threadIdx.x; e < n * cw; e += blockDim.x) {
-    const int i1 = e / cw, cc = e - i1 * cw;
-    const int q1 = (i1 - half) & (K - 1);
-    A[size_t(i1) * K + c0 + cc] = s[cc * pitch + q1];
-  }
+    return v;
+  };
+  auto store = [&](int q, C v) {
+    const int i1 = (q + half) & (K - 1);
+    if (i1 < n) A[size_t(i1) * K + c] = v;
+  };
+  fft_seq<LOGN>(t, s, tw, +1, load, store);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kRowThreads) k_row_inv(Geometry g, const typename cplx_t<T>::type* __restrict__ A,
-                                                          const T* __restrict__ deapod, RowEp<T> ep,
-                                                          const typename cplx_t<T>::type* __restrict__ tw, int nseq,
-                                                          int logK) {
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(kRowCta) k_row_inv(Geometry g, const typename cplx_t<T>::type* __restrict__ A,
+                                                  const T* __restrict__ deapod, RowEp<T> ep,
+                                                  const typename cplx_t<T>::type* __restrict__ tw, int nseq) {
   typedef typename cplx_t<T>::type C;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ double red[32];
-  C* s = reinterpret_cast<C*>(sm_raw);
   const int K = g.K, n = g.n, half = n / 2;
-  const int row0 = blockIdx.x * nseq;
-  for (int e = threadIdx.x; e < nseq * K; e += blockDim.x) s[e] = A[size_t(row0) * K + e];
-  __syncthreads();
-  fft_smem(s, K, logK, nseq, K, tw, +1);
+  const int seq = threadIdx.x / Plan<LOGN>::T, t = threadIdx.x - seq * Plan<LOGN>::T;
+  const int i1 = blockIdx.x * nseq + seq;
+  C* s = reinterpret_cast<C*>(sm_raw) + seq * padded(K);
+  const C* in = A + size_t(i1) * K;
+  auto load = [&](int m) -> C { return in[t + m * Plan<LOGN>::T]; };
+  const T s1 = deapod[i1];
   double part = 0.0;
-  for (int e = threadIdx.x; e < nseq * n; e += blockDim.x) {
-    const int r = e / n, i2 = e - r * n, i1 = row0 + r;
+  auto store = [&](int q, C v) {
+    const int i2 = (q + half) & (K - 1);
+    if (i2 >= n) return;
     const size_t idx = size_t(i1) * n + i2;
-    const int q2 = (i2 - half) & (K - 1);
-    const T val = s[r * K + q2].x * deapod[i1] * deapod[i2];
+    const T val = v.x * s1 * deapod[i2];
     switch (ep.mode) {
       case EP_CG_AP: {
         const T pv = ep.p[idx];
@@ -287,10 +342,18 @@ __global__ void __launch_bounds__(kRowThreads) k_row_inv(Geometry g, const typen
       default:
         ep.out[idx] = val;
     }
-  }
+  };
+  fft_seq<LOGN>(t, s, tw, +1, load, store);
   if (ep.partials) {
-    const double t = block_sum<kRowThreads>(part, red);
-    if (threadIdx.x == 0) ep.partials[blockIdx.x] = t;
+    part = warp_sum(part);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int k = 0; k < int((blockDim.x + 31) >> 5); ++k) tot += red[k];
+      ep.partials[blockIdx.x] = tot;
+    }
   }
 }
 
@@ -298,12 +361,31 @@ __global__ void __launch_bounds__(kRowThreads) k_row_inv(Geometry g, const typen
 
 int row_inv_blocks(const Geometry& g) { return g.n / row_nseq(g); }
 
+#define PURIFY_LOGN_SWITCH(K, BODY)     \
+  switch (K) {                          \
+    case 32: { constexpr int L = 5; BODY; } break;   \
+    case 64: { constexpr int L = 6; BODY; } break;   \
+    case 128: { constexpr int L = 7; BODY; } break;  \
+    case 256: { constexpr int L = 8; BODY; } break;  \
+    case 512: { constexpr int L = 9; BODY; } break;  \
+    case 1024: { constexpr int L = 10; BODY; } break; \
+    case 2048: { constexpr int L = 11; BODY; } break; \
+    default: { constexpr int L = 12; BODY; } break;  \
+  }
+
+template <typename T, int L> cudaError_t configure_one() {
+  cudaError_t e = raise_smem_limit(k_row_fwd<T, L>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_row_inv<T, L>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_col_fwd<T, L>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_col_inv<T, L>);
+  return e;
+}
+
 template <typename T> cudaError_t configure_fft() {
-  const int mx = 227 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_row_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaError_t e = cudaSuccess;
+  for (int K = 32; K <= 4096 && e == cudaSuccess; K *= 2) {
+    PURIFY_LOGN_SWITCH(K, e = (configure_one<T, L>()));
+  }
   return e;
 }
 template cudaError_t configure_fft<float>();
@@ -314,17 +396,17 @@ void launch_row_fwd(const Geometry& g, const RowPro<T>& pro, const T* deapod, ty
                     const typename cplx_t<T>::type* tw, cudaStream_t s) {
   typedef typename cplx_t<T>::type C;
   const int nseq = row_nseq(g);
-  const size_t sm = size_t(nseq) * g.K * sizeof(C);
-  k_row_fwd<T><<<g.n / nseq, kRowThreads, sm, s>>>(g, pro, deapod, A, tw, nseq, ilog2(g.K));
+  const size_t sm = nseq * padded(g.K) * sizeof(C);
+  PURIFY_LOGN_SWITCH(g.K, (k_row_fwd<T, L><<<g.n / nseq, nseq * Plan<L>::T, sm, s>>>(g, pro, deapod, A, tw, nseq)));
 }
 
 template <typename T>
-void launch_col_fwd(const Geometry& g, const typename cplx_t<T>::type* A, typename cplx_t<T>::type* P,
+void launch_col_fwd(const Geometry& g, const typename cplx_t<T>::type* A, typename cplx_t<T>::type* Pg,
                     const typename cplx_t<T>::type* tw, cudaStream_t s) {
   typedef typename cplx_t<T>::type C;
   const int cw = col_width<T>();
-  const size_t sm = size_t(cw) * (g.K + 1) * sizeof(C);
-  k_col_fwd<T><<<g.K / cw, col_threads(cw, g.K), sm, s>>>(g, A, P, tw, cw, ilog2(g.K));
+  const size_t sm = cw * padded(g.K) * sizeof(C);
+  PURIFY_LOGN_SWITCH(g.K, (k_col_fwd<T, L><<<g.K / cw, cw * Plan<L>::T, sm, s>>>(g, A, Pg, tw, cw)));
 }
 
 template <typename T>
@@ -332,8 +414,8 @@ void launch_col_inv(const Geometry& g, const typename cplx_t<T>::type* Q, typena
                     const typename cplx_t<T>::type* tw, cudaStream_t s) {
   typedef typename cplx_t<T>::type C;
   const int cw = col_width<T>();
-  const size_t sm = size_t(cw) * (g.K + 1) * sizeof(C);
-  k_col_inv<T><<<g.K / cw, col_threads(cw, g.K), sm, s>>>(g, Q, A, tw, cw, ilog2(g.K));
+  const size_t sm = cw * padded(g.K) * sizeof(C);
+  PURIFY_LOGN_SWITCH(g.K, (k_col_inv<T, L><<<g.K / cw, cw * Plan<L>::T, sm, s>>>(g, Q, A, tw, cw)));
 }
 
 template <typename T>
@@ -341,8 +423,8 @@ int launch_row_inv(const Geometry& g, const typename cplx_t<T>::type* A, const T
                    const typename cplx_t<T>::type* tw, cudaStream_t s) {
   typedef typename cplx_t<T>::type C;
   const int nseq = row_nseq(g);
-  const size_t sm = size_t(nseq) * g.K * sizeof(C);
-  k_row_inv<T><<<g.n / nseq, kRowThreads, sm, s>>>(g, A, deapod, ep, tw, nseq, ilog2(g.K));
+  const size_t sm = nseq * padded(g.K) * sizeof(C);
+  PURIFY_LOGN_SWITCH(g.K, (k_row_inv<T, L><<<g.n / nseq, nseq * Plan<L>::T, sm, s>>>(g, A, deapod, ep, tw, nseq)));
   return g.n / nseq;
 }
 

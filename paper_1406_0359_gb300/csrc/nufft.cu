@@ -17,6 +17,7 @@
 // Kernel weights come from a per-tap polynomial in the fractional offset
 // (Chebyshev fit of the Kaiser-Bessel kernel, computed on the host).
 #include <cstdio>
+#include <cstring>
 
 #include "internal.h"
 
@@ -41,15 +42,24 @@ PD void decode(const Pos<double>& p, int& cu, double& fu, int& cv, double& fv) {
   fv = p.v - b;
 }
 
+// Kernel weights of the J taps at fractional offset f.  The kernel is even,
+// so tap J-1-a at f equals tap a at 1-f, i.e. its polynomial in x = 2f-1 is
+// tap a's at -x: with P_a(x) = E_a(x^2) + x O_a(x^2) both taps of a pair come
+// from one even and one odd Horner chain in x^2.
 template <typename T> PD void kb_eval(const KbPoly<T>& kb, T f, T (&w)[kJ]) {
   constexpr int D = KbDeg<T>::value;
   const T x = T(2) * f - T(1);
+  const T x2 = x * x;
 #pragma unroll
-  for (int a = 0; a < kJ; ++a) {
-    T acc = kb.c[a][D];
+  for (int a = 0; a < kJ / 2; ++a) {
+    T e = kb.c[a][D - (D & 1)];
 #pragma unroll
-    for (int d = D - 1; d >= 0; --d) acc = fma(acc, x, kb.c[a][d]);
-    w[a] = acc;
+    for (int d = D - (D & 1) - 2; d >= 0; d -= 2) e = fma(e, x2, kb.c[a][d]);
+    T o = kb.c[a][D - 1 + (D & 1)];
+#pragma unroll
+    for (int d = D - 1 + (D & 1) - 2; d >= 1; d -= 2) o = fma(o, x2, kb.c[a][d]);
+    w[a] = fma(x, o, e);
+    w[kJ - 1 - a] = fma(-x, o, e);
   }
 }
 
@@ -60,7 +70,8 @@ template <> PD void atomic_add_global<double2>(double2* p, double2 v) {
   atomicAdd(&p->y, v.y);
 }
 
-// Stage the work item's grid patch by TMA; returns false on a timed-out wait.
+// Stage the work item's grid patch by TMA; false (for every thread) when the
+// bounded wait gave up in any thread.
 template <typename C>
 PD bool stage_patch(C* patch, uint64_t* bar, const CUtensorMap* map, int tu, int tv, int TB, int PW, int* err) {
   if (threadIdx.x == 0) {
@@ -73,198 +84,237 @@ PD bool stage_patch(C* patch, uint64_t* bar, const CUtensorMap* map, int tu, int
     const int cw = int(sizeof(C) / 8);
     tma_load_2d(patch, map, tv * TB * cw, tu * TB, bar);
   }
-  // every thread waits (bounded); the CTA leaves together if any wait gave up
   const bool ok = mbar_wait_bounded(bar, 0, err);
   return __syncthreads_and(ok) != 0;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_degrid(Geometry g, const __grid_constant__ CUtensorMap map,
-                                                     const WorkItem* __restrict__ items,
-                                                     const Pos<T>* __restrict__ pos, const int* __restrict__ perm,
-                                                     KbPoly<T> kb, DegridEp<typename cplx_t<T>::type> ep, int* err) {
+enum TileMode : int { TM_DEGRID = 0, TM_GRID = 1, TM_GRAM = 2 };
+constexpr int kWarps = kThreads / 32;
+constexpr int kStage = 2 * kJ + 3;  // wu[J], wv[J], u.re, u.im, packed cell
+
+template <typename T> __host__ __device__ inline size_t tile_patch_bytes(int TB) {
+  const size_t PW = size_t(TB + kJ);
+  return PW * PW * sizeof(typename cplx_t<T>::type);
+}
+template <typename T> __host__ __device__ inline size_t tile_acc_bytes(int TB) {
+  const size_t PW = size_t(TB + kJ);
+  return size_t(kWarps) * PW * (PW + 1) * sizeof(typename cplx_t<T>::type);
+}
+template <typename T> __host__ __device__ inline size_t tile_stage_bytes() {
+  return size_t(kWarps) * 32 * kStage * sizeof(T);
+}
+
+template <typename C> PD C warp_allsum(C v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+// One CTA per work item; visibilities arrive sorted by grid cell inside the
+// tile.  Warp w takes a contiguous slice of the item.  In 32-wide batches
+// every lane first computes its own visibility's kernel weights (and, for
+// gridding, its value) into a per-warp staging row; then the warp walks the
+// batch one visibility at a time with lane l owning taps (l/4, 2(l%4)) and
+// (l/4, 2(l%4)+1) of the J x J footprint.  For a run of visibilities in the
+// same cell the lanes keep the footprint's grid values (gather) and its
+// scatter sums (gridding) in registers; shared memory is touched only when
+// the cell changes.  Gathered values are summed across the warp by a
+// butterfly of shuffles.  Scatter sums go to the warp's private accumulator
+// patch (no atomics); the patches are merged and flushed with one vector
+// atomic per non-zero cell at the end.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) k_tile(Geometry g, const __grid_constant__ CUtensorMap map,
+                                                   const WorkItem* __restrict__ items,
+                                                   const Pos<T>* __restrict__ pos, const int* __restrict__ perm,
+                                                   KbPoly<T> kb, DegridEp<typename cplx_t<T>::type> dep,
+                                                   GridPro<typename cplx_t<T>::type> gpro,
+                                                   typename cplx_t<T>::type* __restrict__ Q, int* err) {
   typedef typename cplx_t<T>::type C;
+  constexpr bool kGather = MODE != TM_GRID;
+  constexpr bool kScatter = MODE != TM_DEGRID;
   extern __shared__ __align__(128) unsigned char sm_raw[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ double red[32];
-  C* patch = reinterpret_cast<C*>(sm_raw);
   const WorkItem it = items[blockIdx.x];
   const int tu = it.tile / g.ntile1d, tv = it.tile - tu * g.ntile1d;
-  const int PW = g.TB + kJ;
-  if (!stage_patch(patch, &bar, &map, tu, tv, g.TB, PW, err)) return;
-  double p0 = 0.0, p1 = 0.0;
-  for (int i = it.begin + threadIdx.x; i < it.end; i += kThreads) {
-    int cu, cv;
-    T fu, fv;
-    decode(pos[i], cu, fu, cv, fv);
-    T wu[kJ], wv[kJ];
-    kb_eval(kb, fu, wu);
-    kb_eval(kb, fv, wv);
-    T ax = 0, ay = 0;
-#pragma unroll
-    for (int a = 0; a < kJ; ++a) {
-      const C* row = patch + (cu + a) * PW + cv;
-      T hx = 0, hy = 0;
-#pragma unroll
-      for (int b = 0; b < kJ; ++b) {
-        const C gv = row[b];
-        hx = fma(wv[b], gv.x, hx);
-        hy = fma(wv[b], gv.y, hy);
-      }
-      ax = fma(wu[a], hx, ax);
-      ay = fma(wu[a], hy, ay);
-    }
-    if (ep.mode == DG_STORE_PERM) {
-      ep.y[perm[i]] = cmk<C>(ax, ay);
-    } else if (ep.mode == DG_STORE_SORTED) {
-      ep.y[i] = cmk<C>(ax, ay);
-    } else {  // DG_BALL
-      const C z = ep.z[i], yv = ep.ys[i];
-      const T nu = T(ep.nu);
-      const C v = cmk<C>(fma(nu, ax, z.x), fma(nu, ay, z.y));
-      ep.z[i] = v;
-      const double dx = double(v.x) - ep.nu * double(yv.x), dy = double(v.y) - ep.nu * double(yv.y);
-      p0 += dx * dx + dy * dy;
-      const double ex = double(ax) - double(yv.x), ey = double(ay) - double(yv.y);
-      p1 += ex * ex + ey * ey;
-    }
+  const int PW = g.TB + kJ, PA = PW + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* cur = sm_raw;
+  C* patch = reinterpret_cast<C*>(cur);
+  if (kGather) cur += tile_patch_bytes<T>(g.TB);
+  C* acc = reinterpret_cast<C*>(cur);
+  if (kScatter) {
+    cur += tile_acc_bytes<T>(g.TB);
+    for (int e = threadIdx.x; e < kWarps * PW * PA; e += kThreads) acc[e] = cz<C>();
   }
-  if (ep.mode == DG_BALL) {
-    const double s0 = block_sum<kThreads>(p0, red);
-    const double s1 = block_sum<kThreads>(p1, red);
-    if (threadIdx.x == 0) {
-      ep.part0[blockIdx.x] = s0;
-      ep.part1[blockIdx.x] = s1;
-    }
+  T* stage = reinterpret_cast<T*>(cur);
+  if (kGather) {
+    if (!stage_patch(patch, &bar, &map, tu, tv, g.TB, PW, err)) return;
+  } else {
+    __syncthreads();
   }
-}
-
-template <typename C>
-PD void flush_patch(const C* acc, C* Q, int tu, int tv, int TB, int PW, int KP) {
-  for (int e = threadIdx.x; e < PW * PW; e += kThreads) {
-    const C v = acc[e];
-    if (v.x != 0 || v.y != 0) {
-      const int r = e / PW, c = e - r * PW;
-      atomic_add_global(Q + size_t(tu * TB + r) * KP + (tv * TB + c), v);
-    }
-  }
-}
-
-template <typename T>
-PD void scatter_taps(typename cplx_t<T>::type* acc, int PW, int cu, int cv, const T (&wu)[kJ], const T (&wv)[kJ],
-                     T ux, T uy) {
-#pragma unroll
-  for (int a = 0; a < kJ; ++a) {
-    typename cplx_t<T>::type* row = acc + (cu + a) * PW + cv;
-    const T sx = wu[a] * ux, sy = wu[a] * uy;
-#pragma unroll
-    for (int b = 0; b < kJ; ++b) {
-      atomicAdd(&row[b].x, wv[b] * sx);
-      atomicAdd(&row[b].y, wv[b] * sy);
-    }
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_grid(Geometry g, const WorkItem* __restrict__ items,
-                                                   const Pos<T>* __restrict__ pos, const int* __restrict__ perm,
-                                                   KbPoly<T> kb, GridPro<typename cplx_t<T>::type> pro,
-                                                   typename cplx_t<T>::type* __restrict__ Q) {
-  typedef typename cplx_t<T>::type C;
-  extern __shared__ __align__(128) unsigned char sm_raw[];
-  C* acc = reinterpret_cast<C*>(sm_raw);
-  const WorkItem it = items[blockIdx.x];
-  const int tu = it.tile / g.ntile1d, tv = it.tile - tu * g.ntile1d;
-  const int PW = g.TB + kJ;
-  for (int e = threadIdx.x; e < PW * PW; e += kThreads) acc[e] = cz<C>();
-  __syncthreads();
+  C* wacc = acc + warp * PW * PA;
+  T* wst = stage + warp * 32 * kStage;
   T scale = 0;
-  if (pro.mode == GP_BALL) scale = T(pro.scalars[pro.scale_idx]);
-  for (int i = it.begin + threadIdx.x; i < it.end; i += kThreads) {
-    C u;
-    if (pro.mode == GP_PERM) {
-      u = pro.y[perm[i]];
-    } else if (pro.mode == GP_SORTED) {
-      u = pro.y[i];
-    } else {  // GP_BALL
-      const C v = pro.z[i], yv = pro.ys[i];
-      const T nu = T(pro.nu);
-      const T cx = nu * yv.x, cy = nu * yv.y;
-      const T rx = fma(v.x - cx, scale, cx), ry = fma(v.y - cy, scale, cy);
-      pro.z[i] = cmk<C>(v.x - rx, v.y - ry);
-      u = cmk<C>(T(2) * rx - v.x, T(2) * ry - v.y);
+  if (MODE == TM_GRID && gpro.mode == GP_BALL) scale = T(gpro.scalars[gpro.scale_idx]);
+  // this warp's contiguous slice of the work item
+  const int cnt = it.end - it.begin;
+  const int per = (cnt + kWarps - 1) / kWarps;
+  const int w0 = it.begin + min(cnt, warp * per), w1 = it.begin + min(cnt, (warp + 1) * per);
+  const int ta = lane >> 2, tb = (lane & 3) * 2;
+  int cell_cur = -1;
+  C g0 = cz<C>(), g1 = cz<C>();   // footprint grid values of the current cell (gather)
+  C s0 = cz<C>(), s1 = cz<C>();   // footprint scatter sums of the current cell
+  double p0 = 0.0, p1 = 0.0;
+  for (int base = w0; base < w1; base += 32) {
+    const int i = base + lane;
+    const bool valid = i < w1;
+    T wu[kJ], wv[kJ];
+    int cu = 0, cv = 0;
+    C u = cz<C>();
+    if (valid) {
+      T fu, fv;
+      decode(pos[i], cu, fu, cv, fv);
+      kb_eval(kb, fu, wu);
+      kb_eval(kb, fv, wv);
+      if (MODE == TM_GRID) {
+        if (gpro.mode == GP_PERM) {
+          u = gpro.y[perm[i]];
+        } else if (gpro.mode == GP_SORTED) {
+          u = gpro.y[i];
+        } else {  // GP_BALL
+          const C v = gpro.z[i], yv = gpro.ys[i];
+          const T nu = T(gpro.nu);
+          const T cx = nu * yv.x, cy = nu * yv.y;
+          const T rx = fma(v.x - cx, scale, cx), ry = fma(v.y - cy, scale, cy);
+          gpro.z[i] = cmk<C>(v.x - rx, v.y - ry);
+          u = cmk<C>(T(2) * rx - v.x, T(2) * ry - v.y);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < kJ; ++a) wu[a] = wv[a] = T(0);
     }
-    int cu, cv;
-    T fu, fv;
-    decode(pos[i], cu, fu, cv, fv);
-    T wu[kJ], wv[kJ];
-    kb_eval(kb, fu, wu);
-    kb_eval(kb, fv, wv);
-    scatter_taps<T>(acc, PW, cu, cv, wu, wv, u.x, u.y);
-  }
-  __syncthreads();
-  flush_patch(acc, Q, tu, tv, g.TB, PW, g.KP);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_gram(Geometry g, const __grid_constant__ CUtensorMap map,
-                                                   const WorkItem* __restrict__ items,
-                                                   const Pos<T>* __restrict__ pos, KbPoly<T> kb,
-                                                   typename cplx_t<T>::type* __restrict__ Q, int* err) {
-  typedef typename cplx_t<T>::type C;
-  extern __shared__ __align__(128) unsigned char sm_raw[];
-  __shared__ __align__(8) uint64_t bar;
-  const WorkItem it = items[blockIdx.x];
-  const int tu = it.tile / g.ntile1d, tv = it.tile - tu * g.ntile1d;
-  const int PW = g.TB + kJ;
-  C* patch = reinterpret_cast<C*>(sm_raw);
-  C* acc = patch + PW * PW;
-  for (int e = threadIdx.x; e < PW * PW; e += kThreads) acc[e] = cz<C>();
-  if (!stage_patch(patch, &bar, &map, tu, tv, g.TB, PW, err)) return;
-  for (int i = it.begin + threadIdx.x; i < it.end; i += kThreads) {
-    int cu, cv;
-    T fu, fv;
-    decode(pos[i], cu, fu, cv, fv);
-    T wu[kJ], wv[kJ];
-    kb_eval(kb, fu, wu);
-    kb_eval(kb, fv, wv);
-    T ax = 0, ay = 0;
+    T* st = wst + lane * kStage;
 #pragma unroll
     for (int a = 0; a < kJ; ++a) {
-      const C* row = patch + (cu + a) * PW + cv;
-      T hx = 0, hy = 0;
-#pragma unroll
-      for (int b = 0; b < kJ; ++b) {
-        const C gv = row[b];
-        hx = fma(wv[b], gv.x, hx);
-        hy = fma(wv[b], gv.y, hy);
-      }
-      ax = fma(wu[a], hx, ax);
-      ay = fma(wu[a], hy, ay);
+      st[a] = wu[a];
+      st[kJ + a] = wv[a];
     }
-    scatter_taps<T>(acc, PW, cu, cv, wu, wv, ax, ay);
+    st[2 * kJ] = u.x;
+    st[2 * kJ + 1] = u.y;
+    st[2 * kJ + 2] = T(cu * 256 + cv);
+    __syncwarp();
+    const int nv = min(32, w1 - base);
+    C mine = cz<C>();  // gathered value of this lane's own visibility
+    for (int j = 0; j < nv; ++j) {
+      const T* sj = wst + j * kStage;
+      const int cell = int(sj[2 * kJ + 2]);
+      if (cell != cell_cur) {  // warp-uniform
+        const int ro = ((cell >> 8) + ta) * PW + (cell & 255) + tb;
+        if (kScatter && cell_cur >= 0) {
+          C* row = wacc + ((cell_cur >> 8) + ta) * PA + (cell_cur & 255) + tb;
+          row[0] = cadd(row[0], s0);
+          row[1] = cadd(row[1], s1);
+          s0 = s1 = cz<C>();
+        }
+        if (kGather) {
+          g0 = patch[ro];
+          g1 = patch[ro + 1];
+        }
+        cell_cur = cell;
+      }
+      const T wa = sj[ta];
+      const T wb0 = wa * sj[kJ + tb], wb1 = wa * sj[kJ + tb + 1];
+      C uj;
+      if (kGather) {
+        C part = cmk<C>(fma(wb0, g0.x, wb1 * g1.x), fma(wb0, g0.y, wb1 * g1.y));
+        uj = warp_allsum(part);
+        if (lane == j) mine = uj;
+      } else {
+        uj = cmk<C>(sj[2 * kJ], sj[2 * kJ + 1]);
+      }
+      if (kScatter) {
+        s0.x = fma(wb0, uj.x, s0.x);
+        s0.y = fma(wb0, uj.y, s0.y);
+        s1.x = fma(wb1, uj.x, s1.x);
+        s1.y = fma(wb1, uj.y, s1.y);
+      }
+    }
+    __syncwarp();
+    if (MODE == TM_DEGRID && valid) {
+      if (dep.mode == DG_STORE_PERM) {
+        dep.y[perm[i]] = mine;
+      } else if (dep.mode == DG_STORE_SORTED) {
+        dep.y[i] = mine;
+      } else {  // DG_BALL
+        const C z = dep.z[i], yv = dep.ys[i];
+        const T nu = T(dep.nu);
+        const C v = cmk<C>(fma(nu, mine.x, z.x), fma(nu, mine.y, z.y));
+        dep.z[i] = v;
+        const double dx = double(v.x) - dep.nu * double(yv.x), dy = double(v.y) - dep.nu * double(yv.y);
+        p0 += dx * dx + dy * dy;
+        const double ex = double(mine.x) - double(yv.x), ey = double(mine.y) - double(yv.y);
+        p1 += ex * ex + ey * ey;
+      }
+    }
+  }
+  if (MODE == TM_DEGRID) {
+    if (dep.mode == DG_BALL) {
+      const double r0 = block_sum<kThreads>(p0, red);
+      const double r1 = block_sum<kThreads>(p1, red);
+      if (threadIdx.x == 0) {
+        dep.part0[blockIdx.x] = r0;
+        dep.part1[blockIdx.x] = r1;
+      }
+    }
+    return;
+  }
+  if (cell_cur >= 0) {
+    C* row = wacc + ((cell_cur >> 8) + ta) * PA + (cell_cur & 255) + tb;
+    row[0] = cadd(row[0], s0);
+    row[1] = cadd(row[1], s1);
   }
   __syncthreads();
-  flush_patch(acc, Q, tu, tv, g.TB, PW, g.KP);
+  // merge the warps' accumulators and flush the patch (one vector atomic per non-zero cell)
+  for (int e = threadIdx.x; e < PW * PW; e += kThreads) {
+    const int r = e / PW, c = e - r * PW;
+    C v = cz<C>();
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) v = cadd(v, acc[w * PW * PA + r * PA + c]);
+    if (v.x != 0 || v.y != 0) atomic_add_global(Q + size_t(tu * g.TB + r) * g.KP + (tv * g.TB + c), v);
+  }
 }
 
 // ----------------------------------------------------------------- binning
-// Grid coordinate of a uv sample on the K-periodic grid, in [0, K).
-PD double grid_coord(double u, int K) {
-  double t = u * (double(K) / (2.0 * 3.14159265358979323846));
-  t -= double(K) * floor(t / double(K));
-  if (t >= double(K)) t -= double(K);
-  if (t < 0.0) t = 0.0;
-  return t;
+// Grid cell and fractional offset of a uv sample: t = u K / (2 pi), cell =
+// floor(t) taken modulo K, f = t - floor(t) in [0, 1).  The expression order
+// matches the plain definition so that samples lying exactly on grid nodes
+// fall in the same cell.
+PD void grid_cell(double u, int K, int& cell, double& f) {
+  const double t = (u * double(K)) / (2.0 * 3.14159265358979323846);
+  const double fl = floor(t);
+  f = t - fl;
+  long long c = (long long)fl % K;
+  if (c < 0) c += K;
+  cell = int(c);
 }
 
-__global__ void k_bin_keys(const double* __restrict__ uv, int64_t M, int K, int TB, int ntile1d,
+// Sort key: tile id, then the cell inside the tile (row-major), so that a
+// tile's visibilities come grouped by grid cell.
+__global__ void k_bin_keys(const double* __restrict__ uv, int64_t M, int K, int TB, int lb, int ntile1d,
                            uint32_t* __restrict__ keys, int* __restrict__ vals) {
   const int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (m >= M) return;
-  const double tu = grid_coord(uv[2 * m], K), tv = grid_coord(uv[2 * m + 1], K);
-  const int cu = min(int(tu), K - 1), cv = min(int(tv), K - 1);
-  keys[m] = uint32_t((cu / TB) * ntile1d + (cv / TB));
+  int cu, cv;
+  double fu, fv;
+  grid_cell(uv[2 * m], K, cu, fu);
+  grid_cell(uv[2 * m + 1], K, cv, fv);
+  const uint32_t tile = uint32_t((cu / TB) * ntile1d + (cv / TB));
+  keys[m] = (tile << (2 * lb)) | (uint32_t(cu % TB) << lb) | uint32_t(cv % TB);
   vals[m] = int(m);
 }
 
@@ -356,13 +406,13 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
   }
 }
 
-__global__ void k_tile_bounds(const uint32_t* __restrict__ keys, int64_t M, int* __restrict__ start,
+__global__ void k_tile_bounds(const uint32_t* __restrict__ keys, int64_t M, int shift, int* __restrict__ start,
                               int* __restrict__ end) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= M) return;
-  const uint32_t k = keys[i];
-  if (i == 0 || keys[i - 1] != k) start[k] = int(i);
-  if (i == M - 1 || keys[i + 1] != k) end[k] = int(i + 1);
+  const uint32_t k = keys[i] >> shift;
+  if (i == 0 || (keys[i - 1] >> shift) != k) start[k] = int(i);
+  if (i == M - 1 || (keys[i + 1] >> shift) != k) end[k] = int(i + 1);
 }
 
 __global__ void k_chunk_counts(const int* __restrict__ start, const int* __restrict__ end, int ntiles, int chunk,
@@ -398,11 +448,11 @@ __global__ void k_encode<float>(const double* __restrict__ uv, const int* __rest
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= M) return;
   const int64_t m = perm[i];
-  const double t[2] = {grid_coord(uv[2 * m], K), grid_coord(uv[2 * m + 1], K)};
   uint32_t e[2];
   for (int a = 0; a < 2; ++a) {
-    const int cell = min(int(t[a]), K - 1);
-    double f = t[a] - double(cell);
+    int cell;
+    double f;
+    grid_cell(uv[2 * m + a], K, cell, f);
     uint32_t q = uint32_t(f * 16777216.0);
     if (q > 0xFFFFFFu) q = 0xFFFFFFu;
     e[a] = (uint32_t(cell % TB) << 24) | q;
@@ -418,38 +468,51 @@ __global__ void k_encode<double>(const double* __restrict__ uv, const int* __res
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= M) return;
   const int64_t m = perm[i];
-  const double tu = grid_coord(uv[2 * m], K), tv = grid_coord(uv[2 * m + 1], K);
-  const int cu = min(int(tu), K - 1), cv = min(int(tv), K - 1);
+  int cu, cv;
+  double fu, fv;
+  grid_cell(uv[2 * m], K, cu, fu);
+  grid_cell(uv[2 * m + 1], K, cv, fv);
   Pos<double> p;
-  p.u = tu - double((cu / TB) * TB);
-  p.v = tv - double((cv / TB) * TB);
+  // cell + f may round up to the next integer when f is within an ulp of 1:
+  // keep the sum inside the cell
+  p.u = fmin(double(cu % TB) + fu, nextafter(double(cu % TB + 1), 0.0));
+  p.v = fmin(double(cv % TB) + fv, nextafter(double(cv % TB + 1), 0.0));
   pos[i] = p;
-}
-
-template <typename T> inline size_t patch_bytes(const Geometry& g) {
-  const size_t PW = size_t(g.TB + kJ);
-  return PW * PW * sizeof(typename cplx_t<T>::type);
 }
 
 }  // namespace
 
 template <typename T> cudaError_t configure_nufft() {
-  const int mx = 227 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_degrid<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_grid<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = raise_smem_limit(k_tile<T, TM_DEGRID>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_tile<T, TM_GRID>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_tile<T, TM_GRAM>);
   return e;
 }
 template cudaError_t configure_nufft<float>();
 template cudaError_t configure_nufft<double>();
+
+size_t tile_smem_bytes(int precision_bytes, int TB, int mode) {
+  if (precision_bytes == 4) {
+    size_t b = tile_stage_bytes<float>();
+    if (mode != TM_GRID) b += tile_patch_bytes<float>(TB);
+    if (mode != TM_DEGRID) b += tile_acc_bytes<float>(TB);
+    return b;
+  }
+  size_t b = tile_stage_bytes<double>();
+  if (mode != TM_GRID) b += tile_patch_bytes<double>(TB);
+  if (mode != TM_DEGRID) b += tile_acc_bytes<double>(TB);
+  return b;
+}
 
 template <typename T>
 void launch_degrid(const Geometry& g, const CUtensorMap& map, const WorkItem* items, int n_items, const Pos<T>* pos,
                    const int* perm, const KbPoly<T>& kb, const DegridEp<typename cplx_t<T>::type>& ep, int* err,
                    cudaStream_t s) {
   if (n_items <= 0) return;
-  const size_t sm = patch_bytes<T>(g);
-  k_degrid<T><<<n_items, kThreads, sm, s>>>(g, map, items, pos, perm, kb, ep, err);
+  const size_t sm = tile_smem_bytes(sizeof(T), g.TB, TM_DEGRID);
+  GridPro<typename cplx_t<T>::type> gp{};
+  k_tile<T, TM_DEGRID><<<n_items, kThreads, sm, s>>>(g, map, items, pos, perm, kb, ep, gp, nullptr, err);
 }
 
 template <typename T>
@@ -457,24 +520,31 @@ void launch_grid(const Geometry& g, const WorkItem* items, int n_items, const Po
                  const KbPoly<T>& kb, const GridPro<typename cplx_t<T>::type>& pro, typename cplx_t<T>::type* Q,
                  cudaStream_t s) {
   if (n_items <= 0) return;
-  const size_t sm = patch_bytes<T>(g);
-  k_grid<T><<<n_items, kThreads, sm, s>>>(g, items, pos, perm, kb, pro, Q);
+  const size_t sm = tile_smem_bytes(sizeof(T), g.TB, TM_GRID);
+  DegridEp<typename cplx_t<T>::type> ep{};
+  CUtensorMap dummy;
+  memset(&dummy, 0, sizeof(dummy));
+  k_tile<T, TM_GRID><<<n_items, kThreads, sm, s>>>(g, dummy, items, pos, perm, kb, ep, pro, Q, nullptr);
 }
 
 template <typename T>
 void launch_gram(const Geometry& g, const CUtensorMap& map, const WorkItem* items, int n_items, const Pos<T>* pos,
                  const KbPoly<T>& kb, typename cplx_t<T>::type* Q, int* err, cudaStream_t s) {
   if (n_items <= 0) return;
-  const size_t sm = 2 * patch_bytes<T>(g);
-  k_gram<T><<<n_items, kThreads, sm, s>>>(g, map, items, pos, kb, Q, err);
+  const size_t sm = tile_smem_bytes(sizeof(T), g.TB, TM_GRAM);
+  DegridEp<typename cplx_t<T>::type> ep{};
+  GridPro<typename cplx_t<T>::type> gp{};
+  k_tile<T, TM_GRAM><<<n_items, kThreads, sm, s>>>(g, map, items, pos, nullptr, kb, ep, gp, Q, err);
 }
 
 template <typename T>
 int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>* pos, int* perm,
                WorkItem** items_out, int* n_items_out, cudaStream_t s) {
   const int ntiles = g.ntile1d * g.ntile1d;
-  int bits = 0;
-  while ((1 << bits) < ntiles) ++bits;
+  int lb = 0;
+  while ((1 << lb) < g.TB) ++lb;
+  int bits = 2 * lb;
+  while ((1 << (bits - 2 * lb)) < ntiles) ++bits;
   const int passes = (bits + 7) / 8;
   const int nblocks = int((M + kSortTile - 1) / kSortTile);
   uint32_t *k0 = nullptr, *k1 = nullptr;
@@ -495,7 +565,7 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
   fail(cudaMalloc(&total, sizeof(int)));
   if (rc == 0) {
     const int tb = 256;
-    k_bin_keys<<<int((M + tb - 1) / tb), tb, 0, s>>>(uv, M, g.K, g.TB, g.ntile1d, k0, perm);
+    k_bin_keys<<<int((M + tb - 1) / tb), tb, 0, s>>>(uv, M, g.K, g.TB, lb, g.ntile1d, k0, perm);
     uint32_t* kin = k0;
     uint32_t* kout = k1;
     int* vin = perm;
@@ -510,7 +580,7 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
     if (vin != perm) fail(cudaMemcpyAsync(perm, vin, M * sizeof(int), cudaMemcpyDeviceToDevice, s));
     fail(cudaMemsetAsync(tstart, 0, size_t(ntiles) * sizeof(int), s));
     fail(cudaMemsetAsync(tend, 0, size_t(ntiles) * sizeof(int), s));
-    k_tile_bounds<<<int((M + tb - 1) / tb), tb, 0, s>>>(kin, M, tstart, tend);
+    k_tile_bounds<<<int((M + tb - 1) / tb), tb, 0, s>>>(kin, M, 2 * lb, tstart, tend);
     k_chunk_counts<<<(ntiles + tb - 1) / tb, tb, 0, s>>>(tstart, tend, ntiles, chunk, cnt);
     k_scan<<<1, 1024, 0, s>>>(cnt, ntiles, total);
     fail(cudaMemcpyAsync(&h_total, total, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -373,10 +373,10 @@ void run_synthesis(const SaraPlan<T>& P, const T* c, T* x, int pos_block, const 
 }  // namespace
 
 template <typename T> cudaError_t configure_sara() {
-  const int mx = 227 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_ana_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_syn_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_syn_final<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = raise_smem_limit(k_ana_level<T>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_syn_level<T>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_syn_final<T>);
   return e;
 }
 template cudaError_t configure_sara<float>();

@@ -48,7 +48,9 @@ def test_edge_coverages(prec):
     uv = np.array([[-math.pi, -math.pi], [0.0, 0.0], [math.pi - 1e-13, math.pi - 1e-13],
                    [3 * cell, -5 * cell], [0.5 * cell, 0.25 * cell], [-math.pi, 0.3],
                    [7.0, -9.0]])  # last point outside [-pi, pi): wrapped
-    ref = NUFFT(np.mod(uv + math.pi, 2 * math.pi) - math.pi, n)
+    wrapped = uv.copy()
+    wrapped[-1] = np.mod(uv[-1] + math.pi, 2 * math.pi) - math.pi  # only the out-of-range point
+    ref = NUFFT(wrapped, n)
     op = make_op(uv, n, 1, prec)
     x = synth.random_image(n, 3)
     assert rel(host(op.phi(to_dev(x, prec))), ref.phi(x)) < TOL[prec]
