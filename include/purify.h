@@ -111,6 +111,26 @@ int purify_sara_fwd(purify_op* op, const void* x, void* c, void* stream);
 /* purify_sara_adj -- x = Psi c, the adjoint (and left inverse) of purify_sara_fwd. */
 int purify_sara_adj(purify_op* op, const void* c, void* x, void* stream);
 
+/*
+ * purify_sara_fwd_static -- the same c = Psi^H x as purify_sara_fwd (FP32),
+ * for callers that cannot allocate device memory: no operator is needed and
+ * the call makes no cudaMalloc, cudaFree or other allocating call.  (The
+ * paper has no counterpart; this serves pipelines that reserve all device
+ * memory up front and must not allocate while streaming, or hosts that hand
+ * the library pre-sized buffers only.)
+ *   x  device, float[n][n];  c  device, float[9][n][n] (as purify_sara_fwd).
+ *   n  a power of two, 16 <= n <= 512; n / 2^levels >= 2.  Larger n returns
+ *      PURIFY_ERR_INVALID (purify_last_error names the limit).
+ * The multi-level scratch lives in one fixed 4 MiB device array per device,
+ * held until the process exits.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) with the device current;
+ * make that first call before any stream capture.  Every call shares the
+ * array, which keeps the last call's contents (each call overwrites what it
+ * reads, so nothing needs clearing): calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.
+ */
+int purify_sara_fwd_static(const float* x, float* c, int n, int levels, void* stream);
+
 /* Solver parameters (Algorithm 1 and the SARA loop). */
 typedef struct {
   double eps;         /* l2 bound on the noise, Eq. 2-3 (> 0) */

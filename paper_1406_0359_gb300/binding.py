@@ -51,7 +51,7 @@ class purify_stats(ctypes.Structure):
 EXPORTS = ["purify_op_create", "purify_op_destroy", "purify_op_info", "purify_phi", "purify_phi_adj",
            "purify_sara_fwd", "purify_sara_adj", "purify_sdmm_solve", "purify_default_params",
            "purify_strerror", "purify_profile", "purify_profile_read", "purify_kernel_name",
-           "purify_last_error"]
+           "purify_last_error", "purify_sara_fwd_static"]
 KERNEL_KINDS = ["row_fwd", "col_fwd", "degrid", "grid", "gram", "col_inv", "row_inv", "sara_analysis",
                 "sara_synthesis", "vector", "memset"]
 
@@ -83,6 +83,7 @@ def lib() -> ctypes.CDLL:
     L.purify_profile_read.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
     L.purify_kernel_name.argtypes = [ci]
     L.purify_kernel_name.restype = ctypes.c_char_p
+    L.purify_sara_fwd_static.argtypes = [vp, vp, ci, ci, vp]
     L.purify_last_error.argtypes = []
     L.purify_last_error.restype = ctypes.c_char_p
     for f in EXPORTS:
@@ -149,6 +150,12 @@ def purify_sara_fwd(h, x_ptr, c_ptr, stream=None) -> None:
 
 def purify_sara_adj(h, c_ptr, x_ptr, stream=None) -> None:
     _check(lib().purify_sara_adj(h, c_ptr, x_ptr, _stream(stream)), "purify_sara_adj")
+
+
+def purify_sara_fwd_static(x_ptr, c_ptr, n: int, levels: int, stream=None) -> None:
+    """Psi^H x without an operator and without device allocation (FP32,
+    n <= 512; see include/purify.h)."""
+    _check(lib().purify_sara_fwd_static(x_ptr, c_ptr, n, levels, _stream(stream)), "purify_sara_fwd_static")
 
 
 def purify_default_params() -> purify_params:

@@ -89,6 +89,10 @@ struct purify_op {
   } while (0)
 
 namespace purify {
+
+thread_local char g_last_error[256] = "";
+void set_last_error(const char* msg) { std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
 namespace {
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -108,10 +112,10 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-thread_local char g_last_error[256] = "";
-
 void note_error(const char* what, int line, const char* detail) {
-  std::snprintf(g_last_error, sizeof(g_last_error), "%s (api.cu:%d): %s", what, line, detail);
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), "%s (api.cu:%d): %s", what, line, detail);
+  set_last_error(buf);
 }
 
 int map_err(cudaError_t e, int line = 0) {

@@ -115,6 +115,9 @@ template <typename C> struct GridPro {
   int scale_idx;
 };
 
+// Record the detail returned by purify_last_error() on this thread.
+void set_last_error(const char* msg);
+
 // ----------------------------------------------------------------- launchers
 // Raise the dynamic shared-memory limit of every kernel (once per operator,
 // outside any stream capture).

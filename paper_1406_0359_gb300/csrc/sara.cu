@@ -16,6 +16,12 @@
 // gamma w), updates z_1 and emits 2 r_1 - v_1 for the synthesis, plus FP64
 // partial sums of the objective ||W Psi^H x_hat||_1; the final synthesis
 // epilogue applies the positivity block and writes x_1 + x_2.
+#include <cstdio>
+#include <mutex>
+#include <vector>
+
+#include "../../include/purify.h"
+#include "host_math.h"
 #include "internal.h"
 
 namespace purify {
@@ -427,4 +433,98 @@ INST(float)
 INST(double)
 #undef INST
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free SARA analysis.
+//
+// Some callers cannot call cudaMalloc once they are running: pipelines that
+// reserve all device memory at start-up and must not allocate while they
+// stream (an allocation can stall or fail when memory is fragmented or held
+// by another framework's caching allocator), and hosts that hand this library
+// only pre-sized buffers.  For them the scratch bands of the multi-level
+// analysis live in one fixed file-scope device array instead of operator
+// memory.  The array exists once per device that loads the library and
+// stays allocated until the process exits.
+constexpr int kStaticMaxN = 512;  // largest image side served from the fixed scratch
+constexpr size_t kStaticBand = size_t(kMaxDb) * (kStaticMaxN / 2) * (kStaticMaxN / 2);
+static __device__ __align__(256) float g_static_scratch[2 * kStaticBand];  // 4 MiB
+
+namespace {
+std::mutex g_static_mu;
+float* g_static_ptr[128] = {nullptr};
+DbFilters<float> g_static_filters;
+bool g_static_filters_ready = false;
+
+// Device address of the fixed scratch for the current device (host code may
+// not use the symbol itself as a device address).
+int static_scratch(float** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 128) {
+    set_last_error("purify_sara_fwd_static: cannot query the current device");
+    return PURIFY_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+      char buf[160];
+      std::snprintf(buf, sizeof(buf), "purify_sara_fwd_static: cudaGetSymbolAddress failed: %s",
+                    cudaGetErrorName(e));
+      set_last_error(buf);
+      return PURIFY_ERR_CUDA;
+    }
+    g_static_ptr[dev] = static_cast<float*>(p);
+  }
+  if (!g_static_filters_ready) {
+    for (int k = 1; k <= kMaxDb; ++k) {
+      const std::vector<double> h = daubechies_lowpass(k);
+      const int F = 2 * k;
+      for (int m = 0; m < kMaxTaps; ++m) {
+        g_static_filters.h[k - 1][m] = m < F ? float(h[m]) : 0.0f;
+        g_static_filters.g[k - 1][m] = m < F ? float(((m & 1) ? -1.0 : 1.0) * h[F - 1 - m]) : 0.0f;
+      }
+    }
+    g_static_filters_ready = true;
+  }
+  *out = g_static_ptr[dev];
+  return PURIFY_OK;
+}
+}  // namespace
+
 }  // namespace purify
+
+extern "C" int purify_sara_fwd_static(const float* x, float* c, int n, int levels, void* stream) {
+  using namespace purify;
+  if (!x || !c || n < 16 || (n & (n - 1)) || levels < 1 || (n >> levels) < 2) {
+    set_last_error("purify_sara_fwd_static: need non-null x and c, n a power of two >= 16, n / 2^levels >= 2");
+    return PURIFY_ERR_INVALID;
+  }
+  if (n > kStaticMaxN) {
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "purify_sara_fwd_static: n = %d exceeds the fixed-scratch limit n <= %d", n,
+                  kStaticMaxN);
+    set_last_error(buf);
+    return PURIFY_ERR_INVALID;
+  }
+  float* scratch = nullptr;
+  const int rc = static_scratch(&scratch);
+  if (rc) return rc;
+  SaraPlan<float> P{};
+  P.n = n;
+  P.levels = levels;
+  P.s0 = scratch;
+  P.s1 = scratch + kStaticBand;
+  P.cs = nullptr;
+  P.f = g_static_filters;
+  sara_analysis<float>(P, x, c, static_cast<cudaStream_t>(stream));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "purify_sara_fwd_static: launch failed: %s", cudaGetErrorName(e));
+    set_last_error(buf);
+    return PURIFY_ERR_CUDA;
+  }
+  return PURIFY_OK;
+}
