@@ -29,6 +29,9 @@ if ROOT not in sys.path:
 METRIC = "SDMM iters/s & Phi+Phi^H vis/s at 1024^2,M=4M vs plain GPU; solves/s, p99 latency"
 UNIT = "iters/s"
 WORKLOAD = "large_1024"
+# DRAM bytes (read + write) per launch from the committed ncu capture of each
+# kernel at this workload (profiles/); kernels changed since have no entry.
+MEASURED_TRAFFIC = {"gram": 88.370688e6 + 3.189504e6}
 
 
 # ----------------------------------------------------------------- helpers
@@ -266,7 +269,8 @@ def run_ours(args, ws, rank, local):
         "phi_phiH_vis_per_s": round(vis_per_s, 1),
         "plain_fp64_gpu_iters_per_s": None if plain is None else round(plain, 3),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
-                     "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                     "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                     "traffic": MEASURED_TRAFFIC.get(dom) if args.workload == WORKLOAD else None,
                      "peak_source": peak_kind, "bytes_per_launch": bytes_launch,
                      "ms_per_launch": round(dom_ms / dom_n, 4)},
         "kernels": per_kernel,
