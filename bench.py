@@ -121,6 +121,7 @@ def algorithmic_bytes(kind: str, n: int, M: int, rsize: int = 4) -> float:
         "col_fwd": 2 * N * c + 4 * N * c,         # compact rows in, full grid out
         "col_inv": 4 * N * c + 2 * N * c,
         "row_inv": 2 * N * c + 2 * N * rsize,
+        "col_conv": 2 * N * c + 4 * N * rsize + 2 * N * c,  # compact rows in, PSF spectrum, compact rows out
     }
     return float(table.get(kind, 0))
 

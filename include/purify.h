@@ -131,6 +131,22 @@ int purify_sara_adj(purify_op* op, const void* c, void* x, void* stream);
  */
 int purify_sara_fwd_static(const float* x, float* c, int n, int levels, void* stream);
 
+/*
+ * purify_gram -- out = Re(Phi^H Phi x), the data term of the composite
+ * operator sum_i L_i^H L_i = Phi^H Phi + 2I that the SDMM global update
+ * inverts (Section 3).
+ *   mode 0: Phi then Phi^H through the NUFFT (degridding and gridding fused).
+ *   mode 1: the composite precomputed once, as Section 3 suggests: the PSF
+ *           k(d) = sum_m exp(i (u_m d1 + v_m d2)) over offsets d in [-n, n)^2
+ *           (from the NUFFT adjoint of unit visibilities on a 2n x 2n image)
+ *           applied as a circular convolution on the 2n grid; needs n <= 1024.
+ *           It equals the exact (NUDFT) normal operator up to the NUFFT error
+ *           of the PSF.  The first call builds and keeps the spectrum
+ *           (K^2 reals of operator memory; synchronises `stream`).
+ *   x, out  device, real[n][n].
+ */
+int purify_gram(purify_op* op, const void* x, void* out, int mode, void* stream);
+
 /* Solver parameters (Algorithm 1 and the SARA loop). */
 typedef struct {
   double eps;         /* l2 bound on the noise, Eq. 2-3 (> 0) */
@@ -146,6 +162,8 @@ typedef struct {
   int warm_start;     /* non-zero: each reweighted round starts from the previous solution */
   int power_iters;    /* power-iteration steps used when nu <= 0 (>= 1) */
   int use_graph;      /* non-zero: replay one SDMM iteration as a captured CUDA graph */
+  int gram;           /* CG operator Re(Phi^H Phi): 0 NUFFT (G^H G each application), 1 precomputed
+                         composite as a PSF convolution (Section 3), -1 the latter when n <= 1024 */
 } purify_params;
 
 /* Solver statistics, filled by purify_sdmm_solve. */
@@ -181,9 +199,9 @@ int purify_sdmm_solve(purify_op* op, const void* y, const purify_params* params,
  * returns, per kernel kind, the summed device time and launch count since
  * profiling was enabled.  Kinds: 0 row_fwd, 1 col_fwd, 2 degrid, 3 grid,
  * 4 gram, 5 col_inv, 6 row_inv, 7 sara_analysis, 8 sara_synthesis,
- * 9 vector (CG updates and scalar finalisation), 10 memset.
+ * 9 vector (CG updates and scalar finalisation), 10 memset, 11 col_conv.
  */
-enum { PURIFY_NUM_KERNEL_KINDS = 11 };
+enum { PURIFY_NUM_KERNEL_KINDS = 12 };
 int purify_profile(purify_op* op, int enable);
 int purify_profile_read(purify_op* op, int kind, double* total_ms, int64_t* launches);
 const char* purify_kernel_name(int kind);

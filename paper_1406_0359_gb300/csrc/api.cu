@@ -22,11 +22,12 @@ struct purify_op {
   virtual int sara_fwd(const void* x, void* c, cudaStream_t s) = 0;
   virtual int sara_adj(const void* c, void* x, cudaStream_t s) = 0;
   virtual int solve(const void* y, const purify_params* p, void* x, purify_stats* st, cudaStream_t s) = 0;
+  virtual int gram(const void* x, void* out, int mode, cudaStream_t s) = 0;
   virtual void info(int* n, int64_t* M, int* K, int* tile, int* n_items, int* precision, int64_t* bytes) const = 0;
 
   // ---- kernel timing (instrumentation)
   enum Kind { KK_ROW_FWD = 0, KK_COL_FWD, KK_DEGRID, KK_GRID, KK_GRAM, KK_COL_INV, KK_ROW_INV, KK_SARA_ANA,
-              KK_SARA_SYN, KK_VEC, KK_MEMSET, KK_COUNT };
+              KK_SARA_SYN, KK_VEC, KK_MEMSET, KK_COL_CONV, KK_COUNT };
   bool prof = false;
   struct Pending { int kind; cudaEvent_t a, b; };
   std::vector<Pending> pending;
@@ -156,6 +157,11 @@ template <typename T> class OpImpl : public purify_op {
   T *xh = nullptr, *xs = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr;
   T *z1 = nullptr, *z2 = nullptr, *w = nullptr;
   C *z3 = nullptr, *ys = nullptr;
+  // composite operator by convolution (Section 3: precompute Phi^H Phi)
+  double* uv_keep = nullptr;  // device copy of uv, for the PSF set-up
+  T* ones = nullptr;          // unit deapodisation for the convolution path
+  T* khat = nullptr;          // real PSF spectrum, launch_col_conv layout
+  bool toep = false;          // current normal-operator mode
   int64_t bytes = 0;
   std::vector<void*> allocs;
   cudaStream_t own = nullptr;  // solver stream (capturable, non-blocking)
@@ -229,6 +235,8 @@ template <typename T> class OpImpl : public purify_op {
     if ((rc = alloc(&deapod, n))) return rc;
     if ((rc = alloc(&tw, g.K))) return rc;
     if ((rc = alloc(&pos, M))) return rc;
+    if ((rc = alloc(&uv_keep, 2 * size_t(M)))) return rc;
+    CK(cudaMemcpyAsync(uv_keep, uv, 2 * size_t(M) * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if ((rc = alloc(&perm, M))) return rc;
     if ((rc = alloc(&gridA, size_t(n) * g.K))) return rc;
     if ((rc = alloc(&gridP, size_t(g.KP) * g.KP))) return rc;
@@ -325,6 +333,84 @@ template <typename T> class OpImpl : public purify_op {
     return np;
   }
 
+  // Set-up of the convolution form of Re(Phi^H Phi): the PSF
+  // k(d) = sum_m exp(i k_m . d) over offsets d in [-n, n)^2 is Re Phi^H of
+  // all-ones visibilities on a 2n x 2n image (same uv), and its spectrum on
+  // the 2n grid is stored once.  Needs 2n <= 2048.
+  int ensure_toeplitz(cudaStream_t s) {
+    if (khat) return PURIFY_OK;
+    if (2 * g.n > 2048) {
+      note_error("convolution normal operator", __LINE__, "needs n <= 1024");
+      return PURIFY_ERR_INVALID;
+    }
+    int rc;
+    T* ones_l = nullptr;
+    T* khat_l = nullptr;
+    if ((rc = alloc(&ones_l, g.n)) || (rc = alloc(&khat_l, size_t(g.K) * g.K))) return rc;
+    launch_fill<T>(ones_l, g.n, T(1), s);
+    {
+      OpImpl<T> big;
+      rc = big.create(uv_keep, g.M, 2 * g.n, 1, s);
+      if (rc) return rc;
+      C* y1 = nullptr;
+      T* psf = nullptr;
+      C* X = nullptr;
+      cudaError_t e = cudaMalloc(&y1, size_t(g.M) * sizeof(C));
+      if (e == cudaSuccess) e = cudaMalloc(&psf, size_t(g.K) * g.K * sizeof(T));
+      if (e == cudaSuccess) e = cudaMalloc(&X, size_t(g.K) * g.K * sizeof(C));
+      if (e == cudaSuccess) {
+        C one;
+        one.x = T(1);
+        one.y = T(0);
+        launch_fill<C>(y1, size_t(g.M), one, s);
+      }
+      if (e == cudaSuccess) rc = big.phi_adj(y1, psf, s);
+      if (e == cudaSuccess && rc == 0) {
+        build_psf_spectrum<T>(psf, g.n, khat_l, X, tw, s);
+        e = cudaStreamSynchronize(s);
+      }
+      cudaFree(y1);
+      cudaFree(psf);
+      cudaFree(X);
+      if (e != cudaSuccess) return map_err(e, __LINE__);
+      if (rc) return rc;
+    }
+    ones = ones_l;
+    khat = khat_l;
+    return PURIFY_OK;
+  }
+
+  // Front half of Re(Phi^H Phi) x: up to the compact rows in gridA, by the
+  // NUFFT (G^H G per application) or by the precomputed convolution.
+  void normal_front(const RowPro<T>& pro, cudaStream_t s) {
+    if (toep) {
+      PROF(KK_ROW_FWD, s, launch_row_fwd<T>(g, pro, ones, gridA, tw, s));
+      PROF(KK_COL_CONV, s, launch_col_conv<T>(g, gridA, khat, tw, s));
+    } else {
+      gram_front(pro, s);
+    }
+  }
+  int normal_back(const RowEp<T>& ep, cudaStream_t s) {
+    int np = 0;
+    PROF(KK_ROW_INV, s, np = launch_row_inv<T>(g, gridA, toep ? ones : deapod, ep, tw, s));
+    return np;
+  }
+
+  int gram(const void* x, void* out, int mode, cudaStream_t s) override {
+    if (mode != 0 && mode != 1) return PURIFY_ERR_INVALID;
+    if (mode == 1) {
+      const int rc = ensure_toeplitz(s);
+      if (rc) return rc;
+    }
+    toep = mode == 1;
+    normal_front(plain(static_cast<const T*>(x)), s);
+    RowEp<T> ep{};
+    ep.mode = EP_STORE;
+    ep.out = static_cast<T*>(out);
+    normal_back(ep, s);
+    return check(s, false);
+  }
+
   int check(cudaStream_t s, bool sync) {
     CK(cudaGetLastError());
     if (sync) {
@@ -403,12 +489,12 @@ template <typename T> class OpImpl : public purify_op {
         pro.scalars = sc;
         pro.idx = S_INVNORM;
       }
-      gram_front(pro, s);
+      normal_front(pro, s);
       RowEp<T> ep{};
       ep.mode = EP_POWER;
       ep.out = Ap;
       ep.partials = partials;
-      const int np = row_ep(ep, s);
+      const int np = normal_back(ep, s);
       fin(partials, np, nullptr, 0, FIN_NORM, 0.0, s);
     }
     int rc = check(s, true);
@@ -460,7 +546,7 @@ template <typename T> class OpImpl : public purify_op {
     const double nu2 = nu * nu;
     const size_t n2 = N();
     // step 5: x_hat = (Phi^H Phi + 2I)^-1 sum_i x_i by CG, warm-started at x_hat
-    gram_front(plain(xh), s);
+    normal_front(plain(xh), s);
     {
       RowEp<T> ep{};
       ep.mode = EP_CG_R0;
@@ -470,7 +556,7 @@ template <typename T> class OpImpl : public purify_op {
       ep.b = xs;
       ep.nu2 = nu2;
       ep.partials = partials;
-      const int np = row_ep(ep, s);
+      const int np = normal_back(ep, s);
       fin(partials, np, nullptr, 0, FIN_RR0, 0.0, s);
     }
     for (int it = 0; it < cg_iters; ++it) {
@@ -482,14 +568,14 @@ template <typename T> class OpImpl : public purify_op {
         pro.scalars = sc;
         pro.idx = S_BETA;
       }
-      gram_front(pro, s);
+      normal_front(pro, s);
       RowEp<T> ep{};
       ep.mode = EP_CG_AP;
       ep.out = Ap;
       ep.p = p;
       ep.nu2 = nu2;
       ep.partials = partials;
-      int np = row_ep(ep, s);
+      int np = normal_back(ep, s);
       fin(partials, np, nullptr, 0, FIN_ALPHA, 0.0, s);
       PROF(KK_VEC, s, np = launch_cg_xr<T>(xh, r, p, Ap, sc, n2, partials, s));
       fin(partials, np, nullptr, 0, FIN_BETA, 0.0, s);
@@ -559,6 +645,9 @@ template <typename T> class OpImpl : public purify_op {
     CK(cudaEventCreate(&e1));
     CK(cudaEventRecord(e0, s));
     const size_t n2 = N(), M = size_t(g.M);
+    const int gmode = P->gram < 0 ? (g.n <= 1024 ? 1 : 0) : P->gram;
+    if (gmode == 1 && (rc = ensure_toeplitz(s))) return rc;
+    toep = gmode == 1;
     launch_gather<C>(static_cast<const C*>(y), perm, M, ys, s);
     double nu = P->nu;
     if (!(nu > 0)) {
@@ -608,13 +697,13 @@ template <typename T> class OpImpl : public purify_op {
       cudaMemsetAsync(z3, 0, M * sizeof(C), s);
       if (round > 0 && P->warm_start) {
         // steps 1-3 with x_hat^(0) = previous solution: sum_i x_i = (Phi^H Phi + 2I) x_hat^(0)
-        gram_front(plain(xh), s);
+        normal_front(plain(xh), s);
         RowEp<T> ep{};
         ep.mode = EP_QX;
         ep.out = xs;
         ep.p = xh;
         ep.nu2 = nu * nu;
-        row_ep(ep, s);
+        normal_back(ep, s);
       } else {
         cudaMemsetAsync(xh, 0, n2 * sizeof(T), s);
         cudaMemsetAsync(xs, 0, n2 * sizeof(T), s);
@@ -736,6 +825,11 @@ int purify_sara_adj(purify_op* op, const void* c, void* x, void* stream) {
   return op->sara_adj(c, x, static_cast<cudaStream_t>(stream));
 }
 
+int purify_gram(purify_op* op, const void* x, void* out, int mode, void* stream) {
+  if (!op || !x || !out) return PURIFY_ERR_INVALID;
+  return op->gram(x, out, mode, static_cast<cudaStream_t>(stream));
+}
+
 int purify_profile(purify_op* op, int enable) {
   if (!op) return PURIFY_ERR_INVALID;
   op->prof_reset();
@@ -753,7 +847,7 @@ int purify_profile_read(purify_op* op, int kind, double* total_ms, int64_t* laun
 
 const char* purify_kernel_name(int kind) {
   static const char* names[] = {"row_fwd", "col_fwd", "degrid", "grid", "gram", "col_inv",
-                                "row_inv", "sara_analysis", "sara_synthesis", "vector", "memset"};
+                                "row_inv", "sara_analysis", "sara_synthesis", "vector", "memset", "col_conv"};
   if (kind < 0 || kind >= PURIFY_NUM_KERNEL_KINDS) return "unknown";
   return names[kind];
 }
@@ -774,6 +868,7 @@ void purify_default_params(purify_params* p) {
   p->warm_start = 1;
   p->power_iters = 30;
   p->use_graph = 1;
+  p->gram = -1;
 }
 
 int purify_sdmm_solve(purify_op* op, const void* y, const purify_params* params, void* x_out, purify_stats* stats,

@@ -357,6 +357,88 @@ __global__ void __launch_bounds__(kRowCta) k_row_inv(Geometry g, const typename 
   }
 }
 
+// Composite operator by convolution (Section 3: precompute Phi^H Phi).  One
+// CTA takes cw columns of the n compact rows (after the row FFT): forward
+// column FFT, multiply by the precomputed real spectrum of the PSF
+// (layout [column block][row][cw]), inverse column FFT, and keep the n rows
+// the crop retains -- the transform of the column never leaves the SM.
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN>::value <= 512 ? 2 : 1)
+    k_col_conv(Geometry g, typename cplx_t<T>::type* __restrict__ A, const T* __restrict__ khat,
+               const typename cplx_t<T>::type* __restrict__ tw, int cw) {
+  typedef typename cplx_t<T>::type C;
+  constexpr int TT = Plan<LOGN>::T;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int K = g.K, n = g.n, half = n / 2;
+  const int cc = threadIdx.x % cw, t = threadIdx.x / cw;
+  const int c = blockIdx.x * cw + cc;
+  C* s = reinterpret_cast<C*>(sm_raw) + cc * padded(K);
+  auto load = [&](int m) -> C {
+    const int q = t + m * TT;
+    const int i1 = (q + half) & (K - 1);
+    return i1 < n ? A[size_t(i1) * K + c] : cz<C>();
+  };
+  auto to_smem = [&](int q, C v) { s[sidx(q)] = v; };
+  fft_seq<LOGN>(t, s, tw, -1, load, to_smem);
+  __syncthreads();
+  C v[16];
+  const T* kc = khat + (size_t(blockIdx.x) * K) * cw + cc;
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int q = t + m * TT;
+    v[m] = cscale(s[sidx(q)], kc[size_t(q) * cw]);
+  }
+  __syncthreads();
+  auto store = [&](int q, C x) {
+    const int i1 = (q + half) & (K - 1);
+    if (i1 < n) A[size_t(i1) * K + c] = x;
+  };
+  run_stages<LOGN, 0>(v, t, 1, s, tw, +1, store);
+}
+
+// Plain in-place transforms of a K x K complex array (set-up of the PSF spectrum).
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(kRowCta) k_rows_plain(typename cplx_t<T>::type* __restrict__ X,
+                                                        const typename cplx_t<T>::type* __restrict__ tw, int nseq,
+                                                        int dir) {
+  typedef typename cplx_t<T>::type C;
+  constexpr int TT = Plan<LOGN>::T, K = Plan<LOGN>::N;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int seq = threadIdx.x / TT, t = threadIdx.x - seq * TT;
+  C* row = X + size_t(blockIdx.x * nseq + seq) * K;
+  C* s = reinterpret_cast<C*>(sm_raw) + seq * padded(K);
+  auto load = [&](int m) -> C { return row[t + m * TT]; };
+  C out[16];
+  int qs[16];
+  int cnt = 0;
+  auto store = [&](int q, C v) { out[cnt] = v; qs[cnt] = q; ++cnt; };
+  fft_seq<LOGN>(t, s, tw, dir, load, store);
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < 16; ++m) row[qs[m]] = out[m];
+}
+
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(ColThreads<T, LOGN>::value) k_cols_plain(typename cplx_t<T>::type* __restrict__ X,
+                                                                         const typename cplx_t<T>::type* __restrict__ tw,
+                                                                         int cw, int dir) {
+  typedef typename cplx_t<T>::type C;
+  constexpr int TT = Plan<LOGN>::T, K = Plan<LOGN>::N;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int cc = threadIdx.x % cw, t = threadIdx.x / cw;
+  const int c = blockIdx.x * cw + cc;
+  C* s = reinterpret_cast<C*>(sm_raw) + cc * padded(K);
+  auto load = [&](int m) -> C { return X[size_t(t + m * TT) * K + c]; };
+  C out[16];
+  int qs[16];
+  int cnt = 0;
+  auto store = [&](int q, C v) { out[cnt] = v; qs[cnt] = q; ++cnt; };
+  fft_seq<LOGN>(t, s, tw, dir, load, store);
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < 16; ++m) X[size_t(qs[m]) * K + c] = out[m];
+}
+
 }  // namespace
 
 int row_inv_blocks(const Geometry& g) { return g.n / row_nseq(g); }
@@ -378,6 +460,9 @@ template <typename T, int L> cudaError_t configure_one() {
   if (e == cudaSuccess) e = raise_smem_limit(k_row_inv<T, L>);
   if (e == cudaSuccess) e = raise_smem_limit(k_col_fwd<T, L>);
   if (e == cudaSuccess) e = raise_smem_limit(k_col_inv<T, L>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_col_conv<T, L>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_rows_plain<T, L>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_cols_plain<T, L>);
   return e;
 }
 
@@ -428,6 +513,61 @@ int launch_row_inv(const Geometry& g, const typename cplx_t<T>::type* A, const T
   return g.n / nseq;
 }
 
+template <typename T>
+__global__ void k_embed_psf(const T* __restrict__ psf, int n, typename cplx_t<T>::type* __restrict__ X) {
+  typedef typename cplx_t<T>::type C;
+  const int K = 2 * n;
+  const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= size_t(K) * K) return;
+  const int q1 = int(idx / K), q2 = int(idx % K);
+  // kernel offset d = q - K for q >= n; the PSF image holds offsets [-n, n)
+  const int i1 = (q1 + n) & (K - 1), i2 = (q2 + n) & (K - 1);
+  X[idx] = cmk<C>(psf[size_t(i1) * K + i2], T(0));
+}
+
+template <typename T>
+__global__ void k_spectrum_layout(const typename cplx_t<T>::type* __restrict__ X, int K, int cw, double scale,
+                                  T* __restrict__ khat) {
+  const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= size_t(K) * K) return;
+  const int q = int(idx / K), c = int(idx % K);
+  khat[(size_t(c / cw) * K + q) * cw + (c % cw)] = T(double(X[idx].x) * scale);
+}
+
+template <typename T>
+void build_psf_spectrum(const T* psf, int n, T* khat, typename cplx_t<T>::type* X, const typename cplx_t<T>::type* tw,
+                        cudaStream_t s) {
+  const int K = 2 * n;
+  const size_t tot = size_t(K) * K;
+  const int tb = 256;
+  k_embed_psf<T><<<int((tot + tb - 1) / tb), tb, 0, s>>>(psf, n, X);
+  launch_fft2_plain<T>(K, X, tw, -1, s);
+  k_spectrum_layout<T><<<int((tot + tb - 1) / tb), tb, 0, s>>>(X, K, col_width<T>(), 1.0 / (double(K) * K), khat);
+}
+
+template <typename T>
+void launch_col_conv(const Geometry& g, typename cplx_t<T>::type* A, const T* khat,
+                     const typename cplx_t<T>::type* tw, cudaStream_t s) {
+  typedef typename cplx_t<T>::type C;
+  const int cw = col_width<T>();
+  const size_t sm = cw * padded(g.K) * sizeof(C);
+  PURIFY_LOGN_SWITCH(g.K, (k_col_conv<T, L><<<g.K / cw, cw * Plan<L>::T, sm, s>>>(g, A, khat, tw, cw)));
+}
+
+template <typename T>
+void launch_fft2_plain(int K, typename cplx_t<T>::type* X, const typename cplx_t<T>::type* tw, int dir,
+                       cudaStream_t s) {
+  typedef typename cplx_t<T>::type C;
+  const int cw = col_width<T>();
+  int nseq = kRowCta / (K / 16);
+  if (nseq < 1) nseq = 1;
+  if (nseq > K) nseq = K;
+  const size_t smr = nseq * padded(K) * sizeof(C);
+  const size_t smc = cw * padded(K) * sizeof(C);
+  PURIFY_LOGN_SWITCH(K, (k_rows_plain<T, L><<<K / nseq, nseq * Plan<L>::T, smr, s>>>(X, tw, nseq, dir)));
+  PURIFY_LOGN_SWITCH(K, (k_cols_plain<T, L><<<K / cw, cw * Plan<L>::T, smc, s>>>(X, tw, cw, dir)));
+}
+
 #define INST(T)                                                                                              \
   template void launch_row_fwd<T>(const Geometry&, const RowPro<T>&, const T*, cplx_t<T>::type*,                \
                                   const cplx_t<T>::type*, cudaStream_t);                                        \
@@ -436,7 +576,11 @@ int launch_row_inv(const Geometry& g, const typename cplx_t<T>::type* A, const T
   template void launch_col_inv<T>(const Geometry&, const cplx_t<T>::type*, cplx_t<T>::type*,                   \
                                   const cplx_t<T>::type*, cudaStream_t);                                        \
   template int launch_row_inv<T>(const Geometry&, const cplx_t<T>::type*, const T*, const RowEp<T>&,            \
-                                 const cplx_t<T>::type*, cudaStream_t);
+                                 const cplx_t<T>::type*, cudaStream_t);                                        \
+  template void launch_col_conv<T>(const Geometry&, cplx_t<T>::type*, const T*, const cplx_t<T>::type*,         \
+                                   cudaStream_t);                                                              \
+  template void launch_fft2_plain<T>(int, cplx_t<T>::type*, const cplx_t<T>::type*, int, cudaStream_t);     \
+  template void build_psf_spectrum<T>(const T*, int, T*, cplx_t<T>::type*, const cplx_t<T>::type*, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -139,6 +139,22 @@ template <typename T>
 int launch_row_inv(const Geometry& g, const typename cplx_t<T>::type* A, const T* deapod, const RowEp<T>& ep,
                    const typename cplx_t<T>::type* tw, cudaStream_t s);
 int row_inv_blocks(const Geometry& g);
+// Composite operator Phi^H Phi as a convolution: forward column FFT of the
+// compact rows, multiply by the real PSF spectrum khat ([K/cw][K][cw]),
+// inverse column FFT, crop rows back into A (in place).
+template <typename T>
+void launch_col_conv(const Geometry& g, typename cplx_t<T>::type* A, const T* khat,
+                     const typename cplx_t<T>::type* tw, cudaStream_t s);
+// Real spectrum of the convolution kernel from the PSF image (2n x 2n real,
+// pixel offsets [-n, n)^2): circulant embedding on the K = 2n grid, forward
+// FFT, scaled by 1/K^2, stored in launch_col_conv's layout.  X: K x K scratch.
+template <typename T>
+void build_psf_spectrum(const T* psf, int n, T* khat, typename cplx_t<T>::type* X,
+                        const typename cplx_t<T>::type* tw, cudaStream_t s);
+// In-place 2D FFT of a K x K complex array (dir -1 forward, +1 inverse, unnormalised).
+template <typename T>
+void launch_fft2_plain(int K, typename cplx_t<T>::type* X, const typename cplx_t<T>::type* tw, int dir,
+                       cudaStream_t s);
 
 template <typename T>
 void launch_degrid(const Geometry& g, const CUtensorMap& map, const WorkItem* items, int n_items,

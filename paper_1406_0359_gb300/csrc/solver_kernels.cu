@@ -179,6 +179,8 @@ template <typename C> void launch_gather(const C* src, const int* perm, size_t M
 INST(float)
 INST(double)
 #undef INST
+template void launch_fill<float2>(float2*, size_t, float2, cudaStream_t);
+template void launch_fill<double2>(double2*, size_t, double2, cudaStream_t);
 template void launch_gather<float2>(const float2*, const int*, size_t, float2*, cudaStream_t);
 template void launch_gather<double2>(const double2*, const int*, size_t, double2*, cudaStream_t);
 

@@ -1,0 +1,61 @@
+"""The CG operator Re(Phi^H Phi) on the GPU (purify_gram), both forms, against
+the oracle's NUFFT and the exact NUDFT normal operator."""
+import numpy as np
+import pytest
+import torch
+
+from oracle.nudft import nudft_matrix
+from oracle.nufft import NUFFT
+from paper_1406_0359_gb300 import synth
+from tests._gpu import TOL, host, need_gpu, rel, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    need_gpu()
+
+
+def make_op(uv, n, prec):
+    from paper_1406_0359_gb300.binding import Operator
+
+    return Operator(torch.as_tensor(uv).cuda(), n, 2, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("n,M,seed", [(16, 700, 3), (32, 2500, 4)])
+def test_gram_forms_match_exact_normal_operator(prec, n, M, seed):
+    uv = synth.uv_coverage(M, n, seed)
+    A = nudft_matrix(uv, n)
+    x = synth.random_image(n, seed)
+    exact = np.real(A.conj().T @ (A @ x.reshape(-1))).reshape(n, n)
+    nufft = NUFFT(uv, n).gram_real(x)
+    op = make_op(uv, n, prec)
+    g0 = host(op.gram(to_dev(x, prec), mode=0))
+    g1 = host(op.gram(to_dev(x, prec), mode=1))
+    assert rel(g0, nufft) < TOL[prec]
+    # the convolution form is the exact normal operator up to the NUFFT error of the PSF
+    assert rel(g1, exact) < (1e-5 if prec == "fp32" else 1e-6)
+    assert rel(g1, nufft) < (1e-5 if prec == "fp32" else 1e-6)
+
+
+@pytest.mark.parametrize("n,M,seed", [(64, 4096, 1), (256, 131072, 2)])
+def test_gram_convolution_at_config_sizes(n, M, seed):
+    uv = synth.uv_coverage(M, n, seed)
+    x = synth.sky(n, seed, 3, 10)
+    ref = NUFFT(uv, n).gram_real(x)
+    op = make_op(uv, n, "fp32")
+    assert rel(host(op.gram(to_dev(x, "fp32"), mode=1)), ref) < 1e-5
+    assert rel(host(op.gram(to_dev(x, "fp32"), mode=0)), ref) < 1e-5
+
+
+def test_gram_convolution_symmetric_psd():
+    n, M = 64, 3000
+    uv = synth.uv_coverage(M, n, 8)
+    op = make_op(uv, n, "fp64")
+    a, b = synth.random_image(n, 1), synth.random_image(n, 2)
+    ga = host(op.gram(to_dev(a, "fp64"), mode=1))
+    gb = host(op.gram(to_dev(b, "fp64"), mode=1))
+    assert abs(np.sum(b * ga) - np.sum(a * gb)) < 1e-10 * abs(np.sum(a * ga))
+    assert np.sum(a * ga) > 0

@@ -39,27 +39,31 @@ def small():
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_auto_nu_and_gamma_match_oracle(small, prec):
     op = make_op(small, 3, prec)
-    res = op.solve(to_dev(small["y"], prec), small["eps"], t_max=1, cg_iters=1)
+    res = op.solve(to_dev(small["y"], prec), small["eps"], t_max=1, cg_iters=1, gram=0)
     tol = 1e-5 if prec == "fp32" else 1e-10
     assert res.stats["nu"] == pytest.approx(small["nu"], rel=tol)
     assert res.stats["gamma"] == pytest.approx(small["gamma"], rel=tol)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec,gram", [("fp32", 0), ("fp32", 1), ("fp64", 0), ("fp64", 1)])
 @pytest.mark.parametrize("use_graph", [True, False])
-def test_sara_solve_matches_oracle(small, prec, use_graph):
+def test_sara_solve_matches_oracle(small, prec, gram, use_graph):
+    """Fixed-count SARA solve.  With gram = 1 the CG operator is the exact
+    normal operator (PSF convolution) while the oracle applies the NUFFT's;
+    they differ by the NUFFT error (~1e-7), so FP64 is held to 1e-5 there."""
     T, cg_iters, n_rw = 30, 10, 1
     x_ref, rounds = osdmm.sara_solve(small["op"], small["psi"], small["y"], small["eps"], small["gamma"], T,
                                      cg_iters, small["nu"], n_rw)
     op = make_op(small, 3, prec)
     res = op.solve(to_dev(small["y"], prec), small["eps"], t_max=T, cg_iters=cg_iters, n_reweight=n_rw,
-                   gamma=small["gamma"], nu=small["nu"], use_graph=use_graph)
+                   gamma=small["gamma"], nu=small["nu"], use_graph=use_graph, gram=gram)
     xg = host(res.x)
-    assert rel(xg, x_ref) < IMG_TOL[prec]
+    tol = IMG_TOL[prec] if (gram == 0 or prec == "fp32") else 1e-5
+    assert rel(xg, x_ref) < tol
     assert res.stats["iterations"] == T * (n_rw + 1)
     last = rounds[-1].history[-1]
-    assert res.stats["objective"] == pytest.approx(last["objective"], rel=10 * IMG_TOL[prec])
-    assert res.stats["residual"] == pytest.approx(last["residual"], rel=10 * IMG_TOL[prec])
+    assert res.stats["objective"] == pytest.approx(last["objective"], rel=10 * tol)
+    assert res.stats["residual"] == pytest.approx(last["residual"], rel=10 * tol)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
@@ -98,7 +102,7 @@ def test_full_small_config_matches_oracle(prec):
     x_ref, _ = osdmm.sara_solve(P["op"], psi, P["y"], P["eps"], gamma, w.t_max, w.cg_iters, nu, w.n_reweight)
     op = make_op(P, w.levels, prec)
     res = op.solve(to_dev(P["y"], prec), P["eps"], t_max=w.t_max, cg_iters=w.cg_iters, n_reweight=w.n_reweight,
-                   gamma=gamma, nu=nu)
+                   gamma=gamma, nu=nu, gram=0 if prec == "fp64" else -1)
     xg = host(res.x)
     assert rel(xg, x_ref) < IMG_TOL[prec]
     assert abs(simulate.snr_db(P["x_true"], xg) - simulate.snr_db(P["x_true"], x_ref)) < 0.05
