@@ -150,6 +150,9 @@ template <typename T> class OpImpl : public purify_op {
   KbPoly<T> kb;
   SaraPlan<T> sara{};
   double* partials = nullptr;
+  double* cg_part = nullptr;        // CG partial sums (row pass, CG update)
+  unsigned int* tickets = nullptr;  // last-block tickets of the CG reductions
+  static constexpr int kCgPart = 4096;
   double* sc = nullptr;
   double* h_sc = nullptr;
   int* err = nullptr;
@@ -263,6 +266,9 @@ template <typename T> class OpImpl : public purify_op {
     bytes += int64_t(n_items) * sizeof(WorkItem);
     const int np = std::max({2 * n_items, row_inv_blocks(g), sara_partials_capacity(n, L), vec_blocks(9 * N()), 1});
     if ((rc = alloc(&partials, np))) return rc;
+    if ((rc = alloc(&cg_part, 2 * kCgPart))) return rc;
+    if ((rc = alloc(&tickets, 4))) return rc;
+    CK(cudaMemsetAsync(tickets, 0, 4 * sizeof(unsigned int), s));
     // TMA descriptor of the padded forward grid, 8-byte elements
     EncodeTiledFn enc = encode_fn();
     if (!enc) {
@@ -273,7 +279,7 @@ template <typename T> class OpImpl : public purify_op {
     const int PW = g.TB + kJ;
     cuuint64_t dims[2] = {cuuint64_t(g.KP) * cw, cuuint64_t(g.KP)};
     cuuint64_t strides[1] = {cuuint64_t(g.KP) * sizeof(C)};
-    cuuint32_t box[2] = {cuuint32_t(PW * cw), cuuint32_t(PW)};
+    cuuint32_t box[2] = {cuuint32_t((PW + 2) * cw), cuuint32_t(PW)};  // PW rows of PW + 2 (bank spread)
     cuuint32_t estr[2] = {1, 1};
     CUresult cr = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, gridP, dims, strides, box, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -545,7 +551,10 @@ template <typename T> class OpImpl : public purify_op {
   void iteration(double nu, double gamma, double eps, int cg_iters, cudaStream_t s) {
     const double nu2 = nu * nu;
     const size_t n2 = N();
-    // step 5: x_hat = (Phi^H Phi + 2I)^-1 sum_i x_i by CG, warm-started at x_hat
+    // step 5: x_hat = (Phi^H Phi + 2I)^-1 sum_i x_i by CG, warm-started at x_hat.
+    // The scalars stay on the device and need no launches of their own: the
+    // last block of the inverse row pass sets <r,r> (initial residual) or
+    // alpha; the last block of the CG update sets beta and the new <r,r>.
     normal_front(plain(xh), s);
     {
       RowEp<T> ep{};
@@ -555,9 +564,10 @@ template <typename T> class OpImpl : public purify_op {
       ep.p = xh;
       ep.b = xs;
       ep.nu2 = nu2;
-      ep.partials = partials;
-      const int np = normal_back(ep, s);
-      fin(partials, np, nullptr, 0, FIN_RR0, 0.0, s);
+      ep.partials = cg_part;
+      ep.scalars = sc;
+      ep.ticket = tickets;
+      normal_back(ep, s);
     }
     for (int it = 0; it < cg_iters; ++it) {
       RowPro<T> pro = plain(p);
@@ -574,11 +584,11 @@ template <typename T> class OpImpl : public purify_op {
       ep.out = Ap;
       ep.p = p;
       ep.nu2 = nu2;
-      ep.partials = partials;
-      int np = normal_back(ep, s);
-      fin(partials, np, nullptr, 0, FIN_ALPHA, 0.0, s);
-      PROF(KK_VEC, s, np = launch_cg_xr<T>(xh, r, p, Ap, sc, n2, partials, s));
-      fin(partials, np, nullptr, 0, FIN_BETA, 0.0, s);
+      ep.partials = cg_part;
+      ep.scalars = sc;
+      ep.ticket = tickets + 1;
+      normal_back(ep, s);
+      PROF(KK_VEC, s, launch_cg_xr<T>(xh, r, p, Ap, sc, n2, cg_part + kCgPart, tickets + 2, s));
     }
     // block 1 (l1 on Psi^H x_hat) fused into the analysis, block 2 (positivity)
     // fused into the synthesis: xs = x_1 + x_2

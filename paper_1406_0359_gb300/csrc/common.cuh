@@ -90,6 +90,37 @@ template <int NT> __device__ double block_max(double v, double* sh) {
   return r;
 }
 
+// Last-block reduction: every block has written partials[blockIdx.x]; the
+// block that finishes last (atomic ticket, no waiting) returns true in all
+// its threads, after which it may read all partials.  It resets the ticket.
+__device__ __forceinline__ bool last_block_done(unsigned int* ticket) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int t = atomicAdd(ticket, 1u);
+    last = (t == gridDim.x * gridDim.y * gridDim.z - 1);
+    if (last) *ticket = 0u;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// Fixed-order sum of n partials by one block (any blockDim multiple of 32).
+__device__ __forceinline__ double block_sum_array(const double* p, int n, double* sh) {
+  double a = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) a += p[k];
+  a = warp_sum(a);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = a;
+  __syncthreads();
+  double t = 0.0;
+  for (int k = 0; k < int((blockDim.x + 31) >> 5); ++k) t += sh[k];
+  __syncthreads();
+  return t;
+}
+
 // ---------------------------------------------------------------- mbarrier + TMA
 PD uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 

@@ -156,30 +156,34 @@ PD void stage(C (&v)[16], int t, int Ns, const C* __restrict__ tw, int dir, Sink
   }
 }
 
+// Shared buffers hold element q of a sequence at s[sidx(q) * ss]: ss = 1 for
+// one sequence per buffer (rows), ss = cw for cw interleaved columns, so that
+// the lanes that read 32 contiguous bytes of cw columns from global memory
+// also touch contiguous shared words.
 template <int LOGN, int ST, typename C, typename Store>
-PD void run_stages(C (&v)[16], int t, int Ns, C* s, const C* tw, int dir, Store store) {
+PD void run_stages(C (&v)[16], int t, int Ns, C* s, int ss, const C* tw, int dir, Store store) {
   typedef Plan<LOGN> P;
   constexpr int R = P::radix(ST);
   if constexpr (ST + 1 == P::NST) {
     stage<R, P::N, P::T>(v, t, Ns, tw, dir, store);
   } else {
-    stage<R, P::N, P::T>(v, t, Ns, tw, dir, [&](int q, C x) { s[sidx(q)] = x; });
+    stage<R, P::N, P::T>(v, t, Ns, tw, dir, [&](int q, C x) { s[sidx(q) * ss] = x; });
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = s[sidx(t + m * P::T)];
+    for (int m = 0; m < 16; ++m) v[m] = s[sidx(t + m * P::T) * ss];
     __syncthreads();
-    run_stages<LOGN, ST + 1>(v, t, Ns * R, s, tw, dir, store);
+    run_stages<LOGN, ST + 1>(v, t, Ns * R, s, ss, tw, dir, store);
   }
 }
 
 // All stages of one sequence: load(m) supplies input element t + m T,
-// store(q, value) receives output q.  s is this sequence's padded shared buffer.
+// store(q, value) receives output q.
 template <int LOGN, typename C, typename Load, typename Store>
-PD void fft_seq(int t, C* s, const C* tw, int dir, Load load, Store store) {
+PD void fft_seq(int t, C* s, int ss, const C* tw, int dir, Load load, Store store) {
   C v[16];
 #pragma unroll
   for (int m = 0; m < 16; ++m) v[m] = load(m);
-  run_stages<LOGN, 0>(v, t, 1, s, tw, dir, store);
+  run_stages<LOGN, 0>(v, t, 1, s, ss, tw, dir, store);
 }
 
 constexpr int kRowCta = 256;
@@ -227,7 +231,7 @@ __global__ void __launch_bounds__(kRowCta) k_row_fwd(Geometry g, RowPro<T> pro, 
   };
   C* out = A + size_t(i1) * K;
   auto store = [&](int q, C v) { out[q] = v; };
-  fft_seq<LOGN>(t, s, tw, -1, load, store);
+  fft_seq<LOGN>(t, s, 1, tw, -1, load, store);
 }
 
 template <typename T, int LOGN>
@@ -239,7 +243,7 @@ __global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN
   const int K = g.K, n = g.n, half = n / 2, pl = g.pad_lo, KP = g.KP;
   const int cc = threadIdx.x % cw, t = threadIdx.x / cw;
   const int c = blockIdx.x * cw + cc;
-  C* s = reinterpret_cast<C*>(sm_raw) + cc * padded(K);
+  C* s = reinterpret_cast<C*>(sm_raw) + cc;  // cw interleaved columns
   auto load = [&](int m) -> C {
     const int q = t + m * Plan<LOGN>::T;  // grid row
     const int i1 = (q + half) & (K - 1);
@@ -259,7 +263,7 @@ __global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN
       for (int b = 0; b < 2; ++b)
         if (rows[a] >= 0 && cols[b] >= 0) Pg[size_t(rows[a]) * KP + cols[b]] = v;
   };
-  fft_seq<LOGN>(t, s, tw, -1, load, store);
+  fft_seq<LOGN>(t, s, cw, tw, -1, load, store);
 }
 
 template <typename T, int LOGN>
@@ -271,7 +275,7 @@ __global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN
   const int K = g.K, n = g.n, half = n / 2, pl = g.pad_lo, KP = g.KP;
   const int cc = threadIdx.x % cw, t = threadIdx.x / cw;
   const int c = blockIdx.x * cw + cc;
-  C* s = reinterpret_cast<C*>(sm_raw) + cc * padded(K);
+  C* s = reinterpret_cast<C*>(sm_raw) + cc;  // cw interleaved columns
   const int jhi = kJ - pl;
   int cols[2] = {c + pl, -1};
   if (c >= K - pl) cols[1] = c + pl - K;
@@ -293,7 +297,7 @@ __global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN
     const int i1 = (q + half) & (K - 1);
     if (i1 < n) A[size_t(i1) * K + c] = v;
   };
-  fft_seq<LOGN>(t, s, tw, +1, load, store);
+  fft_seq<LOGN>(t, s, cw, tw, +1, load, store);
 }
 
 template <typename T, int LOGN>
@@ -343,7 +347,7 @@ __global__ void __launch_bounds__(kRowCta) k_row_inv(Geometry g, const typename 
         ep.out[idx] = val;
     }
   };
-  fft_seq<LOGN>(t, s, tw, +1, load, store);
+  fft_seq<LOGN>(t, s, 1, tw, +1, load, store);
   if (ep.partials) {
     part = warp_sum(part);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -353,6 +357,16 @@ __global__ void __launch_bounds__(kRowCta) k_row_inv(Geometry g, const typename 
       double tot = 0.0;
       for (int k = 0; k < int((blockDim.x + 31) >> 5); ++k) tot += red[k];
       ep.partials[blockIdx.x] = tot;
+    }
+    if (ep.ticket && last_block_done(ep.ticket)) {
+      const double sum = block_sum_array(ep.partials, int(gridDim.x), red);
+      if (threadIdx.x == 0) {
+        if (ep.mode == EP_CG_R0) {
+          ep.scalars[0] = sum;  // <r, r>
+        } else if (ep.mode == EP_CG_AP) {
+          ep.scalars[1] = sum > 0.0 ? ep.scalars[0] / sum : 0.0;  // alpha = <r, r> / <p, Ap>
+        }
+      }
     }
   }
 }
@@ -372,28 +386,28 @@ __global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN
   const int K = g.K, n = g.n, half = n / 2;
   const int cc = threadIdx.x % cw, t = threadIdx.x / cw;
   const int c = blockIdx.x * cw + cc;
-  C* s = reinterpret_cast<C*>(sm_raw) + cc * padded(K);
+  C* s = reinterpret_cast<C*>(sm_raw) + cc;  // cw interleaved columns
   auto load = [&](int m) -> C {
     const int q = t + m * TT;
     const int i1 = (q + half) & (K - 1);
     return i1 < n ? A[size_t(i1) * K + c] : cz<C>();
   };
-  auto to_smem = [&](int q, C v) { s[sidx(q)] = v; };
-  fft_seq<LOGN>(t, s, tw, -1, load, to_smem);
+  auto to_smem = [&](int q, C v) { s[sidx(q) * cw] = v; };
+  fft_seq<LOGN>(t, s, cw, tw, -1, load, to_smem);
   __syncthreads();
   C v[16];
   const T* kc = khat + (size_t(blockIdx.x) * K) * cw + cc;
 #pragma unroll
   for (int m = 0; m < 16; ++m) {
     const int q = t + m * TT;
-    v[m] = cscale(s[sidx(q)], kc[size_t(q) * cw]);
+    v[m] = cscale(s[sidx(q) * cw], kc[size_t(q) * cw]);
   }
   __syncthreads();
   auto store = [&](int q, C x) {
     const int i1 = (q + half) & (K - 1);
     if (i1 < n) A[size_t(i1) * K + c] = x;
   };
-  run_stages<LOGN, 0>(v, t, 1, s, tw, +1, store);
+  run_stages<LOGN, 0>(v, t, 1, s, cw, tw, +1, store);
 }
 
 // Plain in-place transforms of a K x K complex array (set-up of the PSF spectrum).
@@ -412,7 +426,7 @@ __global__ void __launch_bounds__(kRowCta) k_rows_plain(typename cplx_t<T>::type
   int qs[16];
   int cnt = 0;
   auto store = [&](int q, C v) { out[cnt] = v; qs[cnt] = q; ++cnt; };
-  fft_seq<LOGN>(t, s, tw, dir, load, store);
+  fft_seq<LOGN>(t, s, 1, tw, dir, load, store);
   __syncthreads();
 #pragma unroll
   for (int m = 0; m < 16; ++m) row[qs[m]] = out[m];
@@ -427,13 +441,13 @@ __global__ void __launch_bounds__(ColThreads<T, LOGN>::value) k_cols_plain(typen
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int cc = threadIdx.x % cw, t = threadIdx.x / cw;
   const int c = blockIdx.x * cw + cc;
-  C* s = reinterpret_cast<C*>(sm_raw) + cc * padded(K);
+  C* s = reinterpret_cast<C*>(sm_raw) + cc;  // cw interleaved columns
   auto load = [&](int m) -> C { return X[size_t(t + m * TT) * K + c]; };
   C out[16];
   int qs[16];
   int cnt = 0;
   auto store = [&](int q, C v) { out[cnt] = v; qs[cnt] = q; ++cnt; };
-  fft_seq<LOGN>(t, s, tw, dir, load, store);
+  fft_seq<LOGN>(t, s, cw, tw, dir, load, store);
   __syncthreads();
 #pragma unroll
   for (int m = 0; m < 16; ++m) X[size_t(qs[m]) * K + c] = out[m];

@@ -66,12 +66,16 @@ template <typename T> struct RowEp {
   const T* b;
   double nu, nu2;
   double* partials;
+  // CG scalars finalised by the last block: EP_CG_R0 sets scalars[S_RR];
+  // EP_CG_AP sets scalars[S_ALPHA] = scalars[S_RR] / <p, Ap> (0 if <p, Ap> = 0)
+  double* scalars;
+  unsigned int* ticket;
 };
 
 // Forward row-pass prologues (image -> row FFT input).
 enum RowProMode : int {
   PRO_PLAIN = 0,    // src = x
-  PRO_CG_P = 1,     // p = r + beta p (beta = scalars[beta_idx]); write p; src = p
+  PRO_CG_P = 1,     // p = r + beta p, beta = scalars[idx]; write p; src = p
   PRO_SCALE = 2     // src = x * scalars[scale_idx]   (power iteration normalisation)
 };
 template <typename T> struct RowPro {

@@ -17,7 +17,9 @@
 // Kernel weights come from a per-tap polynomial in the fractional offset
 // (Chebyshev fit of the Kaiser-Bessel kernel, computed on the host).
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "internal.h"
 
@@ -72,6 +74,10 @@ template <> PD void atomic_add_global<double2>(double2* p, double2 v) {
 
 // Stage the work item's grid patch by TMA; false (for every thread) when the
 // bounded wait gave up in any thread.
+// Staged patch: PW = TB + J rows of PP = PW + 2 grid values (the wider pitch
+// spreads consecutive patch rows over distinct shared banks; the two extra
+// columns are read past the grid's edge on the last tile column, where the
+// tensor copy fills zeros, and never used).
 template <typename C>
 PD bool stage_patch(C* patch, uint64_t* bar, const CUtensorMap* map, int tu, int tv, int TB, int PW, int* err) {
   if (threadIdx.x == 0) {
@@ -80,7 +86,7 @@ PD bool stage_patch(C* patch, uint64_t* bar, const CUtensorMap* map, int tu, int
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(bar, uint32_t(PW * PW * sizeof(C)));
+    mbar_arrive_expect_tx(bar, uint32_t(PW * (PW + 2) * sizeof(C)));
     const int cw = int(sizeof(C) / 8);
     tma_load_2d(patch, map, tv * TB * cw, tu * TB, bar);
   }
@@ -90,11 +96,15 @@ PD bool stage_patch(C* patch, uint64_t* bar, const CUtensorMap* map, int tu, int
 
 enum TileMode : int { TM_DEGRID = 0, TM_GRID = 1, TM_GRAM = 2 };
 constexpr int kWarps = kThreads / 32;
-constexpr int kStage = 2 * kJ + 3;  // wu[J], wv[J], u.re, u.im, packed cell
+constexpr int kStage = 2 * kJ + 4;  // wu[J], wv[J], u.re, u.im, packed cell (int bits), pad
+
+template <typename T> struct Pair2;
+template <> struct Pair2<float> { typedef float2 type; };
+template <> struct Pair2<double> { typedef double2 type; };
 
 template <typename T> __host__ __device__ inline size_t tile_patch_bytes(int TB) {
   const size_t PW = size_t(TB + kJ);
-  return PW * PW * sizeof(typename cplx_t<T>::type);
+  return PW * (PW + 2) * sizeof(typename cplx_t<T>::type);
 }
 template <typename T> __host__ __device__ inline size_t tile_acc_bytes(int TB) {
   const size_t PW = size_t(TB + kJ);
@@ -133,6 +143,7 @@ __global__ void __launch_bounds__(kThreads) k_tile(Geometry g, const __grid_cons
                                                    GridPro<typename cplx_t<T>::type> gpro,
                                                    typename cplx_t<T>::type* __restrict__ Q, int* err) {
   typedef typename cplx_t<T>::type C;
+  typedef typename Pair2<T>::type T2;
   constexpr bool kGather = MODE != TM_GRID;
   constexpr bool kScatter = MODE != TM_DEGRID;
   extern __shared__ __align__(128) unsigned char sm_raw[];
@@ -206,15 +217,15 @@ __global__ void __launch_bounds__(kThreads) k_tile(Geometry g, const __grid_cons
     }
     st[2 * kJ] = u.x;
     st[2 * kJ + 1] = u.y;
-    st[2 * kJ + 2] = T(cu * 256 + cv);
+    *reinterpret_cast<int*>(st + 2 * kJ + 2) = cu * 256 + cv;
     __syncwarp();
     const int nv = min(32, w1 - base);
     C mine = cz<C>();  // gathered value of this lane's own visibility
     for (int j = 0; j < nv; ++j) {
       const T* sj = wst + j * kStage;
-      const int cell = int(sj[2 * kJ + 2]);
+      const int cell = *reinterpret_cast<const int*>(sj + 2 * kJ + 2);
       if (cell != cell_cur) {  // warp-uniform
-        const int ro = ((cell >> 8) + ta) * PW + (cell & 255) + tb;
+        const int ro = ((cell >> 8) + ta) * (PW + 2) + (cell & 255) + tb;
         if (kScatter && cell_cur >= 0) {
           C* row = wacc + ((cell_cur >> 8) + ta) * PA + (cell_cur & 255) + tb;
           row[0] = cadd(row[0], s0);
@@ -228,7 +239,8 @@ __global__ void __launch_bounds__(kThreads) k_tile(Geometry g, const __grid_cons
         cell_cur = cell;
       }
       const T wa = sj[ta];
-      const T wb0 = wa * sj[kJ + tb], wb1 = wa * sj[kJ + tb + 1];
+      const T2 wbp = *reinterpret_cast<const T2*>(sj + kJ + tb);
+      const T wb0 = wa * wbp.x, wb1 = wa * wbp.y;
       C uj;
       if (kGather) {
         C part = cmk<C>(fma(wb0, g0.x, wb1 * g1.x), fma(wb0, g0.y, wb1 * g1.y));
@@ -285,6 +297,364 @@ __global__ void __launch_bounds__(kThreads) k_tile(Geometry g, const __grid_cons
     C v = cz<C>();
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) v = cadd(v, acc[w * PW * PA + r * PA + c]);
+    if (v.x != 0 || v.y != 0) atomic_add_global(Q + size_t(tu * g.TB + r) * g.KP + (tv * g.TB + c), v);
+  }
+}
+
+// Degridding (no scatter, so visibilities of one warp never conflict): one
+// CTA per work item, warp w a contiguous slice.  Per 32-wide batch every
+// lane computes its visibility's weights into the warp's staging rows; then
+// each step serves 8 visibilities with 4 lanes each, lane k of a group
+// gathering footprint rows 2k and 2k+1 (16 taps) from the staged patch, and
+// two shuffle levels sum the group.  The owner lane runs the epilogue.
+constexpr int kDgStage = 2 * kJ + 4;  // wu[J], wv[J], y.re, y.im, cell, pad
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_degrid(Geometry g, const __grid_constant__ CUtensorMap map,
+                                                     const WorkItem* __restrict__ items,
+                                                     const Pos<T>* __restrict__ pos, const int* __restrict__ perm,
+                                                     KbPoly<T> kb, DegridEp<typename cplx_t<T>::type> dep, int* err) {
+  typedef typename cplx_t<T>::type C;
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ double red[32];
+  const WorkItem it = items[blockIdx.x];
+  const int tu = it.tile / g.ntile1d, tv = it.tile - tu * g.ntile1d;
+  const int PW = g.TB + kJ, PP = PW + 2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  C* patch = reinterpret_cast<C*>(sm_raw);
+  T* stage = reinterpret_cast<T*>(sm_raw + tile_patch_bytes<T>(g.TB));
+  if (!stage_patch(patch, &bar, &map, tu, tv, g.TB, PW, err)) return;
+  T* wst = stage + warp * 32 * kDgStage;
+  const int cnt = it.end - it.begin;
+  const int per = (cnt + kWarps - 1) / kWarps;
+  const int w0 = it.begin + min(cnt, warp * per), w1 = it.begin + min(cnt, (warp + 1) * per);
+  const int grp = lane >> 2, k = lane & 3;
+  double p0 = 0.0, p1 = 0.0;
+  for (int base = w0; base < w1; base += 32) {
+    const int i = base + lane;
+    const bool valid = i < w1;
+    const int nv = min(32, w1 - base);
+    {
+      T wu[kJ], wv[kJ];
+      int cu = 0, cv = 0;
+      if (valid) {
+        T fu, fv;
+        decode(pos[i], cu, fu, cv, fv);
+        kb_eval(kb, fu, wu);
+        kb_eval(kb, fv, wv);
+      } else {
+#pragma unroll
+        for (int a = 0; a < kJ; ++a) wu[a] = wv[a] = T(0);
+      }
+      T* st = wst + lane * kDgStage;
+#pragma unroll
+      for (int a = 0; a < kJ; ++a) {
+        st[a] = wu[a];
+        st[kJ + a] = wv[a];
+      }
+      *reinterpret_cast<int*>(st + 2 * kJ + 2) = cu * 256 + cv;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s4 = 0; s4 < 4; ++s4) {
+      const int j = s4 * 8 + grp;
+      C part = cz<C>();
+      if (j < nv) {
+        const T* sj = wst + j * kDgStage;
+        const int cell = *reinterpret_cast<const int*>(sj + 2 * kJ + 2);
+        const T wa0 = sj[2 * k], wa1 = sj[2 * k + 1];
+        T wv[kJ];
+#pragma unroll
+        for (int b = 0; b < kJ; ++b) wv[b] = sj[kJ + b];
+        const C* r0 = patch + ((cell >> 8) + 2 * k) * PP + (cell & 255);
+        const C* r1 = r0 + PP;
+        T hx0 = 0, hy0 = 0, hx1 = 0, hy1 = 0;
+#pragma unroll
+        for (int b = 0; b < kJ; ++b) {
+          const C g0 = r0[b], g1 = r1[b];
+          hx0 = fma(wv[b], g0.x, hx0);
+          hy0 = fma(wv[b], g0.y, hy0);
+          hx1 = fma(wv[b], g1.x, hx1);
+          hy1 = fma(wv[b], g1.y, hy1);
+        }
+        part = cmk<C>(fma(wa0, hx0, wa1 * hx1), fma(wa0, hy0, wa1 * hy1));
+      }
+      part.x += __shfl_xor_sync(0xffffffffu, part.x, 1);
+      part.y += __shfl_xor_sync(0xffffffffu, part.y, 1);
+      part.x += __shfl_xor_sync(0xffffffffu, part.x, 2);
+      part.y += __shfl_xor_sync(0xffffffffu, part.y, 2);
+      if (k == 0 && j < nv) {
+        T* sj = wst + j * kDgStage;
+        sj[2 * kJ] = part.x;
+        sj[2 * kJ + 1] = part.y;
+      }
+    }
+    __syncwarp();
+    if (valid) {
+      const T* st = wst + lane * kDgStage;
+      const C acc_v = cmk<C>(st[2 * kJ], st[2 * kJ + 1]);
+      if (dep.mode == DG_STORE_PERM) {
+        dep.y[perm[i]] = acc_v;
+      } else if (dep.mode == DG_STORE_SORTED) {
+        dep.y[i] = acc_v;
+      } else {  // DG_BALL
+        const C z = dep.z[i], yv = dep.ys[i];
+        const T nu = T(dep.nu);
+        const C v = cmk<C>(fma(nu, acc_v.x, z.x), fma(nu, acc_v.y, z.y));
+        dep.z[i] = v;
+        const double dx = double(v.x) - dep.nu * double(yv.x), dy = double(v.y) - dep.nu * double(yv.y);
+        p0 += dx * dx + dy * dy;
+        const double ex = double(acc_v.x) - double(yv.x), ey = double(acc_v.y) - double(yv.y);
+        p1 += ex * ex + ey * ey;
+      }
+    }
+    __syncwarp();
+  }
+  if (dep.mode == DG_BALL) {
+    const double r0 = block_sum<kThreads>(p0, red);
+    const double r1 = block_sum<kThreads>(p1, red);
+    if (threadIdx.x == 0) {
+      dep.part0[blockIdx.x] = r0;
+      dep.part1[blockIdx.x] = r1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-per-item forms of degridding and gridding (the ball block and the
+// operator calls).  Each warp owns one work item end to end: its own TMA-staged
+// patch and mbarrier (degridding) or its own accumulator patch (gridding), so
+// there are no CTA-wide barriers and no cross-warp merges; items are ordered
+// largest first so the hardware's CTA scheduling balances the load.
+constexpr int kWItems = kThreads / 32;  // items (warps) per CTA
+
+template <typename T> __host__ __device__ inline size_t warp_patch_elems(int TB) {
+  const size_t PW = size_t(TB + kJ);
+  return PW * (PW + 2);
+}
+
+template <typename C>
+PD bool warp_stage_patch(C* patch, uint64_t* bar, const CUtensorMap* map, int tu, int tv, int TB, int PW, int lane,
+                         int* err) {
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+    mbar_arrive_expect_tx(bar, uint32_t(PW * (PW + 2) * sizeof(C)));
+    const int cw = int(sizeof(C) / 8);
+    tma_load_2d(patch, map, tv * TB * cw, tu * TB, bar);
+  }
+  __syncwarp();
+  const bool ok = mbar_wait_bounded(bar, 0, err);
+  return __all_sync(0xffffffffu, ok) != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_degrid_w(Geometry g, const __grid_constant__ CUtensorMap map,
+                                                       const WorkItem* __restrict__ items, int n_items,
+                                                       const Pos<T>* __restrict__ pos, const int* __restrict__ perm,
+                                                       KbPoly<T> kb, DegridEp<typename cplx_t<T>::type> dep,
+                                                       int* err) {
+  typedef typename cplx_t<T>::type C;
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  __shared__ __align__(8) uint64_t bars[kWItems];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int item = blockIdx.x * kWItems + warp;
+  if (item >= n_items) return;
+  const WorkItem it = items[item];
+  const int tu = it.tile / g.ntile1d, tv = it.tile - tu * g.ntile1d;
+  const int PW = g.TB + kJ, PP = PW + 2;
+  const size_t pe = warp_patch_elems<T>(g.TB);
+  C* patch = reinterpret_cast<C*>(sm_raw) + warp * pe;
+  T* wst = reinterpret_cast<T*>(reinterpret_cast<C*>(sm_raw) + kWItems * pe) + warp * 32 * kDgStage;
+  if (!warp_stage_patch(patch, &bars[warp], &map, tu, tv, g.TB, PW, lane, err)) return;
+  const int grp = lane >> 2, k = lane & 3;
+  double p0 = 0.0, p1 = 0.0;
+  for (int base = it.begin; base < it.end; base += 32) {
+    const int i = base + lane;
+    const bool valid = i < it.end;
+    const int nv = min(32, it.end - base);
+    {
+      T wu[kJ], wv[kJ];
+      int cu = 0, cv = 0;
+      if (valid) {
+        T fu, fv;
+        decode(pos[i], cu, fu, cv, fv);
+        kb_eval(kb, fu, wu);
+        kb_eval(kb, fv, wv);
+      } else {
+#pragma unroll
+        for (int a = 0; a < kJ; ++a) wu[a] = wv[a] = T(0);
+      }
+      T* st = wst + lane * kDgStage;
+#pragma unroll
+      for (int a = 0; a < kJ; ++a) {
+        st[a] = wu[a];
+        st[kJ + a] = wv[a];
+      }
+      *reinterpret_cast<int*>(st + 2 * kJ + 2) = cu * 256 + cv;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s4 = 0; s4 < 4; ++s4) {
+      const int j = s4 * 8 + grp;
+      C part = cz<C>();
+      if (j < nv) {
+        const T* sj = wst + j * kDgStage;
+        const int cell = *reinterpret_cast<const int*>(sj + 2 * kJ + 2);
+        const T wa0 = sj[2 * k], wa1 = sj[2 * k + 1];
+        T wv[kJ];
+#pragma unroll
+        for (int b = 0; b < kJ; ++b) wv[b] = sj[kJ + b];
+        const C* r0 = patch + ((cell >> 8) + 2 * k) * PP + (cell & 255);
+        const C* r1 = r0 + PP;
+        T hx0 = 0, hy0 = 0, hx1 = 0, hy1 = 0;
+#pragma unroll
+        for (int b = 0; b < kJ; ++b) {
+          const C g0 = r0[b], g1 = r1[b];
+          hx0 = fma(wv[b], g0.x, hx0);
+          hy0 = fma(wv[b], g0.y, hy0);
+          hx1 = fma(wv[b], g1.x, hx1);
+          hy1 = fma(wv[b], g1.y, hy1);
+        }
+        part = cmk<C>(fma(wa0, hx0, wa1 * hx1), fma(wa0, hy0, wa1 * hy1));
+      }
+      part.x += __shfl_xor_sync(0xffffffffu, part.x, 1);
+      part.y += __shfl_xor_sync(0xffffffffu, part.y, 1);
+      part.x += __shfl_xor_sync(0xffffffffu, part.x, 2);
+      part.y += __shfl_xor_sync(0xffffffffu, part.y, 2);
+      if (k == 0 && j < nv) {
+        T* sj = wst + j * kDgStage;
+        sj[2 * kJ] = part.x;
+        sj[2 * kJ + 1] = part.y;
+      }
+    }
+    __syncwarp();
+    if (valid) {
+      const T* st = wst + lane * kDgStage;
+      const C acc_v = cmk<C>(st[2 * kJ], st[2 * kJ + 1]);
+      if (dep.mode == DG_STORE_PERM) {
+        dep.y[perm[i]] = acc_v;
+      } else if (dep.mode == DG_STORE_SORTED) {
+        dep.y[i] = acc_v;
+      } else {  // DG_BALL
+        const C z = dep.z[i], yv = dep.ys[i];
+        const T nu = T(dep.nu);
+        const C v = cmk<C>(fma(nu, acc_v.x, z.x), fma(nu, acc_v.y, z.y));
+        dep.z[i] = v;
+        const double dx = double(v.x) - dep.nu * double(yv.x), dy = double(v.y) - dep.nu * double(yv.y);
+        p0 += dx * dx + dy * dy;
+        const double ex = double(acc_v.x) - double(yv.x), ey = double(acc_v.y) - double(yv.y);
+        p1 += ex * ex + ey * ey;
+      }
+    }
+    __syncwarp();
+  }
+  if (dep.mode == DG_BALL) {
+    p0 = warp_sum(p0);
+    p1 = warp_sum(p1);
+    if (lane == 0) {
+      dep.part0[item] = p0;
+      dep.part1[item] = p1;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_grid_w(Geometry g, const WorkItem* __restrict__ items, int n_items,
+                                                     const Pos<T>* __restrict__ pos, const int* __restrict__ perm,
+                                                     KbPoly<T> kb, GridPro<typename cplx_t<T>::type> gpro,
+                                                     typename cplx_t<T>::type* __restrict__ Q) {
+  typedef typename cplx_t<T>::type C;
+  typedef typename Pair2<T>::type T2;
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int item = blockIdx.x * kWItems + warp;
+  if (item >= n_items) return;
+  const WorkItem it = items[item];
+  const int tu = it.tile / g.ntile1d, tv = it.tile - tu * g.ntile1d;
+  const int PW = g.TB + kJ, PA = PW + 1;
+  C* wacc = reinterpret_cast<C*>(sm_raw) + warp * PW * PA;
+  T* wst = reinterpret_cast<T*>(reinterpret_cast<C*>(sm_raw) + kWItems * PW * PA) + warp * 32 * kStage;
+  for (int e = lane; e < PW * PA; e += 32) wacc[e] = cz<C>();
+  __syncwarp();
+  T scale = 0;
+  if (gpro.mode == GP_BALL) scale = T(gpro.scalars[gpro.scale_idx]);
+  const int ta = lane >> 2, tb = (lane & 3) * 2;
+  int scell = -1;
+  C s0 = cz<C>(), s1 = cz<C>();
+  for (int base = it.begin; base < it.end; base += 32) {
+    const int i = base + lane;
+    const bool valid = i < it.end;
+    const int nv = min(32, it.end - base);
+    {
+      T wu[kJ], wv[kJ];
+      int cu = 0, cv = 0;
+      C u = cz<C>();
+      if (valid) {
+        T fu, fv;
+        decode(pos[i], cu, fu, cv, fv);
+        kb_eval(kb, fu, wu);
+        kb_eval(kb, fv, wv);
+        if (gpro.mode == GP_PERM) {
+          u = gpro.y[perm[i]];
+        } else if (gpro.mode == GP_SORTED) {
+          u = gpro.y[i];
+        } else {  // GP_BALL
+          const C v = gpro.z[i], yv = gpro.ys[i];
+          const T nu = T(gpro.nu);
+          const T cx = nu * yv.x, cy = nu * yv.y;
+          const T rx = fma(v.x - cx, scale, cx), ry = fma(v.y - cy, scale, cy);
+          gpro.z[i] = cmk<C>(v.x - rx, v.y - ry);
+          u = cmk<C>(T(2) * rx - v.x, T(2) * ry - v.y);
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < kJ; ++a) wu[a] = wv[a] = T(0);
+      }
+      T* st = wst + lane * kStage;
+#pragma unroll
+      for (int a = 0; a < kJ; ++a) {
+        st[a] = wu[a];
+        st[kJ + a] = wv[a];
+      }
+      st[2 * kJ] = u.x;
+      st[2 * kJ + 1] = u.y;
+      *reinterpret_cast<int*>(st + 2 * kJ + 2) = cu * 256 + cv;
+    }
+    __syncwarp();
+    for (int j = 0; j < nv; ++j) {
+      const T* sj = wst + j * kStage;
+      const int cell = *reinterpret_cast<const int*>(sj + 2 * kJ + 2);
+      if (cell != scell) {  // warp-uniform
+        if (scell >= 0) {
+          C* row = wacc + ((scell >> 8) + ta) * PA + (scell & 255) + tb;
+          row[0] = cadd(row[0], s0);
+          row[1] = cadd(row[1], s1);
+          s0 = s1 = cz<C>();
+        }
+        scell = cell;
+      }
+      const T wa = sj[ta];
+      const T2 wbp = *reinterpret_cast<const T2*>(sj + kJ + tb);
+      const T a0 = wa * wbp.x, a1 = wa * wbp.y;
+      const T ux = sj[2 * kJ], uy = sj[2 * kJ + 1];
+      s0.x = fma(a0, ux, s0.x);
+      s0.y = fma(a0, uy, s0.y);
+      s1.x = fma(a1, ux, s1.x);
+      s1.y = fma(a1, uy, s1.y);
+    }
+    __syncwarp();
+  }
+  if (scell >= 0) {
+    C* row = wacc + ((scell >> 8) + ta) * PA + (scell & 255) + tb;
+    row[0] = cadd(row[0], s0);
+    row[1] = cadd(row[1], s1);
+  }
+  __syncwarp();
+  for (int e = lane; e < PW * PW; e += 32) {
+    const int r = e / PW, c = e - r * PW;
+    const C v = wacc[r * PA + c];
     if (v.x != 0 || v.y != 0) atomic_add_global(Q + size_t(tu * g.TB + r) * g.KP + (tv * g.TB + c), v);
   }
 }
@@ -484,7 +854,9 @@ __global__ void k_encode<double>(const double* __restrict__ uv, const int* __res
 
 template <typename T> cudaError_t configure_nufft() {
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = raise_smem_limit(k_tile<T, TM_DEGRID>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_degrid<T>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_degrid_w<T>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_grid_w<T>);
   if (e == cudaSuccess) e = raise_smem_limit(k_tile<T, TM_GRID>);
   if (e == cudaSuccess) e = raise_smem_limit(k_tile<T, TM_GRAM>);
   return e;
@@ -510,9 +882,9 @@ void launch_degrid(const Geometry& g, const CUtensorMap& map, const WorkItem* it
                    const int* perm, const KbPoly<T>& kb, const DegridEp<typename cplx_t<T>::type>& ep, int* err,
                    cudaStream_t s) {
   if (n_items <= 0) return;
-  const size_t sm = tile_smem_bytes(sizeof(T), g.TB, TM_DEGRID);
-  GridPro<typename cplx_t<T>::type> gp{};
-  k_tile<T, TM_DEGRID><<<n_items, kThreads, sm, s>>>(g, map, items, pos, perm, kb, ep, gp, nullptr, err);
+  const size_t sm = kWItems * (warp_patch_elems<T>(g.TB) * sizeof(typename cplx_t<T>::type) + 32 * kDgStage * sizeof(T));
+  k_degrid_w<T><<<(n_items + kWItems - 1) / kWItems, kThreads, sm, s>>>(g, map, items, n_items, pos, perm, kb, ep,
+                                                                       err);
 }
 
 template <typename T>
@@ -520,11 +892,9 @@ void launch_grid(const Geometry& g, const WorkItem* items, int n_items, const Po
                  const KbPoly<T>& kb, const GridPro<typename cplx_t<T>::type>& pro, typename cplx_t<T>::type* Q,
                  cudaStream_t s) {
   if (n_items <= 0) return;
-  const size_t sm = tile_smem_bytes(sizeof(T), g.TB, TM_GRID);
-  DegridEp<typename cplx_t<T>::type> ep{};
-  CUtensorMap dummy;
-  memset(&dummy, 0, sizeof(dummy));
-  k_tile<T, TM_GRID><<<n_items, kThreads, sm, s>>>(g, dummy, items, pos, perm, kb, ep, pro, Q, nullptr);
+  const size_t PW = size_t(g.TB + kJ);
+  const size_t sm = kWItems * (PW * (PW + 1) * sizeof(typename cplx_t<T>::type) + 32 * kStage * sizeof(T));
+  k_grid_w<T><<<(n_items + kWItems - 1) / kWItems, kThreads, sm, s>>>(g, items, n_items, pos, perm, kb, pro, Q);
 }
 
 template <typename T>
@@ -595,6 +965,15 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
       k_encode<T><<<int((M + tb - 1) / tb), tb, 0, s>>>(uv, perm, M, g.K, g.TB, pos);
       fail(cudaStreamSynchronize(s));
       fail(cudaGetLastError());
+      // largest items first (stable): whole-warp items then finish together
+      if (rc == 0 && h_total > 1) {
+        std::vector<WorkItem> h(h_total);
+        fail(cudaMemcpy(h.data(), items, h.size() * sizeof(WorkItem), cudaMemcpyDeviceToHost));
+        std::stable_sort(h.begin(), h.end(), [](const WorkItem& a, const WorkItem& b) {
+          return (a.end - a.begin) > (b.end - b.begin);
+        });
+        fail(cudaMemcpy(items, h.data(), h.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+      }
     }
   }
   cudaFree(k0);

@@ -8,11 +8,15 @@ namespace purify {
 
 namespace {
 constexpr int kT = 256;
+constexpr int kCgBlocks = 512;
 
+// CG update x += alpha p, r -= alpha Ap (alpha = sc[S_ALPHA]); partials of
+// <r, r>, and the last block sets beta = <r, r>_new / <r, r>_old and
+// <r, r> = <r, r>_new in the device scalars.
 template <typename T>
 __global__ void __launch_bounds__(kT) k_cg_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
-                                              const T* __restrict__ Ap, const double* __restrict__ sc, size_t N,
-                                              double* __restrict__ partials) {
+                                              const T* __restrict__ Ap, double* __restrict__ sc, size_t N,
+                                              double* __restrict__ partials, unsigned int* ticket) {
   __shared__ double red[32];
   const T alpha = T(sc[S_ALPHA]);
   double part = 0.0;
@@ -24,6 +28,14 @@ __global__ void __launch_bounds__(kT) k_cg_xr(T* __restrict__ x, T* __restrict__
   }
   const double t = block_sum<kT>(part, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  if (last_block_done(ticket)) {
+    const double rr_new = block_sum_array(partials, int(gridDim.x), red);
+    if (threadIdx.x == 0) {
+      const double rr = sc[S_RR];
+      sc[S_BETA] = rr > 0.0 ? rr_new / rr : 0.0;
+      sc[S_RR] = rr_new;
+    }
+  }
 }
 
 // One block: sum partials in a fixed order, then apply `op`.
@@ -134,10 +146,16 @@ inline int nblk(size_t N) {
 
 int vec_blocks(size_t N) { return nblk(N); }
 
-template <typename T>
-int launch_cg_xr(T* x, T* r, const T* p, const T* Ap, const double* sc, size_t N, double* partials, cudaStream_t s) {
+int cg_xr_blocks(size_t N) {
   const int b = nblk(N);
-  k_cg_xr<T><<<b, kT, 0, s>>>(x, r, p, Ap, sc, N, partials);
+  return b < kCgBlocks ? b : kCgBlocks;
+}
+
+template <typename T>
+int launch_cg_xr(T* x, T* r, const T* p, const T* Ap, double* sc, size_t N, double* partials, unsigned int* ticket,
+                 cudaStream_t s) {
+  const int b = cg_xr_blocks(N);
+  k_cg_xr<T><<<b, kT, 0, s>>>(x, r, p, Ap, sc, N, partials, ticket);
   return b;
 }
 
@@ -171,7 +189,8 @@ template <typename C> void launch_gather(const C* src, const int* perm, size_t M
 }
 
 #define INST(T)                                                                                       \
-  template int launch_cg_xr<T>(T*, T*, const T*, const T*, const double*, size_t, double*, cudaStream_t); \
+  template int launch_cg_xr<T>(T*, T*, const T*, const T*, double*, size_t, double*, unsigned int*,     \
+                               cudaStream_t);                                                          \
   template int launch_reduce<T>(const T*, size_t, int, const double*, double*, cudaStream_t);           \
   template void launch_reweight<T>(T*, size_t, double, cudaStream_t);                                   \
   template void launch_fill<T>(T*, size_t, T, cudaStream_t);                                            \
