@@ -132,6 +132,19 @@ int purify_sara_adj(purify_op* op, const void* c, void* x, void* stream);
 int purify_sara_fwd_static(const float* x, float* c, int n, int levels, void* stream);
 
 /*
+ * purify_op_set_blocks -- partition the visibilities into R blocks (Eq. 4):
+ * the solver then imposes one constraint ||y_b - Phi_b x||_2 <= eps_b per
+ * block (Eq. 5), i.e. S = R + 2 functions in Eq. 6, each block with its own
+ * l2-ball projection; the composite operator sum_b Phi_b^H Phi_b = Phi^H Phi is
+ * unchanged (Section 3).  Visibilities are re-binned by (block, uv tile).
+ *   block_ids  device, int32[M] in the caller's uv order, values in [0, R);
+ *              may be NULL when R == 1 (one block).
+ *   R          1 <= R <= 64.
+ * Synchronises `stream`; PURIFY_ERR_INVALID for out-of-range ids.
+ */
+int purify_op_set_blocks(purify_op* op, const int* block_ids, int R, void* stream);
+
+/*
  * purify_gram -- out = Re(Phi^H Phi x), the data term of the composite
  * operator sum_i L_i^H L_i = Phi^H Phi + 2I that the SDMM global update
  * inverts (Section 3).
@@ -164,6 +177,8 @@ typedef struct {
   int use_graph;      /* non-zero: replay one SDMM iteration as a captured CUDA graph */
   int gram;           /* CG operator Re(Phi^H Phi): 0 NUFFT (G^H G each application), 1 precomputed
                          composite as a PSF convolution (Section 3), -1 the latter when n <= 1024 */
+  const double* eps_blocks; /* host, one bound per visibility block (Eq. 5) when
+                               purify_op_set_blocks gave R > 1; NULL: eps sqrt(M_b / M) */
 } purify_params;
 
 /* Solver statistics, filled by purify_sdmm_solve. */
@@ -172,7 +187,7 @@ typedef struct {
   int rounds;           /* SARA rounds run (1 + reweighted) */
   int converged;        /* halting rule met in the last round (always 0 when xi == 0) */
   double objective;     /* ||W Psi^H x||_1 at the returned x, last round's W */
-  double residual;      /* ||y - Phi x||_2 at the returned x */
+  double residual;      /* ||y - Phi x||_2 at the returned x (all blocks) */
   double nu;            /* scale used for Phi inside SDMM */
   double gamma;         /* gamma used */
   double elapsed_ms;    /* wall time of the solve on the device stream */

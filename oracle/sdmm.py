@@ -10,11 +10,15 @@ Algorithm 1 then alternates the global update
 Phi^H Phi + 2I because Psi Psi^H = I, Section 3) with, for every i,
     r_i = prox_{gamma f_i}(L_i x_hat + z_i),  z_i += L_i x_hat - r_i,
     x_i = L_i^H (r_i - z_i).
+With the visibilities split into R blocks (Eq. 4) the data term becomes R
+balls ||y_i - Phi_i x|| <= eps_i (Eq. 5), S = R + 2 functions, L_{i+2} = Phi_i
+(Eq. 6); each block gets its own projection, and sum_i Phi_i^H Phi_i = Phi^H Phi
+keeps the composite operator unchanged (Section 3).
 Readings (the paper is silent): x is real, so L_3^H = Re Phi^H; inside the
-solver Phi is scaled by nu = 1/||Phi||_2 together with the ball centre and
-radius, which leaves problem (3) unchanged; the halting rule is
-|f_t - f_{t-1}| < xi f_{t-1} together with ||y - Phi x_hat|| <= eps (1 + 1e-3),
-f_t = ||W Psi^H x_hat||_1; xi = 0 never halts.
+solver Phi is scaled by nu = 1/||Phi||_2 together with the ball centres and
+radii, which leaves problem (3) unchanged; the halting rule is
+|f_t - f_{t-1}| < xi f_{t-1} together with ||y_i - Phi_i x_hat|| <= eps_i (1 + 1e-3)
+for every block, f_t = ||W Psi^H x_hat||_1; xi = 0 never halts.
 """
 from __future__ import annotations
 
@@ -86,8 +90,17 @@ def sdmm_init(op, psi, x0: np.ndarray, nu: float) -> SDMMState:
     )
 
 
-def sdmm_iteration(st: SDMMState, op, psi, y, eps, gamma, w, cg_iters, nu) -> dict:
-    """One pass of steps 5-10 of Algorithm 1 (in place); returns diagnostics."""
+def _blocks(M, eps, blocks):
+    """(index arrays, radii): one block of all visibilities unless given."""
+    if blocks is None:
+        return [np.arange(M)], [float(eps)]
+    idx, radii = blocks
+    return [np.asarray(i) for i in idx], [float(e) for e in radii]
+
+
+def sdmm_iteration(st: SDMMState, op, psi, y, eps, gamma, w, cg_iters, nu, blocks=None) -> dict:
+    """One pass of steps 5-10 of Algorithm 1 (in place); returns diagnostics.
+    `blocks` = (list of index arrays, list of eps_i) for R > 1 (Eq. 4-5)."""
 
     def Q(v):  # sum_i L_i^H L_i = nu^2 Re Phi^H Phi + 2 I
         return nu * nu * op.gram_real(v) + 2.0 * v
@@ -105,33 +118,39 @@ def sdmm_iteration(st: SDMMState, op, psi, y, eps, gamma, w, cg_iters, nu) -> di
     r2 = proj_positive(v2)
     st.z2 = v2 - r2
     x2 = r2 - st.z2
-    # block 3: data fidelity (scaled ball)
+    # blocks 3..S: data fidelity, one scaled ball per visibility block
     phx = op.phi(xh)
     v3 = nu * phx + st.z3
-    r3 = proj_l2_ball(v3, nu * y, nu * eps)
+    r3 = np.empty_like(v3)
+    idx, radii = _blocks(op.M, eps, blocks)
+    for ib, eb in zip(idx, radii):
+        r3[ib] = proj_l2_ball(v3[ib], nu * y[ib], nu * eb)
     st.z3 = v3 - r3
-    x3 = nu * op.phi_adj_real(r3 - st.z3)
+    x3 = nu * op.phi_adj_real(r3 - st.z3)  # sum_i Phi_i^H (r_i - z_i)
     st.xs = x1 + x2 + x3
     st.t += 1
     diag = {
         "objective": float(np.sum(w * np.abs(a1))),
         "residual": float(np.linalg.norm(y - phx)),
+        "block_residuals": [float(np.linalg.norm(y[ib] - phx[ib])) for ib in idx],
     }
     st.history.append(diag)
     return diag
 
 
-def sdmm(op, psi, y, eps, gamma, w, t_max, cg_iters, nu, x0=None, xi=0.0):
+def sdmm(op, psi, y, eps, gamma, w, t_max, cg_iters, nu, x0=None, xi=0.0, blocks=None):
     """Run Algorithm 1 for t_max iterations or until the halting rule fires."""
     n = op.n
     x0 = np.zeros((n, n)) if x0 is None else x0
     st = sdmm_init(op, psi, x0, nu)
+    _, radii = _blocks(op.M, eps, blocks)
     prev = None
     for _ in range(t_max):
-        d = sdmm_iteration(st, op, psi, y, eps, gamma, w, cg_iters, nu)
+        d = sdmm_iteration(st, op, psi, y, eps, gamma, w, cg_iters, nu, blocks)
         if xi > 0.0 and prev is not None:
             rel = abs(d["objective"] - prev) / max(prev, 1e-300)
-            if rel < xi and d["residual"] <= eps * (1.0 + 1e-3):
+            feas = all(rb <= eb * (1.0 + 1e-3) for rb, eb in zip(d["block_residuals"], radii))
+            if rel < xi and feas:
                 break
         prev = d["objective"]
     return st
@@ -156,11 +175,11 @@ def reweight(alpha: np.ndarray, delta: float) -> np.ndarray:
 
 
 def sara_solve(op, psi, y, eps, gamma, t_max, cg_iters, nu, n_reweight,
-               decay=0.1, delta0=None, delta_min=None, warm_start=True, xi=0.0):
+               decay=0.1, delta0=None, delta_min=None, warm_start=True, xi=0.0, blocks=None):
     """SARA: an unweighted solve of (3) followed by n_reweight reweighted solves.
     Returns (x, list of per-round SDMMState)."""
     w = np.ones_like(psi.analysis(np.zeros((op.n, op.n))))
-    st = sdmm(op, psi, y, eps, gamma, w, t_max, cg_iters, nu, None, xi)
+    st = sdmm(op, psi, y, eps, gamma, w, t_max, cg_iters, nu, None, xi, blocks)
     rounds = [st]
     alpha0 = psi.analysis(st.x)
     for k in range(1, n_reweight + 1):
@@ -168,6 +187,6 @@ def sara_solve(op, psi, y, eps, gamma, t_max, cg_iters, nu, n_reweight,
         delta = delta_schedule(alpha0, k, decay, delta0, delta_min)
         w = reweight(alpha, delta)
         x0 = st.x if warm_start else None
-        st = sdmm(op, psi, y, eps, gamma, w, t_max, cg_iters, nu, x0, xi)
+        st = sdmm(op, psi, y, eps, gamma, w, t_max, cg_iters, nu, x0, xi, blocks)
         rounds.append(st)
     return st.x, rounds

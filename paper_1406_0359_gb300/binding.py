@@ -36,7 +36,8 @@ class purify_params(ctypes.Structure):
                 ("t_max", ctypes.c_int), ("cg_iters", ctypes.c_int), ("xi", ctypes.c_double),
                 ("n_reweight", ctypes.c_int), ("delta0", ctypes.c_double), ("delta_min", ctypes.c_double),
                 ("delta_decay", ctypes.c_double), ("warm_start", ctypes.c_int), ("power_iters", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("gram", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("gram", ctypes.c_int),
+                ("eps_blocks", ctypes.POINTER(ctypes.c_double))]
 
 
 class purify_stats(ctypes.Structure):
@@ -51,7 +52,7 @@ class purify_stats(ctypes.Structure):
 EXPORTS = ["purify_op_create", "purify_op_destroy", "purify_op_info", "purify_phi", "purify_phi_adj",
            "purify_sara_fwd", "purify_sara_adj", "purify_sdmm_solve", "purify_default_params",
            "purify_strerror", "purify_profile", "purify_profile_read", "purify_kernel_name",
-           "purify_last_error", "purify_sara_fwd_static", "purify_gram"]
+           "purify_last_error", "purify_sara_fwd_static", "purify_gram", "purify_op_set_blocks"]
 KERNEL_KINDS = ["row_fwd", "col_fwd", "degrid", "grid", "gram", "col_inv", "row_inv", "sara_analysis",
                 "sara_synthesis", "vector", "memset", "col_conv"]
 
@@ -85,6 +86,7 @@ def lib() -> ctypes.CDLL:
     L.purify_kernel_name.restype = ctypes.c_char_p
     L.purify_sara_fwd_static.argtypes = [vp, vp, ci, ci, vp]
     L.purify_gram.argtypes = [vp, vp, vp, ci, vp]
+    L.purify_op_set_blocks.argtypes = [vp, vp, ci, vp]
     L.purify_last_error.argtypes = []
     L.purify_last_error.restype = ctypes.c_char_p
     for f in EXPORTS:
@@ -157,6 +159,10 @@ def purify_sara_fwd_static(x_ptr, c_ptr, n: int, levels: int, stream=None) -> No
     """Psi^H x without an operator and without device allocation (FP32,
     n <= 512; see include/purify.h)."""
     _check(lib().purify_sara_fwd_static(x_ptr, c_ptr, n, levels, _stream(stream)), "purify_sara_fwd_static")
+
+
+def purify_op_set_blocks(h, block_ptr, R: int, stream=None) -> None:
+    _check(lib().purify_op_set_blocks(h, block_ptr, R, _stream(stream)), "purify_op_set_blocks")
 
 
 def purify_gram(h, x_ptr, out_ptr, mode: int, stream=None) -> None:
@@ -249,6 +255,12 @@ class Operator:
         purify_phi_adj(self.h, _dptr(y, self.cdtype, (self.M,)), _dptr(x, self.rdtype, (n, n)), stream)
         return x
 
+    def set_blocks(self, block_ids, R: int, stream=None) -> None:
+        """Split the visibilities into R blocks (caller-order int32 ids in [0, R))."""
+        b = torch.as_tensor(block_ids, dtype=torch.int32).cuda().contiguous()
+        purify_op_set_blocks(self.h, _dptr(b, torch.int32, (self.M,)), R, stream)
+        self.R = R
+
     def gram(self, x: torch.Tensor, mode: int = 1, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """Re(Phi^H Phi x); mode 0 NUFFT, 1 precomputed PSF convolution."""
         n = self.n
@@ -271,13 +283,17 @@ class Operator:
     def solve(self, y: torch.Tensor, eps: float, t_max: int = 200, cg_iters: int = 10, n_reweight: int = 0,
               gamma: float = 0.0, nu: float = 0.0, xi: float = 0.0, delta0: float = 0.0,
               delta_min: float = 0.0, delta_decay: float = 0.1, warm_start: bool = True,
-              power_iters: int = 30, use_graph: bool = True, gram: int = -1,
+              power_iters: int = 30, use_graph: bool = True, gram: int = -1, eps_blocks=None,
               out: torch.Tensor | None = None, stream=None) -> SolveResult:
         p = purify_default_params()
         p.eps, p.gamma, p.nu, p.t_max, p.cg_iters = eps, gamma, nu, t_max, cg_iters
         p.xi, p.n_reweight, p.delta0, p.delta_min = xi, n_reweight, delta0, delta_min
         p.delta_decay, p.warm_start, p.power_iters, p.use_graph = delta_decay, int(warm_start), power_iters, int(use_graph)
         p.gram = gram
+        if eps_blocks is not None:
+            arr = (ctypes.c_double * len(eps_blocks))(*[float(e) for e in eps_blocks])
+            p.eps_blocks = ctypes.cast(arr, ctypes.POINTER(ctypes.c_double))
+            self._eps_keep = arr
         n = self.n
         x = out if out is not None else torch.empty(n, n, dtype=self.rdtype, device=y.device)
         rc, st = purify_sdmm_solve(self.h, _dptr(y, self.cdtype, (self.M,)), p, _dptr(x, self.rdtype, (n, n)),

@@ -23,6 +23,7 @@ struct purify_op {
   virtual int sara_adj(const void* c, void* x, cudaStream_t s) = 0;
   virtual int solve(const void* y, const purify_params* p, void* x, purify_stats* st, cudaStream_t s) = 0;
   virtual int gram(const void* x, void* out, int mode, cudaStream_t s) = 0;
+  virtual int set_blocks(const int* blocks, int R, cudaStream_t s) = 0;
   virtual void info(int* n, int64_t* M, int* K, int* tile, int* n_items, int* precision, int64_t* bytes) const = 0;
 
   // ---- kernel timing (instrumentation)
@@ -165,14 +166,67 @@ template <typename T> class OpImpl : public purify_op {
   T* ones = nullptr;          // unit deapodisation for the convolution path
   T* khat = nullptr;          // real PSF spectrum, launch_col_conv layout
   bool toep = false;          // current normal-operator mode
+  // visibility blocks (Eq. 4-5)
+  int nblocks = 1;
+  std::vector<int64_t> block_sizes;
+  double* eps_dev = nullptr;    // nu-independent radii eps_b (R)
+  double* scale_dev = nullptr;  // projection scale per block (R)
   int64_t bytes = 0;
   std::vector<void*> allocs;
   cudaStream_t own = nullptr;  // solver stream (capturable, non-blocking)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 
+  int partials_cap = 0;
+  int size_partials() {
+    const int np = std::max({2 * n_items, row_inv_blocks(g), sara_partials_capacity(g.n, levels),
+                             vec_blocks(9 * N()), 1});
+    if (np <= partials_cap) return PURIFY_OK;
+    double* pnew = nullptr;
+    const int rc = alloc(&pnew, np);
+    if (rc) return rc;
+    partials = pnew;
+    partials_cap = np;
+    return PURIFY_OK;
+  }
+
+  // Re-bin the visibilities by (block, tile, cell) for R data blocks.
+  int set_blocks(const int* blocks, int R, cudaStream_t s) override {
+    if (R < 1 || R > 64 || (R > 1 && !blocks)) return PURIFY_ERR_INVALID;
+    std::vector<int> hb;
+    std::vector<int64_t> sizes(R, 0);
+    if (R > 1) {
+      hb.resize(size_t(g.M));
+      CK(cudaMemcpyAsync(hb.data(), blocks, hb.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int b : hb) {
+        if (b < 0 || b >= R) {
+          note_error("purify_op_set_blocks", __LINE__, "block index out of range");
+          return PURIFY_ERR_INVALID;
+        }
+        sizes[b] += 1;
+      }
+    } else {
+      sizes[0] = g.M;
+    }
+    WorkItem* new_items = nullptr;
+    int new_n = 0;
+    const int rc = build_bins<T>(uv_keep, g.M, g, chunk, pos, perm, &new_items, &new_n, s, blocks, R);
+    if (rc) {
+      note_error("uv binning failed", __LINE__, cudaGetErrorName(cudaGetLastError()));
+      return rc;
+    }
+    cudaFree(items);
+    items = new_items;
+    n_items = new_n;
+    nblocks = R;
+    block_sizes = sizes;
+    return size_partials();
+  }
+
   ~OpImpl() override {
     prof_release();
     if (own) cudaStreamSynchronize(own);
+    cudaFree(items);
     for (void* a : allocs) cudaFree(a);
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
@@ -262,10 +316,9 @@ template <typename T> class OpImpl : public purify_op {
       note_error("uv binning failed", __LINE__, cudaGetErrorName(cudaGetLastError()));
       return rc;
     }
-    allocs.push_back(items);
-    bytes += int64_t(n_items) * sizeof(WorkItem);
-    const int np = std::max({2 * n_items, row_inv_blocks(g), sara_partials_capacity(n, L), vec_blocks(9 * N()), 1});
-    if ((rc = alloc(&partials, np))) return rc;
+    block_sizes.assign(1, M);
+    if ((rc = size_partials())) return rc;
+    if ((rc = alloc(&eps_dev, 64)) || (rc = alloc(&scale_dev, 64))) return rc;
     if ((rc = alloc(&cg_part, 2 * kCgPart))) return rc;
     if ((rc = alloc(&tickets, 4))) return rc;
     CK(cudaMemsetAsync(tickets, 0, 4 * sizeof(unsigned int), s));
@@ -612,7 +665,8 @@ template <typename T> class OpImpl : public purify_op {
     dep.part0 = partials;
     dep.part1 = partials + n_items;
     degrid(dep, s);
-    fin(partials, n_items, partials + n_items, n_items, FIN_BALL, nu * eps, s);
+    PROF(KK_VEC, s, launch_finalize_blocks(partials, partials + n_items, reinterpret_cast<const int*>(items), n_items,
+                                           nblocks, nu, eps_dev, scale_dev, sc, s));
     zero_q(s);
     GridPro<C> gp{};
     gp.mode = GP_BALL;
@@ -621,6 +675,7 @@ template <typename T> class OpImpl : public purify_op {
     gp.nu = nu;
     gp.scalars = sc;
     gp.scale_idx = S_BALLSCALE;
+    gp.block_scale = scale_dev;
     grid(gp, s);
     col_inv(s);
     RowEp<T> ep{};
@@ -655,6 +710,15 @@ template <typename T> class OpImpl : public purify_op {
     CK(cudaEventCreate(&e1));
     CK(cudaEventRecord(e0, s));
     const size_t n2 = N(), M = size_t(g.M);
+    {
+      std::vector<double> eb(nblocks);
+      for (int b = 0; b < nblocks; ++b)
+        eb[b] = (nblocks > 1 && P->eps_blocks) ? P->eps_blocks[b]
+                                                : P->eps * std::sqrt(double(block_sizes[b]) / double(g.M));
+      for (double e : eb)
+        if (!(e > 0)) return PURIFY_ERR_INVALID;
+      CK(cudaMemcpyAsync(eps_dev, eb.data(), nblocks * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
     const int gmode = P->gram < 0 ? (g.n <= 1024 ? 1 : 0) : P->gram;
     if (gmode == 1 && (rc = ensure_toeplitz(s))) return rc;
     toep = gmode == 1;
@@ -730,8 +794,8 @@ template <typename T> class OpImpl : public purify_op {
         ++total_iters;
         if (P->xi > 0) {
           if ((rc = check(s, true)) || (rc = read_scalars(s))) break;
-          const double f = h_sc[S_OBJ], res = h_sc[S_RESID];
-          if (prev >= 0 && std::fabs(f - prev) / std::max(prev, 1e-300) < P->xi && res <= P->eps * (1 + 1e-3)) {
+          const double f = h_sc[S_OBJ], feas = h_sc[S_FEAS];
+          if (prev >= 0 && std::fabs(f - prev) / std::max(prev, 1e-300) < P->xi && feas <= 1 + 1e-3) {
             converged = 1;
             break;
           }
@@ -833,6 +897,11 @@ int purify_sara_fwd(purify_op* op, const void* x, void* c, void* stream) {
 int purify_sara_adj(purify_op* op, const void* c, void* x, void* stream) {
   if (!op || !x || !c) return PURIFY_ERR_INVALID;
   return op->sara_adj(c, x, static_cast<cudaStream_t>(stream));
+}
+
+int purify_op_set_blocks(purify_op* op, const int* block_ids, int R, void* stream) {
+  if (!op) return PURIFY_ERR_INVALID;
+  return op->set_blocks(block_ids, R, static_cast<cudaStream_t>(stream));
 }
 
 int purify_gram(purify_op* op, const void* x, void* out, int mode, void* stream) {

@@ -39,7 +39,7 @@ template <typename T> struct Pos;
 template <> struct Pos<float> { uint32_t u, v; };
 template <> struct Pos<double> { double u, v; };
 
-struct WorkItem { int tile, begin, end, pad; };
+struct WorkItem { int tile, begin, end, pad; };  // pad: visibility block of the item
 
 struct Geometry {
   int n, K, KP, pad_lo, TB, ntile1d;
@@ -117,6 +117,7 @@ template <typename C> struct GridPro {
   double nu;
   const double* scalars;
   int scale_idx;
+  const double* block_scale;  // per visibility block (R > 1), else null
 };
 
 // Record the detail returned by purify_last_error() on this thread.
@@ -173,9 +174,12 @@ void launch_gram(const Geometry& g, const CUtensorMap& map, const WorkItem* item
                  const KbPoly<T>& kb, typename cplx_t<T>::type* Q, int* err, cudaStream_t s);
 
 // uv binning (once per operator).  Fills pos/perm and returns the work list.
+// With R > 1 visibility blocks (device int32 block index per visibility, in
+// caller order), visibilities are binned by (block, tile, cell) and every work
+// item lies in one block (its `pad` field).
 template <typename T>
 int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>* pos, int* perm,
-               WorkItem** items_out, int* n_items_out, cudaStream_t s);
+               WorkItem** items_out, int* n_items_out, cudaStream_t s, const int* blocks = nullptr, int R = 1);
 
 // SARA dictionary.
 template <typename T>

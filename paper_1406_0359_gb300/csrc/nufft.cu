@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(kThreads) k_grid_w(Geometry g, const WorkItem*
   for (int e = lane; e < PW * PA; e += 32) wacc[e] = cz<C>();
   __syncwarp();
   T scale = 0;
-  if (gpro.mode == GP_BALL) scale = T(gpro.scalars[gpro.scale_idx]);
+  if (gpro.mode == GP_BALL) scale = T(gpro.block_scale ? gpro.block_scale[it.pad] : gpro.scalars[gpro.scale_idx]);
   const int ta = lane >> 2, tb = (lane & 3) * 2;
   int scell = -1;
   C s0 = cz<C>(), s1 = cz<C>();
@@ -675,8 +675,10 @@ PD void grid_cell(double u, int K, int& cell, double& f) {
 
 // Sort key: tile id, then the cell inside the tile (row-major), so that a
 // tile's visibilities come grouped by grid cell.
-__global__ void k_bin_keys(const double* __restrict__ uv, int64_t M, int K, int TB, int lb, int ntile1d,
-                           uint32_t* __restrict__ keys, int* __restrict__ vals) {
+// With visibility blocks (Eq. 4) the block index leads the key, so that every
+// work item lies in one block.
+__global__ void k_bin_keys(const double* __restrict__ uv, const int* __restrict__ blocks, int64_t M, int K, int TB,
+                           int lb, int ntile1d, int tbits, uint32_t* __restrict__ keys, int* __restrict__ vals) {
   const int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (m >= M) return;
   int cu, cv;
@@ -684,7 +686,8 @@ __global__ void k_bin_keys(const double* __restrict__ uv, int64_t M, int K, int 
   grid_cell(uv[2 * m], K, cu, fu);
   grid_cell(uv[2 * m + 1], K, cv, fv);
   const uint32_t tile = uint32_t((cu / TB) * ntile1d + (cv / TB));
-  keys[m] = (tile << (2 * lb)) | (uint32_t(cu % TB) << lb) | uint32_t(cv % TB);
+  const uint32_t blk = blocks ? uint32_t(blocks[m]) : 0u;
+  keys[m] = (blk << (tbits + 2 * lb)) | (tile << (2 * lb)) | (uint32_t(cu % TB) << lb) | uint32_t(cv % TB);
   vals[m] = int(m);
 }
 
@@ -793,18 +796,21 @@ __global__ void k_chunk_counts(const int* __restrict__ start, const int* __restr
   cnt[t] = (c + chunk - 1) / chunk;
 }
 
+// Bins are (block, tile) pairs, bin = block * tiles_per_block + tile; the
+// item records the tile and (in `pad`) the block.
 __global__ void k_fill_items(const int* __restrict__ start, const int* __restrict__ end,
-                             const int* __restrict__ off, int ntiles, int chunk, WorkItem* __restrict__ items) {
+                             const int* __restrict__ off, int nbins, int tiles_per_block, int chunk,
+                             WorkItem* __restrict__ items) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ntiles) return;
+  if (t >= nbins) return;
   const int s = start[t], e = end[t];
   int o = off[t];
   for (int b = s; b < e; b += chunk, ++o) {
     WorkItem w;
-    w.tile = t;
+    w.tile = t % tiles_per_block;
     w.begin = b;
     w.end = min(e, b + chunk);
-    w.pad = 0;
+    w.pad = t / tiles_per_block;
     items[o] = w;
   }
 }
@@ -909,12 +915,16 @@ void launch_gram(const Geometry& g, const CUtensorMap& map, const WorkItem* item
 
 template <typename T>
 int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>* pos, int* perm,
-               WorkItem** items_out, int* n_items_out, cudaStream_t s) {
-  const int ntiles = g.ntile1d * g.ntile1d;
+               WorkItem** items_out, int* n_items_out, cudaStream_t s, const int* blocks, int R) {
+  const int tiles_per_block = g.ntile1d * g.ntile1d;
+  const int ntiles = tiles_per_block * (R > 1 ? R : 1);  // bins
   int lb = 0;
   while ((1 << lb) < g.TB) ++lb;
-  int bits = 2 * lb;
-  while ((1 << (bits - 2 * lb)) < ntiles) ++bits;
+  int tbits = 0;
+  while ((1 << tbits) < tiles_per_block) ++tbits;
+  int rbits = 0;
+  while ((1 << rbits) < (R > 1 ? R : 1)) ++rbits;
+  const int bits = 2 * lb + tbits + rbits;
   const int passes = (bits + 7) / 8;
   const int nblocks = int((M + kSortTile - 1) / kSortTile);
   uint32_t *k0 = nullptr, *k1 = nullptr;
@@ -935,7 +945,8 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
   fail(cudaMalloc(&total, sizeof(int)));
   if (rc == 0) {
     const int tb = 256;
-    k_bin_keys<<<int((M + tb - 1) / tb), tb, 0, s>>>(uv, M, g.K, g.TB, lb, g.ntile1d, k0, perm);
+    k_bin_keys<<<int((M + tb - 1) / tb), tb, 0, s>>>(uv, R > 1 ? blocks : nullptr, M, g.K, g.TB, lb, g.ntile1d,
+                                                     tbits, k0, perm);
     uint32_t* kin = k0;
     uint32_t* kout = k1;
     int* vin = perm;
@@ -950,6 +961,8 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
     if (vin != perm) fail(cudaMemcpyAsync(perm, vin, M * sizeof(int), cudaMemcpyDeviceToDevice, s));
     fail(cudaMemsetAsync(tstart, 0, size_t(ntiles) * sizeof(int), s));
     fail(cudaMemsetAsync(tend, 0, size_t(ntiles) * sizeof(int), s));
+    // bin index = key >> 2 lb = block << tbits | tile; with tiles_per_block a power of
+    // two this equals block * tiles_per_block + tile
     k_tile_bounds<<<int((M + tb - 1) / tb), tb, 0, s>>>(kin, M, 2 * lb, tstart, tend);
     k_chunk_counts<<<(ntiles + tb - 1) / tb, tb, 0, s>>>(tstart, tend, ntiles, chunk, cnt);
     k_scan<<<1, 1024, 0, s>>>(cnt, ntiles, total);
@@ -961,7 +974,7 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
     fail(cudaMalloc(&items, size_t(h_total > 0 ? h_total : 1) * sizeof(WorkItem)));
     if (rc == 0) {
       const int tb = 256;
-      k_fill_items<<<(ntiles + tb - 1) / tb, tb, 0, s>>>(tstart, tend, cnt, ntiles, chunk, items);
+      k_fill_items<<<(ntiles + tb - 1) / tb, tb, 0, s>>>(tstart, tend, cnt, ntiles, tiles_per_block, chunk, items);
       k_encode<T><<<int((M + tb - 1) / tb), tb, 0, s>>>(uv, perm, M, g.K, g.TB, pos);
       fail(cudaStreamSynchronize(s));
       fail(cudaGetLastError());
@@ -1003,7 +1016,7 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
   template void launch_gram<T>(const Geometry&, const CUtensorMap&, const WorkItem*, int, const Pos<T>*,        \
                                const KbPoly<T>&, cplx_t<T>::type*, int*, cudaStream_t);                         \
   template int build_bins<T>(const double*, int64_t, const Geometry&, int, Pos<T>*, int*, WorkItem**, int*,     \
-                             cudaStream_t);
+                             cudaStream_t, const int*, int);
 INST(float)
 INST(double)
 #undef INST

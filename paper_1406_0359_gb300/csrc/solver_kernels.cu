@@ -88,6 +88,42 @@ __global__ void __launch_bounds__(kT) k_finalize(const double* __restrict__ pa, 
   }
 }
 
+// Per-block l2-ball scalars (Eq. 5): for every visibility block b, ||v - nu y||
+// and ||Phi x - y|| over the work items of that block (fixed order), the
+// projection scale min(1, nu eps_b / ||v - nu y||_b), the total residual and
+// the worst feasibility ratio max_b ||y_b - Phi_b x|| / eps_b.
+__global__ void __launch_bounds__(kT) k_finalize_blocks(const double* __restrict__ part0,
+                                                        const double* __restrict__ part1,
+                                                        const int* __restrict__ item_block, int n_items, int R,
+                                                        double nu, const double* __restrict__ eps_b,
+                                                        double* __restrict__ scale_b, double* __restrict__ sc) {
+  __shared__ double red[32];
+  double tot1 = 0.0, worst = 0.0;
+  for (int b = 0; b < R; ++b) {
+    double a = 0.0, c = 0.0;
+    for (int i = threadIdx.x; i < n_items; i += kT) {
+      if (item_block[4 * i] == b) {  // WorkItem::pad
+        a += part0[i];
+        c += part1[i];
+      }
+    }
+    a = block_sum<kT>(a, red);
+    c = block_sum<kT>(c, red);
+    if (threadIdx.x == 0) {
+      const double s = sqrt(a), rad = nu * eps_b[b];
+      scale_b[b] = s <= rad ? 1.0 : rad / s;
+      tot1 += c;
+      const double ratio = sqrt(c) / eps_b[b];
+      worst = ratio > worst ? ratio : worst;
+    }
+  }
+  if (threadIdx.x == 0) {
+    sc[S_RESID] = sqrt(tot1);
+    sc[S_FEAS] = worst;
+    sc[S_BALLSCALE] = scale_b[0];
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kT) k_sum_partials(const T* __restrict__ v, size_t N, int op,
                                                      const double* __restrict__ sc, double* __restrict__ partials) {
@@ -169,6 +205,11 @@ int launch_reduce(const T* v, size_t N, int op, const double* sc, double* partia
   const int b = nblk(N);
   k_sum_partials<T><<<b, kT, 0, s>>>(v, N, op, sc, partials);
   return b;
+}
+
+void launch_finalize_blocks(const double* part0, const double* part1, const int* items_as_int, int n_items, int R,
+                            double nu, const double* eps_b, double* scale_b, double* sc, cudaStream_t s) {
+  k_finalize_blocks<<<1, kT, 0, s>>>(part0, part1, items_as_int + 3, n_items, R, nu, eps_b, scale_b, sc);
 }
 
 void launch_max_partials(const double* p, int np, double* sc, cudaStream_t s) {

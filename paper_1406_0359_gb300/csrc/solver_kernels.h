@@ -10,7 +10,7 @@ namespace purify {
 // Device scalar slots (double[kNumScalars]).
 enum ScalarSlot : int {
   S_RR = 0, S_ALPHA, S_BETA, S_PAP, S_BALLSCALE, S_BALLNORM, S_RESID, S_OBJ,
-  S_LAMBDA, S_INVNORM, S_MEAN, S_STD, S_MAXABS, kNumScalars
+  S_LAMBDA, S_INVNORM, S_MEAN, S_STD, S_MAXABS, S_FEAS, kNumScalars
 };
 enum FinOp : int { FIN_RR0 = 0, FIN_ALPHA, FIN_BETA, FIN_BALL, FIN_OBJ, FIN_NORM, FIN_MEAN, FIN_VAR, FIN_MAX };
 enum RedOp : int { RED_SQ = 0, RED_SUM, RED_VAR, RED_MAXABS };
@@ -27,6 +27,10 @@ void launch_finalize(const double* pa, int na, const double* pb, int nb, int op,
 template <typename T>
 int launch_reduce(const T* v, size_t N, int op, const double* sc, double* partials, cudaStream_t s);
 void launch_max_partials(const double* p, int np, double* sc, cudaStream_t s);
+// Ball scalars per visibility block; items_as_int points at the WorkItem array
+// (four ints per item, the block in the fourth).
+void launch_finalize_blocks(const double* part0, const double* part1, const int* items_as_int, int n_items, int R,
+                            double nu, const double* eps_b, double* scale_b, double* sc, cudaStream_t s);
 template <typename T> void launch_reweight(T* w, size_t N, double delta, cudaStream_t s);
 template <typename T> void launch_fill(T* v, size_t N, T val, cudaStream_t s);
 template <typename T> void launch_scale(T* v, size_t N, const double* sc, int idx, double mul, cudaStream_t s);

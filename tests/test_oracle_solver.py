@@ -190,3 +190,53 @@ def test_sara_outer_loop_runs_and_is_feasible():
     assert len(rounds) == 3
     assert np.linalg.norm(T["y"] - T["dop"].phi(x)) <= T["eps"] * 1.01
     assert x.min() >= -1e-6
+
+
+# ---------------------------------------------------------------- R blocks (Eq. 4-5)
+def _split(M, R, seed=0):
+    perm = np.random.default_rng(seed).permutation(M)
+    return [np.sort(perm[i::R]) for i in range(R)]
+
+
+def test_single_block_equals_unblocked():
+    T = tiny_problem()
+    w = np.ones(9 * 64)
+    g = 10.0 * S.default_gamma(T["dop"], T["dpsi"], T["y"], T["nu"])
+    a = S.sdmm(T["dop"], T["dpsi"], T["y"], T["eps"], g, w, 40, 10, T["nu"])
+    b = S.sdmm(T["dop"], T["dpsi"], T["y"], T["eps"], g, w, 40, 10, T["nu"],
+               blocks=([np.arange(T["M"])], [T["eps"]]))
+    assert np.array_equal(a.x, b.x)
+
+
+def test_blocks_each_feasible_zero():
+    T = tiny_problem()
+    idx = _split(T["M"], 3)
+    radii = [1.01 * np.linalg.norm(T["y"][i]) for i in idx]
+    st = S.sdmm(T["dop"], T["dpsi"], T["y"], T["eps"], 1e-3, np.ones(9 * 64), 30, 10, T["nu"],
+                blocks=(idx, radii))
+    assert np.all(st.x == 0.0)
+
+
+@pytest.mark.slow
+def test_blocked_sdmm_closes_duality_gap():
+    """R = 3 blocks with eps_i = eps sqrt(M_i / M): the Fenchel dual now has one
+    ball term per block, -sum_i (Re<u_i, nu y_i> + nu eps_i ||u_i||)."""
+    T = tiny_problem()
+    M, nu = T["M"], T["nu"]
+    idx = _split(M, 3)
+    radii = [T["eps"] * np.sqrt(len(i) / M) for i in idx]
+    w = np.random.default_rng(1).uniform(0.5, 1.5, 9 * 64)
+    gamma = 10.0 * S.default_gamma(T["dop"], T["dpsi"], T["y"], nu)
+    st = S.sdmm(T["dop"], T["dpsi"], T["y"], T["eps"], gamma, w, 2000, 20, nu, blocks=(idx, radii))
+    u1 = np.clip(st.z1 / gamma, -w, w)
+    u3 = st.z3 / gamma
+    s = T["dpsi"].synthesis(u1) + nu * T["dop"].phi_adj_real(u3)
+    u2 = np.minimum(-s, 0.0)
+    resid = np.linalg.norm(s + u2) / np.linalg.norm(T["dpsi"].synthesis(u1))
+    dual = -sum(np.real(np.vdot(u3[i], nu * T["y"][i])) + nu * e * np.linalg.norm(u3[i]) for i, e in zip(idx, radii))
+    primal = float(np.sum(w * np.abs(T["dpsi"].analysis(st.x))))
+    # weak duality up to the residual infeasibility of both iterates
+    assert -1e-9 <= (primal - dual) / primal < 1e-5
+    assert resid < 1e-3
+    for i, e in zip(idx, radii):
+        assert np.linalg.norm(T["y"][i] - T["dop"].phi(st.x)[i]) <= e * (1 + 1e-5)
