@@ -221,6 +221,36 @@ int purify_profile(purify_op* op, int enable);
 int purify_profile_read(purify_op* op, int kind, double* total_ms, int64_t* launches);
 const char* purify_kernel_name(int kind);
 
+/*
+ * Request server (continuous batching; the paper has no counterpart -- it is
+ * the serving form of Algorithm 1 for many independent imaging requests).
+ * Requests wait in a FIFO queue; each scheduling round admits queued requests
+ * while a slot is free and their estimated device memory
+ * (purify_estimate_bytes) fits the budget, keeps each admitted solve's image,
+ * dual variables and sorted uv tiles resident on the device, and advances
+ * every admitted solve by one SDMM iteration on its own stream so that their
+ * kernels overlap.  A finished solve frees its slot and memory for the next
+ * round.  The caller drives rounds with purify_server_step; not thread-safe.
+ * All solves run on the current device (at create time).
+ */
+typedef struct purify_server purify_server;
+int purify_server_create(int64_t budget_bytes, int max_slots, purify_server** out);
+int purify_server_destroy(purify_server* srv);
+/* Copies uv (host double[M][2]) and y (host complex[M] of the precision) and
+ * queues the request; PURIFY_ERR_BUDGET if it can never fit the budget. */
+int purify_server_submit(purify_server* srv, const double* uv_host, const void* y_host, int64_t M, int n,
+                         int dwt_levels, int precision, const purify_params* params, int* request_id);
+/* One scheduling round; reports how many solves are active and queued after it. */
+int purify_server_step(purify_server* srv, int* n_active, int* n_queued);
+/* 1 and the image (host real[n][n]), stats, latency (submit to done) and
+ * queueing time (submit to admission) when the request has finished; 0 while
+ * it is queued or running; its negative status if it failed. */
+int purify_server_result(purify_server* srv, int request_id, void* x_host, purify_stats* stats,
+                         double* latency_s, double* queue_s);
+/* Device bytes an operator plus solver state of this size may hold (an upper
+ * bound used for admission, including the transient PSF set-up). */
+int purify_estimate_bytes(int64_t M, int n, int dwt_levels, int precision, int64_t* bytes);
+
 /* purify_default_params -- the defaults described in purify_params. */
 void purify_default_params(purify_params* p);
 

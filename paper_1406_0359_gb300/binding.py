@@ -52,7 +52,9 @@ class purify_stats(ctypes.Structure):
 EXPORTS = ["purify_op_create", "purify_op_destroy", "purify_op_info", "purify_phi", "purify_phi_adj",
            "purify_sara_fwd", "purify_sara_adj", "purify_sdmm_solve", "purify_default_params",
            "purify_strerror", "purify_profile", "purify_profile_read", "purify_kernel_name",
-           "purify_last_error", "purify_sara_fwd_static", "purify_gram", "purify_op_set_blocks"]
+           "purify_last_error", "purify_sara_fwd_static", "purify_gram", "purify_op_set_blocks",
+           "purify_server_create", "purify_server_destroy", "purify_server_submit", "purify_server_step",
+           "purify_server_result", "purify_estimate_bytes"]
 KERNEL_KINDS = ["row_fwd", "col_fwd", "degrid", "grid", "gram", "col_inv", "row_inv", "sara_analysis",
                 "sara_synthesis", "vector", "memset", "col_conv"]
 
@@ -87,6 +89,14 @@ def lib() -> ctypes.CDLL:
     L.purify_sara_fwd_static.argtypes = [vp, vp, ci, ci, vp]
     L.purify_gram.argtypes = [vp, vp, vp, ci, vp]
     L.purify_op_set_blocks.argtypes = [vp, vp, ci, vp]
+    L.purify_server_create.argtypes = [i64, ci, ctypes.POINTER(vp)]
+    L.purify_server_destroy.argtypes = [vp]
+    L.purify_server_submit.argtypes = [vp, vp, vp, i64, ci, ci, ci, ctypes.POINTER(purify_params),
+                                       ctypes.POINTER(ci)]
+    L.purify_server_step.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci)]
+    L.purify_server_result.argtypes = [vp, ci, vp, ctypes.POINTER(purify_stats), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]
+    L.purify_estimate_bytes.argtypes = [i64, ci, ci, ci, ctypes.POINTER(i64)]
     L.purify_last_error.argtypes = []
     L.purify_last_error.restype = ctypes.c_char_p
     for f in EXPORTS:
@@ -299,6 +309,71 @@ class Operator:
         rc, st = purify_sdmm_solve(self.h, _dptr(y, self.cdtype, (self.M,)), p, _dptr(x, self.rdtype, (n, n)),
                                    stream)
         return SolveResult(x, st.as_dict(), rc)
+
+
+def purify_estimate_bytes(M: int, n: int, levels: int, precision: int = PURIFY_FP32) -> int:
+    b = ctypes.c_int64()
+    _check(lib().purify_estimate_bytes(M, n, levels, precision, ctypes.byref(b)), "purify_estimate_bytes")
+    return b.value
+
+
+class Server:
+    """Continuous-batching request server (C-ABI purify_server_*).  Requests
+    are host arrays; results come back as host arrays."""
+
+    def __init__(self, budget_bytes: int, max_slots: int):
+        self.h = ctypes.c_void_p()
+        _check(lib().purify_server_create(int(budget_bytes), int(max_slots), ctypes.byref(self.h)),
+               "purify_server_create")
+        self.meta = {}
+
+    def close(self) -> None:
+        if self.h:
+            lib().purify_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, uv, y, n: int, levels: int, eps: float, precision: str = "fp32", **kw) -> int:
+        import numpy as np
+
+        prec = PURIFY_FP32 if precision == "fp32" else PURIFY_FP64
+        uv = np.ascontiguousarray(uv, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.complex64 if prec == PURIFY_FP32 else np.complex128)
+        p = purify_default_params()
+        p.eps = eps
+        for k, v in kw.items():
+            setattr(p, k, v)
+        rid = ctypes.c_int()
+        _check(lib().purify_server_submit(self.h, uv.ctypes.data_as(ctypes.c_void_p),
+                                          y.ctypes.data_as(ctypes.c_void_p), uv.shape[0], n, levels, prec,
+                                          ctypes.byref(p), ctypes.byref(rid)), "purify_server_submit")
+        self.meta[rid.value] = (n, prec)
+        return rid.value
+
+    def step(self) -> tuple[int, int]:
+        a, q = ctypes.c_int(), ctypes.c_int()
+        _check(lib().purify_server_step(self.h, ctypes.byref(a), ctypes.byref(q)), "purify_server_step")
+        return a.value, q.value
+
+    def result(self, rid: int):
+        """None while pending, else (image, stats, latency_s, queue_s)."""
+        import numpy as np
+
+        n, prec = self.meta[rid]
+        x = np.empty((n, n), dtype=np.float32 if prec == PURIFY_FP32 else np.float64)
+        st = purify_stats()
+        lat, qs = ctypes.c_double(), ctypes.c_double()
+        rc = lib().purify_server_result(self.h, rid, x.ctypes.data_as(ctypes.c_void_p), ctypes.byref(st),
+                                        ctypes.byref(lat), ctypes.byref(qs))
+        if rc == 0:
+            return None
+        _check(rc if rc < 0 else 0, "purify_server_result")
+        return x, st.as_dict(), lat.value, qs.value
 
 
 def solve_from_host(uv_host, y_host, n: int, levels: int, eps: float, precision: str = "fp32",

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpurify_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "fft.cu", "nufft.cu", "sara.cu", "solver_kernels.cu", "host_math.cpp"]
+SOURCES = ["api.cu", "fft.cu", "nufft.cu", "sara.cu", "solver_kernels.cu", "host_math.cpp", "server.cpp"]
 
 
 def _nvcc() -> str:
@@ -46,7 +46,7 @@ def _compile(src: str, verbose: bool) -> str:
             cmd += ["-Xptxas", "-v"]
     else:
         cmd = [nvcc, "-x", "c++", "-c", os.path.join(CSRC, src), "-o", obj, "-O2", "-std=c++17",
-               "-Xcompiler", "-fPIC"]
+               "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -15,73 +15,7 @@
 #include "internal.h"
 #include "solver_kernels.h"
 
-struct purify_op {
-  virtual ~purify_op() {}
-  virtual int phi(const void* x, void* y, cudaStream_t s) = 0;
-  virtual int phi_adj(const void* y, void* x, cudaStream_t s) = 0;
-  virtual int sara_fwd(const void* x, void* c, cudaStream_t s) = 0;
-  virtual int sara_adj(const void* c, void* x, cudaStream_t s) = 0;
-  virtual int solve(const void* y, const purify_params* p, void* x, purify_stats* st, cudaStream_t s) = 0;
-  virtual int gram(const void* x, void* out, int mode, cudaStream_t s) = 0;
-  virtual int set_blocks(const int* blocks, int R, cudaStream_t s) = 0;
-  virtual void info(int* n, int64_t* M, int* K, int* tile, int* n_items, int* precision, int64_t* bytes) const = 0;
-
-  // ---- kernel timing (instrumentation)
-  enum Kind { KK_ROW_FWD = 0, KK_COL_FWD, KK_DEGRID, KK_GRID, KK_GRAM, KK_COL_INV, KK_ROW_INV, KK_SARA_ANA,
-              KK_SARA_SYN, KK_VEC, KK_MEMSET, KK_COL_CONV, KK_COUNT };
-  bool prof = false;
-  struct Pending { int kind; cudaEvent_t a, b; };
-  std::vector<Pending> pending;
-  std::vector<cudaEvent_t> pool;
-  double prof_ms[KK_COUNT] = {0};
-  int64_t prof_n[KK_COUNT] = {0};
-  cudaStream_t prof_stream = nullptr;
-  int prof_kind = -1;
-  cudaEvent_t ev() {
-    if (!pool.empty()) {
-      cudaEvent_t e = pool.back();
-      pool.pop_back();
-      return e;
-    }
-    cudaEvent_t e = nullptr;
-    cudaEventCreate(&e);
-    return e;
-  }
-  void prof_begin(int kind, cudaStream_t s) {
-    if (!prof) return;
-    Pending p{kind, ev(), ev()};
-    cudaEventRecord(p.a, s);
-    pending.push_back(p);
-  }
-  void prof_end(cudaStream_t s) {
-    if (!prof || pending.empty()) return;
-    cudaEventRecord(pending.back().b, s);
-  }
-  void prof_collect() {
-    for (auto& p : pending) {
-      float ms = 0.f;
-      if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-        prof_ms[p.kind] += ms;
-        prof_n[p.kind] += 1;
-      }
-      pool.push_back(p.a);
-      pool.push_back(p.b);
-    }
-    pending.clear();
-  }
-  void prof_reset() {
-    prof_collect();
-    for (int k = 0; k < KK_COUNT; ++k) {
-      prof_ms[k] = 0;
-      prof_n[k] = 0;
-    }
-  }
-  void prof_release() {
-    prof_collect();
-    for (cudaEvent_t e : pool) cudaEventDestroy(e);
-    pool.clear();
-  }
-};
+#include "op.h"
 
 #define PROF(kind, stream, stmt) \
   do {                           \
@@ -224,6 +158,7 @@ template <typename T> class OpImpl : public purify_op {
   }
 
   ~OpImpl() override {
+    run_release();
     prof_release();
     if (own) cudaStreamSynchronize(own);
     cudaFree(items);
@@ -686,150 +621,221 @@ template <typename T> class OpImpl : public purify_op {
     row_ep(ep, s);
   }
 
-  // The solve runs on the operator's own stream (the caller's stream may be the
-  // legacy default stream, which cannot be captured into a graph), ordered
-  // after the caller's prior work and before its later work by events.
-  int solve(const void* y, const purify_params* P, void* x_out, purify_stats* st, cudaStream_t user) override {
+  // ---- resumable solve: begin, then (launch one iteration, check) pairs, then
+  // end.  The blocking purify_sdmm_solve and the request server share it.
+  // Everything runs on the operator's own stream (the caller's stream may be
+  // the legacy default stream, which cannot be captured into a graph),
+  // ordered after the caller's prior work and before its later work by events.
+  struct Run {
+    purify_params P{};
+    std::vector<double> eps_b;
+    double nu = 0, gamma = 0, decay = 0.1, delta1 = 0, prev = -1;
+    int round = 0, t = 0, total = 0, converged = 0;
+    bool active = false, round_ready = false;
+    cudaGraphExec_t gexec = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, ev_sc = nullptr;
+  } run;
+
+  void run_release() {
+    if (run.gexec) cudaGraphExecDestroy(run.gexec);
+    if (run.e0) cudaEventDestroy(run.e0);
+    if (run.e1) cudaEventDestroy(run.e1);
+    if (run.ev_sc) cudaEventDestroy(run.ev_sc);
+    run.gexec = nullptr;
+    run.e0 = run.e1 = run.ev_sc = nullptr;
+    run.active = false;
+  }
+
+  int begin(const void* y, const purify_params* P, cudaStream_t user) override {
     if (!(P->eps > 0) || P->t_max < 1 || P->cg_iters < 1 || P->n_reweight < 0 || P->xi < 0 ||
         (P->nu <= 0 && P->power_iters < 1))
       return PURIFY_ERR_INVALID;
+    if (run.active) run_release();
     int rc = ensure_solver();
     if (rc) return rc;
+    cudaStream_t s = own;
     CK(cudaEventRecord(ev_in, user));
-    CK(cudaStreamWaitEvent(own, ev_in, 0));
-    rc = solve_on(y, P, x_out, st, own);
-    cudaEventRecord(ev_out, own);
-    cudaStreamWaitEvent(user, ev_out, 0);
-    return rc;
-  }
-
-  int solve_on(const void* y, const purify_params* P, void* x_out, purify_stats* st, cudaStream_t s) {
-    int rc = PURIFY_OK;
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    CK(cudaEventRecord(e0, s));
+    CK(cudaStreamWaitEvent(s, ev_in, 0));
+    run = Run();
+    run.P = *P;
+    run.P.eps_blocks = nullptr;
+    CK(cudaEventCreate(&run.e0));
+    CK(cudaEventCreate(&run.e1));
+    CK(cudaEventCreateWithFlags(&run.ev_sc, cudaEventDisableTiming));
+    CK(cudaEventRecord(run.e0, s));
     const size_t n2 = N(), M = size_t(g.M);
-    {
-      std::vector<double> eb(nblocks);
-      for (int b = 0; b < nblocks; ++b)
-        eb[b] = (nblocks > 1 && P->eps_blocks) ? P->eps_blocks[b]
-                                                : P->eps * std::sqrt(double(block_sizes[b]) / double(g.M));
-      for (double e : eb)
-        if (!(e > 0)) return PURIFY_ERR_INVALID;
-      CK(cudaMemcpyAsync(eps_dev, eb.data(), nblocks * sizeof(double), cudaMemcpyHostToDevice, s));
-    }
+    run.eps_b.resize(nblocks);
+    for (int b = 0; b < nblocks; ++b)
+      run.eps_b[b] = (nblocks > 1 && P->eps_blocks) ? P->eps_blocks[b]
+                                                     : P->eps * std::sqrt(double(block_sizes[b]) / double(g.M));
+    for (double e : run.eps_b)
+      if (!(e > 0)) return PURIFY_ERR_INVALID;
+    CK(cudaMemcpyAsync(eps_dev, run.eps_b.data(), nblocks * sizeof(double), cudaMemcpyHostToDevice, s));
     const int gmode = P->gram < 0 ? (g.n <= 1024 ? 1 : 0) : P->gram;
     if (gmode == 1 && (rc = ensure_toeplitz(s))) return rc;
     toep = gmode == 1;
     launch_gather<C>(static_cast<const C*>(y), perm, M, ys, s);
-    double nu = P->nu;
-    if (!(nu > 0)) {
+    run.nu = P->nu;
+    if (!(run.nu > 0)) {
       double lam = 0;
       if ((rc = power_norm_sq(P->power_iters, &lam, s))) return rc;
-      nu = lam > 0 ? 1.0 / std::sqrt(lam) : 1.0;
+      run.nu = lam > 0 ? 1.0 / std::sqrt(lam) : 1.0;
     }
-    double gamma = P->gamma;
-    if (!(gamma > 0)) {
-      if ((rc = default_gamma(nu, &gamma, s))) return rc;
-      if (!(gamma > 0)) gamma = 1e-12;
+    run.gamma = P->gamma;
+    if (!(run.gamma > 0)) {
+      if ((rc = default_gamma(run.nu, &run.gamma, s))) return rc;
+      if (!(run.gamma > 0)) run.gamma = 1e-12;
     }
-    const double decay = P->delta_decay > 0 ? P->delta_decay : 0.1;
-    double delta1 = 0.0;
-    int total_iters = 0, converged = 0;
-    double obj = 0.0, resid = 0.0;
-    cudaGraphExec_t gexec = nullptr;
+    run.decay = P->delta_decay > 0 ? P->delta_decay : 0.1;
     if (P->use_graph && !prof) {
       cudaGraph_t graph = nullptr;
       CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      iteration(nu, gamma, P->eps, P->cg_iters, s);
+      iteration(run.nu, run.gamma, P->eps, P->cg_iters, s);
       cudaError_t ce = cudaStreamEndCapture(s, &graph);
       if (ce != cudaSuccess) return map_err(ce, __LINE__);
-      ce = cudaGraphInstantiate(&gexec, graph, 0);
+      ce = cudaGraphInstantiate(&run.gexec, graph, 0);
       cudaGraphDestroy(graph);
       if (ce != cudaSuccess) return map_err(ce, __LINE__);
     }
     launch_fill<T>(w, 9 * n2, T(1), s);
     CK(cudaMemsetAsync(xh, 0, n2 * sizeof(T), s));
-    for (int round = 0; round <= P->n_reweight; ++round) {
-      if (round > 0) {
-        if (round == 1) {
-          if (P->delta0 > 0) {
-            delta1 = P->delta0;
-          } else {
-            if ((rc = coef_std(&delta1, s))) break;
-          }
-          if (!(delta1 > 0)) delta1 = 1.0;
+    run.active = true;
+    return check(s, false);
+  }
+
+  // Round set-up (Algorithm 1 steps 1-3; SARA weights from the previous round).
+  int start_round(cudaStream_t s) {
+    const size_t n2 = N(), M = size_t(g.M);
+    const purify_params& P = run.P;
+    int rc;
+    if (run.round > 0) {
+      if (run.round == 1) {
+        if (P.delta0 > 0) {
+          run.delta1 = P.delta0;
+        } else if ((rc = coef_std(&run.delta1, s))) {
+          return rc;
         }
-        const double dmin = P->delta_min > 0 ? P->delta_min : 1e-4 * delta1;
-        const double delta = std::max(std::pow(decay, round - 1) * delta1, dmin);
-        sara_analysis<T>(sara, xh, w, s);
-        launch_reweight<T>(w, 9 * n2, delta, s);
+        if (!(run.delta1 > 0)) run.delta1 = 1.0;
       }
-      cudaMemsetAsync(z1, 0, 9 * n2 * sizeof(T), s);
-      cudaMemsetAsync(z2, 0, n2 * sizeof(T), s);
-      cudaMemsetAsync(z3, 0, M * sizeof(C), s);
-      if (round > 0 && P->warm_start) {
-        // steps 1-3 with x_hat^(0) = previous solution: sum_i x_i = (Phi^H Phi + 2I) x_hat^(0)
-        normal_front(plain(xh), s);
-        RowEp<T> ep{};
-        ep.mode = EP_QX;
-        ep.out = xs;
-        ep.p = xh;
-        ep.nu2 = nu * nu;
-        normal_back(ep, s);
+      const double dmin = P.delta_min > 0 ? P.delta_min : 1e-4 * run.delta1;
+      const double delta = std::max(std::pow(run.decay, run.round - 1) * run.delta1, dmin);
+      sara_analysis<T>(sara, xh, w, s);
+      launch_reweight<T>(w, 9 * n2, delta, s);
+    }
+    cudaMemsetAsync(z1, 0, 9 * n2 * sizeof(T), s);
+    cudaMemsetAsync(z2, 0, n2 * sizeof(T), s);
+    cudaMemsetAsync(z3, 0, M * sizeof(C), s);
+    if (run.round > 0 && P.warm_start) {
+      // steps 1-3 with x_hat^(0) = previous solution: sum_i x_i = (Phi^H Phi + 2I) x_hat^(0)
+      normal_front(plain(xh), s);
+      RowEp<T> ep{};
+      ep.mode = EP_QX;
+      ep.out = xs;
+      ep.p = xh;
+      ep.nu2 = run.nu * run.nu;
+      normal_back(ep, s);
+    } else {
+      cudaMemsetAsync(xh, 0, n2 * sizeof(T), s);
+      cudaMemsetAsync(xs, 0, n2 * sizeof(T), s);
+    }
+    run.t = 0;
+    run.prev = -1.0;
+    run.converged = 0;
+    run.round_ready = true;
+    return check(s, false);
+  }
+
+  // Enqueue one SDMM iteration (after the round set-up when a round starts).
+  int step_launch() override {
+    if (!run.active) return PURIFY_ERR_INVALID;
+    cudaStream_t s = own;
+    int rc;
+    if (!run.round_ready && (rc = start_round(s))) return rc;
+    if (run.gexec) {
+      CK(cudaGraphLaunch(run.gexec, s));
+    } else {
+      iteration(run.nu, run.gamma, run.P.eps, run.P.cg_iters, s);
+    }
+    if (run.P.xi > 0) {
+      CK(cudaMemcpyAsync(h_sc, sc, kNumScalars * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaEventRecord(run.ev_sc, s));
+    }
+    return check(s, false);
+  }
+
+  // After the launched iteration: the halting test (Section 3) and the round
+  // bookkeeping; *done = 1 when the last round has finished.
+  int step_check(int* done) override {
+    *done = 0;
+    if (!run.active) return PURIFY_ERR_INVALID;
+    ++run.t;
+    ++run.total;
+    if (run.P.xi > 0) {
+      CK(cudaEventSynchronize(run.ev_sc));
+      const double f = h_sc[S_OBJ], feas = h_sc[S_FEAS];
+      if (run.prev >= 0 && std::fabs(f - run.prev) / std::max(run.prev, 1e-300) < run.P.xi && feas <= 1 + 1e-3)
+        run.converged = 1;
+      run.prev = f;
+    }
+    if (run.converged || run.t >= run.P.t_max) {
+      if (run.round >= run.P.n_reweight) {
+        *done = 1;
       } else {
-        cudaMemsetAsync(xh, 0, n2 * sizeof(T), s);
-        cudaMemsetAsync(xs, 0, n2 * sizeof(T), s);
+        ++run.round;
+        run.round_ready = false;
       }
-      if ((rc = check(s, false))) break;
-      double prev = -1.0;
-      converged = 0;
-      for (int t = 0; t < P->t_max; ++t) {
-        if (gexec) {
-          CK(cudaGraphLaunch(gexec, s));
-        } else {
-          iteration(nu, gamma, P->eps, P->cg_iters, s);
-        }
-        ++total_iters;
-        if (P->xi > 0) {
-          if ((rc = check(s, true)) || (rc = read_scalars(s))) break;
-          const double f = h_sc[S_OBJ], feas = h_sc[S_FEAS];
-          if (prev >= 0 && std::fabs(f - prev) / std::max(prev, 1e-300) < P->xi && feas <= 1 + 1e-3) {
-            converged = 1;
-            break;
-          }
-          prev = f;
-        }
-      }
-      if (rc) break;
     }
-    if (gexec) cudaGraphExecDestroy(gexec);
-    if (rc) return rc;
-    CK(cudaMemcpyAsync(x_out, xh, n2 * sizeof(T), cudaMemcpyDeviceToDevice, s));
-    CK(cudaEventRecord(e1, s));
-    if ((rc = check(s, true))) return rc;
-    if ((rc = read_scalars(s))) return rc;
-    prof_collect();
-    obj = h_sc[S_OBJ];
-    resid = h_sc[S_RESID];
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (st) {
-      st->iterations = total_iters;
-      st->rounds = P->n_reweight + 1;
-      st->converged = converged;
-      st->objective = obj;
-      st->residual = resid;
-      st->nu = nu;
-      st->gamma = gamma;
-      st->elapsed_ms = ms;
-    }
-    if (P->xi > 0 && !converged) return PURIFY_ERR_NOT_CONVERGED;
     return PURIFY_OK;
   }
+
+  int end(void* x_out, purify_stats* st, cudaStream_t user) override {
+    if (!run.active) return PURIFY_ERR_INVALID;
+    cudaStream_t s = own;
+    int rc = PURIFY_OK;
+    const size_t n2 = N();
+    cudaError_t e = cudaMemcpyAsync(x_out, xh, n2 * sizeof(T), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(run.e1, s);
+    if (e != cudaSuccess) rc = map_err(e, __LINE__);
+    if (!rc) rc = check(s, true);
+    if (!rc) rc = read_scalars(s);
+    prof_collect();
+    float ms = 0.f;
+    if (!rc) cudaEventElapsedTime(&ms, run.e0, run.e1);
+    if (!rc && st) {
+      st->iterations = run.total;
+      st->rounds = run.round + 1;
+      st->converged = run.converged;
+      st->objective = h_sc[S_OBJ];
+      st->residual = h_sc[S_RESID];
+      st->nu = run.nu;
+      st->gamma = run.gamma;
+      st->elapsed_ms = ms;
+    }
+    const bool not_conv = run.P.xi > 0 && !run.converged;
+    run_release();
+    cudaEventRecord(ev_out, s);
+    cudaStreamWaitEvent(user, ev_out, 0);
+    if (rc) return rc;
+    return not_conv ? PURIFY_ERR_NOT_CONVERGED : PURIFY_OK;
+  }
+
+  int solve(const void* y, const purify_params* P, void* x_out, purify_stats* st, cudaStream_t user) override {
+    int rc = begin(y, P, user);
+    int done = 0;
+    while (!rc && !done) {
+      rc = step_launch();
+      if (!rc) rc = step_check(&done);
+    }
+    if (rc) {
+      if (run.active) run_release();
+      cudaEventRecord(ev_out, own);
+      cudaStreamWaitEvent(user, ev_out, 0);
+      return rc;
+    }
+    return end(x_out, st, user);
+  }
+
+  cudaStream_t stream() const override { return own; }
 };
 
 }  // namespace

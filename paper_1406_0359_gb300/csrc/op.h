@@ -1,0 +1,84 @@
+// The operator object behind the opaque purify_op handle: the virtual
+// interface implemented per precision in api.cu, plus kernel-timing state.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/purify.h"
+
+struct purify_op {
+  virtual ~purify_op() {}
+  virtual int phi(const void* x, void* y, cudaStream_t s) = 0;
+  virtual int phi_adj(const void* y, void* x, cudaStream_t s) = 0;
+  virtual int sara_fwd(const void* x, void* c, cudaStream_t s) = 0;
+  virtual int sara_adj(const void* c, void* x, cudaStream_t s) = 0;
+  virtual int solve(const void* y, const purify_params* p, void* x, purify_stats* st, cudaStream_t s) = 0;
+  virtual int gram(const void* x, void* out, int mode, cudaStream_t s) = 0;
+  virtual int set_blocks(const int* blocks, int R, cudaStream_t s) = 0;
+  // resumable solve (request server)
+  virtual int begin(const void* y, const purify_params* p, cudaStream_t user) = 0;
+  virtual int step_launch() = 0;
+  virtual int step_check(int* done) = 0;
+  virtual int end(void* x, purify_stats* st, cudaStream_t user) = 0;
+  virtual cudaStream_t stream() const = 0;
+  virtual void info(int* n, int64_t* M, int* K, int* tile, int* n_items, int* precision, int64_t* bytes) const = 0;
+
+  // ---- kernel timing (instrumentation)
+  enum Kind { KK_ROW_FWD = 0, KK_COL_FWD, KK_DEGRID, KK_GRID, KK_GRAM, KK_COL_INV, KK_ROW_INV, KK_SARA_ANA,
+              KK_SARA_SYN, KK_VEC, KK_MEMSET, KK_COL_CONV, KK_COUNT };
+  bool prof = false;
+  struct Pending { int kind; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[KK_COUNT] = {0};
+  int64_t prof_n[KK_COUNT] = {0};
+  cudaStream_t prof_stream = nullptr;
+  int prof_kind = -1;
+  cudaEvent_t ev() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void prof_begin(int kind, cudaStream_t s) {
+    if (!prof) return;
+    Pending p{kind, ev(), ev()};
+    cudaEventRecord(p.a, s);
+    pending.push_back(p);
+  }
+  void prof_end(cudaStream_t s) {
+    if (!prof || pending.empty()) return;
+    cudaEventRecord(pending.back().b, s);
+  }
+  void prof_collect() {
+    for (auto& p : pending) {
+      float ms = 0.f;
+      if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        prof_ms[p.kind] += ms;
+        prof_n[p.kind] += 1;
+      }
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+  void prof_reset() {
+    prof_collect();
+    for (int k = 0; k < KK_COUNT; ++k) {
+      prof_ms[k] = 0;
+      prof_n[k] = 0;
+    }
+  }
+  void prof_release() {
+    prof_collect();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+  }
+};
+

@@ -1,0 +1,89 @@
+"""Continuous-batching request server: results alone vs. in the mix, budget
+admission, and the device-memory estimate."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1406_0359_gb300 import synth
+from tests._gpu import need_gpu, rel
+
+pytestmark = pytest.mark.gpu
+
+MIX = [(64, 3000, 11), (128, 20000, 12), (256, 60000, 13), (64, 5000, 14), (128, 9000, 15), (256, 130000, 16)]
+
+
+def problem(n, M, seed):
+    from paper_1406_0359_gb300.binding import Operator
+
+    uv = synth.uv_coverage(M, n, seed)
+    x = synth.sky(n, seed, 3, 10)
+    op = Operator(torch.as_tensor(uv).cuda(), n, 3, "fp32")
+    y0 = op.phi(torch.as_tensor(x, dtype=torch.float32, device="cuda")).cpu().numpy().astype(np.complex128)
+    op.close()
+    a, b = synth.noise_draws(M, seed)
+    sigma = np.linalg.norm(y0) / math.sqrt(M) * 10 ** (-1.5)
+    y = y0 + sigma / math.sqrt(2) * (a + 1j * b)
+    eps = sigma * math.sqrt(M + 2 * math.sqrt(M))
+    return uv, y, eps
+
+
+def run_server(reqs, slots, budget=int(40e9)):
+    from paper_1406_0359_gb300.binding import Server
+
+    srv = Server(budget, slots)
+    ids = [srv.submit(uv, y, n, 3, eps, t_max=15, cg_iters=8, n_reweight=1) for (n, uv, y, eps) in reqs]
+    max_active = 0
+    for _ in range(100000):
+        a, q = srv.step()
+        max_active = max(max_active, a)
+        if a == 0 and q == 0:
+            break
+    out = [srv.result(i) for i in ids]
+    srv.close()
+    return out, max_active
+
+
+def test_results_same_alone_and_in_mix():
+    need_gpu()
+    reqs = []
+    for n, M, seed in MIX:
+        uv, y, eps = problem(n, M, seed)
+        reqs.append((n, uv, y, eps))
+    alone = [run_server([r], 1)[0][0] for r in reqs]
+    mixed, max_active = run_server(reqs, 8)
+    assert max_active >= 4
+    for a, m in zip(alone, mixed):
+        assert a is not None and m is not None
+        assert m[1]["iterations"] == a[1]["iterations"] == 30
+        assert rel(m[0], a[0]) < 1e-5
+        assert m[2] >= m[3] >= 0.0
+
+
+def test_budget_limits_admission():
+    need_gpu()
+    from paper_1406_0359_gb300.binding import PurifyError, Server, purify_estimate_bytes
+
+    reqs = [(128, *problem(128, 20000, s)) for s in (21, 22, 23)]
+    one = purify_estimate_bytes(20000, 128, 3)
+    _, max_active = run_server(reqs, 8, budget=int(one * 1.5))
+    assert max_active == 1
+    _, max_active = run_server(reqs, 8, budget=int(one * 3.5))
+    assert max_active == 3
+    srv = Server(int(one * 0.1), 4)
+    with pytest.raises(PurifyError):
+        srv.submit(reqs[2][1], reqs[2][2], reqs[2][0], 3, reqs[2][3])
+    srv.close()
+
+
+def test_estimate_bounds_operator_memory():
+    need_gpu()
+    from paper_1406_0359_gb300.binding import Operator, purify_estimate_bytes
+
+    for n, M, seed in MIX[:3]:
+        uv, y, eps = problem(n, M, seed)
+        op = Operator(torch.as_tensor(uv).cuda(), n, 3, "fp32")
+        op.solve(torch.as_tensor(y, dtype=torch.complex64).cuda(), eps, t_max=2, cg_iters=2)
+        assert op.info()["device_bytes"] <= purify_estimate_bytes(M, n, 3)
+        op.close()

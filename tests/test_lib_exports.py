@@ -44,3 +44,13 @@ def test_strerror_without_gpu():
     assert "invalid" in binding.purify_strerror(-1)
     p = binding.purify_default_params()
     assert p.t_max == 200 and p.cg_iters == 10 and p.use_graph == 1
+
+
+def test_memory_estimate_is_monotone_without_gpu():
+    from paper_1406_0359_gb300 import binding, build
+
+    build.build()
+    a = binding.purify_estimate_bytes(100_000, 256, 4)
+    assert binding.purify_estimate_bytes(200_000, 256, 4) > a
+    assert binding.purify_estimate_bytes(100_000, 512, 4) > a
+    assert binding.purify_estimate_bytes(100_000, 256, 4, binding.PURIFY_FP64) > a
