@@ -359,6 +359,141 @@ def run_reference(args, ws, rank):
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------------- systems patterns
+def _make_request(n, M, seed, dev):
+    """Seeded sky, uv and noisy visibilities (y from this library's own Phi)."""
+    import numpy as np
+    import torch
+
+    from paper_1406_0359_gb300 import synth
+    from paper_1406_0359_gb300.binding import Operator
+
+    uv = synth.uv_coverage(M, n, seed)
+    x = synth.sky(n, seed, 3 + n // 128, 10 + n // 16)
+    op = Operator(torch.as_tensor(uv, device=dev), n, 3, "fp32")
+    y0 = op.phi(torch.as_tensor(x, dtype=torch.float32, device=dev)).cpu().numpy().astype(np.complex128)
+    op.close()
+    a, b = synth.noise_draws(M, seed)
+    sigma = float(np.linalg.norm(y0)) / math.sqrt(M) * 10 ** (-1.5)
+    y = y0 + sigma / math.sqrt(2) * (a + 1j * b)
+    return dict(n=n, M=M, uv=uv, y=y, eps=sigma * math.sqrt(M + 2 * math.sqrt(M)))
+
+
+def _drain(srv, ids, arrivals=None, reqs=None, params=None):
+    """Drive scheduling rounds until every request is done; with `arrivals`
+    (seconds from start) requests are submitted as their time comes."""
+    t0 = time.perf_counter()
+    pending = list(range(len(arrivals))) if arrivals is not None else []
+    while True:
+        now = time.perf_counter() - t0
+        while pending and arrivals[pending[0]] <= now:
+            k = pending.pop(0)
+            r = reqs[k]
+            ids[k] = srv.submit(r["uv"], r["y"], r["n"], 3, r["eps"], **params)
+        a, q = srv.step()
+        if a == 0 and q == 0:
+            if not pending:
+                break
+            time.sleep(max(0.0, min(0.002, arrivals[pending[0]] - (time.perf_counter() - t0))))
+    wall = time.perf_counter() - t0
+    res = [srv.result(i) for i in ids]
+    return wall, res
+
+
+def run_batch(args):
+    """64 uneven instances (images 128/256/512 square, M uniform in [0.5N, 3N])
+    advanced together by the request server (all admitted at once), against
+    the same instances solved one at a time.  Tile/chunk per image size come
+    from the autotuner."""
+    import numpy as np
+    import torch
+
+    from paper_1406_0359_gb300 import build as _build
+    from paper_1406_0359_gb300.binding import Server, purify_autotune
+
+    _build.build()
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(4)
+    reqs = []
+    for i in range(args.batch_size):
+        n = int(rng.choice([128, 256, 512]))
+        M = int(rng.uniform(0.5, 3.0) * n * n)
+        reqs.append(_make_request(n, M, 4 + i, dev))
+    tuned = {}
+    for n in (128, 256, 512):
+        r = next(q for q in reqs if q["n"] == n)
+        tuned[n] = purify_autotune(torch.as_tensor(r["uv"], device=dev), n, 3)
+    params = dict(t_max=args.batch_iters, cg_iters=10)
+    out = {}
+    for label, slots in (("batched", len(reqs)), ("sequential", 1)):
+        srv = Server(int(150e9), slots)
+        for n, (tile, chunk, _) in tuned.items():
+            srv.set_options(n, tile, chunk)
+        ids = [srv.submit(r["uv"], r["y"], r["n"], 3, r["eps"], **params) for r in reqs]
+        wall, res = _drain(srv, ids)
+        srv.close()
+        out[label] = (wall, res)
+    xb = [r[0] for r in out["batched"][1]]
+    xs = [r[0] for r in out["sequential"][1]]
+    worst = max(float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(xb, xs))
+    line = {"metric": "batched SARA-SDMM solves/s, 64 uneven instances (128..512 square, M in [0.5N, 3N])",
+            "value": round(len(reqs) / out["batched"][0], 3), "unit": "solves/s", "higher_is_better": True,
+            "sequential_solves_per_s": round(len(reqs) / out["sequential"][0], 3),
+            "speedup": round(out["sequential"][0] / out["batched"][0], 3),
+            "iterations_per_solve": args.batch_iters, "dtype": "f32 (FP64 reductions)", "data": "synthetic",
+            "max_rel_diff_batched_vs_alone": worst,
+            "autotuned": {str(k): {"tile": v[0], "chunk": v[1], "phi_phiH_ms": round(v[2], 4)} for k, v in tuned.items()},
+            "config": {"workload": "64 independent solves, seeds 4+i", "mode": "request server, all admitted"}}
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """Poisson arrivals of mixed-size solve requests (images 128..1024 square,
+    M log-uniform in [16K, 1M], SDMM to xi = 1e-4 or 300 iterations) through the
+    continuous-batching server (150 GB budget, 16 slots), at rates relative to
+    the one-at-a-time throughput; p50/p99 latency and solves/s per rate."""
+    import numpy as np
+    import torch
+
+    from paper_1406_0359_gb300 import build as _build
+    from paper_1406_0359_gb300.binding import Server
+
+    _build.build()
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(5)
+    reqs = []
+    for i in range(args.serve_requests):
+        n = int(rng.choice([128, 256, 512, 1024], p=[0.35, 0.3, 0.25, 0.1]))
+        M = int(np.exp(rng.uniform(np.log(16384), np.log(1 << 20))))
+        reqs.append(_make_request(n, M, 500 + i, dev))
+    params = dict(t_max=300, cg_iters=10, xi=1e-4)
+    srv = Server(int(150e9), 1)
+    ids = [srv.submit(r["uv"], r["y"], r["n"], 3, r["eps"], **params) for r in reqs]
+    seq_wall, seq_res = _drain(srv, ids)
+    srv.close()
+    seq_rate = len(reqs) / seq_wall
+    rates = []
+    for mult in (0.5, 1.0, 2.0, 4.0):
+        lam = mult * seq_rate
+        arr = np.cumsum(np.random.default_rng(int(mult * 10)).exponential(1.0 / lam, len(reqs)))
+        srv = Server(int(150e9), 16)
+        ids = [None] * len(reqs)
+        wall, res = _drain(srv, ids, list(arr), reqs, params)
+        srv.close()
+        lat = np.array([r[2] for r in res])
+        worst = max(float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0])) for a, b in zip(res, seq_res))
+        rates.append({"offered_rps": round(lam, 3), "solves_per_s": round(len(reqs) / wall, 3),
+                      "p50_s": round(float(np.percentile(lat, 50)), 4), "p99_s": round(float(np.percentile(lat, 99)), 4),
+                      "max_rel_diff_vs_alone": worst})
+    best = max(rates, key=lambda r: r["solves_per_s"])
+    line = {"metric": "serving solves/s and p50/p99 latency (continuous batching)", "value": best["solves_per_s"],
+            "unit": "solves/s", "higher_is_better": True, "one_at_a_time_solves_per_s": round(seq_rate, 3),
+            "rates": rates, "requests": len(reqs), "dtype": "f32 (FP64 reductions)", "data": "synthetic",
+            "config": {"workload": "Poisson arrivals, images 128..1024, M log-uniform 16K..1M, xi=1e-4 or 300 it.",
+                       "budget_gb": 150, "slots": 16}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -368,7 +503,18 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--batch", action="store_true", help="64 uneven instances: batched vs one at a time")
+    ap.add_argument("--batch-size", type=int, default=64)
+    ap.add_argument("--batch-iters", type=int, default=50)
+    ap.add_argument("--serving", action="store_true", help="Poisson-arrival serving benchmark")
+    ap.add_argument("--serve-requests", type=int, default=40)
     args = ap.parse_args()
+    if args.batch:
+        run_batch(args)
+        return
+    if args.serving:
+        run_serving(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = dist_info()

@@ -72,6 +72,25 @@ enum purify_status {
 int purify_op_create(const double* uv, int64_t M, int n, int oversample, int J,
                      int dwt_levels, int precision, void* stream, purify_op** out);
 
+/* Work decomposition of the gridding kernels (0 = default). */
+typedef struct {
+  int tile;   /* uv tile side in grid cells: 8, 16 (default) or 32 (32: FP32 only) */
+  int chunk;  /* visibilities per work item, 64..8192 (default 1024) */
+} purify_op_options;
+
+/* purify_op_create_ex -- purify_op_create with an explicit tile / chunk. */
+int purify_op_create_ex(const double* uv, int64_t M, int n, int oversample, int J, int dwt_levels,
+                        int precision, const purify_op_options* opt, void* stream, purify_op** out);
+
+/*
+ * purify_autotune -- time Phi + Phi^H (`reps` pairs after one warm-up) for
+ * every tile in {8, 16, 32} and chunk in {256, 512, 1024, 2048} on this uv
+ * coverage and return the fastest options (and their time per pair in ms).
+ * Builds and frees one operator per candidate; synchronises `stream`.
+ */
+int purify_autotune(const double* uv, int64_t M, int n, int dwt_levels, int precision, int reps,
+                    void* stream, purify_op_options* best, double* best_ms);
+
 /* purify_op_destroy -- free everything the operator owns (NULL is a no-op). */
 int purify_op_destroy(purify_op* op);
 
@@ -236,6 +255,8 @@ const char* purify_kernel_name(int kind);
 typedef struct purify_server purify_server;
 int purify_server_create(int64_t budget_bytes, int max_slots, purify_server** out);
 int purify_server_destroy(purify_server* srv);
+/* Work decomposition used for requests of image side n (e.g. from purify_autotune). */
+int purify_server_set_options(purify_server* srv, int n, const purify_op_options* opt);
 /* Copies uv (host double[M][2]) and y (host complex[M] of the precision) and
  * queues the request; PURIFY_ERR_BUDGET if it can never fit the budget. */
 int purify_server_submit(purify_server* srv, const double* uv_host, const void* y_host, int64_t M, int n,

@@ -40,6 +40,10 @@ class purify_params(ctypes.Structure):
                 ("eps_blocks", ctypes.POINTER(ctypes.c_double))]
 
 
+class purify_op_options(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int), ("chunk", ctypes.c_int)]
+
+
 class purify_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("rounds", ctypes.c_int), ("converged", ctypes.c_int),
                 ("objective", ctypes.c_double), ("residual", ctypes.c_double), ("nu", ctypes.c_double),
@@ -54,7 +58,8 @@ EXPORTS = ["purify_op_create", "purify_op_destroy", "purify_op_info", "purify_ph
            "purify_strerror", "purify_profile", "purify_profile_read", "purify_kernel_name",
            "purify_last_error", "purify_sara_fwd_static", "purify_gram", "purify_op_set_blocks",
            "purify_server_create", "purify_server_destroy", "purify_server_submit", "purify_server_step",
-           "purify_server_result", "purify_estimate_bytes"]
+           "purify_server_result", "purify_estimate_bytes", "purify_op_create_ex", "purify_autotune",
+           "purify_server_set_options"]
 KERNEL_KINDS = ["row_fwd", "col_fwd", "degrid", "grid", "gram", "col_inv", "row_inv", "sara_analysis",
                 "sara_synthesis", "vector", "memset", "col_conv"]
 
@@ -91,12 +96,17 @@ def lib() -> ctypes.CDLL:
     L.purify_op_set_blocks.argtypes = [vp, vp, ci, vp]
     L.purify_server_create.argtypes = [i64, ci, ctypes.POINTER(vp)]
     L.purify_server_destroy.argtypes = [vp]
+    L.purify_server_set_options.argtypes = [vp, ci, ctypes.POINTER(purify_op_options)]
     L.purify_server_submit.argtypes = [vp, vp, vp, i64, ci, ci, ci, ctypes.POINTER(purify_params),
                                        ctypes.POINTER(ci)]
     L.purify_server_step.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci)]
     L.purify_server_result.argtypes = [vp, ci, vp, ctypes.POINTER(purify_stats), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]
     L.purify_estimate_bytes.argtypes = [i64, ci, ci, ci, ctypes.POINTER(i64)]
+    L.purify_op_create_ex.argtypes = [vp, i64, ci, ci, ci, ci, ci, ctypes.POINTER(purify_op_options), vp,
+                                      ctypes.POINTER(vp)]
+    L.purify_autotune.argtypes = [vp, i64, ci, ci, ci, ci, vp, ctypes.POINTER(purify_op_options),
+                                  ctypes.POINTER(ctypes.c_double)]
     L.purify_last_error.argtypes = []
     L.purify_last_error.restype = ctypes.c_char_p
     for f in EXPORTS:
@@ -133,6 +143,25 @@ def purify_op_create(uv: torch.Tensor, n: int, dwt_levels: int, precision: int =
     _check(lib().purify_op_create(_dptr(uv, torch.float64), uv.shape[0], n, oversample, J, dwt_levels,
                                   precision, _stream(stream), ctypes.byref(h)), "purify_op_create")
     return h
+
+
+def purify_op_create_ex(uv: torch.Tensor, n: int, dwt_levels: int, precision: int = PURIFY_FP32, tile: int = 0,
+                        chunk: int = 0, stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    o = purify_op_options(tile, chunk)
+    _check(lib().purify_op_create_ex(_dptr(uv, torch.float64), uv.shape[0], n, 2, 8, dwt_levels, precision,
+                                     ctypes.byref(o), _stream(stream), ctypes.byref(h)), "purify_op_create_ex")
+    return h
+
+
+def purify_autotune(uv: torch.Tensor, n: int, dwt_levels: int, precision: int = PURIFY_FP32, reps: int = 3,
+                    stream=None) -> tuple[int, int, float]:
+    """(tile, chunk, ms per Phi + Phi^H) of the fastest work decomposition."""
+    o = purify_op_options()
+    ms = ctypes.c_double()
+    _check(lib().purify_autotune(_dptr(uv, torch.float64), uv.shape[0], n, dwt_levels, precision, reps,
+                                 _stream(stream), ctypes.byref(o), ctypes.byref(ms)), "purify_autotune")
+    return o.tile, o.chunk, ms.value
 
 
 def purify_op_destroy(h) -> None:
@@ -221,7 +250,8 @@ class SolveResult:
 class Operator:
     """One measurement operator + SARA dictionary on the current CUDA device."""
 
-    def __init__(self, uv, n: int, levels: int, precision: str = "fp32", stream=None):
+    def __init__(self, uv, n: int, levels: int, precision: str = "fp32", stream=None, tile: int = 0,
+                 chunk: int = 0):
         self.n, self.levels = n, levels
         self.prec = PURIFY_FP32 if precision == "fp32" else PURIFY_FP64
         self.rdtype = torch.float32 if self.prec == PURIFY_FP32 else torch.float64
@@ -230,7 +260,10 @@ class Operator:
         if not uv_t.is_cuda:
             uv_t = uv_t.cuda()
         self.M = uv_t.shape[0]
-        self.h = purify_op_create(uv_t.contiguous(), n, levels, self.prec, stream=stream)
+        if tile or chunk:
+            self.h = purify_op_create_ex(uv_t.contiguous(), n, levels, self.prec, tile, chunk, stream=stream)
+        else:
+            self.h = purify_op_create(uv_t.contiguous(), n, levels, self.prec, stream=stream)
 
     def close(self) -> None:
         if getattr(self, "h", None):
@@ -354,6 +387,10 @@ class Server:
                                           ctypes.byref(p), ctypes.byref(rid)), "purify_server_submit")
         self.meta[rid.value] = (n, prec)
         return rid.value
+
+    def set_options(self, n: int, tile: int, chunk: int) -> None:
+        o = purify_op_options(tile, chunk)
+        _check(lib().purify_server_set_options(self.h, n, ctypes.byref(o)), "purify_server_set_options")
 
     def step(self) -> tuple[int, int]:
         a, q = ctypes.c_int(), ctypes.c_int()

@@ -182,17 +182,17 @@ template <typename T> class OpImpl : public purify_op {
   size_t N() const { return size_t(g.n) * g.n; }
   size_t grid_bytes() const { return size_t(g.KP) * g.KP * sizeof(C); }
 
-  int create(const double* uv, int64_t M, int n, int L, cudaStream_t s) {
+  int create(const double* uv, int64_t M, int n, int L, cudaStream_t s, int tile = 0, int chunk_opt = 0) {
     g.n = n;
     g.K = 2 * n;
     g.KP = g.K + kJ;
     g.pad_lo = kJ / 2 - 1;
-    g.TB = 16;
+    g.TB = tile > 0 ? tile : 16;
     if (g.TB > g.K) g.TB = g.K;
     g.ntile1d = g.K / g.TB;
     g.M = M;
     levels = L;
-    chunk = 1024;
+    chunk = chunk_opt > 0 ? chunk_opt : 1024;
     CK(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
@@ -870,6 +870,95 @@ int purify_op_create(const double* uv, int64_t M, int n, int oversample, int J, 
     return rc;
   }
   *out = op;
+  return PURIFY_OK;
+}
+
+int purify_op_create_ex(const double* uv, int64_t M, int n, int oversample, int J, int dwt_levels, int precision,
+                        const purify_op_options* opt, void* stream, purify_op** out) {
+  const int tile = opt ? opt->tile : 0, chunk = opt ? opt->chunk : 0;
+  if (tile != 0 && tile != 8 && tile != 16 && !(tile == 32 && precision == PURIFY_FP32)) return PURIFY_ERR_INVALID;
+  if (tile > 2 * n || (chunk != 0 && (chunk < 64 || chunk > 8192))) return PURIFY_ERR_INVALID;
+  if (!uv || !out || M < 1 || M >= (int64_t(1) << 31) || n < 16 || n > 2048 || (n & (n - 1)) ||
+      oversample != 2 || J != purify::kJ || dwt_levels < 1 || (n >> dwt_levels) < 2 ||
+      (precision != PURIFY_FP32 && precision != PURIFY_FP64))
+    return PURIFY_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  purify_op* op = nullptr;
+  int rc;
+  if (precision == PURIFY_FP32) {
+    OpImpl<float>* o = new (std::nothrow) OpImpl<float>();
+    if (!o) return PURIFY_ERR_NOMEM;
+    rc = o->create(uv, M, n, dwt_levels, s, tile, chunk);
+    op = o;
+  } else {
+    OpImpl<double>* o = new (std::nothrow) OpImpl<double>();
+    if (!o) return PURIFY_ERR_NOMEM;
+    rc = o->create(uv, M, n, dwt_levels, s, tile, chunk);
+    op = o;
+  }
+  if (rc) {
+    delete op;
+    return rc;
+  }
+  *out = op;
+  return PURIFY_OK;
+}
+
+int purify_autotune(const double* uv, int64_t M, int n, int dwt_levels, int precision, int reps, void* stream,
+                    purify_op_options* best, double* best_ms) {
+  if (!best || reps < 1) return PURIFY_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t rb = precision == PURIFY_FP32 ? 4 : 8;
+  void* x = nullptr;
+  void* y = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&x, size_t(n) * n * rb);
+  if (e == cudaSuccess) e = cudaMalloc(&y, size_t(M) * 2 * rb);
+  if (e == cudaSuccess) e = cudaMemset(x, 0, size_t(n) * n * rb);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  int rc = e == cudaSuccess ? PURIFY_OK : PURIFY_ERR_CUDA;
+  double best_t = 1e300;
+  purify_op_options bo{16, 1024};
+  const int tiles[3] = {8, 16, 32};
+  const int chunks[4] = {256, 512, 1024, 2048};
+  for (int ti = 0; ti < 3 && !rc; ++ti) {
+    if (tiles[ti] > 2 * n || (tiles[ti] == 32 && precision != PURIFY_FP32)) continue;
+    for (int ci = 0; ci < 4 && !rc; ++ci) {
+      purify_op_options o{tiles[ti], chunks[ci]};
+      purify_op* op = nullptr;
+      int r = purify_op_create_ex(uv, M, n, 2, 8, dwt_levels, precision, &o, stream, &op);
+      if (r) {
+        if (r == PURIFY_ERR_NOMEM) continue;
+        rc = r;
+        break;
+      }
+      r = op->phi(x, y, s);
+      if (!r) r = op->phi_adj(y, x, s);
+      cudaEventRecord(e0, s);
+      for (int k = 0; k < reps && !r; ++k) {
+        r = op->phi(x, y, s);
+        if (!r) r = op->phi_adj(y, x, s);
+      }
+      cudaEventRecord(e1, s);
+      float ms = 0.f;
+      if (!r && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+        if (ms / reps < best_t) {
+          best_t = ms / reps;
+          bo = o;
+        }
+      }
+      delete op;
+      if (r) rc = r;
+    }
+  }
+  cudaFree(x);
+  cudaFree(y);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc) return rc;
+  *best = bo;
+  if (best_ms) *best_ms = best_t;
   return PURIFY_OK;
 }
 

@@ -78,6 +78,7 @@ struct purify_server {
   std::deque<Request*> queue;
   std::vector<Request*> active;
   std::map<int, Request*> all;
+  std::map<int, purify_op_options> opts;  // per image side (from the autotuner)
 
   ~purify_server() {
     for (auto& kv : all) {
@@ -118,7 +119,11 @@ struct purify_server {
         e = cudaMemcpy(uv_dev, r->uv.data(), r->uv.size() * sizeof(double), cudaMemcpyHostToDevice);
       if (e == cudaSuccess) e = cudaMemcpy(r->y_dev, r->y.data(), r->y.size(), cudaMemcpyHostToDevice);
       int rc = e == cudaSuccess ? PURIFY_OK : (e == cudaErrorMemoryAllocation ? PURIFY_ERR_NOMEM : PURIFY_ERR_CUDA);
-      if (!rc) rc = purify_op_create(uv_dev, r->M, r->n, 2, 8, r->levels, r->precision, nullptr, &r->op);
+      if (!rc) {
+        auto oi = opts.find(r->n);
+        rc = purify_op_create_ex(uv_dev, r->M, r->n, 2, 8, r->levels, r->precision,
+                                 oi == opts.end() ? nullptr : &oi->second, nullptr, &r->op);
+      }
       cudaFree(uv_dev);
       if (!rc) rc = r->op->begin(r->y_dev, &r->P, r->op->stream());
       if (rc) {
@@ -178,6 +183,12 @@ int purify_server_create(int64_t budget_bytes, int max_slots, purify_server** ou
   s->budget = budget_bytes;
   s->max_slots = max_slots;
   *out = s;
+  return PURIFY_OK;
+}
+
+int purify_server_set_options(purify_server* srv, int n, const purify_op_options* opt) {
+  if (!srv || !opt) return PURIFY_ERR_INVALID;
+  srv->opts[n] = *opt;
   return PURIFY_OK;
 }
 

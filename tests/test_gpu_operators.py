@@ -113,3 +113,27 @@ def test_full_size_phi_sampled_and_adjoint_identity():
     lhs = float(np.real(np.vdot(y, yg)))
     rhs = float(np.sum(x * xg))
     assert abs(lhs - rhs) / abs(lhs) < 1e-5
+
+
+@pytest.mark.parametrize("prec,tile,chunk", [("fp32", 8, 256), ("fp32", 32, 2048), ("fp64", 8, 512)])
+def test_tile_options_keep_parity(prec, tile, chunk):
+    from paper_1406_0359_gb300.binding import Operator
+
+    n, M = 64, 4096
+    uv = synth.uv_coverage(M, n, 1)
+    ref = NUFFT(uv, n)
+    op = Operator(torch.as_tensor(uv).cuda(), n, 2, prec, tile=tile, chunk=chunk)
+    assert op.info()["tile"] == tile
+    x = synth.random_image(n, 3)
+    y = synth.random_vis(M, 4)
+    assert rel(host(op.phi(to_dev(x, prec))), ref.phi(x)) < TOL[prec]
+    assert rel(host(op.phi_adj(to_dev(y, prec))), ref.phi_adj_real(y)) < TOL[prec]
+
+
+def test_autotuner_returns_a_valid_choice():
+    from paper_1406_0359_gb300.binding import purify_autotune
+
+    n, M = 128, 20000
+    uv = torch.as_tensor(synth.uv_coverage(M, n, 2)).cuda()
+    tile, chunk, ms = purify_autotune(uv, n, 3)
+    assert tile in (8, 16, 32) and chunk in (256, 512, 1024, 2048) and ms > 0
