@@ -74,7 +74,7 @@ int purify_op_create(const double* uv, int64_t M, int n, int oversample, int J,
 
 /* Work decomposition of the gridding kernels (0 = default). */
 typedef struct {
-  int tile;   /* uv tile side in grid cells: 8, 16 (default) or 32 (32: FP32 only) */
+  int tile;   /* uv tile side in grid cells: 8 or 16 (default) */
   int chunk;  /* visibilities per work item, 64..8192 (default 1024) */
 } purify_op_options;
 
@@ -83,9 +83,10 @@ int purify_op_create_ex(const double* uv, int64_t M, int n, int oversample, int 
                         int precision, const purify_op_options* opt, void* stream, purify_op** out);
 
 /*
- * purify_autotune -- time Phi + Phi^H (`reps` pairs after one warm-up) for
- * every tile in {8, 16, 32} and chunk in {256, 512, 1024, 2048} on this uv
- * coverage and return the fastest options (and their time per pair in ms).
+ * purify_autotune -- time Phi + Phi^H as the solver applies them (visibilities
+ * in the operator's sorted order; `reps` pairs after one warm-up) for every
+ * tile in {8, 16} and chunk in {256, 512, 1024, 2048} on this uv coverage and
+ * return the fastest options (and their time per pair in ms).
  * Builds and frees one operator per candidate; synchronises `stream`.
  */
 int purify_autotune(const double* uv, int64_t M, int n, int dwt_levels, int precision, int reps,

@@ -836,6 +836,25 @@ template <typename T> class OpImpl : public purify_op {
   }
 
   cudaStream_t stream() const override { return own; }
+
+  int sorted_pair(const void* x, void* y, void* out, cudaStream_t s) override {
+    fwd_grid(plain(static_cast<const T*>(x)), s);
+    DegridEp<C> ep{};
+    ep.mode = DG_STORE_SORTED;
+    ep.y = static_cast<C*>(y);
+    degrid(ep, s);
+    zero_q(s);
+    GridPro<C> pro{};
+    pro.mode = GP_SORTED;
+    pro.y = static_cast<const C*>(y);
+    grid(pro, s);
+    col_inv(s);
+    RowEp<T> rep{};
+    rep.mode = EP_STORE;
+    rep.out = static_cast<T*>(out);
+    row_ep(rep, s);
+    return check(s, false);
+  }
 };
 
 }  // namespace
@@ -876,7 +895,7 @@ int purify_op_create(const double* uv, int64_t M, int n, int oversample, int J, 
 int purify_op_create_ex(const double* uv, int64_t M, int n, int oversample, int J, int dwt_levels, int precision,
                         const purify_op_options* opt, void* stream, purify_op** out) {
   const int tile = opt ? opt->tile : 0, chunk = opt ? opt->chunk : 0;
-  if (tile != 0 && tile != 8 && tile != 16 && !(tile == 32 && precision == PURIFY_FP32)) return PURIFY_ERR_INVALID;
+  if (tile != 0 && tile != 8 && tile != 16) return PURIFY_ERR_INVALID;
   if (tile > 2 * n || (chunk != 0 && (chunk < 64 || chunk > 8192))) return PURIFY_ERR_INVALID;
   if (!uv || !out || M < 1 || M >= (int64_t(1) << 31) || n < 16 || n > 2048 || (n & (n - 1)) ||
       oversample != 2 || J != purify::kJ || dwt_levels < 1 || (n >> dwt_levels) < 2 ||
@@ -920,10 +939,10 @@ int purify_autotune(const double* uv, int64_t M, int n, int dwt_levels, int prec
   int rc = e == cudaSuccess ? PURIFY_OK : PURIFY_ERR_CUDA;
   double best_t = 1e300;
   purify_op_options bo{16, 1024};
-  const int tiles[3] = {8, 16, 32};
+  const int tiles[2] = {8, 16};
   const int chunks[4] = {256, 512, 1024, 2048};
-  for (int ti = 0; ti < 3 && !rc; ++ti) {
-    if (tiles[ti] > 2 * n || (tiles[ti] == 32 && precision != PURIFY_FP32)) continue;
+  for (int ti = 0; ti < 2 && !rc; ++ti) {
+    if (tiles[ti] > 2 * n) continue;
     for (int ci = 0; ci < 4 && !rc; ++ci) {
       purify_op_options o{tiles[ti], chunks[ci]};
       purify_op* op = nullptr;
@@ -933,13 +952,9 @@ int purify_autotune(const double* uv, int64_t M, int n, int dwt_levels, int prec
         rc = r;
         break;
       }
-      r = op->phi(x, y, s);
-      if (!r) r = op->phi_adj(y, x, s);
+      r = op->sorted_pair(x, y, x, s);
       cudaEventRecord(e0, s);
-      for (int k = 0; k < reps && !r; ++k) {
-        r = op->phi(x, y, s);
-        if (!r) r = op->phi_adj(y, x, s);
-      }
+      for (int k = 0; k < reps && !r; ++k) r = op->sorted_pair(x, y, x, s);
       cudaEventRecord(e1, s);
       float ms = 0.f;
       if (!r && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {

@@ -560,6 +560,20 @@ __global__ void __launch_bounds__(kThreads) k_degrid_w(Geometry g, const __grid_
   }
 }
 
+// Compensated (Kahan) accumulation of a run sum into a patch cell: the cell
+// keeps its running sum and the low-order part lost so far.
+template <typename C> PD void kahan_add(C* sum, C* comp, C v) {
+  C s = *sum, c = *comp;
+  const decltype(v.x) yx = v.x - c.x, yy = v.y - c.y;
+  const decltype(v.x) tx = s.x + yx, ty = s.y + yy;
+  c.x = (tx - s.x) - yx;
+  c.y = (ty - s.y) - yy;
+  s.x = tx;
+  s.y = ty;
+  *sum = s;
+  *comp = c;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_grid_w(Geometry g, const WorkItem* __restrict__ items, int n_items,
                                                      const Pos<T>* __restrict__ pos, const int* __restrict__ perm,
@@ -574,9 +588,11 @@ __global__ void __launch_bounds__(kThreads) k_grid_w(Geometry g, const WorkItem*
   const WorkItem it = items[item];
   const int tu = it.tile / g.ntile1d, tv = it.tile - tu * g.ntile1d;
   const int PW = g.TB + kJ, PA = PW + 1;
-  C* wacc = reinterpret_cast<C*>(sm_raw) + warp * PW * PA;
-  T* wst = reinterpret_cast<T*>(reinterpret_cast<C*>(sm_raw) + kWItems * PW * PA) + warp * 32 * kStage;
-  for (int e = lane; e < PW * PA; e += 32) wacc[e] = cz<C>();
+  // per warp: accumulator patch and its Kahan compensation patch
+  C* wacc = reinterpret_cast<C*>(sm_raw) + warp * 2 * PW * PA;
+  C* wcmp = wacc + PW * PA;
+  T* wst = reinterpret_cast<T*>(reinterpret_cast<C*>(sm_raw) + kWItems * 2 * PW * PA) + warp * 32 * kStage;
+  for (int e = lane; e < PW * PA; e += 32) wacc[e] = wcmp[e] = cz<C>();
   __syncwarp();
   T scale = 0;
   if (gpro.mode == GP_BALL) scale = T(gpro.block_scale ? gpro.block_scale[it.pad] : gpro.scalars[gpro.scale_idx]);
@@ -628,9 +644,9 @@ __global__ void __launch_bounds__(kThreads) k_grid_w(Geometry g, const WorkItem*
       const int cell = *reinterpret_cast<const int*>(sj + 2 * kJ + 2);
       if (cell != scell) {  // warp-uniform
         if (scell >= 0) {
-          C* row = wacc + ((scell >> 8) + ta) * PA + (scell & 255) + tb;
-          row[0] = cadd(row[0], s0);
-          row[1] = cadd(row[1], s1);
+          const int o = ((scell >> 8) + ta) * PA + (scell & 255) + tb;
+          kahan_add(wacc + o, wcmp + o, s0);
+          kahan_add(wacc + o + 1, wcmp + o + 1, s1);
           s0 = s1 = cz<C>();
         }
         scell = cell;
@@ -647,14 +663,14 @@ __global__ void __launch_bounds__(kThreads) k_grid_w(Geometry g, const WorkItem*
     __syncwarp();
   }
   if (scell >= 0) {
-    C* row = wacc + ((scell >> 8) + ta) * PA + (scell & 255) + tb;
-    row[0] = cadd(row[0], s0);
-    row[1] = cadd(row[1], s1);
+    const int o = ((scell >> 8) + ta) * PA + (scell & 255) + tb;
+    kahan_add(wacc + o, wcmp + o, s0);
+    kahan_add(wacc + o + 1, wcmp + o + 1, s1);
   }
   __syncwarp();
   for (int e = lane; e < PW * PW; e += 32) {
     const int r = e / PW, c = e - r * PW;
-    const C v = wacc[r * PA + c];
+    const C v = csub(wacc[r * PA + c], wcmp[r * PA + c]);
     if (v.x != 0 || v.y != 0) atomic_add_global(Q + size_t(tu * g.TB + r) * g.KP + (tv * g.TB + c), v);
   }
 }
@@ -899,7 +915,7 @@ void launch_grid(const Geometry& g, const WorkItem* items, int n_items, const Po
                  cudaStream_t s) {
   if (n_items <= 0) return;
   const size_t PW = size_t(g.TB + kJ);
-  const size_t sm = kWItems * (PW * (PW + 1) * sizeof(typename cplx_t<T>::type) + 32 * kStage * sizeof(T));
+  const size_t sm = kWItems * (2 * PW * (PW + 1) * sizeof(typename cplx_t<T>::type) + 32 * kStage * sizeof(T));
   k_grid_w<T><<<(n_items + kWItems - 1) / kWItems, kThreads, sm, s>>>(g, items, n_items, pos, perm, kb, pro, Q);
 }
 

@@ -23,6 +23,8 @@ struct purify_op {
   virtual int step_check(int* done) = 0;
   virtual int end(void* x, purify_stats* st, cudaStream_t user) = 0;
   virtual cudaStream_t stream() const = 0;
+  // Phi then Phi^H in the solver's sorted visibility order (autotuner timing).
+  virtual int sorted_pair(const void* x, void* y, void* out, cudaStream_t s) = 0;
   virtual void info(int* n, int64_t* M, int* K, int* tile, int* n_items, int* precision, int64_t* bytes) const = 0;
 
   // ---- kernel timing (instrumentation)

@@ -115,7 +115,7 @@ def test_full_size_phi_sampled_and_adjoint_identity():
     assert abs(lhs - rhs) / abs(lhs) < 1e-5
 
 
-@pytest.mark.parametrize("prec,tile,chunk", [("fp32", 8, 256), ("fp32", 32, 2048), ("fp64", 8, 512)])
+@pytest.mark.parametrize("prec,tile,chunk", [("fp32", 8, 256), ("fp32", 16, 2048), ("fp64", 8, 512)])
 def test_tile_options_keep_parity(prec, tile, chunk):
     from paper_1406_0359_gb300.binding import Operator
 
@@ -136,4 +136,4 @@ def test_autotuner_returns_a_valid_choice():
     n, M = 128, 20000
     uv = torch.as_tensor(synth.uv_coverage(M, n, 2)).cuda()
     tile, chunk, ms = purify_autotune(uv, n, 3)
-    assert tile in (8, 16, 32) and chunk in (256, 512, 1024, 2048) and ms > 0
+    assert tile in (8, 16) and chunk in (256, 512, 1024, 2048) and ms > 0
