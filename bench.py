@@ -121,7 +121,10 @@ def algorithmic_bytes(kind: str, n: int, M: int, rsize: int = 4) -> float:
         "col_fwd": 2 * N * c + 4 * N * c,         # compact rows in, full grid out
         "col_inv": 4 * N * c + 2 * N * c,
         "row_inv": 2 * N * c + 2 * N * rsize,
-        "col_conv": 2 * N * c + 4 * N * rsize + 2 * N * c,  # compact rows in, PSF spectrum, compact rows out
+        # convolution form (real image, half spectra n x n complex)
+        "row_fwd_h": 3 * N * rsize + N * c,       # r, p in, p out (CG direction), half-spectrum rows out
+        "col_conv": N * c + 2 * N * rsize + N * c,  # half-spectrum rows in, PSF half spectrum, rows out
+        "row_inv_h": N * c + 2 * N * rsize,       # half-spectrum rows in, p in, image out
     }
     return float(table.get(kind, 0))
 

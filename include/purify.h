@@ -234,9 +234,10 @@ int purify_sdmm_solve(purify_op* op, const void* y, const purify_params* params,
  * returns, per kernel kind, the summed device time and launch count since
  * profiling was enabled.  Kinds: 0 row_fwd, 1 col_fwd, 2 degrid, 3 grid,
  * 4 gram, 5 col_inv, 6 row_inv, 7 sara_analysis, 8 sara_synthesis,
- * 9 vector (CG updates and scalar finalisation), 10 memset, 11 col_conv.
+ * 9 vector (CG updates and scalar finalisation), 10 memset, 11 col_conv,
+ * 12 row_fwd_h, 13 row_inv_h (the row passes of the convolution form).
  */
-enum { PURIFY_NUM_KERNEL_KINDS = 12 };
+enum { PURIFY_NUM_KERNEL_KINDS = 14 };
 int purify_profile(purify_op* op, int enable);
 int purify_profile_read(purify_op* op, int kind, double* total_ms, int64_t* launches);
 const char* purify_kernel_name(int kind);

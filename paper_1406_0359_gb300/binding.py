@@ -61,7 +61,7 @@ EXPORTS = ["purify_op_create", "purify_op_destroy", "purify_op_info", "purify_ph
            "purify_server_result", "purify_estimate_bytes", "purify_op_create_ex", "purify_autotune",
            "purify_server_set_options"]
 KERNEL_KINDS = ["row_fwd", "col_fwd", "degrid", "grid", "gram", "col_inv", "row_inv", "sara_analysis",
-                "sara_synthesis", "vector", "memset", "col_conv"]
+                "sara_synthesis", "vector", "memset", "col_conv", "row_fwd_h", "row_inv_h"]
 
 _lib = None
 

@@ -97,8 +97,7 @@ template <typename T> class OpImpl : public purify_op {
   C *z3 = nullptr, *ys = nullptr;
   // composite operator by convolution (Section 3: precompute Phi^H Phi)
   double* uv_keep = nullptr;  // device copy of uv, for the PSF set-up
-  T* ones = nullptr;          // unit deapodisation for the convolution path
-  T* khat = nullptr;          // real PSF spectrum, launch_col_conv layout
+  T* khat = nullptr;          // real PSF half spectrum, launch_col_conv_h layout
   bool toep = false;          // current normal-operator mode
   // visibility blocks (Eq. 4-5)
   int nblocks = 1;
@@ -254,7 +253,7 @@ template <typename T> class OpImpl : public purify_op {
     block_sizes.assign(1, M);
     if ((rc = size_partials())) return rc;
     if ((rc = alloc(&eps_dev, 64)) || (rc = alloc(&scale_dev, 64))) return rc;
-    if ((rc = alloc(&cg_part, 2 * kCgPart))) return rc;
+    if ((rc = alloc(&cg_part, 5 * kCgPart))) return rc;
     if ((rc = alloc(&tickets, 4))) return rc;
     CK(cudaMemsetAsync(tickets, 0, 4 * sizeof(unsigned int), s));
     // TMA descriptor of the padded forward grid, 8-byte elements
@@ -338,10 +337,8 @@ template <typename T> class OpImpl : public purify_op {
       return PURIFY_ERR_INVALID;
     }
     int rc;
-    T* ones_l = nullptr;
     T* khat_l = nullptr;
-    if ((rc = alloc(&ones_l, g.n)) || (rc = alloc(&khat_l, size_t(g.K) * g.K))) return rc;
-    launch_fill<T>(ones_l, g.n, T(1), s);
+    if ((rc = alloc(&khat_l, size_t(g.K / 2 + 1) * g.K))) return rc;
     {
       OpImpl<T> big;
       rc = big.create(uv_keep, g.M, 2 * g.n, 1, s);
@@ -369,7 +366,6 @@ template <typename T> class OpImpl : public purify_op {
       if (e != cudaSuccess) return map_err(e, __LINE__);
       if (rc) return rc;
     }
-    ones = ones_l;
     khat = khat_l;
     return PURIFY_OK;
   }
@@ -378,15 +374,18 @@ template <typename T> class OpImpl : public purify_op {
   // NUFFT (G^H G per application) or by the precomputed convolution.
   void normal_front(const RowPro<T>& pro, cudaStream_t s) {
     if (toep) {
-      PROF(KK_ROW_FWD, s, launch_row_fwd<T>(g, pro, ones, gridA, tw, s));
-      PROF(KK_COL_CONV, s, launch_col_conv<T>(g, gridA, khat, tw, s));
+      PROF(KK_ROW_FWD_H, s, launch_row_fwd_h<T>(g, pro, gridA, tw, s));
+      PROF(KK_COL_CONV, s, launch_col_conv_h<T>(g, gridA, khat, tw, s));
     } else {
       gram_front(pro, s);
     }
   }
-  int normal_back(const RowEp<T>& ep, cudaStream_t s) {
+  int normal_back(const RowEp<T>& ep_in, cudaStream_t s) {
+    RowEp<T> ep = ep_in;
+    if (!ep.err) ep.err = err;
     int np = 0;
-    PROF(KK_ROW_INV, s, np = launch_row_inv<T>(g, gridA, toep ? ones : deapod, ep, tw, s));
+    if (toep) PROF(KK_ROW_INV_H, s, np = launch_row_inv_h<T>(g, gridA, ep, tw, s));
+    else PROF(KK_ROW_INV, s, np = launch_row_inv<T>(g, gridA, deapod, ep, tw, s));
     return np;
   }
 
@@ -541,8 +540,10 @@ template <typename T> class OpImpl : public purify_op {
     const size_t n2 = N();
     // step 5: x_hat = (Phi^H Phi + 2I)^-1 sum_i x_i by CG, warm-started at x_hat.
     // The scalars stay on the device and need no launches of their own: the
-    // last block of the inverse row pass sets <r,r> (initial residual) or
-    // alpha; the last block of the CG update sets beta and the new <r,r>.
+    // last block of the inverse row pass sets <r,r> (initial residual), or
+    // alpha and beta (CG step, from five inner products of the step's vectors);
+    // the forward row pass of the next step applies x += alpha p,
+    // r -= alpha Ap, p = r + beta p on the fly.
     normal_front(plain(xh), s);
     {
       RowEp<T> ep{};
@@ -553,6 +554,7 @@ template <typename T> class OpImpl : public purify_op {
       ep.b = xs;
       ep.nu2 = nu2;
       ep.partials = cg_part;
+      ep.pstride = kCgPart;
       ep.scalars = sc;
       ep.ticket = tickets;
       normal_back(ep, s);
@@ -560,24 +562,27 @@ template <typename T> class OpImpl : public purify_op {
     for (int it = 0; it < cg_iters; ++it) {
       RowPro<T> pro = plain(p);
       if (it > 0) {
-        pro.mode = PRO_CG_P;
+        pro.mode = PRO_CG_STEP;
         pro.p = p;
         pro.r = r;
+        pro.xu = xh;
+        pro.ap = Ap;
         pro.scalars = sc;
-        pro.idx = S_BETA;
       }
       normal_front(pro, s);
       RowEp<T> ep{};
       ep.mode = EP_CG_AP;
       ep.out = Ap;
       ep.p = p;
+      ep.r = r;
       ep.nu2 = nu2;
       ep.partials = cg_part;
+      ep.pstride = kCgPart;
       ep.scalars = sc;
       ep.ticket = tickets + 1;
       normal_back(ep, s);
-      PROF(KK_VEC, s, launch_cg_xr<T>(xh, r, p, Ap, sc, n2, cg_part + kCgPart, tickets + 2, s));
     }
+    if (cg_iters > 0) PROF(KK_VEC, s, launch_axpy<T>(xh, p, sc, S_ALPHA, n2, s));  // last step: x += alpha p
     // block 1 (l1 on Psi^H x_hat) fused into the analysis, block 2 (positivity)
     // fused into the synthesis: xs = x_1 + x_2
     L1Block<T> b1{};
@@ -1036,7 +1041,8 @@ int purify_profile_read(purify_op* op, int kind, double* total_ms, int64_t* laun
 
 const char* purify_kernel_name(int kind) {
   static const char* names[] = {"row_fwd", "col_fwd", "degrid", "grid", "gram", "col_inv",
-                                "row_inv", "sara_analysis", "sara_synthesis", "vector", "memset", "col_conv"};
+                                "row_inv", "sara_analysis", "sara_synthesis", "vector", "memset", "col_conv",
+                                "row_fwd_h", "row_inv_h"};
   if (kind < 0 || kind >= PURIFY_NUM_KERNEL_KINDS) return "unknown";
   return names[kind];
 }

@@ -51,6 +51,35 @@ template <typename K> inline cudaError_t raise_smem_limit(K kernel) {
 }
 
 // ---------------------------------------------------------------- reductions
+// Per-thread partial sums (inner products, norms, objective terms).  On the
+// FP32 path a Kahan-compensated FP32 sum, each product split exactly into its
+// rounded value and an FMA-recovered error that joins the compensation; the
+// pair goes to FP64 once per thread, and everything across threads is summed
+// in FP64.  GB300 runs FP64 arithmetic at a small fraction of its FP32 rate,
+// so converting every element to double would dominate these kernels.
+template <typename T> struct Acc;
+template <> struct Acc<float> {
+  float s = 0.f, c = 0.f;  // the sum is s - c
+  PD void add(float a) {
+    const float y = a - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  PD void add_prod(float a, float b) {
+    const float p = a * b;
+    add(p);
+    c -= fmaf(a, b, -p);
+  }
+  PD double value() const { return double(s) - double(c); }
+};
+template <> struct Acc<double> {
+  double s = 0.0;
+  PD void add(double a) { s += a; }
+  PD void add_prod(double a, double b) { s = fma(a, b, s); }
+  PD double value() const { return s; }
+};
+
 PD double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -67,6 +96,30 @@ template <int NT> __device__ double block_sum(double v, double* sh /*[32]*/) {
   v = warp_sum(v);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = (lane < NT / 32) ? sh[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  __syncthreads();
+  return r;
+}
+// Warp sum of compensated partials (the FP32 pairs merge in FP32), then the
+// block sum of the warps' values in FP64; result valid in thread 0.
+PD void warp_merge(Acc<float>& a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_down_sync(0xffffffffu, a.s, o), c2 = __shfl_down_sync(0xffffffffu, a.c, o);
+    a.c += c2;
+    a.add(s2);
+  }
+}
+PD void warp_merge(Acc<double>& a) { a.s = warp_sum(a.s); }
+template <int NT, typename T> __device__ double block_sum(Acc<T> a, double* sh /*[32]*/) {
+  warp_merge(a);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = a.value();
   __syncthreads();
   double r = 0.0;
   if (w == 0) {
@@ -98,6 +151,21 @@ __device__ __forceinline__ bool last_block_done(unsigned int* ticket) {
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    const unsigned int t = atomicAdd(ticket, 1u);
+    last = (t == gridDim.x * gridDim.y * gridDim.z - 1);
+    if (last) *ticket = 0u;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// As last_block_done, for blocks whose global results for the last block
+// were all written by thread 0 (only thread 0 fences before the ticket).
+__device__ __forceinline__ bool last_block_done_t0(unsigned int* ticket) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
     const unsigned int t = atomicAdd(ticket, 1u);
     last = (t == gridDim.x * gridDim.y * gridDim.z - 1);
     if (last) *ticket = 0u;
@@ -154,6 +222,14 @@ PD bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, int* err) {
   for (uint32_t i = 0; i < kSpinLimit; ++i)
     if (mbar_try_wait(bar, phase)) break;
   return false;
+}
+// Untiled bulk copy global -> shared: both addresses 16-byte aligned, bytes a
+// multiple of 16; completion counted on `bar`.
+PD void bulk_load(void* smem_dst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(smem_dst)),
+               "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 PD void tma_load_2d(void* smem_dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
   asm volatile(

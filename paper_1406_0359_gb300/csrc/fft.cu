@@ -18,6 +18,7 @@
 //                  crop Z^T keeps; row pass fused with the crop, the
 //                  deapodisation and the solver epilogues.
 #include "internal.h"
+#include "solver_kernels.h"
 
 namespace purify {
 
@@ -186,6 +187,15 @@ PD void fft_seq(int t, C* s, int ss, const C* tw, int dir, Load load, Store stor
   run_stages<LOGN, 0>(v, t, 1, s, ss, tw, dir, store);
 }
 
+// Output position of the cnt-th value a thread's final stage hands to its
+// sink: the final radix-R stage has Ns = K/R and butterflies j = t + q T < Ns,
+// so its outputs come in the order (q, r) at t + q T + r K/R.
+template <int LOGN> PD int last_pos(int t, int cnt) {
+  typedef Plan<LOGN> P;
+  constexpr int R = P::radix(P::NST - 1);
+  return t + (cnt / R) * P::T + (cnt % R) * (P::N / R);
+}
+
 constexpr int kRowCta = 256;
 
 inline int row_nseq(const Geometry& g) {
@@ -196,6 +206,245 @@ inline int row_nseq(const Geometry& g) {
 }
 template <typename T> inline int col_width() { return 32 / int(sizeof(typename cplx_t<T>::type)); }
 __host__ __device__ inline size_t padded(int N) { return size_t(N) + size_t(N) / 16 + 1; }
+
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Row-pass epilogues (see RowEpMode), split so that every operand an output
+// needs is loaded (for a chunk of a thread's outputs) before the first output
+// of the chunk is stored: the stores may alias the operands, which would
+// otherwise serialise one memory round trip per output.
+template <typename T> struct EpOpd { T a, b; };
+template <typename T> struct EpAcc { Acc<T> a[5]; };
+template <int MODE, typename T> PD EpOpd<T> row_ep_operand(const RowEp<T>& ep, size_t idx) {
+  EpOpd<T> o{T(0), T(0)};
+  if constexpr (MODE == EP_CG_AP) {
+    o.a = ep.p[idx];
+    o.b = ep.r[idx];
+  } else if constexpr (MODE == EP_QX) {
+    o.a = ep.p[idx];
+  } else if constexpr (MODE == EP_CG_R0) {
+    o.a = ep.b[idx] - T(2) * ep.p[idx];
+  } else if constexpr (MODE == EP_XS_ADD) {
+    o.a = ep.b[idx];
+  }
+  return o;
+}
+template <int MODE, typename T>
+PD void row_ep_store(const RowEp<T>& ep, size_t idx, T val, EpOpd<T> opd, EpAcc<T>& part) {
+  if constexpr (MODE == EP_CG_AP) {
+    const T o = T(ep.nu2) * val + T(2) * opd.a;  // (A p)_i
+    ep.out[idx] = o;
+    part.a[0].add_prod(opd.a, o);
+    part.a[1].add_prod(opd.b, o);
+    part.a[2].add_prod(o, o);
+    part.a[3].add_prod(opd.b, opd.a);
+    part.a[4].add_prod(opd.b, opd.b);
+  } else if constexpr (MODE == EP_CG_R0) {
+    const T o = opd.a - T(ep.nu2) * val;
+    ep.out[idx] = o;
+    ep.out2[idx] = o;
+    part.a[0].add_prod(o, o);
+  } else if constexpr (MODE == EP_POWER) {
+    ep.out[idx] = val;
+    part.a[0].add_prod(val, val);
+  } else if constexpr (MODE == EP_XS_ADD) {
+    ep.out[idx] = opd.a + T(ep.nu) * val;
+  } else if constexpr (MODE == EP_QX) {
+    ep.out[idx] = T(ep.nu2) * val + T(2) * opd.a;
+  } else {
+    ep.out[idx] = val;
+  }
+}
+// Image column of the m-th output of thread t of an inverse row pass (grid
+// column q maps to image column (q + K/4) mod K, kept when < n = K/2).
+template <int LOGN> PD int ep_col(int t, int m) {
+  constexpr int K = 1 << LOGN;
+  return (last_pos<LOGN>(t, m) + K / 4) & (K - 1);
+}
+// Outputs val[r][m] (the final stage's values in sink order) of image rows
+// row0[r], in chunks of CH outputs: operands of the chunk first, then its
+// stores.
+template <int LOGN, int MODE, int NR, typename T>
+PD EpAcc<T> row_ep_run_mode(const RowEp<T>& ep, const T (&val)[NR][16], int t, const size_t (&row0)[NR]) {
+  constexpr int CH = MODE == EP_CG_AP ? 8 : 16, n = (1 << LOGN) / 2;
+  EpAcc<T> part;
+#pragma unroll
+  for (int c0 = 0; c0 < 16; c0 += CH) {
+    EpOpd<T> opd[NR][CH];
+#pragma unroll
+    for (int m = 0; m < CH; ++m) {
+      const int i2 = ep_col<LOGN>(t, c0 + m);
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        opd[r][m] = i2 < n ? row_ep_operand<MODE>(ep, row0[r] + i2) : EpOpd<T>{T(0), T(0)};
+    }
+#pragma unroll
+    for (int m = 0; m < CH; ++m) {
+      const int i2 = ep_col<LOGN>(t, c0 + m);
+      if (i2 < n) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) row_ep_store<MODE>(ep, row0[r] + i2, val[r][c0 + m], opd[r][m], part);
+      }
+    }
+  }
+  return part;
+}
+template <int LOGN, int NR, typename T>
+PD EpAcc<T> row_ep_run(const RowEp<T>& ep, const T (&val)[NR][16], int t, const size_t (&row0)[NR]) {
+  switch (ep.mode) {
+    case EP_CG_AP: return row_ep_run_mode<LOGN, EP_CG_AP>(ep, val, t, row0);
+    case EP_CG_R0: return row_ep_run_mode<LOGN, EP_CG_R0>(ep, val, t, row0);
+    case EP_POWER: return row_ep_run_mode<LOGN, EP_POWER>(ep, val, t, row0);
+    case EP_XS_ADD: return row_ep_run_mode<LOGN, EP_XS_ADD>(ep, val, t, row0);
+    case EP_QX: return row_ep_run_mode<LOGN, EP_QX>(ep, val, t, row0);
+    default: return row_ep_run_mode<LOGN, EP_STORE>(ep, val, t, row0);
+  }
+}
+
+// Forward row prologue (see RowProMode) of image rows row0[r] at the 8 grid
+// columns of thread t that hold image pixels: with K = 2n, grid column
+// q = t + m K/16 holds image column i2 = (q + K/4) mod K, inside the image
+// for m < 4 and m >= 12 only.  All loads precede the CG step's stores.
+template <int LOGN, int NR, typename T>
+PD void row_prologue(const RowPro<T>& pro, const size_t (&row0)[NR], int t, T (&val)[NR][8], int (&i2)[8]) {
+  constexpr int K = 1 << LOGN, TT = K / 16;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) i2[j] = (t + (j < 4 ? j : j + 8) * TT + K / 4) & (K - 1);
+  if (pro.mode == PRO_CG_STEP) {
+    // x += alpha p, r -= alpha Ap, p = r + beta p (alpha, beta of the previous step)
+    const T alpha = T(pro.scalars[S_ALPHA]), beta = T(pro.scalars[S_BETA]);
+    T xv[NR][8], rv[NR][8], av[NR][8];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const size_t idx = row0[r] + i2[j];
+        xv[r][j] = pro.xu[idx];
+        rv[r][j] = pro.r[idx];
+        val[r][j] = pro.p[idx];
+        av[r][j] = pro.ap[idx];
+      }
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const size_t idx = row0[r] + i2[j];
+        const T pv = val[r][j];
+        const T rn = fma(-alpha, av[r][j], rv[r][j]);
+        pro.xu[idx] = fma(alpha, pv, xv[r][j]);
+        pro.r[idx] = rn;
+        val[r][j] = fma(beta, pv, rn);
+        pro.p[idx] = val[r][j];
+      }
+  } else {
+    const T scl = pro.mode == PRO_SCALE ? T(pro.scalars[pro.idx]) : T(1);
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) val[r][j] = pro.x[row0[r] + i2[j]] * scl;
+  }
+}
+
+// Per-CTA partials of the epilogue sums (ep.partials + k * ep.pstride for the
+// k-th sum); the last CTA finalises the CG scalars in FP64:
+//   EP_CG_R0: <r, r>.
+//   EP_CG_AP: from <p,Ap>, <r,Ap>, <Ap,Ap>, <r,p> and <r,r> of this step's
+//             vectors: the exact line search alpha = <r,p> / <p,Ap> (equal to
+//             <r,r> / <p,Ap> in exact arithmetic); the next residual norm by
+//             ||r - alpha Ap||^2 = <r,r> - 2 alpha <r,Ap> + alpha^2 <Ap,Ap>
+//             (clamped at 0); beta = ||r_new||^2 / <r,r>.
+template <typename T> PD void row_ep_finish(const RowEp<T>& ep, EpAcc<T> part, double* red /*[5*32]*/) {
+  if (!ep.partials) return;
+  const int nsum = ep.mode == EP_CG_AP ? 5 : 1;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = int((blockDim.x + 31) >> 5);
+  for (int k = 0; k < nsum; ++k) {
+    warp_merge(part.a[k]);
+    if (lane == 0) red[k * 32 + w] = part.a[k].value();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < nsum; ++k) {
+      double tot = 0.0;
+      for (int q = 0; q < nw; ++q) tot += red[k * 32 + q];
+      ep.partials[size_t(k) * ep.pstride + blockIdx.x] = tot;
+    }
+  }
+  if (!ep.ticket || !last_block_done_t0(ep.ticket)) return;
+  // last block: the sums over all blocks, fixed order
+  double sum[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int i = threadIdx.x; i < int(gridDim.x); i += blockDim.x)
+    for (int k = 0; k < nsum; ++k) sum[k] += ep.partials[size_t(k) * ep.pstride + i];
+  for (int k = 0; k < nsum; ++k) {
+    sum[k] = warp_sum(sum[k]);
+    if (lane == 0) red[k * 32 + w] = sum[k];
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int k = 0; k < nsum; ++k) {
+    sum[k] = 0.0;
+    for (int q = 0; q < nw; ++q) sum[k] += red[k * 32 + q];
+  }
+  double* sc = ep.scalars;
+  if (ep.mode == EP_CG_R0) {
+    sc[S_RR] = sum[0];
+  } else if (ep.mode == EP_CG_AP) {
+    const double rr = sum[4];
+    const double alpha = sum[0] > 0.0 ? sum[3] / sum[0] : 0.0;
+    double rr_new = rr - 2.0 * alpha * sum[1] + alpha * alpha * sum[2];
+    if (rr_new < 0.0) rr_new = 0.0;
+    sc[S_PAP] = sum[0];
+    sc[S_ALPHA] = alpha;
+    sc[S_BETA] = rr > 0.0 ? rr_new / rr : 0.0;
+    sc[S_RR] = rr_new;
+  }
+}
+
+// Operand arrays an epilogue reads (staged in shared memory by the real-form
+// inverse row pass): CG_AP p, r; CG_R0 b, p; QX p; XS_ADD b.
+template <typename T> PD int ep_staged(const RowEp<T>& ep, const T** src) {
+  switch (ep.mode) {
+    case EP_CG_AP: src[0] = ep.p; src[1] = ep.r; return 2;
+    case EP_CG_R0: src[0] = ep.b; src[1] = ep.p; return 2;
+    case EP_QX: src[0] = ep.p; return 1;
+    case EP_XS_ADD: src[0] = ep.b; return 1;
+    default: return 0;
+  }
+}
+// Epilogue of both rows of a real-form sequence with the operands in shared
+// memory (ops[k][row][n]).
+template <int LOGN, int MODE, typename T>
+PD EpAcc<T> row_ep_staged_mode(const RowEp<T>& ep, const T (&val)[2][16], int t, const size_t (&row0)[2],
+                               const T* ops) {
+  constexpr int n = (1 << LOGN) / 2;
+  EpAcc<T> part;
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int i2 = ep_col<LOGN>(t, m);
+    if (i2 < n) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const T o0 = ops[r * n + i2], o1 = ops[(2 + r) * n + i2];
+        EpOpd<T> opd{T(0), T(0)};
+        if constexpr (MODE == EP_CG_AP) opd = EpOpd<T>{o0, o1};
+        else if constexpr (MODE == EP_CG_R0) opd.a = o0 - T(2) * o1;
+        else if constexpr (MODE == EP_QX || MODE == EP_XS_ADD) opd.a = o0;
+        row_ep_store<MODE>(ep, row0[r] + i2, val[r][m], opd, part);
+      }
+    }
+  }
+  return part;
+}
+template <int LOGN, typename T>
+PD EpAcc<T> row_ep_staged(const RowEp<T>& ep, const T (&val)[2][16], int t, const size_t (&row0)[2], const T* ops) {
+  switch (ep.mode) {
+    case EP_CG_AP: return row_ep_staged_mode<LOGN, EP_CG_AP>(ep, val, t, row0, ops);
+    case EP_CG_R0: return row_ep_staged_mode<LOGN, EP_CG_R0>(ep, val, t, row0, ops);
+    case EP_POWER: return row_ep_staged_mode<LOGN, EP_POWER>(ep, val, t, row0, ops);
+    case EP_XS_ADD: return row_ep_staged_mode<LOGN, EP_XS_ADD>(ep, val, t, row0, ops);
+    case EP_QX: return row_ep_staged_mode<LOGN, EP_QX>(ep, val, t, row0, ops);
+    default: return row_ep_staged_mode<LOGN, EP_STORE>(ep, val, t, row0, ops);
+  }
+}
 
 // ----------------------------------------------------------------- kernels
 template <typename T, int LOGN> struct ColThreads {
@@ -208,30 +457,23 @@ __global__ void __launch_bounds__(kRowCta) k_row_fwd(Geometry g, RowPro<T> pro, 
                                                   const typename cplx_t<T>::type* __restrict__ tw, int nseq) {
   typedef typename cplx_t<T>::type C;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int K = g.K, n = g.n, half = n / 2;
+  const int K = g.K, n = g.n;
   const int seq = threadIdx.x / Plan<LOGN>::T, t = threadIdx.x - seq * Plan<LOGN>::T;
   const int i1 = blockIdx.x * nseq + seq;
   C* s = reinterpret_cast<C*>(sm_raw) + seq * padded(K);
+  const size_t row0[1] = {size_t(i1) * n};
+  T val[1][8];
+  int i2[8];
+  row_prologue<LOGN>(pro, row0, t, val, i2);
   const T s1 = deapod[i1];
-  const T beta = pro.mode == PRO_CG_P ? T(pro.scalars[pro.idx]) : T(0);
-  const T scl = pro.mode == PRO_SCALE ? T(pro.scalars[pro.idx]) : T(1);
-  auto load = [&](int m) -> C {
-    const int q = t + m * Plan<LOGN>::T;            // grid column
-    const int i2 = (q + half) & (K - 1);  // image column when q is a padded position
-    if (i2 >= n) return cz<C>();
-    const size_t idx = size_t(i1) * n + i2;
-    T v;
-    if (pro.mode == PRO_CG_P) {
-      v = pro.r[idx] + beta * pro.p[idx];
-      pro.p[idx] = v;
-    } else {
-      v = pro.x[idx] * scl;
-    }
-    return cmk<C>(v * s1 * deapod[i2], T(0));
-  };
+  C v[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) v[m] = cz<C>();
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j < 4 ? j : j + 8] = cmk<C>(val[0][j] * s1 * deapod[i2[j]], T(0));
   C* out = A + size_t(i1) * K;
-  auto store = [&](int q, C v) { out[q] = v; };
-  fft_seq<LOGN>(t, s, 1, tw, -1, load, store);
+  auto store = [&](int q, C x) { out[q] = x; };
+  run_stages<LOGN, 0>(v, t, 1, s, 1, tw, -1, store);
 }
 
 template <typename T, int LOGN>
@@ -306,108 +548,196 @@ __global__ void __launch_bounds__(kRowCta) k_row_inv(Geometry g, const typename 
                                                   const typename cplx_t<T>::type* __restrict__ tw, int nseq) {
   typedef typename cplx_t<T>::type C;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  __shared__ double red[32];
-  const int K = g.K, n = g.n, half = n / 2;
+  __shared__ double red[5 * 32];
+  const int K = g.K, n = g.n;
   const int seq = threadIdx.x / Plan<LOGN>::T, t = threadIdx.x - seq * Plan<LOGN>::T;
   const int i1 = blockIdx.x * nseq + seq;
   C* s = reinterpret_cast<C*>(sm_raw) + seq * padded(K);
   const C* in = A + size_t(i1) * K;
   auto load = [&](int m) -> C { return in[t + m * Plan<LOGN>::T]; };
+  T val[1][16];
+  int cnt = 0;
+  auto stash = [&](int, C v) { val[0][cnt++] = v.x; };  // sink order, see last_pos
+  fft_seq<LOGN>(t, s, 1, tw, +1, load, stash);
   const T s1 = deapod[i1];
-  double part = 0.0;
-  auto store = [&](int q, C v) {
-    const int i2 = (q + half) & (K - 1);
-    if (i2 >= n) return;
-    const size_t idx = size_t(i1) * n + i2;
-    const T val = v.x * s1 * deapod[i2];
-    switch (ep.mode) {
-      case EP_CG_AP: {
-        const T pv = ep.p[idx];
-        const T o = T(ep.nu2) * val + T(2) * pv;
-        ep.out[idx] = o;
-        part += double(pv) * double(o);
-      } break;
-      case EP_CG_R0: {
-        const T o = ep.b[idx] - (T(ep.nu2) * val + T(2) * ep.p[idx]);
-        ep.out[idx] = o;
-        ep.out2[idx] = o;
-        part += double(o) * double(o);
-      } break;
-      case EP_POWER:
-        ep.out[idx] = val;
-        part += double(val) * double(val);
-        break;
-      case EP_XS_ADD:
-        ep.out[idx] = ep.b[idx] + T(ep.nu) * val;
-        break;
-      case EP_QX:
-        ep.out[idx] = T(ep.nu2) * val + T(2) * ep.p[idx];
-        break;
-      default:
-        ep.out[idx] = val;
-    }
-  };
-  fft_seq<LOGN>(t, s, 1, tw, +1, load, store);
-  if (ep.partials) {
-    part = warp_sum(part);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) red[w] = part;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double tot = 0.0;
-      for (int k = 0; k < int((blockDim.x + 31) >> 5); ++k) tot += red[k];
-      ep.partials[blockIdx.x] = tot;
-    }
-    if (ep.ticket && last_block_done(ep.ticket)) {
-      const double sum = block_sum_array(ep.partials, int(gridDim.x), red);
-      if (threadIdx.x == 0) {
-        if (ep.mode == EP_CG_R0) {
-          ep.scalars[0] = sum;  // <r, r>
-        } else if (ep.mode == EP_CG_AP) {
-          ep.scalars[1] = sum > 0.0 ? ep.scalars[0] / sum : 0.0;  // alpha = <r, r> / <p, Ap>
-        }
-      }
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int i2 = ep_col<LOGN>(t, m);
+    if (i2 < n) val[0][m] *= s1 * deapod[i2];
+  }
+  const size_t row0[1] = {size_t(i1) * n};
+  row_ep_finish(ep, row_ep_run<LOGN>(ep, val, t, row0), red);
+}
+
+// Composite operator by convolution (Section 3: precompute Phi^H Phi), in its
+// real form.  The image is real and the PSF spectrum real and even, so only
+// the half spectrum k2 in [0, K/2] of each image row is carried: two rows a, b
+// travel as one complex row z = x_a + i x_b, whose transform Z separates as
+// X_a(k) = (Z(k) + conj Z(-k)) / 2 and X_b(k) = (Z(k) - conj Z(-k)) / (2i).
+// A half-spectrum row holds K/2 complex values; its entry 0 carries the two
+// real ones, X(0) + i X(K/2).  Half-spectrum rows are stored n x K/2 in A.
+
+// Forward row pass of the real form: rows 2 pr and 2 pr + 1 of the prologue's
+// image, zero-padded to K columns, to their half spectra.
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(kRowCta) k_row_fwd_h(Geometry g, RowPro<T> pro,
+                                                    typename cplx_t<T>::type* __restrict__ B,
+                                                    const typename cplx_t<T>::type* __restrict__ tw, int nseq) {
+  typedef typename cplx_t<T>::type C;
+  constexpr int TT = Plan<LOGN>::T;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int K = g.K, n = g.n, H = K / 2;
+  const int seq = threadIdx.x / TT, t = threadIdx.x - seq * TT;
+  const int ia = 2 * (blockIdx.x * nseq + seq), ib = ia + 1;
+  C* s = reinterpret_cast<C*>(sm_raw) + seq * padded(K);
+  const size_t row0[2] = {size_t(ia) * n, size_t(ib) * n};
+  T val[2][8];
+  int i2[8];
+  row_prologue<LOGN>(pro, row0, t, val, i2);
+  C v[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) v[m] = cz<C>();
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j < 4 ? j : j + 8] = cmk<C>(val[0][j], val[1][j]);
+  auto to_smem = [&](int q, C x) { s[sidx(q)] = x; };
+  run_stages<LOGN, 0>(v, t, 1, s, 1, tw, -1, to_smem);
+  __syncthreads();
+  C* oa = B + size_t(ia) * H;
+  C* ob = oa + H;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int k = t + m * TT;
+    const C zk = s[sidx(k)];
+    if (k == 0) {
+      const C zh = s[sidx(H)];
+      oa[0] = cmk<C>(zk.x, zh.x);
+      ob[0] = cmk<C>(zk.y, zh.y);
+    } else {
+      const C zm = s[sidx(K - k)];  // Z(-k)
+      oa[k] = cmk<C>(T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y));
+      ob[k] = cmk<C>(T(0.5) * (zk.y + zm.y), T(0.5) * (zm.x - zk.x));
     }
   }
 }
 
-// Composite operator by convolution (Section 3: precompute Phi^H Phi).  One
-// CTA takes cw columns of the n compact rows (after the row FFT): forward
-// column FFT, multiply by the precomputed real spectrum of the PSF
-// (layout [column block][row][cw]), inverse column FFT, and keep the n rows
-// the crop retains -- the transform of the column never leaves the SM.
+// Column pass of the real form: cw half-spectrum columns per CTA, forward
+// FFT over the K rows (n non-zero), multiply by the PSF spectrum, inverse FFT,
+// keep the n rows the crop retains.  Column 0 holds two real-row columns,
+// c0 = X(., 0) + i X(., K/2): its transform P splits into the even part
+// (P(q) + conj P(-q)) / 2 (column 0's) and (P(q) - conj P(-q)) / 2 (i times
+// column K/2's), each multiplied by its own spectrum column.
 template <typename T, int LOGN>
 __global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN>::value <= 512 ? 2 : 1)
-    k_col_conv(Geometry g, typename cplx_t<T>::type* __restrict__ A, const T* __restrict__ khat,
-               const typename cplx_t<T>::type* __restrict__ tw, int cw) {
+    k_col_conv_h(Geometry g, typename cplx_t<T>::type* __restrict__ B, const T* __restrict__ khat,
+                 const T* __restrict__ knyq, const typename cplx_t<T>::type* __restrict__ tw, int cw) {
   typedef typename cplx_t<T>::type C;
   constexpr int TT = Plan<LOGN>::T;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int K = g.K, n = g.n, half = n / 2;
+  const int K = g.K, n = g.n, half = n / 2, H = K / 2;
   const int cc = threadIdx.x % cw, t = threadIdx.x / cw;
   const int c = blockIdx.x * cw + cc;
   C* s = reinterpret_cast<C*>(sm_raw) + cc;  // cw interleaved columns
   auto load = [&](int m) -> C {
-    const int q = t + m * TT;
-    const int i1 = (q + half) & (K - 1);
-    return i1 < n ? A[size_t(i1) * K + c] : cz<C>();
+    const int i1 = (t + m * TT + half) & (K - 1);
+    return i1 < n ? B[size_t(i1) * H + c] : cz<C>();
   };
   auto to_smem = [&](int q, C v) { s[sidx(q) * cw] = v; };
   fft_seq<LOGN>(t, s, cw, tw, -1, load, to_smem);
+  __syncthreads();
+  if (c == 0) {
+    // column 0: the pair (q, -q) per thread, in place; ev(-q) = conj ev(q),
+    // od(-q) = -conj od(q)
+    for (int m = 0; m <= 8; ++m) {
+      const int q = m < 8 ? t + m * TT : H;
+      if (m == 8 && t != 0) break;
+      const int qm = (K - q) & (K - 1);
+      const C P = s[sidx(q) * cw], Pm = s[sidx(qm) * cw];
+      const T evx = T(0.5) * (P.x + Pm.x), evy = T(0.5) * (P.y - Pm.y);
+      const T odx = T(0.5) * (P.x - Pm.x), ody = T(0.5) * (P.y + Pm.y);
+      const T h0 = khat[size_t(q) * cw], hn = knyq[q];
+      s[sidx(q) * cw] = cmk<C>(h0 * evx + hn * odx, h0 * evy + hn * ody);
+      if (qm != q) {
+        const T h0m = khat[size_t(qm) * cw], hnm = knyq[qm];
+        s[sidx(qm) * cw] = cmk<C>(h0m * evx - hnm * odx, hnm * ody - h0m * evy);
+      }
+    }
+  }
   __syncthreads();
   C v[16];
   const T* kc = khat + (size_t(blockIdx.x) * K) * cw + cc;
 #pragma unroll
   for (int m = 0; m < 16; ++m) {
     const int q = t + m * TT;
-    v[m] = cscale(s[sidx(q) * cw], kc[size_t(q) * cw]);
+    v[m] = cscale(s[sidx(q) * cw], c ? kc[size_t(q) * cw] : T(1));
   }
   __syncthreads();
   auto store = [&](int q, C x) {
     const int i1 = (q + half) & (K - 1);
-    if (i1 < n) A[size_t(i1) * K + c] = x;
+    if (i1 < n) B[size_t(i1) * H + c] = x;
   };
   run_stages<LOGN, 0>(v, t, 1, s, cw, tw, +1, store);
+}
+
+// Inverse row pass of the real form: the half spectra of rows a = 2 pr and
+// b = 2 pr + 1 rebuilt into Z = Y_a + i Y_b over all K frequencies
+// (Y(K - k) = conj Y(k)), one inverse FFT, Re -> row a, Im -> row b, crop and
+// row epilogue.
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(kRowCta, 2) k_row_inv_h(Geometry g, const typename cplx_t<T>::type* __restrict__ B,
+                                                       RowEp<T> ep, const typename cplx_t<T>::type* __restrict__ tw,
+                                                       int nseq) {
+  typedef typename cplx_t<T>::type C;
+  constexpr int TT = Plan<LOGN>::T;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __shared__ double red[5 * 32];
+  __shared__ __align__(8) uint64_t bar;
+  const int K = g.K, n = g.n, H = K / 2;
+  const int seq = threadIdx.x / TT, t = threadIdx.x - seq * TT;
+  const int ia = 2 * (blockIdx.x * nseq + seq), ib = ia + 1;
+  C* s = reinterpret_cast<C*>(sm_raw) + seq * padded(K);
+  // The epilogue's operand rows (ops[seq][k][row][n]) arrive by bulk copies
+  // while the transform runs.
+  T* ops_all = reinterpret_cast<T*>(sm_raw + align16(nseq * padded(K) * sizeof(C)));
+  const T* src[2] = {nullptr, nullptr};
+  const int nop = ep_staged(ep, src);
+  if (nop > 0 && threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+    const uint32_t row_bytes = uint32_t(n * sizeof(T));
+    mbar_arrive_expect_tx(&bar, uint32_t(nseq * nop * 2) * row_bytes);
+    for (int q = 0; q < nseq; ++q) {
+      const int r0 = 2 * (blockIdx.x * nseq + q);
+      for (int k = 0; k < nop; ++k)
+        for (int r = 0; r < 2; ++r)
+          bulk_load(ops_all + ((size_t(q) * 2 + k) * 2 + r) * n, src[k] + size_t(r0 + r) * n, row_bytes, &bar);
+    }
+  }
+  __syncthreads();
+  const C* ba = B + size_t(ia) * H;
+  const C* bb = ba + H;
+  // frequency q = t + m K/16: entry q for m < 8, entry K - q (entry 0 for
+  // q = K/2) above; thread 0 unpacks entry 0 into Y(0) and Y(K/2)
+  auto load = [&](int m) -> C {
+    const int q = t + m * TT;
+    const int e = m < 8 ? q : ((K - q) & (H - 1));
+    const C a = ba[e], b = bb[e];
+    if (t == 0 && (m == 0 || m == 8)) return m == 0 ? cmk<C>(a.x, b.x) : cmk<C>(a.y, b.y);
+    return m < 8 ? cmk<C>(a.x - b.y, a.y + b.x) : cmk<C>(a.x + b.y, b.x - a.y);
+  };
+  T val[2][16];
+  int cnt = 0;
+  auto stash = [&](int, C v) {  // sink order, see last_pos
+    val[0][cnt] = v.x;
+    val[1][cnt] = v.y;
+    ++cnt;
+  };
+  fft_seq<LOGN>(t, s, 1, tw, +1, load, stash);
+  const size_t row0[2] = {size_t(ia) * n, size_t(ib) * n};
+  bool ok = true;
+  if (nop > 0) ok = mbar_wait_bounded(&bar, 0, ep.err);
+  EpAcc<T> part;
+  if (ok) part = row_ep_staged<LOGN>(ep, val, t, row0, ops_all + size_t(seq) * 4 * n);
+  row_ep_finish(ep, part, red);
 }
 
 // Plain in-place transforms of a K x K complex array (set-up of the PSF spectrum).
@@ -457,6 +787,14 @@ __global__ void __launch_bounds__(ColThreads<T, LOGN>::value) k_cols_plain(typen
 
 int row_inv_blocks(const Geometry& g) { return g.n / row_nseq(g); }
 
+// Row pairs per CTA of the real-form row passes.
+inline int row_pair_nseq(const Geometry& g) {
+  int s = kRowCta / (g.K / 16);
+  if (s < 1) s = 1;
+  if (s > g.n / 2) s = g.n / 2;
+  return s;
+}
+
 #define PURIFY_LOGN_SWITCH(K, BODY)     \
   switch (K) {                          \
     case 32: { constexpr int L = 5; BODY; } break;   \
@@ -474,7 +812,9 @@ template <typename T, int L> cudaError_t configure_one() {
   if (e == cudaSuccess) e = raise_smem_limit(k_row_inv<T, L>);
   if (e == cudaSuccess) e = raise_smem_limit(k_col_fwd<T, L>);
   if (e == cudaSuccess) e = raise_smem_limit(k_col_inv<T, L>);
-  if (e == cudaSuccess) e = raise_smem_limit(k_col_conv<T, L>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_row_fwd_h<T, L>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_col_conv_h<T, L>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_row_inv_h<T, L>);
   if (e == cudaSuccess) e = raise_smem_limit(k_rows_plain<T, L>);
   if (e == cudaSuccess) e = raise_smem_limit(k_cols_plain<T, L>);
   return e;
@@ -539,13 +879,17 @@ __global__ void k_embed_psf(const T* __restrict__ psf, int n, typename cplx_t<T>
   X[idx] = cmk<C>(psf[size_t(i1) * K + i2], T(0));
 }
 
+// Real part of the spectrum, columns [0, K/2) in launch_col_conv_h's layout
+// [column block][row][cw], column K/2 after them.
 template <typename T>
 __global__ void k_spectrum_layout(const typename cplx_t<T>::type* __restrict__ X, int K, int cw, double scale,
                                   T* __restrict__ khat) {
   const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= size_t(K) * K) return;
-  const int q = int(idx / K), c = int(idx % K);
-  khat[(size_t(c / cw) * K + q) * cw + (c % cw)] = T(double(X[idx].x) * scale);
+  const int q = int(idx / K), c = int(idx % K), H = K / 2;
+  const T v = T(double(X[idx].x) * scale);
+  if (c < H) khat[(size_t(c / cw) * K + q) * cw + (c % cw)] = v;
+  else if (c == H) khat[size_t(H) * K + q] = v;
 }
 
 template <typename T>
@@ -560,12 +904,33 @@ void build_psf_spectrum(const T* psf, int n, T* khat, typename cplx_t<T>::type* 
 }
 
 template <typename T>
-void launch_col_conv(const Geometry& g, typename cplx_t<T>::type* A, const T* khat,
-                     const typename cplx_t<T>::type* tw, cudaStream_t s) {
+void launch_row_fwd_h(const Geometry& g, const RowPro<T>& pro, typename cplx_t<T>::type* B,
+                      const typename cplx_t<T>::type* tw, cudaStream_t s) {
+  typedef typename cplx_t<T>::type C;
+  const int nseq = row_pair_nseq(g);
+  const size_t sm = nseq * padded(g.K) * sizeof(C);
+  PURIFY_LOGN_SWITCH(g.K, (k_row_fwd_h<T, L><<<g.n / 2 / nseq, nseq * Plan<L>::T, sm, s>>>(g, pro, B, tw, nseq)));
+}
+
+template <typename T>
+void launch_col_conv_h(const Geometry& g, typename cplx_t<T>::type* B, const T* khat,
+                       const typename cplx_t<T>::type* tw, cudaStream_t s) {
   typedef typename cplx_t<T>::type C;
   const int cw = col_width<T>();
   const size_t sm = cw * padded(g.K) * sizeof(C);
-  PURIFY_LOGN_SWITCH(g.K, (k_col_conv<T, L><<<g.K / cw, cw * Plan<L>::T, sm, s>>>(g, A, khat, tw, cw)));
+  const T* knyq = khat + size_t(g.K / 2) * g.K;
+  PURIFY_LOGN_SWITCH(g.K, (k_col_conv_h<T, L><<<g.K / 2 / cw, cw * Plan<L>::T, sm, s>>>(g, B, khat, knyq, tw, cw)));
+}
+
+template <typename T>
+int launch_row_inv_h(const Geometry& g, const typename cplx_t<T>::type* B, const RowEp<T>& ep,
+                     const typename cplx_t<T>::type* tw, cudaStream_t s) {
+  typedef typename cplx_t<T>::type C;
+  const int nseq = row_pair_nseq(g);
+  const size_t sm = align16(nseq * padded(g.K) * sizeof(C)) + size_t(nseq) * 4 * g.n * sizeof(T);
+  const int nb = g.n / 2 / nseq;
+  PURIFY_LOGN_SWITCH(g.K, (k_row_inv_h<T, L><<<nb, nseq * Plan<L>::T, sm, s>>>(g, B, ep, tw, nseq)));
+  return nb;
 }
 
 template <typename T>
@@ -591,8 +956,12 @@ void launch_fft2_plain(int K, typename cplx_t<T>::type* X, const typename cplx_t
                                   const cplx_t<T>::type*, cudaStream_t);                                        \
   template int launch_row_inv<T>(const Geometry&, const cplx_t<T>::type*, const T*, const RowEp<T>&,            \
                                  const cplx_t<T>::type*, cudaStream_t);                                        \
-  template void launch_col_conv<T>(const Geometry&, cplx_t<T>::type*, const T*, const cplx_t<T>::type*,         \
-                                   cudaStream_t);                                                              \
+  template void launch_row_fwd_h<T>(const Geometry&, const RowPro<T>&, cplx_t<T>::type*, const cplx_t<T>::type*, \
+                                    cudaStream_t);                                                             \
+  template void launch_col_conv_h<T>(const Geometry&, cplx_t<T>::type*, const T*, const cplx_t<T>::type*,       \
+                                     cudaStream_t);                                                            \
+  template int launch_row_inv_h<T>(const Geometry&, const cplx_t<T>::type*, const RowEp<T>&,                    \
+                                   const cplx_t<T>::type*, cudaStream_t);                                      \
   template void launch_fft2_plain<T>(int, cplx_t<T>::type*, const cplx_t<T>::type*, int, cudaStream_t);     \
   template void build_psf_spectrum<T>(const T*, int, T*, cplx_t<T>::type*, const cplx_t<T>::type*, cudaStream_t);
 INST(float)

@@ -52,7 +52,7 @@ template <typename T> struct DbFilters { T h[kMaxDb][kMaxTaps]; T g[kMaxDb][kMax
 // Row-pass epilogues (inverse row FFT -> image): val = Re(.) * s[i1] s[i2].
 enum RowEpMode : int {
   EP_STORE = 0,     // out = val
-  EP_CG_AP = 1,     // out = nu2 val + 2 p;           partial += p * out
+  EP_CG_AP = 1,     // out = nu2 val + 2 p (= A p);  partials <p,Ap>, <r,Ap>, <Ap,Ap>, <r,p>, <r,r>
   EP_CG_R0 = 2,     // out = b - (nu2 val + 2 p); out2 = out; partial += out^2
   EP_POWER = 3,     // out = val;                      partial += val^2
   EP_XS_ADD = 4,    // out = b + nu val   (b may alias out)
@@ -64,25 +64,31 @@ template <typename T> struct RowEp {
   T* out2;
   const T* p;
   const T* b;
+  const T* r;        // EP_CG_AP: the CG residual
   double nu, nu2;
-  double* partials;
-  // CG scalars finalised by the last block: EP_CG_R0 sets scalars[S_RR];
-  // EP_CG_AP sets scalars[S_ALPHA] = scalars[S_RR] / <p, Ap> (0 if <p, Ap> = 0)
+  double* partials;  // per-CTA partial sums; the k-th sum at partials + k * pstride
+  size_t pstride;
+  // Device scalars (solver slots) finalised by the last block when ticket is
+  // set: EP_CG_R0 sets S_RR; EP_CG_AP sets S_PAP, S_ALPHA = <r,p> / <p,Ap>,
+  // S_BETA and the next <r,r> (from the five sums, see fft.cu).
   double* scalars;
   unsigned int* ticket;
+  int* err;          // device error flag (timed-out operand staging)
 };
 
 // Forward row-pass prologues (image -> row FFT input).
 enum RowProMode : int {
   PRO_PLAIN = 0,    // src = x
-  PRO_CG_P = 1,     // p = r + beta p, beta = scalars[idx]; write p; src = p
+  PRO_CG_STEP = 1,  // x += alpha p, r -= alpha Ap, p = r + beta p (scalars S_ALPHA, S_BETA); src = p
   PRO_SCALE = 2     // src = x * scalars[scale_idx]   (power iteration normalisation)
 };
 template <typename T> struct RowPro {
   int mode;
   const T* x;
   T* p;
-  const T* r;
+  T* r;
+  T* xu;        // PRO_CG_STEP: the CG iterate
+  const T* ap;  // PRO_CG_STEP: A p of the previous step
   const double* scalars;
   int idx;
 };
@@ -144,15 +150,25 @@ template <typename T>
 int launch_row_inv(const Geometry& g, const typename cplx_t<T>::type* A, const T* deapod, const RowEp<T>& ep,
                    const typename cplx_t<T>::type* tw, cudaStream_t s);
 int row_inv_blocks(const Geometry& g);
-// Composite operator Phi^H Phi as a convolution: forward column FFT of the
-// compact rows, multiply by the real PSF spectrum khat ([K/cw][K][cw]),
-// inverse column FFT, crop rows back into A (in place).
+// Composite operator Phi^H Phi as a convolution, in real form: the image
+// rows' half spectra (n x K/2 complex in B, entry 0 = X(0) + i X(K/2)).
+// Forward row pass (prologue, zero-padding, row FFT of row pairs):
 template <typename T>
-void launch_col_conv(const Geometry& g, typename cplx_t<T>::type* A, const T* khat,
+void launch_row_fwd_h(const Geometry& g, const RowPro<T>& pro, typename cplx_t<T>::type* B,
+                      const typename cplx_t<T>::type* tw, cudaStream_t s);
+// Column pass: forward column FFT, multiply by the real PSF spectrum khat
+// ([K/2/cw][K][cw], then column K/2 as K values), inverse FFT, crop (in place).
+template <typename T>
+void launch_col_conv_h(const Geometry& g, typename cplx_t<T>::type* B, const T* khat,
+                       const typename cplx_t<T>::type* tw, cudaStream_t s);
+// Inverse row pass with the row epilogue; returns the number of partial sums.
+template <typename T>
+int launch_row_inv_h(const Geometry& g, const typename cplx_t<T>::type* B, const RowEp<T>& ep,
                      const typename cplx_t<T>::type* tw, cudaStream_t s);
 // Real spectrum of the convolution kernel from the PSF image (2n x 2n real,
 // pixel offsets [-n, n)^2): circulant embedding on the K = 2n grid, forward
-// FFT, scaled by 1/K^2, stored in launch_col_conv's layout.  X: K x K scratch.
+// FFT, scaled by 1/K^2, columns [0, K/2] stored in launch_col_conv_h's layout
+// (K/2 * K + K values).  X: K x K scratch.
 template <typename T>
 void build_psf_spectrum(const T* psf, int n, T* khat, typename cplx_t<T>::type* X,
                         const typename cplx_t<T>::type* tw, cudaStream_t s);

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) k_tile(Geometry g, const __grid_cons
   int cell_cur = -1;
   C g0 = cz<C>(), g1 = cz<C>();   // footprint grid values of the current cell (gather)
   C s0 = cz<C>(), s1 = cz<C>();   // footprint scatter sums of the current cell
-  double p0 = 0.0, p1 = 0.0;
+  Acc<T> p0, p1;
   for (int base = w0; base < w1; base += 32) {
     const int i = base + lane;
     const bool valid = i < w1;
@@ -267,10 +267,12 @@ __global__ void __launch_bounds__(kThreads) k_tile(Geometry g, const __grid_cons
         const T nu = T(dep.nu);
         const C v = cmk<C>(fma(nu, mine.x, z.x), fma(nu, mine.y, z.y));
         dep.z[i] = v;
-        const double dx = double(v.x) - dep.nu * double(yv.x), dy = double(v.y) - dep.nu * double(yv.y);
-        p0 += dx * dx + dy * dy;
-        const double ex = double(mine.x) - double(yv.x), ey = double(mine.y) - double(yv.y);
-        p1 += ex * ex + ey * ey;
+        const T dx = fma(-nu, yv.x, v.x), dy = fma(-nu, yv.y, v.y);
+        p0.add_prod(dx, dx);
+        p0.add_prod(dy, dy);
+        const T ex = mine.x - yv.x, ey = mine.y - yv.y;
+        p1.add_prod(ex, ex);
+        p1.add_prod(ey, ey);
       }
     }
   }
@@ -330,7 +332,7 @@ __global__ void __launch_bounds__(kThreads) k_degrid(Geometry g, const __grid_co
   const int per = (cnt + kWarps - 1) / kWarps;
   const int w0 = it.begin + min(cnt, warp * per), w1 = it.begin + min(cnt, (warp + 1) * per);
   const int grp = lane >> 2, k = lane & 3;
-  double p0 = 0.0, p1 = 0.0;
+  Acc<T> p0, p1;
   for (int base = w0; base < w1; base += 32) {
     const int i = base + lane;
     const bool valid = i < w1;
@@ -403,10 +405,12 @@ __global__ void __launch_bounds__(kThreads) k_degrid(Geometry g, const __grid_co
         const T nu = T(dep.nu);
         const C v = cmk<C>(fma(nu, acc_v.x, z.x), fma(nu, acc_v.y, z.y));
         dep.z[i] = v;
-        const double dx = double(v.x) - dep.nu * double(yv.x), dy = double(v.y) - dep.nu * double(yv.y);
-        p0 += dx * dx + dy * dy;
-        const double ex = double(acc_v.x) - double(yv.x), ey = double(acc_v.y) - double(yv.y);
-        p1 += ex * ex + ey * ey;
+        const T dx = fma(-nu, yv.x, v.x), dy = fma(-nu, yv.y, v.y);
+        p0.add_prod(dx, dx);
+        p0.add_prod(dy, dy);
+        const T ex = acc_v.x - yv.x, ey = acc_v.y - yv.y;
+        p1.add_prod(ex, ex);
+        p1.add_prod(ey, ey);
       }
     }
     __syncwarp();
@@ -469,7 +473,7 @@ __global__ void __launch_bounds__(kThreads) k_degrid_w(Geometry g, const __grid_
   T* wst = reinterpret_cast<T*>(reinterpret_cast<C*>(sm_raw) + kWItems * pe) + warp * 32 * kDgStage;
   if (!warp_stage_patch(patch, &bars[warp], &map, tu, tv, g.TB, PW, lane, err)) return;
   const int grp = lane >> 2, k = lane & 3;
-  double p0 = 0.0, p1 = 0.0;
+  Acc<T> p0, p1;
   for (int base = it.begin; base < it.end; base += 32) {
     const int i = base + lane;
     const bool valid = i < it.end;
@@ -542,20 +546,22 @@ __global__ void __launch_bounds__(kThreads) k_degrid_w(Geometry g, const __grid_
         const T nu = T(dep.nu);
         const C v = cmk<C>(fma(nu, acc_v.x, z.x), fma(nu, acc_v.y, z.y));
         dep.z[i] = v;
-        const double dx = double(v.x) - dep.nu * double(yv.x), dy = double(v.y) - dep.nu * double(yv.y);
-        p0 += dx * dx + dy * dy;
-        const double ex = double(acc_v.x) - double(yv.x), ey = double(acc_v.y) - double(yv.y);
-        p1 += ex * ex + ey * ey;
+        const T dx = fma(-nu, yv.x, v.x), dy = fma(-nu, yv.y, v.y);
+        p0.add_prod(dx, dx);
+        p0.add_prod(dy, dy);
+        const T ex = acc_v.x - yv.x, ey = acc_v.y - yv.y;
+        p1.add_prod(ex, ex);
+        p1.add_prod(ey, ey);
       }
     }
     __syncwarp();
   }
   if (dep.mode == DG_BALL) {
-    p0 = warp_sum(p0);
-    p1 = warp_sum(p1);
+    warp_merge(p0);
+    warp_merge(p1);
     if (lane == 0) {
-      dep.part0[item] = p0;
-      dep.part1[item] = p1;
+      dep.part0[item] = p0.value();
+      dep.part1[item] = p1.value();
     }
   }
 }

@@ -29,7 +29,7 @@ struct purify_op {
 
   // ---- kernel timing (instrumentation)
   enum Kind { KK_ROW_FWD = 0, KK_COL_FWD, KK_DEGRID, KK_GRID, KK_GRAM, KK_COL_INV, KK_ROW_INV, KK_SARA_ANA,
-              KK_SARA_SYN, KK_VEC, KK_MEMSET, KK_COL_CONV, KK_COUNT };
+              KK_SARA_SYN, KK_VEC, KK_MEMSET, KK_COL_CONV, KK_ROW_FWD_H, KK_ROW_INV_H, KK_COUNT };
   bool prof = false;
   struct Pending { int kind; cudaEvent_t a, b; };
   std::vector<Pending> pending;

@@ -49,7 +49,7 @@ template <typename T> struct CoefOut {
   T gamma;
 };
 
-template <typename T> PD void emit(const CoefOut<T>& o, size_t idx, T alpha, double& part) {
+template <typename T> PD void emit(const CoefOut<T>& o, size_t idx, T alpha, Acc<T>& part) {
   if (!o.prox) {
     o.c[idx] = alpha;
     return;
@@ -61,7 +61,7 @@ template <typename T> PD void emit(const CoefOut<T>& o, size_t idx, T alpha, dou
   const T r = av > thr ? copysign(av - thr, v) : T(0);
   o.z1[idx] = v - r;
   o.cs[idx] = T(2) * r - v;
-  part += double(wj) * fabs(double(alpha));
+  part.add_prod(wj, fabs(alpha));
 }
 
 template <typename T> struct AnaArgs {
@@ -103,7 +103,7 @@ __device__ void ana_body(const AnaArgs<T>& A, const T* __restrict__ h, const T* 
     hi[e] = sh;
   }
   __syncthreads();
-  double part = 0.0;
+  Acc<T> part;
   const int r = threadIdx.x / kTH, c = threadIdx.x - r * kTH;
   const int R = r0 + r, Cc = c0 + c;
   if (R < H && Cc < H) {
@@ -158,7 +158,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThr) k_dirac(const T* __restrict__ x, size_t N, CoefOut<T> out,
                                                 double* partials) {
   __shared__ double red[32];
-  double part = 0.0;
+  Acc<T> part;
   const size_t i = size_t(blockIdx.x) * kThr + threadIdx.x;
   if (i < N) emit(out, i, x[i] * third<T>(), part);
   if (partials) {

@@ -62,7 +62,7 @@ extern "C" int purify_estimate_bytes(int64_t M, int n, int dwt_levels, int preci
     // composite operator: spectrum kept; while it is built, a 2n operator,
     // a unit-visibility vector and two K^2 buffers live for a moment
     const double n2 = 2.0 * n, N2 = n2 * n2, K2 = 2 * n2, KP2 = K2 + 8;
-    b += K * K * r;
+    b += (K / 2 + 1) * K * r;
     b += M * (2 * r + 4 + 16) + n2 * K2 * c + 2 * KP2 * KP2 * c + 2 * 8 * (N2 / 4) * r + 9 * N2 * r;
     b += M * c + K * K * (r + c);
   }

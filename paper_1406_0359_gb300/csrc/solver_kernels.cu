@@ -8,33 +8,29 @@ namespace purify {
 
 namespace {
 constexpr int kT = 256;
-constexpr int kCgBlocks = 512;
 
-// CG update x += alpha p, r -= alpha Ap (alpha = sc[S_ALPHA]); partials of
-// <r, r>, and the last block sets beta = <r, r>_new / <r, r>_old and
-// <r, r> = <r, r>_new in the device scalars.
+// 16-byte vectors of the CG update.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { typedef float4 type; static constexpr int W = 4; };
+template <> struct Vec16<double> { typedef double2 type; static constexpr int W = 2; };
+
+// x += sc[idx] p on 16-byte vectors (N / W of them, both arrays 16-byte aligned).
 template <typename T>
-__global__ void __launch_bounds__(kT) k_cg_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
-                                              const T* __restrict__ Ap, double* __restrict__ sc, size_t N,
-                                              double* __restrict__ partials, unsigned int* ticket) {
-  __shared__ double red[32];
-  const T alpha = T(sc[S_ALPHA]);
-  double part = 0.0;
-  for (size_t i = size_t(blockIdx.x) * kT + threadIdx.x; i < N; i += size_t(gridDim.x) * kT) {
-    x[i] = fma(alpha, p[i], x[i]);
-    const T rv = fma(-alpha, Ap[i], r[i]);
-    r[i] = rv;
-    part += double(rv) * double(rv);
-  }
-  const double t = block_sum<kT>(part, red);
-  if (threadIdx.x == 0) partials[blockIdx.x] = t;
-  if (last_block_done(ticket)) {
-    const double rr_new = block_sum_array(partials, int(gridDim.x), red);
-    if (threadIdx.x == 0) {
-      const double rr = sc[S_RR];
-      sc[S_BETA] = rr > 0.0 ? rr_new / rr : 0.0;
-      sc[S_RR] = rr_new;
-    }
+__global__ void __launch_bounds__(kT) k_axpy(T* __restrict__ x, const T* __restrict__ p,
+                                             const double* __restrict__ sc, int idx, size_t N) {
+  typedef typename Vec16<T>::type V;
+  constexpr int W = Vec16<T>::W;
+  const T a = T(sc[idx]);
+  V* xv = reinterpret_cast<V*>(x);
+  const V* pv = reinterpret_cast<const V*>(p);
+  for (size_t i = size_t(blockIdx.x) * kT + threadIdx.x; i < N / W; i += size_t(gridDim.x) * kT) {
+    V xs = xv[i];
+    const V ps = pv[i];
+    T* xe = reinterpret_cast<T*>(&xs);
+    const T* pe = reinterpret_cast<const T*>(&ps);
+#pragma unroll
+    for (int k = 0; k < W; ++k) xe[k] = fma(a, pe[k], xe[k]);
+    xv[i] = xs;
   }
 }
 
@@ -182,17 +178,10 @@ inline int nblk(size_t N) {
 
 int vec_blocks(size_t N) { return nblk(N); }
 
-int cg_xr_blocks(size_t N) {
-  const int b = nblk(N);
-  return b < kCgBlocks ? b : kCgBlocks;
-}
-
-template <typename T>
-int launch_cg_xr(T* x, T* r, const T* p, const T* Ap, double* sc, size_t N, double* partials, unsigned int* ticket,
-                 cudaStream_t s) {
-  const int b = cg_xr_blocks(N);
-  k_cg_xr<T><<<b, kT, 0, s>>>(x, r, p, Ap, sc, N, partials, ticket);
-  return b;
+template <typename T> void launch_axpy(T* x, const T* p, const double* sc, int idx, size_t N, cudaStream_t s) {
+  // one 16-byte vector per thread; N and the pointers are multiples of 16
+  // bytes (n x n images, n >= 16; cudaMalloc'd arrays)
+  k_axpy<T><<<nblk((N + 3) / 4), kT, 0, s>>>(x, p, sc, idx, N);
 }
 
 void launch_finalize(const double* pa, int na, const double* pb, int nb, int op, double arg, double* sc,
@@ -230,8 +219,7 @@ template <typename C> void launch_gather(const C* src, const int* perm, size_t M
 }
 
 #define INST(T)                                                                                       \
-  template int launch_cg_xr<T>(T*, T*, const T*, const T*, double*, size_t, double*, unsigned int*,     \
-                               cudaStream_t);                                                          \
+  template void launch_axpy<T>(T*, const T*, const double*, int, size_t, cudaStream_t);                \
   template int launch_reduce<T>(const T*, size_t, int, const double*, double*, cudaStream_t);           \
   template void launch_reweight<T>(T*, size_t, double, cudaStream_t);                                   \
   template void launch_fill<T>(T*, size_t, T, cudaStream_t);                                            \

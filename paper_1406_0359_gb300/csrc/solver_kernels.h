@@ -16,12 +16,8 @@ enum FinOp : int { FIN_RR0 = 0, FIN_ALPHA, FIN_BETA, FIN_BALL, FIN_OBJ, FIN_NORM
 enum RedOp : int { RED_SQ = 0, RED_SUM, RED_VAR, RED_MAXABS };
 
 int vec_blocks(size_t N);
-// CG update with alpha = sc[S_ALPHA]; the last block sets sc[S_BETA] and
-// sc[S_RR].  Returns the number of <r,r> partials written (cg_xr_blocks(N)).
-template <typename T>
-int launch_cg_xr(T* x, T* r, const T* p, const T* Ap, double* sc, size_t N, double* partials, unsigned int* ticket,
-                 cudaStream_t s);
-int cg_xr_blocks(size_t N);
+// x += sc[idx] p; N a multiple of 4, both arrays 16-byte aligned.
+template <typename T> void launch_axpy(T* x, const T* p, const double* sc, int idx, size_t N, cudaStream_t s);
 void launch_finalize(const double* pa, int na, const double* pb, int nb, int op, double arg, double* sc,
                      cudaStream_t s);
 template <typename T>
