@@ -304,8 +304,8 @@ template <typename T> class OpImpl : public purify_op {
   void grid(const GridPro<C>& pro, cudaStream_t s) {
     PROF(KK_GRID, s, launch_grid<T>(g, items, n_items, pos, perm, kb, pro, gridQ, s));
   }
-  void fin(const double* pa, int na, const double* pb, int nb, int op, double arg, cudaStream_t s) {
-    PROF(KK_VEC, s, launch_finalize(pa, na, pb, nb, op, arg, sc, s));
+  void fin(const double* pa, int na, int op, double arg, cudaStream_t s) {
+    PROF(KK_VEC, s, launch_finalize<T>(pa, na, op, arg, sc, s));
   }
   RowPro<T> plain(const T* x) const {
     RowPro<T> pro{};
@@ -488,7 +488,7 @@ template <typename T> class OpImpl : public purify_op {
       ep.out = Ap;
       ep.partials = partials;
       const int np = normal_back(ep, s);
-      fin(partials, np, nullptr, 0, FIN_NORM, 0.0, s);
+      fin(partials, np, FIN_NORM, 0.0, s);
     }
     int rc = check(s, true);
     if (rc) return rc;
@@ -524,9 +524,9 @@ template <typename T> class OpImpl : public purify_op {
     sara_analysis<T>(sara, xh, z1, s);
     const size_t D = 9 * N();
     int np = launch_reduce<T>(z1, D, RED_SUM, sc, partials, s);
-    launch_finalize(partials, np, nullptr, 0, FIN_MEAN, double(D), sc, s);
+    launch_finalize<T>(partials, np, FIN_MEAN, double(D), sc, s);
     np = launch_reduce<T>(z1, D, RED_VAR, sc, partials, s);
-    launch_finalize(partials, np, nullptr, 0, FIN_VAR, double(D), sc, s);
+    launch_finalize<T>(partials, np, FIN_VAR, double(D), sc, s);
     int rc = check(s, true);
     if (rc) return rc;
     if ((rc = read_scalars(s))) return rc;
@@ -592,7 +592,7 @@ template <typename T> class OpImpl : public purify_op {
     b1.partials = partials;
     int npo = 0;
     PROF(KK_SARA_ANA, s, npo = sara_analysis_prox<T>(sara, xh, b1, s));
-    fin(partials, npo, nullptr, 0, FIN_OBJ, 0.0, s);
+    fin(partials, npo, FIN_OBJ, 0.0, s);
     PROF(KK_SARA_SYN, s, sara_synthesis_pos<T>(sara, xh, z2, xs, s));
     // block 3 (data fidelity): v = nu Phi x_hat + z_3, project on the ball,
     // xs += nu Re Phi^H (2r - v)
@@ -605,7 +605,7 @@ template <typename T> class OpImpl : public purify_op {
     dep.part0 = partials;
     dep.part1 = partials + n_items;
     degrid(dep, s);
-    PROF(KK_VEC, s, launch_finalize_blocks(partials, partials + n_items, reinterpret_cast<const int*>(items), n_items,
+    PROF(KK_VEC, s, launch_finalize_blocks<T>(partials, partials + n_items, reinterpret_cast<const int*>(items), n_items,
                                            nblocks, nu, eps_dev, scale_dev, sc, s));
     zero_q(s);
     GridPro<C> gp{};

@@ -105,29 +105,45 @@ template <int NT> __device__ double block_sum(double v, double* sh /*[32]*/) {
   __syncthreads();
   return r;
 }
-// Warp sum of compensated partials (the FP32 pairs merge in FP32), then the
-// block sum of the warps' values in FP64; result valid in thread 0.
+// Merging of compensated partials.  Per-block partial sums are stored as
+// Acc<T> (8 bytes, in double-sized slots) and merged in the same compensated
+// FP32 form, so the only FP64 arithmetic of a reduction is the final value:
+// the FP64 units of GB300 are few, and chains of dependent FP64 adds in every
+// block's tail would cost microseconds.
+PD void acc_merge(Acc<float>& a, const Acc<float>& b) {
+  a.c += b.c;
+  a.add(b.s);
+}
+PD void acc_merge(Acc<double>& a, const Acc<double>& b) { a.s += b.s; }
 PD void warp_merge(Acc<float>& a) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const float s2 = __shfl_down_sync(0xffffffffu, a.s, o), c2 = __shfl_down_sync(0xffffffffu, a.c, o);
-    a.c += c2;
-    a.add(s2);
+    Acc<float> b;
+    b.s = __shfl_down_sync(0xffffffffu, a.s, o);
+    b.c = __shfl_down_sync(0xffffffffu, a.c, o);
+    acc_merge(a, b);
   }
 }
 PD void warp_merge(Acc<double>& a) { a.s = warp_sum(a.s); }
-template <int NT, typename T> __device__ double block_sum(Acc<T> a, double* sh /*[32]*/) {
+// Block merge; result valid in thread 0.  sh: NT/32 double-sized slots.
+template <int NT, typename T> __device__ Acc<T> block_merge(Acc<T> a, double* sh) {
+  Acc<T>* st = reinterpret_cast<Acc<T>*>(sh);
   warp_merge(a);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) sh[w] = a.value();
+  if (lane == 0) st[w] = a;
   __syncthreads();
-  double r = 0.0;
   if (w == 0) {
-    r = (lane < NT / 32) ? sh[lane] : 0.0;
-    r = warp_sum(r);
+    a = lane < NT / 32 ? st[lane] : Acc<T>();
+    warp_merge(a);
   }
   __syncthreads();
-  return r;
+  return a;
+}
+// Merge of n stored partials by one block of NT threads; result in thread 0.
+template <int NT, typename T> __device__ Acc<T> merge_array(const Acc<T>* p, int n, double* sh) {
+  Acc<T> a;
+  for (int i = threadIdx.x; i < n; i += NT) acc_merge(a, p[i]);
+  return block_merge<NT>(a, sh);
 }
 template <int NT> __device__ double block_max(double v, double* sh) {
   v = warp_max(v);

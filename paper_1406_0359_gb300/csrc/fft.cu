@@ -357,33 +357,38 @@ template <typename T> PD void row_ep_finish(const RowEp<T>& ep, EpAcc<T> part, d
   if (!ep.partials) return;
   const int nsum = ep.mode == EP_CG_AP ? 5 : 1;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = int((blockDim.x + 31) >> 5);
+  Acc<T>* st = reinterpret_cast<Acc<T>*>(red);
+  Acc<T>* P = reinterpret_cast<Acc<T>*>(ep.partials);
   for (int k = 0; k < nsum; ++k) {
     warp_merge(part.a[k]);
-    if (lane == 0) red[k * 32 + w] = part.a[k].value();
+    if (lane == 0) st[k * 32 + w] = part.a[k];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (w == 0) {
     for (int k = 0; k < nsum; ++k) {
-      double tot = 0.0;
-      for (int q = 0; q < nw; ++q) tot += red[k * 32 + q];
-      ep.partials[size_t(k) * ep.pstride + blockIdx.x] = tot;
+      Acc<T> b = lane < nw ? st[k * 32 + lane] : Acc<T>();
+      warp_merge(b);
+      if (lane == 0) P[size_t(k) * ep.pstride + blockIdx.x] = b;
     }
   }
   if (!ep.ticket || !last_block_done_t0(ep.ticket)) return;
-  // last block: the sums over all blocks, fixed order
-  double sum[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  // last block: merge all blocks' partials (fixed order), FP64 only at the end
+  EpAcc<T> tot;
   for (int i = threadIdx.x; i < int(gridDim.x); i += blockDim.x)
-    for (int k = 0; k < nsum; ++k) sum[k] += ep.partials[size_t(k) * ep.pstride + i];
+    for (int k = 0; k < nsum; ++k) acc_merge(tot.a[k], P[size_t(k) * ep.pstride + i]);
   for (int k = 0; k < nsum; ++k) {
-    sum[k] = warp_sum(sum[k]);
-    if (lane == 0) red[k * 32 + w] = sum[k];
+    warp_merge(tot.a[k]);
+    if (lane == 0) st[k * 32 + w] = tot.a[k];
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
+  if (w != 0) return;
+  double sum[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   for (int k = 0; k < nsum; ++k) {
-    sum[k] = 0.0;
-    for (int q = 0; q < nw; ++q) sum[k] += red[k * 32 + q];
+    Acc<T> b = lane < nw ? st[k * 32 + lane] : Acc<T>();
+    warp_merge(b);
+    sum[k] = b.value();
   }
+  if (lane != 0) return;
   double* sc = ep.scalars;
   if (ep.mode == EP_CG_R0) {
     sc[S_RR] = sum[0];

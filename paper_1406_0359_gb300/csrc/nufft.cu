@@ -278,11 +278,11 @@ __global__ void __launch_bounds__(kThreads) k_tile(Geometry g, const __grid_cons
   }
   if (MODE == TM_DEGRID) {
     if (dep.mode == DG_BALL) {
-      const double r0 = block_sum<kThreads>(p0, red);
-      const double r1 = block_sum<kThreads>(p1, red);
+      const Acc<T> r0 = block_merge<kThreads>(p0, red);
+      const Acc<T> r1 = block_merge<kThreads>(p1, red);
       if (threadIdx.x == 0) {
-        dep.part0[blockIdx.x] = r0;
-        dep.part1[blockIdx.x] = r1;
+        reinterpret_cast<Acc<T>*>(dep.part0)[blockIdx.x] = r0;
+        reinterpret_cast<Acc<T>*>(dep.part1)[blockIdx.x] = r1;
       }
     }
     return;
@@ -416,11 +416,11 @@ __global__ void __launch_bounds__(kThreads) k_degrid(Geometry g, const __grid_co
     __syncwarp();
   }
   if (dep.mode == DG_BALL) {
-    const double r0 = block_sum<kThreads>(p0, red);
-    const double r1 = block_sum<kThreads>(p1, red);
+    const Acc<T> r0 = block_merge<kThreads>(p0, red);
+    const Acc<T> r1 = block_merge<kThreads>(p1, red);
     if (threadIdx.x == 0) {
-      dep.part0[blockIdx.x] = r0;
-      dep.part1[blockIdx.x] = r1;
+      reinterpret_cast<Acc<T>*>(dep.part0)[blockIdx.x] = r0;
+      reinterpret_cast<Acc<T>*>(dep.part1)[blockIdx.x] = r1;
     }
   }
 }
@@ -560,8 +560,8 @@ __global__ void __launch_bounds__(kThreads) k_degrid_w(Geometry g, const __grid_
     warp_merge(p0);
     warp_merge(p1);
     if (lane == 0) {
-      dep.part0[item] = p0.value();
-      dep.part1[item] = p1.value();
+      reinterpret_cast<Acc<T>*>(dep.part0)[item] = p0;
+      reinterpret_cast<Acc<T>*>(dep.part1)[item] = p1;
     }
   }
 }

@@ -72,7 +72,7 @@ template <typename T> struct AnaArgs {
   T* s_out;          // LL scratch [8][H*H]
   int last;          // LL band is final
   CoefOut<T> out;
-  double* partials;  // per-CTA objective partials (prox only)
+  double* partials;  // per-CTA objective partials, Acc<T> in double slots (prox only)
 };
 
 template <typename T, int F>
@@ -127,9 +127,9 @@ __device__ void ana_body(const AnaArgs<T>& A, const T* __restrict__ h, const T* 
       A.s_out[size_t(k) * H * H + size_t(R) * H + Cc] = ll;
   }
   if (A.partials) {
-    const double t = block_sum<kThr>(part, red);
+    const Acc<T> t = block_merge<kThr>(part, red);
     if (threadIdx.x == 0)
-      A.partials[(size_t(blockIdx.z) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
+      reinterpret_cast<Acc<T>*>(A.partials)[(size_t(blockIdx.z) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
   }
 }
 
@@ -162,8 +162,8 @@ __global__ void __launch_bounds__(kThr) k_dirac(const T* __restrict__ x, size_t 
   const size_t i = size_t(blockIdx.x) * kThr + threadIdx.x;
   if (i < N) emit(out, i, x[i] * third<T>(), part);
   if (partials) {
-    const double t = block_sum<kThr>(part, red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+    const Acc<T> t = block_merge<kThr>(part, red);
+    if (threadIdx.x == 0) reinterpret_cast<Acc<T>*>(partials)[blockIdx.x] = t;
   }
 }
 

@@ -1,6 +1,6 @@
 // Small vector kernels of the SDMM solver (Algorithm 1) and the SARA
-// reweighting: CG vector updates with FP64 partial sums, deterministic
-// finalisation of device scalars (CG alpha/beta, the l2-ball scale, the
+// reweighting: the last CG update, deterministic finalisation of device
+// scalars from compensated per-block partials (the l2-ball scales, the
 // objective, norms), visibility permutation and the reweighting rule.
 #include "solver_kernels.h"
 
@@ -34,36 +34,15 @@ __global__ void __launch_bounds__(kT) k_axpy(T* __restrict__ x, const T* __restr
   }
 }
 
-// One block: sum partials in a fixed order, then apply `op`.
-__global__ void __launch_bounds__(kT) k_finalize(const double* __restrict__ pa, int na,
-                                                 const double* __restrict__ pb, int nb, int op, double arg,
+// One block: merge the compensated partials (Acc<T>) in a fixed order, then
+// apply `op` (FinOp) in FP64.
+template <typename T>
+__global__ void __launch_bounds__(kT) k_finalize(const double* __restrict__ pa, int na, int op, double arg,
                                                  double* __restrict__ sc) {
   __shared__ double red[32];
-  double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < na; i += kT) a += pa[i];
-  for (int i = threadIdx.x; i < nb; i += kT) b += pb[i];
-  a = block_sum<kT>(a, red);
-  b = block_sum<kT>(b, red);
+  const double a = merge_array<kT>(reinterpret_cast<const Acc<T>*>(pa), na, red).value();
   if (threadIdx.x != 0) return;
   switch (op) {
-    case FIN_RR0:
-      sc[S_RR] = a;
-      break;
-    case FIN_ALPHA:
-      sc[S_PAP] = a;
-      sc[S_ALPHA] = a > 0.0 ? sc[S_RR] / a : 0.0;
-      break;
-    case FIN_BETA: {
-      const double rr = sc[S_RR];
-      sc[S_BETA] = rr > 0.0 ? a / rr : 0.0;
-      sc[S_RR] = a;
-    } break;
-    case FIN_BALL: {  // arg = nu * eps
-      const double s = sqrt(a);
-      sc[S_BALLNORM] = s;
-      sc[S_BALLSCALE] = (s <= arg) ? 1.0 : arg / s;
-      sc[S_RESID] = sqrt(b);
-    } break;
     case FIN_OBJ:
       sc[S_OBJ] = a;
       break;
@@ -78,38 +57,41 @@ __global__ void __launch_bounds__(kT) k_finalize(const double* __restrict__ pa, 
     case FIN_VAR:
       sc[S_STD] = sqrt(a / arg);
       break;
-    case FIN_MAX:
-      sc[S_MAXABS] = a;
+    default:
       break;
   }
 }
 
 // Per-block l2-ball scalars (Eq. 5): for every visibility block b, ||v - nu y||
-// and ||Phi x - y|| over the work items of that block (fixed order), the
-// projection scale min(1, nu eps_b / ||v - nu y||_b), the total residual and
-// the worst feasibility ratio max_b ||y_b - Phi_b x|| / eps_b.
+// and ||Phi x - y|| over the work items of that block (fixed order, from the
+// items' compensated partials), the projection scale
+// min(1, nu eps_b / ||v - nu y||_b), the total residual and the worst
+// feasibility ratio max_b ||y_b - Phi_b x|| / eps_b.
+template <typename T>
 __global__ void __launch_bounds__(kT) k_finalize_blocks(const double* __restrict__ part0,
                                                         const double* __restrict__ part1,
                                                         const int* __restrict__ item_block, int n_items, int R,
                                                         double nu, const double* __restrict__ eps_b,
                                                         double* __restrict__ scale_b, double* __restrict__ sc) {
   __shared__ double red[32];
+  const Acc<T>* p0 = reinterpret_cast<const Acc<T>*>(part0);
+  const Acc<T>* p1 = reinterpret_cast<const Acc<T>*>(part1);
   double tot1 = 0.0, worst = 0.0;
   for (int b = 0; b < R; ++b) {
-    double a = 0.0, c = 0.0;
+    Acc<T> a, c;
     for (int i = threadIdx.x; i < n_items; i += kT) {
-      if (item_block[4 * i] == b) {  // WorkItem::pad
-        a += part0[i];
-        c += part1[i];
+      if (R == 1 || item_block[4 * i] == b) {  // WorkItem::pad
+        acc_merge(a, p0[i]);
+        acc_merge(c, p1[i]);
       }
     }
-    a = block_sum<kT>(a, red);
-    c = block_sum<kT>(c, red);
+    const double av = block_merge<kT>(a, red).value();
+    const double cv = block_merge<kT>(c, red).value();
     if (threadIdx.x == 0) {
-      const double s = sqrt(a), rad = nu * eps_b[b];
+      const double s = sqrt(av), rad = nu * eps_b[b];
       scale_b[b] = s <= rad ? 1.0 : rad / s;
-      tot1 += c;
-      const double ratio = sqrt(c) / eps_b[b];
+      tot1 += cv;
+      const double ratio = sqrt(cv) / eps_b[b];
       worst = ratio > worst ? ratio : worst;
     }
   }
@@ -120,23 +102,36 @@ __global__ void __launch_bounds__(kT) k_finalize_blocks(const double* __restrict
   }
 }
 
+// Per-block partials of a reduction over v: compensated sums (RED_SUM, RED_VAR
+// about sc[S_MEAN], RED_SQ) stored as Acc<T>; RED_MAXABS stores the block
+// maximum as a double.
 template <typename T>
 __global__ void __launch_bounds__(kT) k_sum_partials(const T* __restrict__ v, size_t N, int op,
                                                      const double* __restrict__ sc, double* __restrict__ partials) {
   __shared__ double red[32];
-  double part = 0.0;
-  const double mean = op == RED_VAR ? sc[S_MEAN] : 0.0;
-  for (size_t i = size_t(blockIdx.x) * kT + threadIdx.x; i < N; i += size_t(gridDim.x) * kT) {
-    const double x = double(v[i]);
-    if (op == RED_SUM) part += x;
-    else if (op == RED_VAR) part += (x - mean) * (x - mean);
-    else if (op == RED_MAXABS) part = fmax(part, fabs(x));
-    else part += x * x;
+  if (op == RED_MAXABS) {
+    double m = 0.0;
+    for (size_t i = size_t(blockIdx.x) * kT + threadIdx.x; i < N; i += size_t(gridDim.x) * kT)
+      m = fmax(m, fabs(double(v[i])));
+    m = block_max<kT>(m, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = m;
+    return;
   }
-  double t;
-  if (op == RED_MAXABS) t = block_max<kT>(part, red);
-  else t = block_sum<kT>(part, red);
-  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  Acc<T> part;
+  const T mean = op == RED_VAR ? T(sc[S_MEAN]) : T(0);
+  for (size_t i = size_t(blockIdx.x) * kT + threadIdx.x; i < N; i += size_t(gridDim.x) * kT) {
+    const T x = v[i];
+    if (op == RED_SUM) {
+      part.add(x);
+    } else if (op == RED_VAR) {
+      const T d = x - mean;
+      part.add_prod(d, d);
+    } else {
+      part.add_prod(x, x);
+    }
+  }
+  const Acc<T> t = block_merge<kT>(part, red);
+  if (threadIdx.x == 0) reinterpret_cast<Acc<T>*>(partials)[blockIdx.x] = t;
 }
 
 __global__ void __launch_bounds__(kT) k_max_partials(const double* __restrict__ p, int np, double* __restrict__ sc) {
@@ -184,9 +179,8 @@ template <typename T> void launch_axpy(T* x, const T* p, const double* sc, int i
   k_axpy<T><<<nblk((N + 3) / 4), kT, 0, s>>>(x, p, sc, idx, N);
 }
 
-void launch_finalize(const double* pa, int na, const double* pb, int nb, int op, double arg, double* sc,
-                     cudaStream_t s) {
-  k_finalize<<<1, kT, 0, s>>>(pa, na, pb, nb, op, arg, sc);
+template <typename T> void launch_finalize(const double* pa, int na, int op, double arg, double* sc, cudaStream_t s) {
+  k_finalize<T><<<1, kT, 0, s>>>(pa, na, op, arg, sc);
 }
 
 template <typename T>
@@ -196,9 +190,10 @@ int launch_reduce(const T* v, size_t N, int op, const double* sc, double* partia
   return b;
 }
 
+template <typename T>
 void launch_finalize_blocks(const double* part0, const double* part1, const int* items_as_int, int n_items, int R,
                             double nu, const double* eps_b, double* scale_b, double* sc, cudaStream_t s) {
-  k_finalize_blocks<<<1, kT, 0, s>>>(part0, part1, items_as_int + 3, n_items, R, nu, eps_b, scale_b, sc);
+  k_finalize_blocks<T><<<1, kT, 0, s>>>(part0, part1, items_as_int + 3, n_items, R, nu, eps_b, scale_b, sc);
 }
 
 void launch_max_partials(const double* p, int np, double* sc, cudaStream_t s) {
@@ -220,6 +215,9 @@ template <typename C> void launch_gather(const C* src, const int* perm, size_t M
 
 #define INST(T)                                                                                       \
   template void launch_axpy<T>(T*, const T*, const double*, int, size_t, cudaStream_t);                \
+  template void launch_finalize<T>(const double*, int, int, double, double*, cudaStream_t);             \
+  template void launch_finalize_blocks<T>(const double*, const double*, const int*, int, int, double,           \
+                                          const double*, double*, double*, cudaStream_t);                      \
   template int launch_reduce<T>(const T*, size_t, int, const double*, double*, cudaStream_t);           \
   template void launch_reweight<T>(T*, size_t, double, cudaStream_t);                                   \
   template void launch_fill<T>(T*, size_t, T, cudaStream_t);                                            \

@@ -12,19 +12,20 @@ enum ScalarSlot : int {
   S_RR = 0, S_ALPHA, S_BETA, S_PAP, S_BALLSCALE, S_BALLNORM, S_RESID, S_OBJ,
   S_LAMBDA, S_INVNORM, S_MEAN, S_STD, S_MAXABS, S_FEAS, kNumScalars
 };
-enum FinOp : int { FIN_RR0 = 0, FIN_ALPHA, FIN_BETA, FIN_BALL, FIN_OBJ, FIN_NORM, FIN_MEAN, FIN_VAR, FIN_MAX };
+enum FinOp : int { FIN_OBJ = 0, FIN_NORM, FIN_MEAN, FIN_VAR };
 enum RedOp : int { RED_SQ = 0, RED_SUM, RED_VAR, RED_MAXABS };
 
 int vec_blocks(size_t N);
 // x += sc[idx] p; N a multiple of 4, both arrays 16-byte aligned.
 template <typename T> void launch_axpy(T* x, const T* p, const double* sc, int idx, size_t N, cudaStream_t s);
-void launch_finalize(const double* pa, int na, const double* pb, int nb, int op, double arg, double* sc,
-                     cudaStream_t s);
+// Merge na partials (Acc<T> values in double-sized slots) and apply `op`.
+template <typename T> void launch_finalize(const double* pa, int na, int op, double arg, double* sc, cudaStream_t s);
 template <typename T>
 int launch_reduce(const T* v, size_t N, int op, const double* sc, double* partials, cudaStream_t s);
 void launch_max_partials(const double* p, int np, double* sc, cudaStream_t s);
 // Ball scalars per visibility block; items_as_int points at the WorkItem array
 // (four ints per item, the block in the fourth).
+template <typename T>
 void launch_finalize_blocks(const double* part0, const double* part1, const int* items_as_int, int n_items, int R,
                             double nu, const double* eps_b, double* scale_b, double* sc, cudaStream_t s);
 template <typename T> void launch_reweight(T* w, size_t N, double delta, cudaStream_t s);
