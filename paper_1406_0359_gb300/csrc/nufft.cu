@@ -102,6 +102,33 @@ template <typename T> struct Pair2;
 template <> struct Pair2<float> { typedef float2 type; };
 template <> struct Pair2<double> { typedef double2 type; };
 
+// One lane's staged visibility record (kStage values: wu[J], wv[J], e0, e1,
+// the packed cell as int bits, pad) written as 16-byte vectors: at the 80-byte
+// (FP32) lane stride each quarter-warp's vector stores hit distinct bank
+// groups, where scalar stores at that stride collide four ways.
+template <typename T> PD void stage_store(T* st, const T (&wu)[kJ], const T (&wv)[kJ], T e0, T e1, int cell);
+template <> PD void stage_store<float>(float* st, const float (&wu)[kJ], const float (&wv)[kJ], float e0, float e1,
+                                       int cell) {
+  float4* d = reinterpret_cast<float4*>(st);
+  d[0] = make_float4(wu[0], wu[1], wu[2], wu[3]);
+  d[1] = make_float4(wu[4], wu[5], wu[6], wu[7]);
+  d[2] = make_float4(wv[0], wv[1], wv[2], wv[3]);
+  d[3] = make_float4(wv[4], wv[5], wv[6], wv[7]);
+  d[4] = make_float4(e0, e1, __int_as_float(cell), 0.f);
+}
+template <> PD void stage_store<double>(double* st, const double (&wu)[kJ], const double (&wv)[kJ], double e0,
+                                        double e1, int cell) {
+  double2* d = reinterpret_cast<double2*>(st);
+#pragma unroll
+  for (int a = 0; a < kJ / 2; ++a) {
+    d[a] = make_double2(wu[2 * a], wu[2 * a + 1]);
+    d[kJ / 2 + a] = make_double2(wv[2 * a], wv[2 * a + 1]);
+  }
+  d[kJ] = make_double2(e0, e1);
+  d[kJ + 1] = make_double2(__hiloint2double(0, cell), 0.0);
+}
+static_assert(kStage == 2 * kJ + 4 && kJ == 8, "stage_store writes 2J + 4 values");
+
 template <typename T> __host__ __device__ inline size_t tile_patch_bytes(int TB) {
   const size_t PW = size_t(TB + kJ);
   return PW * (PW + 2) * sizeof(typename cplx_t<T>::type);
@@ -303,127 +330,7 @@ __global__ void __launch_bounds__(kThreads) k_tile(Geometry g, const __grid_cons
   }
 }
 
-// Degridding (no scatter, so visibilities of one warp never conflict): one
-// CTA per work item, warp w a contiguous slice.  Per 32-wide batch every
-// lane computes its visibility's weights into the warp's staging rows; then
-// each step serves 8 visibilities with 4 lanes each, lane k of a group
-// gathering footprint rows 2k and 2k+1 (16 taps) from the staged patch, and
-// two shuffle levels sum the group.  The owner lane runs the epilogue.
-constexpr int kDgStage = 2 * kJ + 4;  // wu[J], wv[J], y.re, y.im, cell, pad
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_degrid(Geometry g, const __grid_constant__ CUtensorMap map,
-                                                     const WorkItem* __restrict__ items,
-                                                     const Pos<T>* __restrict__ pos, const int* __restrict__ perm,
-                                                     KbPoly<T> kb, DegridEp<typename cplx_t<T>::type> dep, int* err) {
-  typedef typename cplx_t<T>::type C;
-  extern __shared__ __align__(128) unsigned char sm_raw[];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ double red[32];
-  const WorkItem it = items[blockIdx.x];
-  const int tu = it.tile / g.ntile1d, tv = it.tile - tu * g.ntile1d;
-  const int PW = g.TB + kJ, PP = PW + 2;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  C* patch = reinterpret_cast<C*>(sm_raw);
-  T* stage = reinterpret_cast<T*>(sm_raw + tile_patch_bytes<T>(g.TB));
-  if (!stage_patch(patch, &bar, &map, tu, tv, g.TB, PW, err)) return;
-  T* wst = stage + warp * 32 * kDgStage;
-  const int cnt = it.end - it.begin;
-  const int per = (cnt + kWarps - 1) / kWarps;
-  const int w0 = it.begin + min(cnt, warp * per), w1 = it.begin + min(cnt, (warp + 1) * per);
-  const int grp = lane >> 2, k = lane & 3;
-  Acc<T> p0, p1;
-  for (int base = w0; base < w1; base += 32) {
-    const int i = base + lane;
-    const bool valid = i < w1;
-    const int nv = min(32, w1 - base);
-    {
-      T wu[kJ], wv[kJ];
-      int cu = 0, cv = 0;
-      if (valid) {
-        T fu, fv;
-        decode(pos[i], cu, fu, cv, fv);
-        kb_eval(kb, fu, wu);
-        kb_eval(kb, fv, wv);
-      } else {
-#pragma unroll
-        for (int a = 0; a < kJ; ++a) wu[a] = wv[a] = T(0);
-      }
-      T* st = wst + lane * kDgStage;
-#pragma unroll
-      for (int a = 0; a < kJ; ++a) {
-        st[a] = wu[a];
-        st[kJ + a] = wv[a];
-      }
-      *reinterpret_cast<int*>(st + 2 * kJ + 2) = cu * 256 + cv;
-    }
-    __syncwarp();
-#pragma unroll
-    for (int s4 = 0; s4 < 4; ++s4) {
-      const int j = s4 * 8 + grp;
-      C part = cz<C>();
-      if (j < nv) {
-        const T* sj = wst + j * kDgStage;
-        const int cell = *reinterpret_cast<const int*>(sj + 2 * kJ + 2);
-        const T wa0 = sj[2 * k], wa1 = sj[2 * k + 1];
-        T wv[kJ];
-#pragma unroll
-        for (int b = 0; b < kJ; ++b) wv[b] = sj[kJ + b];
-        const C* r0 = patch + ((cell >> 8) + 2 * k) * PP + (cell & 255);
-        const C* r1 = r0 + PP;
-        T hx0 = 0, hy0 = 0, hx1 = 0, hy1 = 0;
-#pragma unroll
-        for (int b = 0; b < kJ; ++b) {
-          const C g0 = r0[b], g1 = r1[b];
-          hx0 = fma(wv[b], g0.x, hx0);
-          hy0 = fma(wv[b], g0.y, hy0);
-          hx1 = fma(wv[b], g1.x, hx1);
-          hy1 = fma(wv[b], g1.y, hy1);
-        }
-        part = cmk<C>(fma(wa0, hx0, wa1 * hx1), fma(wa0, hy0, wa1 * hy1));
-      }
-      part.x += __shfl_xor_sync(0xffffffffu, part.x, 1);
-      part.y += __shfl_xor_sync(0xffffffffu, part.y, 1);
-      part.x += __shfl_xor_sync(0xffffffffu, part.x, 2);
-      part.y += __shfl_xor_sync(0xffffffffu, part.y, 2);
-      if (k == 0 && j < nv) {
-        T* sj = wst + j * kDgStage;
-        sj[2 * kJ] = part.x;
-        sj[2 * kJ + 1] = part.y;
-      }
-    }
-    __syncwarp();
-    if (valid) {
-      const T* st = wst + lane * kDgStage;
-      const C acc_v = cmk<C>(st[2 * kJ], st[2 * kJ + 1]);
-      if (dep.mode == DG_STORE_PERM) {
-        dep.y[perm[i]] = acc_v;
-      } else if (dep.mode == DG_STORE_SORTED) {
-        dep.y[i] = acc_v;
-      } else {  // DG_BALL
-        const C z = dep.z[i], yv = dep.ys[i];
-        const T nu = T(dep.nu);
-        const C v = cmk<C>(fma(nu, acc_v.x, z.x), fma(nu, acc_v.y, z.y));
-        dep.z[i] = v;
-        const T dx = fma(-nu, yv.x, v.x), dy = fma(-nu, yv.y, v.y);
-        p0.add_prod(dx, dx);
-        p0.add_prod(dy, dy);
-        const T ex = acc_v.x - yv.x, ey = acc_v.y - yv.y;
-        p1.add_prod(ex, ex);
-        p1.add_prod(ey, ey);
-      }
-    }
-    __syncwarp();
-  }
-  if (dep.mode == DG_BALL) {
-    const Acc<T> r0 = block_merge<kThreads>(p0, red);
-    const Acc<T> r1 = block_merge<kThreads>(p1, red);
-    if (threadIdx.x == 0) {
-      reinterpret_cast<Acc<T>*>(dep.part0)[blockIdx.x] = r0;
-      reinterpret_cast<Acc<T>*>(dep.part1)[blockIdx.x] = r1;
-    }
-  }
-}
+constexpr int kDgStage = 2 * kJ + 4;  // wu[J], wv[J], result re, im, cell, pad
 
 // ---------------------------------------------------------------------------
 // Warp-per-item forms of degridding and gridding (the ball block and the
@@ -490,13 +397,7 @@ __global__ void __launch_bounds__(kThreads) k_degrid_w(Geometry g, const __grid_
 #pragma unroll
         for (int a = 0; a < kJ; ++a) wu[a] = wv[a] = T(0);
       }
-      T* st = wst + lane * kDgStage;
-#pragma unroll
-      for (int a = 0; a < kJ; ++a) {
-        st[a] = wu[a];
-        st[kJ + a] = wv[a];
-      }
-      *reinterpret_cast<int*>(st + 2 * kJ + 2) = cu * 256 + cv;
+      stage_store(wst + lane * kDgStage, wu, wv, T(0), T(0), cu * 256 + cv);
     }
     __syncwarp();
 #pragma unroll
@@ -568,16 +469,20 @@ __global__ void __launch_bounds__(kThreads) k_degrid_w(Geometry g, const __grid_
 
 // Compensated (Kahan) accumulation of a run sum into a patch cell: the cell
 // keeps its running sum and the low-order part lost so far.
-template <typename C> PD void kahan_add(C* sum, C* comp, C v) {
-  C s = *sum, c = *comp;
-  const decltype(v.x) yx = v.x - c.x, yy = v.y - c.y;
-  const decltype(v.x) tx = s.x + yx, ty = s.y + yy;
-  c.x = (tx - s.x) - yx;
-  c.y = (ty - s.y) - yy;
-  s.x = tx;
-  s.y = ty;
-  *sum = s;
-  *comp = c;
+// A gridding accumulator cell: the running sum and its Kahan compensation,
+// side by side so that one 16-byte shared access (two for FP64) moves both;
+// eight lanes updating eight consecutive cells of a row then touch 128
+// contiguous bytes, free of bank conflicts for any row pitch.
+template <typename T> struct __align__(4 * sizeof(T)) KCell { T sx, sy, cx, cy; };
+template <typename T> PD void kahan_cell_add(KCell<T>* cell, T vx, T vy) {
+  KCell<T> k = *cell;
+  const T yx = vx - k.cx, yy = vy - k.cy;
+  const T tx = k.sx + yx, ty = k.sy + yy;
+  k.cx = (tx - k.sx) - yx;
+  k.cy = (ty - k.sy) - yy;
+  k.sx = tx;
+  k.sy = ty;
+  *cell = k;
 }
 
 template <typename T>
@@ -586,23 +491,23 @@ __global__ void __launch_bounds__(kThreads) k_grid_w(Geometry g, const WorkItem*
                                                      KbPoly<T> kb, GridPro<typename cplx_t<T>::type> gpro,
                                                      typename cplx_t<T>::type* __restrict__ Q) {
   typedef typename cplx_t<T>::type C;
-  typedef typename Pair2<T>::type T2;
   extern __shared__ __align__(128) unsigned char sm_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int item = blockIdx.x * kWItems + warp;
   if (item >= n_items) return;
   const WorkItem it = items[item];
   const int tu = it.tile / g.ntile1d, tv = it.tile - tu * g.ntile1d;
-  const int PW = g.TB + kJ, PA = PW + 1;
-  // per warp: accumulator patch and its Kahan compensation patch
-  C* wacc = reinterpret_cast<C*>(sm_raw) + warp * 2 * PW * PA;
-  C* wcmp = wacc + PW * PA;
-  T* wst = reinterpret_cast<T*>(reinterpret_cast<C*>(sm_raw) + kWItems * 2 * PW * PA) + warp * 32 * kStage;
-  for (int e = lane; e < PW * PA; e += 32) wacc[e] = wcmp[e] = cz<C>();
+  const int PW = g.TB + kJ;
+  // per warp: a PW x PW patch of Kahan cells, then the staging rows
+  KCell<T>* wacc = reinterpret_cast<KCell<T>*>(sm_raw) + warp * PW * PW;
+  T* wst = reinterpret_cast<T*>(reinterpret_cast<KCell<T>*>(sm_raw) + kWItems * PW * PW) + warp * 32 * kStage;
+  for (int e = lane; e < PW * PW; e += 32) wacc[e] = KCell<T>{T(0), T(0), T(0), T(0)};
   __syncwarp();
   T scale = 0;
   if (gpro.mode == GP_BALL) scale = T(gpro.block_scale ? gpro.block_scale[it.pad] : gpro.scalars[gpro.scale_idx]);
-  const int ta = lane >> 2, tb = (lane & 3) * 2;
+  // lane (ta, tc) accumulates footprint cells (ta, tc) and (ta + 4, tc), so
+  // each quarter-warp updates 8 consecutive cells of one patch row.
+  const int ta = lane >> 3, tc = lane & 7;
   int scell = -1;
   C s0 = cz<C>(), s1 = cz<C>();
   for (int base = it.begin; base < it.end; base += 32) {
@@ -634,15 +539,7 @@ __global__ void __launch_bounds__(kThreads) k_grid_w(Geometry g, const WorkItem*
 #pragma unroll
         for (int a = 0; a < kJ; ++a) wu[a] = wv[a] = T(0);
       }
-      T* st = wst + lane * kStage;
-#pragma unroll
-      for (int a = 0; a < kJ; ++a) {
-        st[a] = wu[a];
-        st[kJ + a] = wv[a];
-      }
-      st[2 * kJ] = u.x;
-      st[2 * kJ + 1] = u.y;
-      *reinterpret_cast<int*>(st + 2 * kJ + 2) = cu * 256 + cv;
+      stage_store(wst + lane * kStage, wu, wv, u.x, u.y, cu * 256 + cv);
     }
     __syncwarp();
     for (int j = 0; j < nv; ++j) {
@@ -650,16 +547,15 @@ __global__ void __launch_bounds__(kThreads) k_grid_w(Geometry g, const WorkItem*
       const int cell = *reinterpret_cast<const int*>(sj + 2 * kJ + 2);
       if (cell != scell) {  // warp-uniform
         if (scell >= 0) {
-          const int o = ((scell >> 8) + ta) * PA + (scell & 255) + tb;
-          kahan_add(wacc + o, wcmp + o, s0);
-          kahan_add(wacc + o + 1, wcmp + o + 1, s1);
+          const int o = ((scell >> 8) + ta) * PW + (scell & 255) + tc;
+          kahan_cell_add(wacc + o, s0.x, s0.y);
+          kahan_cell_add(wacc + o + 4 * PW, s1.x, s1.y);
           s0 = s1 = cz<C>();
         }
         scell = cell;
       }
-      const T wa = sj[ta];
-      const T2 wbp = *reinterpret_cast<const T2*>(sj + kJ + tb);
-      const T a0 = wa * wbp.x, a1 = wa * wbp.y;
+      const T wb = sj[kJ + tc];
+      const T a0 = sj[ta] * wb, a1 = sj[ta + 4] * wb;
       const T ux = sj[2 * kJ], uy = sj[2 * kJ + 1];
       s0.x = fma(a0, ux, s0.x);
       s0.y = fma(a0, uy, s0.y);
@@ -669,14 +565,15 @@ __global__ void __launch_bounds__(kThreads) k_grid_w(Geometry g, const WorkItem*
     __syncwarp();
   }
   if (scell >= 0) {
-    const int o = ((scell >> 8) + ta) * PA + (scell & 255) + tb;
-    kahan_add(wacc + o, wcmp + o, s0);
-    kahan_add(wacc + o + 1, wcmp + o + 1, s1);
+    const int o = ((scell >> 8) + ta) * PW + (scell & 255) + tc;
+    kahan_cell_add(wacc + o, s0.x, s0.y);
+    kahan_cell_add(wacc + o + 4 * PW, s1.x, s1.y);
   }
   __syncwarp();
   for (int e = lane; e < PW * PW; e += 32) {
     const int r = e / PW, c = e - r * PW;
-    const C v = csub(wacc[r * PA + c], wcmp[r * PA + c]);
+    const KCell<T> kc = wacc[e];
+    const C v = cmk<C>(kc.sx - kc.cx, kc.sy - kc.cy);
     if (v.x != 0 || v.y != 0) atomic_add_global(Q + size_t(tu * g.TB + r) * g.KP + (tv * g.TB + c), v);
   }
 }
@@ -882,10 +779,8 @@ __global__ void k_encode<double>(const double* __restrict__ uv, const int* __res
 
 template <typename T> cudaError_t configure_nufft() {
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = raise_smem_limit(k_degrid<T>);
   if (e == cudaSuccess) e = raise_smem_limit(k_degrid_w<T>);
   if (e == cudaSuccess) e = raise_smem_limit(k_grid_w<T>);
-  if (e == cudaSuccess) e = raise_smem_limit(k_tile<T, TM_GRID>);
   if (e == cudaSuccess) e = raise_smem_limit(k_tile<T, TM_GRAM>);
   return e;
 }
@@ -921,7 +816,7 @@ void launch_grid(const Geometry& g, const WorkItem* items, int n_items, const Po
                  cudaStream_t s) {
   if (n_items <= 0) return;
   const size_t PW = size_t(g.TB + kJ);
-  const size_t sm = kWItems * (2 * PW * (PW + 1) * sizeof(typename cplx_t<T>::type) + 32 * kStage * sizeof(T));
+  const size_t sm = kWItems * (PW * PW * sizeof(KCell<T>) + 32 * kStage * sizeof(T));
   k_grid_w<T><<<(n_items + kWItems - 1) / kWItems, kThreads, sm, s>>>(g, items, n_items, pos, perm, kb, pro, Q);
 }
 
