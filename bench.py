@@ -42,6 +42,23 @@ def dist_info():
     return ws, rank, local
 
 
+def max_over_ranks(ms: float, pg, dev) -> float:
+    """The slowest rank's time (all-reduce MAX over the process group; the
+    local time when there is no group)."""
+    if pg is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, ws: int, ms: float) -> float:
+    """Units all ranks processed per second over the slowest rank's time."""
+    return units_per_rank * ws / (ms / 1e3)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -188,12 +205,8 @@ def run_ours(args, ws, rank, local):
         res = op.solve(y, eps, **kw)
         e1.record()
         barrier()
-    ms = e0.elapsed_time(e1)
-    if pg:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    value = K * ws / (ms / 1e3)
+    ms = max_over_ranks(e0.elapsed_time(e1), pg, dev)
+    value = whole_job_rate(K, ws, ms)
 
     # profiled pass of the same K steps: per-kernel device time (CUDA events on the solver's stream)
     op.profile(True)
