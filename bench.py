@@ -295,7 +295,7 @@ def run_ours(args, ws, rank, local):
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(ms / K, 4), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (FP64 reductions)", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32 (compensated reductions, FP64 finals)", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {n}x{n} sky, M={M} uv points, 2048^2 grid, J=8, "
                                f"SARA {L} levels, {w.cg_iters} CG steps per iteration",
                    "global_batch": ws, "parallelism": f"replicas x{ws}",
@@ -411,12 +411,19 @@ def _make_request(n, M, seed, dev):
     a, b = synth.noise_draws(M, seed)
     sigma = float(np.linalg.norm(y0)) / math.sqrt(M) * 10 ** (-1.5)
     y = y0 + sigma / math.sqrt(2) * (a + 1j * b)
-    return dict(n=n, M=M, uv=uv, y=y, eps=sigma * math.sqrt(M + 2 * math.sqrt(M)))
+    return dict(n=n, M=M, uv=uv, y=y, x=x, eps=sigma * math.sqrt(M + 2 * math.sqrt(M)))
+
+
+def _snr_db(x, xh):
+    import numpy as np
+
+    return float(20 * np.log10(np.linalg.norm(x) / np.linalg.norm(np.asarray(x) - np.asarray(xh, dtype=np.float64))))
 
 
 def _drain(srv, ids, arrivals=None, reqs=None, params=None):
     """Drive scheduling rounds until every request is done; with `arrivals`
-    (seconds from start) requests are submitted as their time comes."""
+    (seconds from start) requests are submitted (with `params`) as their time
+    comes."""
     t0 = time.perf_counter()
     pending = list(range(len(arrivals))) if arrivals is not None else []
     while True:
@@ -459,24 +466,37 @@ def run_batch(args):
         r = next(q for q in reqs if q["n"] == n)
         tuned[n] = purify_autotune(torch.as_tensor(r["uv"], device=dev), n, 3)
     params = dict(t_max=args.batch_iters, cg_iters=10)
+    # batched FP32 (all admitted), FP32 one at a time, and the plain GPU solver:
+    # FP64, no graph replay, one at a time
+    arms = (("batched", len(reqs), "fp32", {}), ("sequential", 1, "fp32", {}),
+            ("plain_fp64", 1, "fp64", {"use_graph": 0}))
     out = {}
-    for label, slots in (("batched", len(reqs)), ("sequential", 1)):
+    for label, slots, prec, extra in arms:
         srv = Server(int(150e9), slots)
         for n, (tile, chunk, _) in tuned.items():
             srv.set_options(n, tile, chunk)
-        ids = [srv.submit(r["uv"], r["y"], r["n"], 3, r["eps"], **params) for r in reqs]
+        ids = [srv.submit(r["uv"], r["y"], r["n"], 3, r["eps"], precision=prec, **params, **extra) for r in reqs]
         wall, res = _drain(srv, ids)
         srv.close()
         out[label] = (wall, res)
     xb = [r[0] for r in out["batched"][1]]
     xs = [r[0] for r in out["sequential"][1]]
+    xp = [r[0] for r in out["plain_fp64"][1]]
     worst = max(float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(xb, xs))
+    worst64 = max(float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(xb, xp))
+    snr_b = [_snr_db(r["x"], x) for r, x in zip(reqs, xb)]
+    snr_p = [_snr_db(r["x"], x) for r, x in zip(reqs, xp)]
     line = {"metric": "batched SARA-SDMM solves/s, 64 uneven instances (128..512 square, M in [0.5N, 3N])",
             "value": round(len(reqs) / out["batched"][0], 3), "unit": "solves/s", "higher_is_better": True,
-            "sequential_solves_per_s": round(len(reqs) / out["sequential"][0], 3),
-            "speedup": round(out["sequential"][0] / out["batched"][0], 3),
-            "iterations_per_solve": args.batch_iters, "dtype": "f32 (FP64 reductions)", "data": "synthetic",
-            "max_rel_diff_batched_vs_alone": worst,
+            "sequential_fp32_solves_per_s": round(len(reqs) / out["sequential"][0], 3),
+            "plain_fp64_solves_per_s": round(len(reqs) / out["plain_fp64"][0], 3),
+            "speedup_vs_sequential_fp32": round(out["sequential"][0] / out["batched"][0], 3),
+            "speedup_vs_plain_fp64": round(out["plain_fp64"][0] / out["batched"][0], 3),
+            "iterations_per_solve": args.batch_iters, "dtype": "f32 (compensated reductions, FP64 finals)",
+            "data": "synthetic",
+            "max_rel_diff_batched_vs_alone": worst, "max_rel_diff_vs_plain_fp64": worst64,
+            "snr_db_mean": round(float(np.mean(snr_b)), 4), "snr_db_mean_plain_fp64": round(float(np.mean(snr_p)), 4),
+            "max_abs_snr_diff_db": round(float(np.max(np.abs(np.array(snr_b) - np.array(snr_p)))), 6),
             "autotuned": {str(k): {"tile": v[0], "chunk": v[1], "phi_phiH_ms": round(v[2], 4)} for k, v in tuned.items()},
             "config": {"workload": "64 independent solves, seeds 4+i", "mode": "request server, all admitted"}}
     print(json.dumps(line), flush=True)
@@ -507,6 +527,11 @@ def run_serving(args):
     seq_wall, seq_res = _drain(srv, ids)
     srv.close()
     seq_rate = len(reqs) / seq_wall
+    # the plain GPU solver (FP64, no graph replay), one request at a time
+    srv = Server(int(150e9), 1)
+    ids = [srv.submit(r["uv"], r["y"], r["n"], 3, r["eps"], precision="fp64", use_graph=0, **params) for r in reqs]
+    p64_wall, p64_res = _drain(srv, ids)
+    srv.close()
     rates = []
     for mult in (0.5, 1.0, 2.0, 4.0):
         lam = mult * seq_rate
@@ -521,9 +546,15 @@ def run_serving(args):
                       "p50_s": round(float(np.percentile(lat, 50)), 4), "p99_s": round(float(np.percentile(lat, 99)), 4),
                       "max_rel_diff_vs_alone": worst})
     best = max(rates, key=lambda r: r["solves_per_s"])
+    snr_s = [_snr_db(r["x"], x[0]) for r, x in zip(reqs, seq_res)]
+    snr_p = [_snr_db(r["x"], x[0]) for r, x in zip(reqs, p64_res)]
     line = {"metric": "serving solves/s and p50/p99 latency (continuous batching)", "value": best["solves_per_s"],
             "unit": "solves/s", "higher_is_better": True, "one_at_a_time_solves_per_s": round(seq_rate, 3),
-            "rates": rates, "requests": len(reqs), "dtype": "f32 (FP64 reductions)", "data": "synthetic",
+            "plain_fp64_one_at_a_time_solves_per_s": round(len(reqs) / p64_wall, 3),
+            "snr_db_mean": round(float(np.mean(snr_s)), 4), "snr_db_mean_plain_fp64": round(float(np.mean(snr_p)), 4),
+            "max_abs_snr_diff_db": round(float(np.max(np.abs(np.array(snr_s) - np.array(snr_p)))), 6),
+            "rates": rates, "requests": len(reqs), "dtype": "f32 (compensated reductions, FP64 finals)",
+            "data": "synthetic",
             "config": {"workload": "Poisson arrivals, images 128..1024, M log-uniform 16K..1M, xi=1e-4 or 300 it.",
                        "budget_gb": 150, "slots": 16}}
     print(json.dumps(line), flush=True)

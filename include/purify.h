@@ -122,9 +122,11 @@ int purify_phi_adj(purify_op* op, const void* y, void* x, void* stream);
 /*
  * purify_sara_fwd -- c = Psi^H x (Section 2.2): the Dirac basis and the
  * Daubechies Db1..Db8 periodic orthonormal wavelet bases with `dwt_levels`
- * levels, each scaled by 1/sqrt(9) so that Psi Psi^H = I.
- *   x  device, real[n][n];   c  device, real[9][n][n], basis-major (block 0
- *   Dirac, block b the Db_b coefficients in Mallat layout).
+ * levels, each scaled by 1/sqrt(9) so that Psi Psi^H = I -- or the q bases
+ * selected by purify_op_set_dictionary, each scaled by 1/sqrt(q).
+ *   x  device, real[n][n];   c  device, real[q][n][n] (q = 9 by default),
+ *   basis-major in increasing basis order (Dirac first, then Db_K in Mallat
+ *   layout).
  */
 int purify_sara_fwd(purify_op* op, const void* x, void* c, void* stream);
 
@@ -150,6 +152,21 @@ int purify_sara_adj(purify_op* op, const void* c, void* x, void* stream);
  * streams, other threads) race and must be serialised by the caller.
  */
 int purify_sara_fwd_static(const float* x, float* c, int n, int levels, void* stream);
+
+/*
+ * purify_op_set_dictionary -- choose the sparsity dictionary Psi of the
+ * operator's analysis calls and of purify_sdmm_solve's l1 block (Section 4
+ * compares the same problem under other dictionaries: BP is the Dirac basis
+ * alone, BPDb8 the Db8 basis alone, BPSA all nine bases without reweighting;
+ * with n_reweight > 0 the solve is the reweighted RWBP / RWBPDb8 / SARA).
+ *   mask  bit 0 the Dirac basis, bit K (1..8) the Daubechies DbK basis; the
+ *         q selected bases are each scaled by 1/sqrt(q) (Psi Psi^H = I).
+ *         The default is 0x1FF (SARA).
+ * PURIFY_ERR_INVALID for mask 0, bits above 8, or while a resumable solve is
+ * active on the operator.  purify_op_dictionary returns the mask and q.
+ */
+int purify_op_set_dictionary(purify_op* op, unsigned mask);
+int purify_op_dictionary(const purify_op* op, unsigned* mask, int* n_bases);
 
 /*
  * purify_op_set_blocks -- partition the visibilities into R blocks (Eq. 4):

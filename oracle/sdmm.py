@@ -32,17 +32,20 @@ from .cg import cg
 
 class SaraDictionary:
     """Psi^H / Psi pair for the SDMM blocks: the SARA dictionary at a fixed
-    number of wavelet levels (sara.py).  Any object with the same two
-    methods (and a tight frame) can stand in, e.g. a dense matrix in tests."""
+    number of wavelet levels (sara.py), or one of its sub-dictionaries
+    (`bases`: 0 = Dirac, K = DbK; Section 4's BP is (0,), BPDb8 is (8,)).  Any
+    object with the same two methods (and a tight frame) can stand in, e.g. a
+    dense matrix in tests."""
 
-    def __init__(self, levels: int):
+    def __init__(self, levels: int, bases=sara_mod.ALL_BASES):
         self.levels = levels
+        self.bases = sara_mod._check(bases)
 
     def analysis(self, x):
-        return sara_mod.analysis(x, self.levels)
+        return sara_mod.analysis(x, self.levels, self.bases)
 
     def synthesis(self, c):
-        return sara_mod.synthesis(c, self.levels)
+        return sara_mod.synthesis(c, self.levels, self.bases)
 from .prox import proj_l2_ball, proj_positive, soft_threshold
 
 

@@ -59,7 +59,7 @@ EXPORTS = ["purify_op_create", "purify_op_destroy", "purify_op_info", "purify_ph
            "purify_last_error", "purify_sara_fwd_static", "purify_gram", "purify_op_set_blocks",
            "purify_server_create", "purify_server_destroy", "purify_server_submit", "purify_server_step",
            "purify_server_result", "purify_estimate_bytes", "purify_op_create_ex", "purify_autotune",
-           "purify_server_set_options"]
+           "purify_server_set_options", "purify_op_set_dictionary", "purify_op_dictionary"]
 KERNEL_KINDS = ["row_fwd", "col_fwd", "degrid", "grid", "gram", "col_inv", "row_inv", "sara_analysis",
                 "sara_synthesis", "vector", "memset", "col_conv", "row_fwd_h", "row_inv_h"]
 
@@ -94,6 +94,8 @@ def lib() -> ctypes.CDLL:
     L.purify_sara_fwd_static.argtypes = [vp, vp, ci, ci, vp]
     L.purify_gram.argtypes = [vp, vp, vp, ci, vp]
     L.purify_op_set_blocks.argtypes = [vp, vp, ci, vp]
+    L.purify_op_set_dictionary.argtypes = [vp, ctypes.c_uint]
+    L.purify_op_dictionary.argtypes = [vp, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ci)]
     L.purify_server_create.argtypes = [i64, ci, ctypes.POINTER(vp)]
     L.purify_server_destroy.argtypes = [vp]
     L.purify_server_set_options.argtypes = [vp, ci, ctypes.POINTER(purify_op_options)]
@@ -204,6 +206,17 @@ def purify_op_set_blocks(h, block_ptr, R: int, stream=None) -> None:
     _check(lib().purify_op_set_blocks(h, block_ptr, R, _stream(stream)), "purify_op_set_blocks")
 
 
+def purify_op_set_dictionary(h, mask: int) -> None:
+    _check(lib().purify_op_set_dictionary(h, mask), "purify_op_set_dictionary")
+
+
+def purify_op_dictionary(h) -> tuple[int, int]:
+    """(mask, number of bases) of the operator's dictionary."""
+    m, q = ctypes.c_uint(), ctypes.c_int()
+    _check(lib().purify_op_dictionary(h, ctypes.byref(m), ctypes.byref(q)), "purify_op_dictionary")
+    return m.value, q.value
+
+
 def purify_gram(h, x_ptr, out_ptr, mode: int, stream=None) -> None:
     _check(lib().purify_gram(h, x_ptr, out_ptr, mode, _stream(stream)), "purify_gram")
 
@@ -311,16 +324,24 @@ class Operator:
         purify_gram(self.h, _dptr(x, self.rdtype, (n, n)), _dptr(o, self.rdtype, (n, n)), mode, stream)
         return o
 
+    def set_dictionary(self, mask: int) -> None:
+        """Bases of Psi: bit 0 Dirac, bit K DbK (default 0x1FF, SARA)."""
+        purify_op_set_dictionary(self.h, mask)
+
+    def dictionary(self) -> tuple[int, int]:
+        """(mask, number of bases q) of Psi."""
+        return purify_op_dictionary(self.h)
+
     def sara_fwd(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-        n = self.n
-        c = out if out is not None else torch.empty(9, n, n, dtype=self.rdtype, device=x.device)
-        purify_sara_fwd(self.h, _dptr(x, self.rdtype, (n, n)), _dptr(c, self.rdtype, (9, n, n)), stream)
+        n, q = self.n, self.dictionary()[1]
+        c = out if out is not None else torch.empty(q, n, n, dtype=self.rdtype, device=x.device)
+        purify_sara_fwd(self.h, _dptr(x, self.rdtype, (n, n)), _dptr(c, self.rdtype, (q, n, n)), stream)
         return c
 
     def sara_adj(self, c: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-        n = self.n
+        n, q = self.n, self.dictionary()[1]
         x = out if out is not None else torch.empty(n, n, dtype=self.rdtype, device=c.device)
-        purify_sara_adj(self.h, _dptr(c, self.rdtype, (9, n, n)), _dptr(x, self.rdtype, (n, n)), stream)
+        purify_sara_adj(self.h, _dptr(c, self.rdtype, (q, n, n)), _dptr(x, self.rdtype, (n, n)), stream)
         return x
 
     def solve(self, y: torch.Tensor, eps: float, t_max: int = 200, cg_iters: int = 10, n_reweight: int = 0,

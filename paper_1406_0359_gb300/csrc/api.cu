@@ -179,6 +179,28 @@ template <typename T> class OpImpl : public purify_op {
   }
 
   size_t N() const { return size_t(g.n) * g.n; }
+  size_t D() const { return size_t(sara.nbases) * N(); }  // dictionary coefficients
+
+  // Dictionary of the l1 block: the SARA bases in `mask` (bit 0 Dirac, bit K DbK).
+  int set_dictionary(unsigned mask) override {
+    if (run.active) {
+      note_error("purify_op_set_dictionary", __LINE__, "a solve is in progress on this operator");
+      return PURIFY_ERR_INVALID;
+    }
+    SaraPlan<T> p = sara;
+    if (sara_select(p, mask) < 0) {
+      note_error("purify_op_set_dictionary", __LINE__, "mask must be a non-empty subset of bits 0..8");
+      return PURIFY_ERR_INVALID;
+    }
+    sara = p;
+    return PURIFY_OK;
+  }
+  unsigned dictionary(int* nbases) const override {
+    unsigned m = sara.dirac ? 1u : 0u;
+    for (int z = 0; z < sara.nf; ++z) m |= 2u << sara.fid[z];
+    if (nbases) *nbases = sara.nbases;
+    return m;
+  }
   size_t grid_bytes() const { return size_t(g.KP) * g.KP * sizeof(C); }
 
   int create(const double* uv, int64_t M, int n, int L, cudaStream_t s, int tile = 0, int chunk_opt = 0) {
@@ -236,6 +258,7 @@ template <typename T> class OpImpl : public purify_op {
     if ((rc = alloc(&err, 1))) return rc;
     sara.n = n;
     sara.levels = L;
+    sara_select(sara, kSaraAll);
     if ((rc = alloc(&sara.s0, 8 * N() / 4))) return rc;
     if ((rc = alloc(&sara.s1, 8 * N() / 4))) return rc;
     if ((rc = alloc(&sara.cs, 9 * N()))) return rc;
@@ -510,7 +533,7 @@ template <typename T> class OpImpl : public purify_op {
     ep.out = Ap;
     row_ep(ep, s);
     sara_analysis<T>(sara, Ap, z1, s);
-    const int np = launch_reduce<T>(z1, 9 * N(), RED_MAXABS, sc, partials, s);
+    const int np = launch_reduce<T>(z1, D(), RED_MAXABS, sc, partials, s);
     launch_max_partials(partials, np, sc, s);
     int rc = check(s, true);
     if (rc) return rc;
@@ -522,7 +545,7 @@ template <typename T> class OpImpl : public purify_op {
   // Population standard deviation of Psi^H x_hat (reweighting delta_1).
   int coef_std(double* out, cudaStream_t s) {
     sara_analysis<T>(sara, xh, z1, s);
-    const size_t D = 9 * N();
+    const size_t D = this->D();
     int np = launch_reduce<T>(z1, D, RED_SUM, sc, partials, s);
     launch_finalize<T>(partials, np, FIN_MEAN, double(D), sc, s);
     np = launch_reduce<T>(z1, D, RED_VAR, sc, partials, s);
@@ -702,7 +725,7 @@ template <typename T> class OpImpl : public purify_op {
       cudaGraphDestroy(graph);
       if (ce != cudaSuccess) return map_err(ce, __LINE__);
     }
-    launch_fill<T>(w, 9 * n2, T(1), s);
+    launch_fill<T>(w, D(), T(1), s);
     CK(cudaMemsetAsync(xh, 0, n2 * sizeof(T), s));
     run.active = true;
     return check(s, false);
@@ -725,9 +748,9 @@ template <typename T> class OpImpl : public purify_op {
       const double dmin = P.delta_min > 0 ? P.delta_min : 1e-4 * run.delta1;
       const double delta = std::max(std::pow(run.decay, run.round - 1) * run.delta1, dmin);
       sara_analysis<T>(sara, xh, w, s);
-      launch_reweight<T>(w, 9 * n2, delta, s);
+      launch_reweight<T>(w, D(), delta, s);
     }
-    cudaMemsetAsync(z1, 0, 9 * n2 * sizeof(T), s);
+    cudaMemsetAsync(z1, 0, D() * sizeof(T), s);
     cudaMemsetAsync(z2, 0, n2 * sizeof(T), s);
     cudaMemsetAsync(z3, 0, M * sizeof(C), s);
     if (run.round > 0 && P.warm_start) {
@@ -1017,6 +1040,17 @@ int purify_sara_adj(purify_op* op, const void* c, void* x, void* stream) {
 int purify_op_set_blocks(purify_op* op, const int* block_ids, int R, void* stream) {
   if (!op) return PURIFY_ERR_INVALID;
   return op->set_blocks(block_ids, R, static_cast<cudaStream_t>(stream));
+}
+
+int purify_op_set_dictionary(purify_op* op, unsigned mask) {
+  if (!op) return PURIFY_ERR_INVALID;
+  return op->set_dictionary(mask);
+}
+
+int purify_op_dictionary(const purify_op* op, unsigned* mask, int* n_bases) {
+  if (!op || !mask) return PURIFY_ERR_INVALID;
+  *mask = op->dictionary(n_bases);
+  return PURIFY_OK;
 }
 
 int purify_gram(purify_op* op, const void* x, void* out, int mode, void* stream) {

@@ -205,8 +205,17 @@ struct SaraPlan {
   T* s1;
   T* cs;   // [9][n][n] scratch coefficients (prox output)
   DbFilters<T> f;
+  // selected bases (sara_select): Dirac in slot 0 when dirac, then the nf
+  // Daubechies filters fid[0..nf) (K - 1, increasing); scale = 1/sqrt(nbases)
+  int dirac, nf, nbases;
+  int fid[kMaxDb];
+  T scale;
 };
-// Psi^H x (plain), c is [9][n][n].
+// Bases of the dictionary: bit 0 Dirac, bit K DbK (K = 1..8).
+constexpr unsigned kSaraAll = 0x1FFu;
+// Select the bases of `mask`; returns their number, or -1 for an invalid mask.
+template <typename T> int sara_select(SaraPlan<T>& P, unsigned mask);
+// Psi^H x (plain), c is [nbases][n][n].
 template <typename T> void sara_analysis(const SaraPlan<T>& P, const T* x, T* c, cudaStream_t s);
 // Psi c (plain).
 template <typename T> void sara_synthesis(const SaraPlan<T>& P, const T* c, T* x, cudaStream_t s);

@@ -17,6 +17,8 @@ struct purify_op {
   virtual int solve(const void* y, const purify_params* p, void* x, purify_stats* st, cudaStream_t s) = 0;
   virtual int gram(const void* x, void* out, int mode, cudaStream_t s) = 0;
   virtual int set_blocks(const int* blocks, int R, cudaStream_t s) = 0;
+  virtual int set_dictionary(unsigned mask) = 0;
+  virtual unsigned dictionary(int* nbases) const = 0;
   // resumable solve (request server)
   virtual int begin(const void* y, const purify_params* p, cudaStream_t user) = 0;
   virtual int step_launch() = 0;

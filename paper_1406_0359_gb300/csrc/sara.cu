@@ -1,7 +1,10 @@
-// SARA dictionary Psi = [Dirac, Db1, ..., Db8] / 3 (Section 2.2) on the GPU.
+// SARA dictionary Psi = [Dirac, Db1, ..., Db8] / 3 (Section 2.2) on the GPU,
+// or a sub-dictionary of it (Section 4's BP = Dirac, BPDb8 = Db8, ...): the q
+// selected bases, each scaled by 1/sqrt(q), coefficients basis-major in
+// increasing basis order (Dirac first).
 //
-// Analysis (Psi^H): one launch per wavelet level covers all eight Daubechies
-// filters (blockIdx.z = filter).  A CTA stages its periodic input tile once in
+// Analysis (Psi^H): one launch per wavelet level covers all selected
+// Daubechies filters (blockIdx.z = filter slot).  A CTA stages its periodic input tile once in
 // shared memory, filters the rows (axis 1) into low/high halves, then the
 // columns (axis 0), and writes the three detail sub-bands of the level to their
 // Mallat positions; the low-low band goes to a scratch band for the next level
@@ -16,6 +19,7 @@
 // gamma w), updates z_1 and emits 2 r_1 - v_1 for the synthesis, plus FP64
 // partial sums of the objective ||W Psi^H x_hat||_1; the final synthesis
 // epilogue applies the positivity block and writes x_1 + x_2.
+#include <cmath>
 #include <cstdio>
 #include <mutex>
 #include <vector>
@@ -32,9 +36,9 @@ constexpr int kTH = 16;  // analysis: output coefficients per tile side
 constexpr int kTO = 32;  // synthesis: output samples per tile side
 constexpr int kThr = 256;
 
-template <typename T> PD T third() { return T(1) / T(3); }
-
+// Periodic index i mod L (the integer modulo only off the common in-range case).
 PD int wrap(int i, int L) {
+  if (i >= 0 && i < L) return i;
   i %= L;
   return i < 0 ? i + L : i;
 }
@@ -69,14 +73,17 @@ template <typename T> struct AnaArgs {
   size_t in_stride;  // elements between filters' input bands (0: shared input)
   int L;             // input band side
   int n;
-  T* s_out;          // LL scratch [8][H*H]
+  T* s_out;          // LL scratch [filter slot][H*H]
   int last;          // LL band is final
+  int slot0;         // coefficient block of filter slot 0 (1 when the Dirac basis is selected)
+  int fid[kMaxDb];   // Daubechies filter (K - 1) of each filter slot
+  T scale;           // 1 / sqrt(number of bases)
   CoefOut<T> out;
   double* partials;  // per-CTA objective partials, Acc<T> in double slots (prox only)
 };
 
 template <typename T, int F>
-__device__ void ana_body(const AnaArgs<T>& A, const T* __restrict__ h, const T* __restrict__ g, int k, T* sm,
+__device__ void ana_body(const AnaArgs<T>& A, const T* __restrict__ h, const T* __restrict__ g, int z, T* sm,
                          double* red) {
   constexpr int W = 2 * kTH + F - 2;
   T* X = sm;
@@ -84,10 +91,20 @@ __device__ void ana_body(const AnaArgs<T>& A, const T* __restrict__ h, const T* 
   T* hi = lo + W * kTH;
   const int L = A.L, H = L / 2, n = A.n;
   const int r0 = blockIdx.y * kTH, c0 = blockIdx.x * kTH;
-  const T* in = A.in + size_t(k) * A.in_stride;
-  for (int e = threadIdx.x; e < W * W; e += kThr) {
-    const int ir = e / W, ic = e - ir * W;
-    X[e] = in[size_t(wrap(2 * r0 + ir, L)) * L + wrap(2 * c0 + ic, L)];
+  const T* in = A.in + size_t(z) * A.in_stride;
+  {
+    // warps take rows, lanes columns: each lane wraps its few columns once
+    constexpr int NC = (W + 31) / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int cols[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) cols[k] = wrap(2 * c0 + lane + 32 * k, L);
+    for (int ir = wid; ir < W; ir += kThr / 32) {
+      const T* row = in + size_t(wrap(2 * r0 + ir, L)) * L;
+#pragma unroll
+      for (int k = 0; k < NC; ++k)
+        if (lane + 32 * k < W) X[ir * W + lane + 32 * k] = row[cols[k]];
+    }
   }
   __syncthreads();
   for (int e = threadIdx.x; e < W * kTH; e += kThr) {
@@ -116,15 +133,15 @@ __device__ void ana_body(const AnaArgs<T>& A, const T* __restrict__ h, const T* 
       hl = fma(g[m], a, hl);
       hh = fma(g[m], b, hh);
     }
-    const size_t base = size_t(k + 1) * n * n;
-    const T t3 = third<T>();
-    emit(A.out, base + size_t(R) * n + (H + Cc), lh * t3, part);
-    emit(A.out, base + size_t(H + R) * n + Cc, hl * t3, part);
-    emit(A.out, base + size_t(H + R) * n + (H + Cc), hh * t3, part);
+    const size_t base = size_t(A.slot0 + z) * n * n;
+    const T sc = A.scale;
+    emit(A.out, base + size_t(R) * n + (H + Cc), lh * sc, part);
+    emit(A.out, base + size_t(H + R) * n + Cc, hl * sc, part);
+    emit(A.out, base + size_t(H + R) * n + (H + Cc), hh * sc, part);
     if (A.last)
-      emit(A.out, base + size_t(R) * n + Cc, ll * t3, part);
+      emit(A.out, base + size_t(R) * n + Cc, ll * sc, part);
     else
-      A.s_out[size_t(k) * H * H + size_t(R) * H + Cc] = ll;
+      A.s_out[size_t(z) * H * H + size_t(R) * H + Cc] = ll;
   }
   if (A.partials) {
     const Acc<T> t = block_merge<kThr>(part, red);
@@ -138,29 +155,29 @@ __global__ void __launch_bounds__(kThr) k_ana_level(AnaArgs<T> A, DbFilters<T> f
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ double red[32];
   T* sm = reinterpret_cast<T*>(sm_raw);
-  const int k = blockIdx.z;
+  const int z = blockIdx.z, k = A.fid[z];
   const T* h = f.h[k];
   const T* g = f.g[k];
   switch (k) {
-    case 0: ana_body<T, 2>(A, h, g, k, sm, red); break;
-    case 1: ana_body<T, 4>(A, h, g, k, sm, red); break;
-    case 2: ana_body<T, 6>(A, h, g, k, sm, red); break;
-    case 3: ana_body<T, 8>(A, h, g, k, sm, red); break;
-    case 4: ana_body<T, 10>(A, h, g, k, sm, red); break;
-    case 5: ana_body<T, 12>(A, h, g, k, sm, red); break;
-    case 6: ana_body<T, 14>(A, h, g, k, sm, red); break;
-    default: ana_body<T, 16>(A, h, g, k, sm, red); break;
+    case 0: ana_body<T, 2>(A, h, g, z, sm, red); break;
+    case 1: ana_body<T, 4>(A, h, g, z, sm, red); break;
+    case 2: ana_body<T, 6>(A, h, g, z, sm, red); break;
+    case 3: ana_body<T, 8>(A, h, g, z, sm, red); break;
+    case 4: ana_body<T, 10>(A, h, g, z, sm, red); break;
+    case 5: ana_body<T, 12>(A, h, g, z, sm, red); break;
+    case 6: ana_body<T, 14>(A, h, g, z, sm, red); break;
+    default: ana_body<T, 16>(A, h, g, z, sm, red); break;
   }
 }
 
-// Dirac block: c_0 = x / 3 (with the prox epilogue when fused).
+// Dirac block: c_0 = x / sqrt(q) (with the prox epilogue when fused).
 template <typename T>
-__global__ void __launch_bounds__(kThr) k_dirac(const T* __restrict__ x, size_t N, CoefOut<T> out,
+__global__ void __launch_bounds__(kThr) k_dirac(const T* __restrict__ x, size_t N, T scale, CoefOut<T> out,
                                                 double* partials) {
   __shared__ double red[32];
   Acc<T> part;
   const size_t i = size_t(blockIdx.x) * kThr + threadIdx.x;
-  if (i < N) emit(out, i, x[i] * third<T>(), part);
+  if (i < N) emit(out, i, x[i] * scale, part);
   if (partials) {
     const Acc<T> t = block_merge<kThr>(part, red);
     if (threadIdx.x == 0) reinterpret_cast<Acc<T>*>(partials)[blockIdx.x] = t;
@@ -168,11 +185,15 @@ __global__ void __launch_bounds__(kThr) k_dirac(const T* __restrict__ x, size_t 
 }
 
 template <typename T> struct SynArgs {
-  const T* c;       // final coefficients [9][n][n] (plain Psi^H layout)
+  const T* c;       // final coefficients [q][n][n] (plain Psi^H layout)
   const T* s_in;    // LL band from the coarser synthesis level, or null (LL is final in c)
   int H;            // coefficient band side; output side L = 2H
   int n;
-  T* s_out;         // [8][L*L] (intermediate levels)
+  T* s_out;         // [filter slot][L*L] (intermediate levels)
+  int slot0;        // coefficient block of filter slot 0 (1 when the Dirac basis is selected)
+  int nf;           // selected Daubechies filters
+  int fid[kMaxDb];  // Daubechies filter (K - 1) of each filter slot
+  T scale;          // 1 / sqrt(number of bases)
   // finest level (fused over filters):
   int fused;
   int pos_block;    // apply the positivity block
@@ -183,7 +204,7 @@ template <typename T> struct SynArgs {
 
 // One filter's level synthesis of the output tile (i0, j0) into Xo[kTO][kTO].
 template <typename T, int F>
-__device__ void syn_body(const SynArgs<T>& S, const T* __restrict__ h, const T* __restrict__ g, int k, T* sm,
+__device__ void syn_body(const SynArgs<T>& S, const T* __restrict__ h, const T* __restrict__ g, int z, T* sm,
                          int i0, int j0, T (&acc)[kTO * kTO / kThr], bool accumulate) {
   constexpr int CT = kTO / 2 + F / 2;
   T* LLt = sm;
@@ -193,16 +214,24 @@ __device__ void syn_body(const SynArgs<T>& S, const T* __restrict__ h, const T* 
   T* Ulo = HHt + CT * CT;      // [kTO][CT]
   T* Uhi = Ulo + kTO * CT;
   const int H = S.H, n = S.n, L = 2 * H;
-  const T* cb = S.c + size_t(k + 1) * n * n;
-  const T t3 = third<T>();
+  const T* cb = S.c + size_t(S.slot0 + z) * n * n;
+  const T t3 = S.scale;
   const int rb = i0 / 2 - F / 2, cbase = j0 / 2 - F / 2;
-  for (int e = threadIdx.x; e < CT * CT; e += kThr) {
-    const int lr = e / CT, lc = e - lr * CT;
-    const int r = wrap(rb + lr, H), c = wrap(cbase + lc, H);
-    LLt[e] = S.s_in ? S.s_in[size_t(k) * H * H + size_t(r) * H + c] : cb[size_t(r) * n + c] * t3;
-    LHt[e] = cb[size_t(r) * n + (H + c)] * t3;
-    HLt[e] = cb[size_t(H + r) * n + c] * t3;
-    HHt[e] = cb[size_t(H + r) * n + (H + c)] * t3;
+  {
+    // warps take rows, lanes columns (CT <= 24 columns)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lc = lane;
+    const int c = wrap(cbase + lc, H);
+    const T* sb = S.s_in ? S.s_in + size_t(z) * H * H : nullptr;
+    for (int lr = wid; lr < CT; lr += kThr / 32) {
+      if (lc >= CT) continue;
+      const int r = wrap(rb + lr, H);
+      const int e = lr * CT + lc;
+      LLt[e] = sb ? sb[size_t(r) * H + c] : cb[size_t(r) * n + c] * t3;
+      LHt[e] = cb[size_t(r) * n + (H + c)] * t3;
+      HLt[e] = cb[size_t(H + r) * n + c] * t3;
+      HHt[e] = cb[size_t(H + r) * n + (H + c)] * t3;
+    }
   }
   __syncthreads();
   for (int e = threadIdx.x; e < kTO * CT; e += kThr) {
@@ -238,40 +267,41 @@ __device__ void syn_body(const SynArgs<T>& S, const T* __restrict__ h, const T* 
     if (accumulate) {
       acc[q] += v;
     } else if (i0 + il < L && j0 + jl < L) {
-      S.s_out[size_t(k) * L * L + size_t(i0 + il) * L + (j0 + jl)] = v;
+      S.s_out[size_t(z) * L * L + size_t(i0 + il) * L + (j0 + jl)] = v;
     }
   }
   __syncthreads();
 }
 
 template <typename T>
-__device__ void syn_dispatch(const SynArgs<T>& S, const DbFilters<T>& f, int k, T* sm, int i0, int j0,
+__device__ void syn_dispatch(const SynArgs<T>& S, const DbFilters<T>& f, int z, int k, T* sm, int i0, int j0,
                              T (&acc)[kTO * kTO / kThr], bool accumulate) {
   const T* h = f.h[k];
   const T* g = f.g[k];
   switch (k) {
-    case 0: syn_body<T, 2>(S, h, g, k, sm, i0, j0, acc, accumulate); break;
-    case 1: syn_body<T, 4>(S, h, g, k, sm, i0, j0, acc, accumulate); break;
-    case 2: syn_body<T, 6>(S, h, g, k, sm, i0, j0, acc, accumulate); break;
-    case 3: syn_body<T, 8>(S, h, g, k, sm, i0, j0, acc, accumulate); break;
-    case 4: syn_body<T, 10>(S, h, g, k, sm, i0, j0, acc, accumulate); break;
-    case 5: syn_body<T, 12>(S, h, g, k, sm, i0, j0, acc, accumulate); break;
-    case 6: syn_body<T, 14>(S, h, g, k, sm, i0, j0, acc, accumulate); break;
-    default: syn_body<T, 16>(S, h, g, k, sm, i0, j0, acc, accumulate); break;
+    case 0: syn_body<T, 2>(S, h, g, z, sm, i0, j0, acc, accumulate); break;
+    case 1: syn_body<T, 4>(S, h, g, z, sm, i0, j0, acc, accumulate); break;
+    case 2: syn_body<T, 6>(S, h, g, z, sm, i0, j0, acc, accumulate); break;
+    case 3: syn_body<T, 8>(S, h, g, z, sm, i0, j0, acc, accumulate); break;
+    case 4: syn_body<T, 10>(S, h, g, z, sm, i0, j0, acc, accumulate); break;
+    case 5: syn_body<T, 12>(S, h, g, z, sm, i0, j0, acc, accumulate); break;
+    case 6: syn_body<T, 14>(S, h, g, z, sm, i0, j0, acc, accumulate); break;
+    default: syn_body<T, 16>(S, h, g, z, sm, i0, j0, acc, accumulate); break;
   }
 }
 
-// Intermediate synthesis level: blockIdx.z = filter, output band -> scratch.
+// Intermediate synthesis level: blockIdx.z = filter slot, output band -> scratch.
 template <typename T>
 __global__ void __launch_bounds__(kThr) k_syn_level(SynArgs<T> S, DbFilters<T> f) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sm = reinterpret_cast<T*>(sm_raw);
   T acc[kTO * kTO / kThr];
-  syn_dispatch(S, f, blockIdx.z, sm, blockIdx.y * kTO, blockIdx.x * kTO, acc, false);
+  syn_dispatch(S, f, blockIdx.z, S.fid[blockIdx.z], sm, blockIdx.y * kTO, blockIdx.x * kTO, acc, false);
 }
 
-// Finest level: all eight filters and the Dirac block summed into the image.
-template <typename T>
+// Finest level: all selected filters and the Dirac block summed into the
+// image (ALL: the eight filters in slots 0..7, unrolled).
+template <typename T, bool ALL>
 __global__ void __launch_bounds__(kThr) k_syn_final(SynArgs<T> S, DbFilters<T> f) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sm = reinterpret_cast<T*>(sm_raw);
@@ -279,16 +309,20 @@ __global__ void __launch_bounds__(kThr) k_syn_final(SynArgs<T> S, DbFilters<T> f
   T acc[kTO * kTO / kThr];
 #pragma unroll
   for (int q = 0; q < kTO * kTO / kThr; ++q) acc[q] = 0;
-  for (int k = 0; k < kMaxDb; ++k) syn_dispatch(S, f, k, sm, i0, j0, acc, true);
+  if constexpr (ALL) {
+#pragma unroll
+    for (int k = 0; k < kMaxDb; ++k) syn_dispatch(S, f, k, k, sm, i0, j0, acc, true);
+  } else {
+    for (int z = 0; z < S.nf; ++z) syn_dispatch(S, f, z, S.fid[z], sm, i0, j0, acc, true);
+  }
   const int n = S.n;
-  const T t3 = third<T>();
 #pragma unroll
   for (int q = 0; q < kTO * kTO / kThr; ++q) {
     const int e = threadIdx.x + q * kThr;
     const int il = e / kTO, jl = e - il * kTO;
     if (i0 + il >= n || j0 + jl >= n) continue;
     const size_t idx = size_t(i0 + il) * n + (j0 + jl);
-    const T x1 = acc[q] + S.c[idx] * t3;  // Dirac block
+    const T x1 = S.slot0 ? acc[q] + S.c[idx] * S.scale : acc[q];  // Dirac block
     if (S.pos_block) {
       const T v2 = S.xh[idx] + S.z2[idx];
       const T r2 = v2 > T(0) ? v2 : T(0);
@@ -317,9 +351,12 @@ int run_analysis(const SaraPlan<T>& P, const T* x, const CoefOut<T>& out, double
   const int n = P.n;
   const size_t N = size_t(n) * n;
   int np = 0;
-  const int nb0 = int((N + kThr - 1) / kThr);
-  k_dirac<T><<<nb0, kThr, 0, s>>>(x, N, out, partials ? partials : nullptr);
-  if (partials) np += nb0;
+  if (P.dirac) {
+    const int nb0 = int((N + kThr - 1) / kThr);
+    k_dirac<T><<<nb0, kThr, 0, s>>>(x, N, P.scale, out, partials ? partials : nullptr);
+    if (partials) np += nb0;
+  }
+  if (P.nf == 0) return np;
   const size_t sm = ana_smem<T>(16);
   const T* in = x;
   size_t in_stride = 0;
@@ -333,9 +370,12 @@ int run_analysis(const SaraPlan<T>& P, const T* x, const CoefOut<T>& out, double
     A.n = n;
     A.s_out = bufs[lev & 1];
     A.last = lev == P.levels;
+    A.slot0 = P.dirac;
+    for (int z = 0; z < kMaxDb; ++z) A.fid[z] = P.fid[z];
+    A.scale = P.scale;
     A.out = out;
     A.partials = partials ? partials + np : nullptr;
-    dim3 grid(cdiv(H, kTH), cdiv(H, kTH), kMaxDb);
+    dim3 grid(cdiv(H, kTH), cdiv(H, kTH), P.nf);
     k_ana_level<T><<<grid, kThr, sm, s>>>(A, P.f);
     if (partials) np += int(grid.x * grid.y * grid.z);
     in = A.s_out;
@@ -350,7 +390,13 @@ void run_synthesis(const SaraPlan<T>& P, const T* c, T* x, int pos_block, const 
   const size_t sm = syn_smem<T>(16);
   T* bufs[2] = {P.s0, P.s1};
   const T* s_in = nullptr;
-  for (int lev = P.levels; lev >= 2; --lev) {
+  auto select = [&](SynArgs<T>& S) {
+    S.slot0 = P.dirac;
+    S.nf = P.nf;
+    for (int z = 0; z < kMaxDb; ++z) S.fid[z] = P.fid[z];
+    S.scale = P.scale;
+  };
+  for (int lev = P.levels; lev >= 2 && P.nf > 0; --lev) {
     const int H = n >> lev, L = 2 * H;
     SynArgs<T> S{};
     S.c = c;
@@ -358,7 +404,8 @@ void run_synthesis(const SaraPlan<T>& P, const T* c, T* x, int pos_block, const 
     S.H = H;
     S.n = n;
     S.s_out = bufs[lev & 1];
-    dim3 grid(cdiv(L, kTO), cdiv(L, kTO), kMaxDb);
+    select(S);
+    dim3 grid(cdiv(L, kTO), cdiv(L, kTO), P.nf);
     k_syn_level<T><<<grid, kThr, sm, s>>>(S, P.f);
     s_in = S.s_out;
   }
@@ -367,13 +414,17 @@ void run_synthesis(const SaraPlan<T>& P, const T* c, T* x, int pos_block, const 
   S.s_in = s_in;
   S.H = n / 2;
   S.n = n;
+  select(S);
   S.fused = 1;
   S.pos_block = pos_block;
   S.x_out = x;
   S.xh = xh;
   S.z2 = z2;
   dim3 grid(cdiv(n, kTO), cdiv(n, kTO), 1);
-  k_syn_final<T><<<grid, kThr, sm, s>>>(S, P.f);
+  if (P.nf == kMaxDb)
+    k_syn_final<T, true><<<grid, kThr, sm, s>>>(S, P.f);
+  else
+    k_syn_final<T, false><<<grid, kThr, sm, s>>>(S, P.f);
 }
 
 }  // namespace
@@ -382,11 +433,27 @@ template <typename T> cudaError_t configure_sara() {
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = raise_smem_limit(k_ana_level<T>);
   if (e == cudaSuccess) e = raise_smem_limit(k_syn_level<T>);
-  if (e == cudaSuccess) e = raise_smem_limit(k_syn_final<T>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_syn_final<T, true>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_syn_final<T, false>);
   return e;
 }
 template cudaError_t configure_sara<float>();
 template cudaError_t configure_sara<double>();
+
+template <typename T> int sara_select(SaraPlan<T>& P, unsigned mask) {
+  if (mask == 0 || (mask & ~kSaraAll)) return -1;
+  P.dirac = int(mask & 1u);
+  P.nf = 0;
+  for (int k = 0; k < kMaxDb; ++k) {
+    P.fid[k] = 0;
+    if (mask & (2u << k)) P.fid[P.nf++] = k;
+  }
+  P.nbases = P.dirac + P.nf;
+  P.scale = T(1.0 / std::sqrt(double(P.nbases)));
+  return P.nbases;
+}
+template int sara_select<float>(SaraPlan<float>&, unsigned);
+template int sara_select<double>(SaraPlan<double>&, unsigned);
 
 int sara_partials_capacity(int n, int levels) {
   int np = (n * n + kThr - 1) / kThr;
@@ -518,6 +585,7 @@ extern "C" int purify_sara_fwd_static(const float* x, float* c, int n, int level
   P.s1 = scratch + kStaticBand;
   P.cs = nullptr;
   P.f = g_static_filters;
+  sara_select(P, kSaraAll);
   sara_analysis<float>(P, x, c, static_cast<cudaStream_t>(stream));
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

@@ -35,13 +35,13 @@ class DensePsi:
         return (self.Psih.T @ c).reshape(self.n, self.n)
 
 
-def tiny_problem(n=8, M=96, levels=1, seed=11):
+def tiny_problem(n=8, M=96, levels=1, seed=11, bases=sara.ALL_BASES):
     uv = synth.uv_coverage(M, n, seed)
     op = NUFFT(uv, n)
     N = n * n
     eye = np.eye(N)
     Phi = np.stack([op.phi(e.reshape(n, n)) for e in eye], axis=1)
-    Psih = np.stack([sara.analysis(e.reshape(n, n), levels).ravel() for e in eye], axis=1)
+    Psih = np.stack([sara.analysis(e.reshape(n, n), levels, bases).ravel() for e in eye], axis=1)
     dop, dpsi = DenseOp(Phi, n), DensePsi(Psih, n)
     x_true = synth.sky(n, seed, 1, 3)
     y0 = dop.phi(x_true)

@@ -144,6 +144,40 @@ def test_sdmm_reaches_the_optimum_of_problem_3():
     assert np.linalg.norm(bal) < 1e-5 * np.linalg.norm(T["dpsi"].synthesis(st.z1))
 
 
+def test_sdmm_reaches_the_optimum_with_the_db8_dictionary():
+    """Section 4's BPDb8 analysis problem (Db8 basis alone): the same
+    duality-gap certificate as for SARA closes."""
+    T = tiny_problem(bases=(8,))
+    w = np.ones(64)
+    gamma = 10.0 * S.default_gamma(T["dop"], T["dpsi"], T["y"], T["nu"])
+    st = S.sdmm(T["dop"], T["dpsi"], T["y"], T["eps"], gamma, w, 1500, 20, T["nu"])
+    gap, resid = _duality_gap(T, st, w, gamma)
+    assert -1e-8 < gap < 1e-6
+    assert resid < 1e-6
+    assert np.linalg.norm(T["y"] - T["dop"].phi(st.x)) <= T["eps"] * (1 + 1e-6)
+
+
+def test_sdmm_reaches_the_optimum_with_the_dirac_dictionary():
+    """Section 4's BP problem (Psi = I): min ||x||_1, x >= 0, in the ball.  Here
+    the dual candidate can be made exactly feasible -- u1 + u2 = -s with
+    |u1| <= w and u2 <= 0 needs s >= -w, so u3 = z3 / gamma is scaled down
+    until it holds -- and weak duality bounds the gap from below by 0."""
+    T = tiny_problem(bases=(0,))
+    nu, w = T["nu"], np.ones(64)
+    gamma = 100.0 * S.default_gamma(T["dop"], T["dpsi"], T["y"], nu)
+    st = S.sdmm(T["dop"], T["dpsi"], T["y"], T["eps"], gamma, w, 5000, 20, nu)
+    u3 = st.z3 / gamma
+    s = (nu * T["dop"].phi_adj_real(u3)).ravel()
+    worst = float(np.max(-s / w))
+    if worst > 1.0:
+        u3 = u3 / worst
+    dual = -np.real(np.vdot(u3, nu * T["y"])) - nu * T["eps"] * np.linalg.norm(u3)
+    primal = float(np.sum(w * np.abs(st.x.ravel())))
+    assert 0.0 <= (primal - dual) / primal < 1e-3
+    assert np.linalg.norm(T["y"] - T["dop"].phi(st.x)) <= T["eps"] * (1 + 1e-4)
+    assert st.x.min() >= -1e-6 * st.x.max()
+
+
 def test_planted_sdmm_mistake_is_caught():
     """Dropping the dual update's sign (z <- z - (Lx - r)) stops SDMM reaching
     the optimum that the correct iteration reaches."""

@@ -102,3 +102,53 @@ def test_planted_dwt_mistake_is_caught():
     x = np.random.default_rng(0).standard_normal((16, 16))
     c = dwt.dwt2(x, h, g_bad, 1)
     assert abs(np.linalg.norm(c) - np.linalg.norm(x)) > 1e-3
+
+
+SUBSETS = [(0,), (8,), (0, 8), (1, 2, 5), tuple(range(9))]
+
+
+@pytest.mark.parametrize("bases", SUBSETS)
+def test_sub_dictionary_is_a_tight_frame(bases):
+    """Every selection of q bases scaled by 1/sqrt(q) keeps Psi Psi^H = I,
+    preserves energy and is the adjoint of its synthesis (Section 4's BP,
+    BPDb8 and SA dictionaries)."""
+    n, levels = 32, 3
+    x = np.random.default_rng(5).standard_normal((n, n))
+    c = sara.analysis(x, levels, bases)
+    assert c.shape == (len(bases), n, n)
+    assert np.max(np.abs(sara.synthesis(c, levels, bases) - x)) < 1e-12
+    assert np.linalg.norm(c) == pytest.approx(np.linalg.norm(x), rel=1e-13)
+    d = np.random.default_rng(6).standard_normal(c.shape)
+    assert np.sum(c * d) == pytest.approx(np.sum(x * sara.synthesis(d, levels, bases)), rel=1e-12)
+
+
+def test_dirac_dictionary_is_the_identity():
+    """BP's dictionary: Psi = I exactly (one basis, scale 1)."""
+    x = np.random.default_rng(7).standard_normal((16, 16))
+    assert np.array_equal(sara.analysis(x, 2, (0,))[0], x)
+    assert np.array_equal(sara.synthesis(x[None], 2, (0,)), x)
+
+
+def test_single_wavelet_basis_is_orthonormal():
+    """BPDb8's dictionary is square and orthonormal: Psi^H Psi = I too."""
+    n, levels = 16, 2
+    c = np.random.default_rng(8).standard_normal((1, n, n))
+    assert np.max(np.abs(sara.analysis(sara.synthesis(c, levels, (8,)), levels, (8,)) - c)) < 1e-12
+
+
+def test_sub_dictionary_blocks_are_rescaled_sara_blocks():
+    """A sub-dictionary's blocks are the SARA blocks of the same bases, rescaled
+    from 1/3 to 1/sqrt(q); the order is increasing basis index."""
+    n, levels = 32, 3
+    x = np.random.default_rng(9).standard_normal((n, n))
+    full = sara.analysis(x, levels)
+    sub = sara.analysis(x, levels, (8, 0, 3))
+    for s, K in enumerate((0, 3, 8)):
+        assert np.allclose(sub[s] * np.sqrt(3), full[K] * 3, rtol=0, atol=1e-12)
+
+
+def test_bad_dictionary_rejected():
+    with pytest.raises(ValueError):
+        sara.analysis(np.zeros((16, 16)), 2, ())
+    with pytest.raises(ValueError):
+        sara.analysis(np.zeros((16, 16)), 2, (9,))
