@@ -107,17 +107,25 @@ __device__ void ana_body(const AnaArgs<T>& A, const T* __restrict__ h, const T* 
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < W * kTH; e += kThr) {
-    const int ir = e / kTH, c = e - ir * kTH;
-    const T* xr = X + ir * W + 2 * c;
-    T sl = 0, sh = 0;
+  // row filtering, CB consecutive outputs per item: they share F + 2 CB - 2 inputs
+  constexpr int CB = 4;
+  for (int e = threadIdx.x; e < W * (kTH / CB); e += kThr) {
+    const int ir = e / (kTH / CB), cg = e - ir * (kTH / CB);
+    const T* xr = X + ir * W + 2 * CB * cg;
+    T xv[F + 2 * CB - 2];
 #pragma unroll
-    for (int m = 0; m < F; ++m) {
-      sl = fma(h[m], xr[m], sl);
-      sh = fma(g[m], xr[m], sh);
+    for (int k = 0; k < F + 2 * CB - 2; ++k) xv[k] = xr[k];
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+      T sl = 0, sh = 0;
+#pragma unroll
+      for (int m = 0; m < F; ++m) {
+        sl = fma(h[m], xv[2 * b + m], sl);
+        sh = fma(g[m], xv[2 * b + m], sh);
+      }
+      lo[ir * kTH + CB * cg + b] = sl;
+      hi[ir * kTH + CB * cg + b] = sh;
     }
-    lo[e] = sl;
-    hi[e] = sh;
   }
   __syncthreads();
   Acc<T> part;
@@ -202,17 +210,29 @@ template <typename T> struct SynArgs {
   T* z2;
 };
 
-// One filter's level synthesis of the output tile (i0, j0) into Xo[kTO][kTO].
+// Output samples of thread t in a synthesis tile: acc[2 q + p] is row
+// il = e / (kTO/2), column jl = 2 (e mod kTO/2) + p of item e = t + q kThr.
+PD void syn_out_pos(int q, int& il, int& jl) {
+  const int e = int(threadIdx.x) + (q >> 1) * kThr;
+  il = e / (kTO / 2);
+  jl = 2 * (e % (kTO / 2)) + (q & 1);
+}
+constexpr int kUP = 48;  // row pitch of the upsampled rows (16 mod 32: two rows of a warp's reads hit distinct banks)
+
+// One filter's level synthesis of the output tile (i0, j0).  Upsampling along
+// rows then columns; outputs 2j and 2j + 1 of either pass read the same
+// inputs (rows / columns j - t + F/2), so each item computes both parities.
 template <typename T, int F>
 __device__ void syn_body(const SynArgs<T>& S, const T* __restrict__ h, const T* __restrict__ g, int z, T* sm,
                          int i0, int j0, T (&acc)[kTO * kTO / kThr], bool accumulate) {
-  constexpr int CT = kTO / 2 + F / 2;
+  constexpr int CT = kTO / 2 + F / 2, HF = F / 2;
+  static_assert(CT <= kUP && kTO * kTO / kThr == 4, "tile shape");
   T* LLt = sm;
   T* LHt = LLt + CT * CT;
   T* HLt = LHt + CT * CT;
   T* HHt = HLt + CT * CT;
-  T* Ulo = HHt + CT * CT;      // [kTO][CT]
-  T* Uhi = Ulo + kTO * CT;
+  T* Ulo = HHt + CT * CT;      // [kTO][kUP]
+  T* Uhi = Ulo + kTO * kUP;
   const int H = S.H, n = S.n, L = 2 * H;
   const T* cb = S.c + size_t(S.slot0 + z) * n * n;
   const T t3 = S.scale;
@@ -234,40 +254,45 @@ __device__ void syn_body(const SynArgs<T>& S, const T* __restrict__ h, const T* 
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < kTO * CT; e += kThr) {
-    const int il = e / CT, lc = e - il * CT;
-    T ul = 0, uh = 0;
-    const int par = il & 1;
+  // rows il = 2j + par: U(il, lc) = sum_t h[par + 2t] LL(j - t + HF, lc) + g[par + 2t] HL(...)
+  for (int e = threadIdx.x; e < (kTO / 2) * CT; e += kThr) {
+    const int j = e / CT, lc = e - j * CT;
+    const int o = (j + HF) * CT + lc;
+    T ul0 = 0, ul1 = 0, uh0 = 0, uh1 = 0;
 #pragma unroll
-    for (int t = 0; t < F / 2; ++t) {
-      const int m = par + 2 * t;
-      const int lr = (il - m) / 2 + F / 2;
-      ul = fma(h[m], LLt[lr * CT + lc], ul);
-      ul = fma(g[m], HLt[lr * CT + lc], ul);
-      uh = fma(h[m], LHt[lr * CT + lc], uh);
-      uh = fma(g[m], HHt[lr * CT + lc], uh);
+    for (int t = 0; t < HF; ++t) {
+      const T a = LLt[o - t * CT], b = HLt[o - t * CT], c = LHt[o - t * CT], d = HHt[o - t * CT];
+      ul0 = fma(h[2 * t], a, fma(g[2 * t], b, ul0));
+      ul1 = fma(h[2 * t + 1], a, fma(g[2 * t + 1], b, ul1));
+      uh0 = fma(h[2 * t], c, fma(g[2 * t], d, uh0));
+      uh1 = fma(h[2 * t + 1], c, fma(g[2 * t + 1], d, uh1));
     }
-    Ulo[e] = ul;
-    Uhi[e] = uh;
+    Ulo[(2 * j) * kUP + lc] = ul0;
+    Ulo[(2 * j + 1) * kUP + lc] = ul1;
+    Uhi[(2 * j) * kUP + lc] = uh0;
+    Uhi[(2 * j + 1) * kUP + lc] = uh1;
   }
   __syncthreads();
+  // columns jl = 2j + par: X(il, jl) = sum_t h[par + 2t] Ulo(il, j - t + HF) + g[par + 2t] Uhi(...)
 #pragma unroll
-  for (int q = 0; q < kTO * kTO / kThr; ++q) {
+  for (int q = 0; q < 2; ++q) {
     const int e = threadIdx.x + q * kThr;
-    const int il = e / kTO, jl = e - il * kTO;
-    T v = 0;
-    const int par = jl & 1;
+    const int il = e / (kTO / 2), j = e % (kTO / 2);
+    const int o = il * kUP + j + HF;
+    T v0 = 0, v1 = 0;
 #pragma unroll
-    for (int t = 0; t < F / 2; ++t) {
-      const int m = par + 2 * t;
-      const int lc = (jl - m) / 2 + F / 2;
-      v = fma(h[m], Ulo[il * CT + lc], v);
-      v = fma(g[m], Uhi[il * CT + lc], v);
+    for (int t = 0; t < HF; ++t) {
+      const T a = Ulo[o - t], b = Uhi[o - t];
+      v0 = fma(h[2 * t], a, fma(g[2 * t], b, v0));
+      v1 = fma(h[2 * t + 1], a, fma(g[2 * t + 1], b, v1));
     }
     if (accumulate) {
-      acc[q] += v;
-    } else if (i0 + il < L && j0 + jl < L) {
-      S.s_out[size_t(z) * L * L + size_t(i0 + il) * L + (j0 + jl)] = v;
+      acc[2 * q] += v0;
+      acc[2 * q + 1] += v1;
+    } else if (i0 + il < L && j0 + 2 * j + 1 < L) {
+      T* dst = S.s_out + size_t(z) * L * L + size_t(i0 + il) * L + (j0 + 2 * j);
+      dst[0] = v0;
+      dst[1] = v1;
     }
   }
   __syncthreads();
@@ -318,8 +343,8 @@ __global__ void __launch_bounds__(kThr) k_syn_final(SynArgs<T> S, DbFilters<T> f
   const int n = S.n;
 #pragma unroll
   for (int q = 0; q < kTO * kTO / kThr; ++q) {
-    const int e = threadIdx.x + q * kThr;
-    const int il = e / kTO, jl = e - il * kTO;
+    int il, jl;
+    syn_out_pos(q, il, jl);
     if (i0 + il >= n || j0 + jl >= n) continue;
     const size_t idx = size_t(i0 + il) * n + (j0 + jl);
     const T x1 = S.slot0 ? acc[q] + S.c[idx] * S.scale : acc[q];  // Dirac block
@@ -340,7 +365,7 @@ template <typename T> size_t ana_smem(int F) {
 }
 template <typename T> size_t syn_smem(int F) {
   const int CT = kTO / 2 + F / 2;
-  return size_t(4 * CT * CT + 2 * kTO * CT) * sizeof(T);
+  return size_t(4 * CT * CT + 2 * kTO * kUP) * sizeof(T);
 }
 
 inline int cdiv(int a, int b) { return (a + b - 1) / b; }
