@@ -107,12 +107,22 @@ template <typename T> class OpImpl : public purify_op {
   int64_t bytes = 0;
   std::vector<void*> allocs;
   cudaStream_t own = nullptr;  // solver stream (capturable, non-blocking)
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaStream_t aux = nullptr;  // second branch of an SDMM iteration (ball block)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr, ev_join = nullptr;
+  double* bpart = nullptr;     // ball-block partials (2 per work item), apart from the l1 block's
+  int bpart_cap = 0;
 
   int partials_cap = 0;
   int size_partials() {
     const int np = std::max({2 * n_items, row_inv_blocks(g), sara_partials_capacity(g.n, levels),
                              vec_blocks(9 * N()), 1});
+    if (2 * n_items > bpart_cap) {
+      double* bnew = nullptr;
+      const int rc = alloc(&bnew, size_t(std::max(2 * n_items, 1)));
+      if (rc) return rc;
+      bpart = bnew;
+      bpart_cap = std::max(2 * n_items, 1);
+    }
     if (np <= partials_cap) return PURIFY_OK;
     double* pnew = nullptr;
     const int rc = alloc(&pnew, np);
@@ -162,9 +172,13 @@ template <typename T> class OpImpl : public purify_op {
     if (own) cudaStreamSynchronize(own);
     cudaFree(items);
     for (void* a : allocs) cudaFree(a);
+    if (aux) cudaStreamSynchronize(aux);
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
     if (own) cudaStreamDestroy(own);
+    if (aux) cudaStreamDestroy(aux);
     if (h_sc) cudaFreeHost(h_sc);
   }
 
@@ -215,8 +229,11 @@ template <typename T> class OpImpl : public purify_op {
     levels = L;
     chunk = chunk_opt > 0 ? chunk_opt : 1024;
     CK(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
     CK(configure_fft<T>());
     CK(configure_nufft<T>());
     CK(configure_sara<T>());
@@ -606,6 +623,41 @@ template <typename T> class OpImpl : public purify_op {
       normal_back(ep, s);
     }
     if (cg_iters > 0) PROF(KK_VEC, s, launch_axpy<T>(xh, p, sc, S_ALPHA, n2, s));  // last step: x += alpha p
+    // The three proximal blocks (steps 6-8) are independent until their sum:
+    // the ball block's degridding, projection and gridding run on the second
+    // stream beside the l1 and positivity blocks, and the join feeds its last
+    // pass, which adds nu Re Phi^H (2 r_3 - v_3) to x_1 + x_2.
+    // (With kernel timing enabled both branches stay on one stream, so that
+    // every kernel's time is its own.)
+    cudaStream_t b3 = prof ? s : aux;
+    if (b3 != s) {
+      cudaEventRecord(ev_fork, s);
+      cudaStreamWaitEvent(b3, ev_fork, 0);
+    }
+    // block 3 (data fidelity): v = nu Phi x_hat + z_3, project on the ball
+    fwd_grid(plain(xh), b3);
+    DegridEp<C> dep{};
+    dep.mode = DG_BALL;
+    dep.z = z3;
+    dep.ys = ys;
+    dep.nu = nu;
+    dep.part0 = bpart;
+    dep.part1 = bpart + n_items;
+    degrid(dep, b3);
+    PROF(KK_VEC, b3, launch_finalize_blocks<T>(bpart, bpart + n_items, reinterpret_cast<const int*>(items), n_items,
+                                                nblocks, nu, eps_dev, scale_dev, sc, b3));
+    zero_q(b3);
+    GridPro<C> gp{};
+    gp.mode = GP_BALL;
+    gp.z = z3;
+    gp.ys = ys;
+    gp.nu = nu;
+    gp.scalars = sc;
+    gp.scale_idx = S_BALLSCALE;
+    gp.block_scale = scale_dev;
+    grid(gp, b3);
+    col_inv(b3);
+    if (b3 != s) cudaEventRecord(ev_join, b3);
     // block 1 (l1 on Psi^H x_hat) fused into the analysis, block 2 (positivity)
     // fused into the synthesis: xs = x_1 + x_2
     L1Block<T> b1{};
@@ -617,30 +669,8 @@ template <typename T> class OpImpl : public purify_op {
     PROF(KK_SARA_ANA, s, npo = sara_analysis_prox<T>(sara, xh, b1, s));
     fin(partials, npo, FIN_OBJ, 0.0, s);
     PROF(KK_SARA_SYN, s, sara_synthesis_pos<T>(sara, xh, z2, xs, s));
-    // block 3 (data fidelity): v = nu Phi x_hat + z_3, project on the ball,
-    // xs += nu Re Phi^H (2r - v)
-    fwd_grid(plain(xh), s);
-    DegridEp<C> dep{};
-    dep.mode = DG_BALL;
-    dep.z = z3;
-    dep.ys = ys;
-    dep.nu = nu;
-    dep.part0 = partials;
-    dep.part1 = partials + n_items;
-    degrid(dep, s);
-    PROF(KK_VEC, s, launch_finalize_blocks<T>(partials, partials + n_items, reinterpret_cast<const int*>(items), n_items,
-                                           nblocks, nu, eps_dev, scale_dev, sc, s));
-    zero_q(s);
-    GridPro<C> gp{};
-    gp.mode = GP_BALL;
-    gp.z = z3;
-    gp.ys = ys;
-    gp.nu = nu;
-    gp.scalars = sc;
-    gp.scale_idx = S_BALLSCALE;
-    gp.block_scale = scale_dev;
-    grid(gp, s);
-    col_inv(s);
+    // join: xs += nu Re Phi^H (2 r_3 - v_3)
+    if (b3 != s) cudaStreamWaitEvent(s, ev_join, 0);
     RowEp<T> ep{};
     ep.mode = EP_XS_ADD;
     ep.out = xs;

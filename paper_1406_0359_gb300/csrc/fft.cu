@@ -115,23 +115,28 @@ template <typename C> struct Dft<16, C> {
 
 PD int sidx(int e) { return e + (e >> 4); }  // padded shared index
 
-// Compile-time plan of a length-2^LOGN transform: radix-16 stages, then one
-// radix-2^(LOGN mod 4) stage; T = N/16 threads per sequence.
-template <int LOGN> struct Plan {
+// Compile-time plan of a length-2^LOGN transform with E (8 or 16) elements
+// per thread: radix-E stages, then one radix-2^r stage for the remaining r
+// bits; T = N/E threads per sequence.
+template <int LOGN, int E = 16> struct Plan {
+  static_assert(E == 8 || E == 16, "8 or 16 elements per thread");
+  static constexpr int LE = E == 16 ? 4 : 3;
   static constexpr int N = 1 << LOGN;
-  static constexpr int T = N / 16;
-  static constexpr int NST = (LOGN + 3) / 4;
-  __host__ __device__ static constexpr int radix(int st) { return (st + 1 < NST || LOGN % 4 == 0) ? 16 : (1 << (LOGN % 4)); }
+  static constexpr int T = N / E;
+  static constexpr int NST = (LOGN + LE - 1) / LE;
+  __host__ __device__ static constexpr int radix(int st) {
+    return st + 1 < NST ? E : (1 << (LOGN - LE * (NST - 1)));
+  }
 };
 
 // One Stockham stage on the registers: v[m] holds element t + m T of the
-// stage input.  Thread t owns butterflies j = t + q T (q < 16/R); input r of
-// butterfly j is element j + r N/R, i.e. register q + r 16/R.  After the
-// twiddles and the DFT, register q + r 16/R is output (j - k) R + k + r Ns
+// stage input.  Thread t owns butterflies j = t + q T (q < E/R); input r of
+// butterfly j is element j + r N/R, i.e. register q + r E/R.  After the
+// twiddles and the DFT, register q + r E/R is output (j - k) R + k + r Ns
 // with k = j mod Ns; sink(position, value) receives every output.
-template <int R, int N, int T, typename C, typename Sink>
-PD void stage(C (&v)[16], int t, int Ns, const C* __restrict__ tw, int dir, Sink sink) {
-  constexpr int Q = 16 / R;
+template <int R, int N, int T, int E, typename C, typename Sink>
+PD void stage(C (&v)[E], int t, int Ns, const C* __restrict__ tw, int dir, Sink sink) {
+  constexpr int Q = E / R;
   const int tstride = N / (Ns * R);
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
@@ -161,42 +166,43 @@ PD void stage(C (&v)[16], int t, int Ns, const C* __restrict__ tw, int dir, Sink
 // one sequence per buffer (rows), ss = cw for cw interleaved columns, so that
 // the lanes that read 32 contiguous bytes of cw columns from global memory
 // also touch contiguous shared words.
-template <int LOGN, int ST, typename C, typename Store>
-PD void run_stages(C (&v)[16], int t, int Ns, C* s, int ss, const C* tw, int dir, Store store) {
-  typedef Plan<LOGN> P;
+template <int LOGN, int ST, int E, typename C, typename Store>
+PD void run_stages(C (&v)[E], int t, int Ns, C* s, int ss, const C* tw, int dir, Store store) {
+  typedef Plan<LOGN, E> P;
   constexpr int R = P::radix(ST);
   if constexpr (ST + 1 == P::NST) {
-    stage<R, P::N, P::T>(v, t, Ns, tw, dir, store);
+    stage<R, P::N, P::T, E>(v, t, Ns, tw, dir, store);
   } else {
-    stage<R, P::N, P::T>(v, t, Ns, tw, dir, [&](int q, C x) { s[sidx(q) * ss] = x; });
+    stage<R, P::N, P::T, E>(v, t, Ns, tw, dir, [&](int q, C x) { s[sidx(q) * ss] = x; });
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = s[sidx(t + m * P::T) * ss];
+    for (int m = 0; m < E; ++m) v[m] = s[sidx(t + m * P::T) * ss];
     __syncthreads();
-    run_stages<LOGN, ST + 1>(v, t, Ns * R, s, ss, tw, dir, store);
+    run_stages<LOGN, ST + 1, E>(v, t, Ns * R, s, ss, tw, dir, store);
   }
 }
 
 // All stages of one sequence: load(m) supplies input element t + m T,
 // store(q, value) receives output q.
-template <int LOGN, typename C, typename Load, typename Store>
+template <int LOGN, int E = 16, typename C, typename Load, typename Store>
 PD void fft_seq(int t, C* s, int ss, const C* tw, int dir, Load load, Store store) {
-  C v[16];
+  C v[E];
 #pragma unroll
-  for (int m = 0; m < 16; ++m) v[m] = load(m);
-  run_stages<LOGN, 0>(v, t, 1, s, ss, tw, dir, store);
+  for (int m = 0; m < E; ++m) v[m] = load(m);
+  run_stages<LOGN, 0, E>(v, t, 1, s, ss, tw, dir, store);
 }
 
 // Output position of the cnt-th value a thread's final stage hands to its
 // sink: the final radix-R stage has Ns = K/R and butterflies j = t + q T < Ns,
 // so its outputs come in the order (q, r) at t + q T + r K/R.
-template <int LOGN> PD int last_pos(int t, int cnt) {
-  typedef Plan<LOGN> P;
+template <int LOGN, int E = 16> PD int last_pos(int t, int cnt) {
+  typedef Plan<LOGN, E> P;
   constexpr int R = P::radix(P::NST - 1);
   return t + (cnt / R) * P::T + (cnt % R) * (P::N / R);
 }
 
 constexpr int kRowCta = 256;
+constexpr int kRowE = 8;  // elements per thread in the real-form row passes
 
 inline int row_nseq(const Geometry& g) {
   int s = kRowCta / (g.K / 16);
@@ -257,30 +263,30 @@ PD void row_ep_store(const RowEp<T>& ep, size_t idx, T val, EpOpd<T> opd, EpAcc<
 }
 // Image column of the m-th output of thread t of an inverse row pass (grid
 // column q maps to image column (q + K/4) mod K, kept when < n = K/2).
-template <int LOGN> PD int ep_col(int t, int m) {
+template <int LOGN, int E = 16> PD int ep_col(int t, int m) {
   constexpr int K = 1 << LOGN;
-  return (last_pos<LOGN>(t, m) + K / 4) & (K - 1);
+  return (last_pos<LOGN, E>(t, m) + K / 4) & (K - 1);
 }
 // Outputs val[r][m] (the final stage's values in sink order) of image rows
 // row0[r], in chunks of CH outputs: operands of the chunk first, then its
 // stores.
-template <int LOGN, int MODE, int NR, typename T>
-PD EpAcc<T> row_ep_run_mode(const RowEp<T>& ep, const T (&val)[NR][16], int t, const size_t (&row0)[NR]) {
-  constexpr int CH = MODE == EP_CG_AP ? 8 : 16, n = (1 << LOGN) / 2;
+template <int LOGN, int MODE, int NR, int E, typename T>
+PD EpAcc<T> row_ep_run_mode(const RowEp<T>& ep, const T (&val)[NR][E], int t, const size_t (&row0)[NR]) {
+  constexpr int CH = MODE == EP_CG_AP ? E / 2 : E, n = (1 << LOGN) / 2;
   EpAcc<T> part;
 #pragma unroll
-  for (int c0 = 0; c0 < 16; c0 += CH) {
+  for (int c0 = 0; c0 < E; c0 += CH) {
     EpOpd<T> opd[NR][CH];
 #pragma unroll
     for (int m = 0; m < CH; ++m) {
-      const int i2 = ep_col<LOGN>(t, c0 + m);
+      const int i2 = ep_col<LOGN, E>(t, c0 + m);
 #pragma unroll
       for (int r = 0; r < NR; ++r)
         opd[r][m] = i2 < n ? row_ep_operand<MODE>(ep, row0[r] + i2) : EpOpd<T>{T(0), T(0)};
     }
 #pragma unroll
     for (int m = 0; m < CH; ++m) {
-      const int i2 = ep_col<LOGN>(t, c0 + m);
+      const int i2 = ep_col<LOGN, E>(t, c0 + m);
       if (i2 < n) {
 #pragma unroll
         for (int r = 0; r < NR; ++r) row_ep_store<MODE>(ep, row0[r] + i2, val[r][c0 + m], opd[r][m], part);
@@ -289,8 +295,8 @@ PD EpAcc<T> row_ep_run_mode(const RowEp<T>& ep, const T (&val)[NR][16], int t, c
   }
   return part;
 }
-template <int LOGN, int NR, typename T>
-PD EpAcc<T> row_ep_run(const RowEp<T>& ep, const T (&val)[NR][16], int t, const size_t (&row0)[NR]) {
+template <int LOGN, int NR, int E, typename T>
+PD EpAcc<T> row_ep_run(const RowEp<T>& ep, const T (&val)[NR][E], int t, const size_t (&row0)[NR]) {
   switch (ep.mode) {
     case EP_CG_AP: return row_ep_run_mode<LOGN, EP_CG_AP>(ep, val, t, row0);
     case EP_CG_R0: return row_ep_run_mode<LOGN, EP_CG_R0>(ep, val, t, row0);
@@ -301,23 +307,26 @@ PD EpAcc<T> row_ep_run(const RowEp<T>& ep, const T (&val)[NR][16], int t, const 
   }
 }
 
-// Forward row prologue (see RowProMode) of image rows row0[r] at the 8 grid
-// columns of thread t that hold image pixels: with K = 2n, grid column
-// q = t + m K/16 holds image column i2 = (q + K/4) mod K, inside the image
-// for m < 4 and m >= 12 only.  All loads precede the CG step's stores.
-template <int LOGN, int NR, typename T>
-PD void row_prologue(const RowPro<T>& pro, const size_t (&row0)[NR], int t, T (&val)[NR][8], int (&i2)[8]) {
-  constexpr int K = 1 << LOGN, TT = K / 16;
+// Register slot m of the j-th of the E/2 grid columns of a thread that hold
+// image pixels: with K = 2n, grid column q = t + m K/E holds image column
+// i2 = (q + K/4) mod K, inside the image for m < E/4 and m >= 3E/4 only.
+template <int E> PD constexpr int kept_slot(int j) { return j < E / 4 ? j : j + E / 2; }
+
+// Forward row prologue (see RowProMode) of image rows row0[r] at the E/2
+// kept grid columns of thread t.  All loads precede the CG step's stores.
+template <int LOGN, int NR, int E, typename T>
+PD void row_prologue(const RowPro<T>& pro, const size_t (&row0)[NR], int t, T (&val)[NR][E / 2], int (&i2)[E / 2]) {
+  constexpr int K = 1 << LOGN, TT = K / E;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) i2[j] = (t + (j < 4 ? j : j + 8) * TT + K / 4) & (K - 1);
+  for (int j = 0; j < E / 2; ++j) i2[j] = (t + kept_slot<E>(j) * TT + K / 4) & (K - 1);
   if (pro.mode == PRO_CG_STEP) {
     // x += alpha p, r -= alpha Ap, p = r + beta p (alpha, beta of the previous step)
     const T alpha = T(pro.scalars[S_ALPHA]), beta = T(pro.scalars[S_BETA]);
-    T xv[NR][8], rv[NR][8], av[NR][8];
+    T xv[NR][E / 2], rv[NR][E / 2], av[NR][E / 2];
 #pragma unroll
     for (int r = 0; r < NR; ++r)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
+      for (int j = 0; j < E / 2; ++j) {
         const size_t idx = row0[r] + i2[j];
         xv[r][j] = pro.xu[idx];
         rv[r][j] = pro.r[idx];
@@ -327,7 +336,7 @@ PD void row_prologue(const RowPro<T>& pro, const size_t (&row0)[NR], int t, T (&
 #pragma unroll
     for (int r = 0; r < NR; ++r)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
+      for (int j = 0; j < E / 2; ++j) {
         const size_t idx = row0[r] + i2[j];
         const T pv = val[r][j];
         const T rn = fma(-alpha, av[r][j], rv[r][j]);
@@ -341,7 +350,7 @@ PD void row_prologue(const RowPro<T>& pro, const size_t (&row0)[NR], int t, T (&
 #pragma unroll
     for (int r = 0; r < NR; ++r)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) val[r][j] = pro.x[row0[r] + i2[j]] * scl;
+      for (int j = 0; j < E / 2; ++j) val[r][j] = pro.x[row0[r] + i2[j]] * scl;
   }
 }
 
@@ -417,14 +426,14 @@ template <typename T> PD int ep_staged(const RowEp<T>& ep, const T** src) {
 }
 // Epilogue of both rows of a real-form sequence with the operands in shared
 // memory (ops[k][row][n]).
-template <int LOGN, int MODE, typename T>
-PD EpAcc<T> row_ep_staged_mode(const RowEp<T>& ep, const T (&val)[2][16], int t, const size_t (&row0)[2],
+template <int LOGN, int MODE, int E, typename T>
+PD EpAcc<T> row_ep_staged_mode(const RowEp<T>& ep, const T (&val)[2][E], int t, const size_t (&row0)[2],
                                const T* ops) {
   constexpr int n = (1 << LOGN) / 2;
   EpAcc<T> part;
 #pragma unroll
-  for (int m = 0; m < 16; ++m) {
-    const int i2 = ep_col<LOGN>(t, m);
+  for (int m = 0; m < E; ++m) {
+    const int i2 = ep_col<LOGN, E>(t, m);
     if (i2 < n) {
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
@@ -439,8 +448,8 @@ PD EpAcc<T> row_ep_staged_mode(const RowEp<T>& ep, const T (&val)[2][16], int t,
   }
   return part;
 }
-template <int LOGN, typename T>
-PD EpAcc<T> row_ep_staged(const RowEp<T>& ep, const T (&val)[2][16], int t, const size_t (&row0)[2], const T* ops) {
+template <int LOGN, int E, typename T>
+PD EpAcc<T> row_ep_staged(const RowEp<T>& ep, const T (&val)[2][E], int t, const size_t (&row0)[2], const T* ops) {
   switch (ep.mode) {
     case EP_CG_AP: return row_ep_staged_mode<LOGN, EP_CG_AP>(ep, val, t, row0, ops);
     case EP_CG_R0: return row_ep_staged_mode<LOGN, EP_CG_R0>(ep, val, t, row0, ops);
@@ -469,7 +478,7 @@ __global__ void __launch_bounds__(kRowCta) k_row_fwd(Geometry g, RowPro<T> pro, 
   const size_t row0[1] = {size_t(i1) * n};
   T val[1][8];
   int i2[8];
-  row_prologue<LOGN>(pro, row0, t, val, i2);
+  row_prologue<LOGN, 1, 16>(pro, row0, t, val, i2);
   const T s1 = deapod[i1];
   C v[16];
 #pragma unroll
@@ -584,33 +593,33 @@ __global__ void __launch_bounds__(kRowCta) k_row_inv(Geometry g, const typename 
 
 // Forward row pass of the real form: rows 2 pr and 2 pr + 1 of the prologue's
 // image, zero-padded to K columns, to their half spectra.
-template <typename T, int LOGN>
+template <typename T, int LOGN, int E>
 __global__ void __launch_bounds__(kRowCta) k_row_fwd_h(Geometry g, RowPro<T> pro,
                                                     typename cplx_t<T>::type* __restrict__ B,
                                                     const typename cplx_t<T>::type* __restrict__ tw, int nseq) {
   typedef typename cplx_t<T>::type C;
-  constexpr int TT = Plan<LOGN>::T;
+  constexpr int TT = Plan<LOGN, E>::T;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int K = g.K, n = g.n, H = K / 2;
   const int seq = threadIdx.x / TT, t = threadIdx.x - seq * TT;
   const int ia = 2 * (blockIdx.x * nseq + seq), ib = ia + 1;
   C* s = reinterpret_cast<C*>(sm_raw) + seq * padded(K);
   const size_t row0[2] = {size_t(ia) * n, size_t(ib) * n};
-  T val[2][8];
-  int i2[8];
-  row_prologue<LOGN>(pro, row0, t, val, i2);
-  C v[16];
+  T val[2][E / 2];
+  int i2[E / 2];
+  row_prologue<LOGN, 2, E>(pro, row0, t, val, i2);
+  C v[E];
 #pragma unroll
-  for (int m = 0; m < 16; ++m) v[m] = cz<C>();
+  for (int m = 0; m < E; ++m) v[m] = cz<C>();
 #pragma unroll
-  for (int j = 0; j < 8; ++j) v[j < 4 ? j : j + 8] = cmk<C>(val[0][j], val[1][j]);
+  for (int j = 0; j < E / 2; ++j) v[kept_slot<E>(j)] = cmk<C>(val[0][j], val[1][j]);
   auto to_smem = [&](int q, C x) { s[sidx(q)] = x; };
-  run_stages<LOGN, 0>(v, t, 1, s, 1, tw, -1, to_smem);
+  run_stages<LOGN, 0, E>(v, t, 1, s, 1, tw, -1, to_smem);
   __syncthreads();
   C* oa = B + size_t(ia) * H;
   C* ob = oa + H;
 #pragma unroll
-  for (int m = 0; m < 8; ++m) {
+  for (int m = 0; m < E / 2; ++m) {
     const int k = t + m * TT;
     const C zk = s[sidx(k)];
     if (k == 0) {
@@ -687,12 +696,12 @@ __global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN
 // b = 2 pr + 1 rebuilt into Z = Y_a + i Y_b over all K frequencies
 // (Y(K - k) = conj Y(k)), one inverse FFT, Re -> row a, Im -> row b, crop and
 // row epilogue.
-template <typename T, int LOGN>
+template <typename T, int LOGN, int E>
 __global__ void __launch_bounds__(kRowCta, 2) k_row_inv_h(Geometry g, const typename cplx_t<T>::type* __restrict__ B,
                                                        RowEp<T> ep, const typename cplx_t<T>::type* __restrict__ tw,
                                                        int nseq) {
   typedef typename cplx_t<T>::type C;
-  constexpr int TT = Plan<LOGN>::T;
+  constexpr int TT = Plan<LOGN, E>::T;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ double red[5 * 32];
   __shared__ __align__(8) uint64_t bar;
@@ -720,23 +729,23 @@ __global__ void __launch_bounds__(kRowCta, 2) k_row_inv_h(Geometry g, const type
   __syncthreads();
   const C* ba = B + size_t(ia) * H;
   const C* bb = ba + H;
-  // frequency q = t + m K/16: entry q for m < 8, entry K - q (entry 0 for
+  // frequency q = t + m K/E: entry q for m < E/2, entry K - q (entry 0 for
   // q = K/2) above; thread 0 unpacks entry 0 into Y(0) and Y(K/2)
   auto load = [&](int m) -> C {
     const int q = t + m * TT;
-    const int e = m < 8 ? q : ((K - q) & (H - 1));
+    const int e = m < E / 2 ? q : ((K - q) & (H - 1));
     const C a = ba[e], b = bb[e];
-    if (t == 0 && (m == 0 || m == 8)) return m == 0 ? cmk<C>(a.x, b.x) : cmk<C>(a.y, b.y);
-    return m < 8 ? cmk<C>(a.x - b.y, a.y + b.x) : cmk<C>(a.x + b.y, b.x - a.y);
+    if (t == 0 && (m == 0 || m == E / 2)) return m == 0 ? cmk<C>(a.x, b.x) : cmk<C>(a.y, b.y);
+    return m < E / 2 ? cmk<C>(a.x - b.y, a.y + b.x) : cmk<C>(a.x + b.y, b.x - a.y);
   };
-  T val[2][16];
+  T val[2][E];
   int cnt = 0;
   auto stash = [&](int, C v) {  // sink order, see last_pos
     val[0][cnt] = v.x;
     val[1][cnt] = v.y;
     ++cnt;
   };
-  fft_seq<LOGN>(t, s, 1, tw, +1, load, stash);
+  fft_seq<LOGN, E>(t, s, 1, tw, +1, load, stash);
   const size_t row0[2] = {size_t(ia) * n, size_t(ib) * n};
   bool ok = true;
   if (nop > 0) ok = mbar_wait_bounded(&bar, 0, ep.err);
@@ -792,9 +801,9 @@ __global__ void __launch_bounds__(ColThreads<T, LOGN>::value) k_cols_plain(typen
 
 int row_inv_blocks(const Geometry& g) { return g.n / row_nseq(g); }
 
-// Row pairs per CTA of the real-form row passes.
-inline int row_pair_nseq(const Geometry& g) {
-  int s = kRowCta / (g.K / 16);
+// Row pairs per CTA of the real-form row passes (E elements per thread).
+inline int row_pair_nseq(const Geometry& g, int E) {
+  int s = kRowCta / (g.K / E);
   if (s < 1) s = 1;
   if (s > g.n / 2) s = g.n / 2;
   return s;
@@ -817,9 +826,9 @@ template <typename T, int L> cudaError_t configure_one() {
   if (e == cudaSuccess) e = raise_smem_limit(k_row_inv<T, L>);
   if (e == cudaSuccess) e = raise_smem_limit(k_col_fwd<T, L>);
   if (e == cudaSuccess) e = raise_smem_limit(k_col_inv<T, L>);
-  if (e == cudaSuccess) e = raise_smem_limit(k_row_fwd_h<T, L>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_row_fwd_h<T, L, kRowE>);
   if (e == cudaSuccess) e = raise_smem_limit(k_col_conv_h<T, L>);
-  if (e == cudaSuccess) e = raise_smem_limit(k_row_inv_h<T, L>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_row_inv_h<T, L, kRowE>);
   if (e == cudaSuccess) e = raise_smem_limit(k_rows_plain<T, L>);
   if (e == cudaSuccess) e = raise_smem_limit(k_cols_plain<T, L>);
   return e;
@@ -912,9 +921,9 @@ template <typename T>
 void launch_row_fwd_h(const Geometry& g, const RowPro<T>& pro, typename cplx_t<T>::type* B,
                       const typename cplx_t<T>::type* tw, cudaStream_t s) {
   typedef typename cplx_t<T>::type C;
-  const int nseq = row_pair_nseq(g);
+  const int nseq = row_pair_nseq(g, kRowE);
   const size_t sm = nseq * padded(g.K) * sizeof(C);
-  PURIFY_LOGN_SWITCH(g.K, (k_row_fwd_h<T, L><<<g.n / 2 / nseq, nseq * Plan<L>::T, sm, s>>>(g, pro, B, tw, nseq)));
+  PURIFY_LOGN_SWITCH(g.K, (k_row_fwd_h<T, L, kRowE><<<g.n / 2 / nseq, nseq * Plan<L, kRowE>::T, sm, s>>>(g, pro, B, tw, nseq)));
 }
 
 template <typename T>
@@ -931,10 +940,10 @@ template <typename T>
 int launch_row_inv_h(const Geometry& g, const typename cplx_t<T>::type* B, const RowEp<T>& ep,
                      const typename cplx_t<T>::type* tw, cudaStream_t s) {
   typedef typename cplx_t<T>::type C;
-  const int nseq = row_pair_nseq(g);
+  const int nseq = row_pair_nseq(g, kRowE);
   const size_t sm = align16(nseq * padded(g.K) * sizeof(C)) + size_t(nseq) * 4 * g.n * sizeof(T);
   const int nb = g.n / 2 / nseq;
-  PURIFY_LOGN_SWITCH(g.K, (k_row_inv_h<T, L><<<nb, nseq * Plan<L>::T, sm, s>>>(g, B, ep, tw, nseq)));
+  PURIFY_LOGN_SWITCH(g.K, (k_row_inv_h<T, L, kRowE><<<nb, nseq * Plan<L, kRowE>::T, sm, s>>>(g, B, ep, tw, nseq)));
   return nb;
 }
 

@@ -68,6 +68,36 @@ template <typename T> PD void emit(const CoefOut<T>& o, size_t idx, T alpha, Acc
   part.add_prod(wj, fabs(alpha));
 }
 
+// emit for NE coefficients at once: every w and z_1 load precedes the first
+// store (the stores may alias them, which would otherwise serialise one memory
+// round trip per coefficient).
+template <int NE, typename T>
+PD void emit_n(const CoefOut<T>& o, const size_t (&idx)[NE], const T (&alpha)[NE], int ne, Acc<T>& part) {
+  if (!o.prox) {
+#pragma unroll
+    for (int k = 0; k < NE; ++k)
+      if (k < ne) o.c[idx[k]] = alpha[k];
+    return;
+  }
+  T wj[NE], z[NE];
+#pragma unroll
+  for (int k = 0; k < NE; ++k) {
+    wj[k] = (k < ne && o.w) ? o.w[idx[k]] : T(1);
+    z[k] = k < ne ? o.z1[idx[k]] : T(0);
+  }
+#pragma unroll
+  for (int k = 0; k < NE; ++k) {
+    if (k >= ne) continue;
+    const T v = alpha[k] + z[k];
+    const T thr = o.gamma * wj[k];
+    const T av = fabs(v);
+    const T r = av > thr ? copysign(av - thr, v) : T(0);
+    o.z1[idx[k]] = v - r;
+    o.cs[idx[k]] = T(2) * r - v;
+    part.add_prod(wj[k], fabs(alpha[k]));
+  }
+}
+
 template <typename T> struct AnaArgs {
   const T* in;
   size_t in_stride;  // elements between filters' input bands (0: shared input)
@@ -143,13 +173,11 @@ __device__ void ana_body(const AnaArgs<T>& A, const T* __restrict__ h, const T* 
     }
     const size_t base = size_t(A.slot0 + z) * n * n;
     const T sc = A.scale;
-    emit(A.out, base + size_t(R) * n + (H + Cc), lh * sc, part);
-    emit(A.out, base + size_t(H + R) * n + Cc, hl * sc, part);
-    emit(A.out, base + size_t(H + R) * n + (H + Cc), hh * sc, part);
-    if (A.last)
-      emit(A.out, base + size_t(R) * n + Cc, ll * sc, part);
-    else
-      A.s_out[size_t(z) * H * H + size_t(R) * H + Cc] = ll;
+    const size_t idx[4] = {base + size_t(R) * n + (H + Cc), base + size_t(H + R) * n + Cc,
+                           base + size_t(H + R) * n + (H + Cc), base + size_t(R) * n + Cc};
+    const T val[4] = {lh * sc, hl * sc, hh * sc, ll * sc};
+    emit_n<4>(A.out, idx, val, A.last ? 4 : 3, part);
+    if (!A.last) A.s_out[size_t(z) * H * H + size_t(R) * H + Cc] = ll;
   }
   if (A.partials) {
     const Acc<T> t = block_merge<kThr>(part, red);
