@@ -129,6 +129,31 @@ template <> PD void stage_store<double>(double* st, const double (&wu)[kJ], cons
 }
 static_assert(kStage == 2 * kJ + 4 && kJ == 8, "stage_store writes 2J + 4 values");
 
+// Gridding's staged record: {u.re, u.im, cell bits, pad}, then wu interleaved
+// as (wu[a], wu[a + 4]) pairs, then wv[0..7] -- lane (ta, tc) reads the first
+// 16 bytes, one 8-byte pair and one value per visibility.
+template <typename T> PD void stage_store_grid(T* st, const T (&wu)[kJ], const T (&wv)[kJ], T ux, T uy, int cell);
+template <> PD void stage_store_grid<float>(float* st, const float (&wu)[kJ], const float (&wv)[kJ], float ux,
+                                            float uy, int cell) {
+  float4* d = reinterpret_cast<float4*>(st);
+  d[0] = make_float4(ux, uy, __int_as_float(cell), 0.f);
+  d[1] = make_float4(wu[0], wu[4], wu[1], wu[5]);
+  d[2] = make_float4(wu[2], wu[6], wu[3], wu[7]);
+  d[3] = make_float4(wv[0], wv[1], wv[2], wv[3]);
+  d[4] = make_float4(wv[4], wv[5], wv[6], wv[7]);
+}
+template <> PD void stage_store_grid<double>(double* st, const double (&wu)[kJ], const double (&wv)[kJ], double ux,
+                                             double uy, int cell) {
+  double2* d = reinterpret_cast<double2*>(st);
+  d[0] = make_double2(ux, uy);
+  d[1] = make_double2(__hiloint2double(0, cell), 0.0);
+#pragma unroll
+  for (int a = 0; a < kJ / 2; ++a) {
+    d[2 + a] = make_double2(wu[a], wu[a + 4]);
+    d[2 + kJ / 2 + a] = make_double2(wv[2 * a], wv[2 * a + 1]);
+  }
+}
+
 template <typename T> __host__ __device__ inline size_t tile_patch_bytes(int TB) {
   const size_t PW = size_t(TB + kJ);
   return PW * (PW + 2) * sizeof(typename cplx_t<T>::type);
@@ -409,8 +434,15 @@ __global__ void __launch_bounds__(kThreads) k_degrid_w(Geometry g, const __grid_
         const int cell = *reinterpret_cast<const int*>(sj + 2 * kJ + 2);
         const T wa0 = sj[2 * k], wa1 = sj[2 * k + 1];
         T wv[kJ];
+        if constexpr (sizeof(T) == 4) {
+          const float4 w0 = *reinterpret_cast<const float4*>(sj + kJ);
+          const float4 w1 = *reinterpret_cast<const float4*>(sj + kJ + 4);
+          wv[0] = w0.x; wv[1] = w0.y; wv[2] = w0.z; wv[3] = w0.w;
+          wv[4] = w1.x; wv[5] = w1.y; wv[6] = w1.z; wv[7] = w1.w;
+        } else {
 #pragma unroll
-        for (int b = 0; b < kJ; ++b) wv[b] = sj[kJ + b];
+          for (int b = 0; b < kJ; ++b) wv[b] = sj[kJ + b];
+        }
         const C* r0 = patch + ((cell >> 8) + 2 * k) * PP + (cell & 255);
         const C* r1 = r0 + PP;
         T hx0 = 0, hy0 = 0, hx1 = 0, hy1 = 0;
@@ -539,12 +571,23 @@ __global__ void __launch_bounds__(kThreads) k_grid_w(Geometry g, const WorkItem*
 #pragma unroll
         for (int a = 0; a < kJ; ++a) wu[a] = wv[a] = T(0);
       }
-      stage_store(wst + lane * kStage, wu, wv, u.x, u.y, cu * 256 + cv);
+      stage_store_grid(wst + lane * kStage, wu, wv, u.x, u.y, cu * 256 + cv);
     }
     __syncwarp();
     for (int j = 0; j < nv; ++j) {
       const T* sj = wst + j * kStage;
-      const int cell = *reinterpret_cast<const int*>(sj + 2 * kJ + 2);
+      T ux, uy;
+      int cell;
+      if constexpr (sizeof(T) == 4) {
+        const float4 h = *reinterpret_cast<const float4*>(sj);
+        ux = h.x;
+        uy = h.y;
+        cell = __float_as_int(h.z);
+      } else {
+        ux = sj[0];
+        uy = sj[1];
+        cell = *reinterpret_cast<const int*>(sj + 2);
+      }
       if (cell != scell) {  // warp-uniform
         if (scell >= 0) {
           const int o = ((scell >> 8) + ta) * PW + (scell & 255) + tc;
@@ -554,9 +597,10 @@ __global__ void __launch_bounds__(kThreads) k_grid_w(Geometry g, const WorkItem*
         }
         scell = cell;
       }
-      const T wb = sj[kJ + tc];
-      const T a0 = sj[ta] * wb, a1 = sj[ta + 4] * wb;
-      const T ux = sj[2 * kJ], uy = sj[2 * kJ + 1];
+      typedef typename Pair2<T>::type T2;
+      const T wb = sj[4 + kJ + tc];
+      const T2 wa = *reinterpret_cast<const T2*>(sj + 4 + 2 * ta);  // (wu[ta], wu[ta + 4])
+      const T a0 = wa.x * wb, a1 = wa.y * wb;
       s0.x = fma(a0, ux, s0.x);
       s0.y = fma(a0, uy, s0.y);
       s1.x = fma(a1, ux, s1.x);
