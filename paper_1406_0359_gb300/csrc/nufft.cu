@@ -672,7 +672,92 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
   hist[int64_t(threadIdx.x) * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of a[0..L) in place by one 1024-thread block; total -> *total.
+// Exclusive scan of a[0..L) in place, three phases: per-chunk sums, a scan of
+// the chunk sums by one block, and per-chunk scans offset by their chunk's
+// prefix (all loads and stores coalesced).  total (if not null) receives the
+// sum of all L values.  Needs L <= kScanChunk * 1024.
+constexpr int kScanT = 256, kScanE = 16, kScanChunk = kScanT * kScanE;
+
+__device__ __forceinline__ int block_excl_scan_int(int v, int* sh /*[32]*/, int* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) sh[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int x = lane < nw ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += u;
+    }
+    sh[lane] = x;  // inclusive prefix of warp sums
+  }
+  __syncthreads();
+  const int before = w > 0 ? sh[w - 1] : 0;
+  if (total) *total = sh[nw - 1];
+  __syncthreads();
+  return before + incl - v;
+}
+
+__global__ void __launch_bounds__(kScanT) k_scan_reduce(const int* __restrict__ a, int64_t L, int* __restrict__ bsum) {
+  __shared__ int sh[32];
+  const int64_t base = int64_t(blockIdx.x) * kScanChunk;
+  int v = 0;
+#pragma unroll
+  for (int j = 0; j < kScanE; ++j) {
+    const int64_t i = base + threadIdx.x + int64_t(j) * kScanT;
+    if (i < L) v += a[i];
+  }
+  int tot = 0;
+  block_excl_scan_int(v, sh, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(int* __restrict__ bsum, int B, int* __restrict__ total) {
+  __shared__ int sh[32];
+  const int v = int(threadIdx.x) < B ? bsum[threadIdx.x] : 0;
+  int tot = 0;
+  const int ex = block_excl_scan_int(v, sh, &tot);
+  if (int(threadIdx.x) < B) bsum[threadIdx.x] = ex;
+  if (threadIdx.x == 0 && total) *total = tot;
+}
+
+__global__ void __launch_bounds__(kScanT) k_scan_down(int* __restrict__ a, int64_t L, const int* __restrict__ bsum) {
+  __shared__ int tile[kScanChunk + kScanChunk / 32];
+  __shared__ int sh[32];
+  auto pad = [](int e) { return e + (e >> 5); };
+  const int64_t base = int64_t(blockIdx.x) * kScanChunk;
+#pragma unroll
+  for (int j = 0; j < kScanE; ++j) {
+    const int e = threadIdx.x + j * kScanT;
+    tile[pad(e)] = base + e < L ? a[base + e] : 0;
+  }
+  __syncthreads();
+  int loc[kScanE];
+  int run = 0;
+#pragma unroll
+  for (int k = 0; k < kScanE; ++k) {
+    loc[k] = run;
+    run += tile[pad(threadIdx.x * kScanE + k)];
+  }
+  const int off = block_excl_scan_int(run, sh, nullptr) + bsum[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanE; ++k) tile[pad(threadIdx.x * kScanE + k)] = loc[k] + off;
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kScanE; ++j) {
+    const int e = threadIdx.x + j * kScanT;
+    if (base + e < L) a[base + e] = tile[pad(e)];
+  }
+}
+
+// Exclusive scan of a[0..L) in place by one 1024-thread block (fallback for
+// L beyond the three-phase limit); total -> *total.
 __global__ void __launch_bounds__(1024) k_scan(int* __restrict__ a, int64_t L, int* __restrict__ total) {
   __shared__ int sums[1024];
   const int64_t per = (L + 1023) / 1024;
@@ -695,6 +780,18 @@ __global__ void __launch_bounds__(1024) k_scan(int* __restrict__ a, int64_t L, i
     run += v;
   }
   if (threadIdx.x == 1023 && total) *total = sums[1023];
+}
+
+// bsum: scratch of at least 1024 ints.
+inline void launch_scan(int* a, int64_t L, int* total, int* bsum, cudaStream_t s) {
+  const int64_t B = (L + kScanChunk - 1) / kScanChunk;
+  if (B <= 1024) {
+    k_scan_reduce<<<int(B > 0 ? B : 1), kScanT, 0, s>>>(a, L, bsum);
+    k_scan_top<<<1, 1024, 0, s>>>(bsum, int(B > 0 ? B : 1), total);
+    k_scan_down<<<int(B > 0 ? B : 1), kScanT, 0, s>>>(a, L, bsum);
+  } else {
+    k_scan<<<1, 1024, 0, s>>>(a, L, total);
+  }
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* __restrict__ kin,
@@ -890,6 +987,7 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
   const int nblocks = int((M + kSortTile - 1) / kSortTile);
   uint32_t *k0 = nullptr, *k1 = nullptr;
   int *v1 = nullptr, *hist = nullptr, *tstart = nullptr, *tend = nullptr, *cnt = nullptr, *total = nullptr;
+  int* bsum = nullptr;
   WorkItem* items = nullptr;
   int rc = 0;
   int h_total = 0;
@@ -904,6 +1002,7 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
   fail(cudaMalloc(&tend, size_t(ntiles) * sizeof(int)));
   fail(cudaMalloc(&cnt, size_t(ntiles) * sizeof(int)));
   fail(cudaMalloc(&total, sizeof(int)));
+  fail(cudaMalloc(&bsum, 1024 * sizeof(int)));
   if (rc == 0) {
     const int tb = 256;
     k_bin_keys<<<int((M + tb - 1) / tb), tb, 0, s>>>(uv, R > 1 ? blocks : nullptr, M, g.K, g.TB, lb, g.ntile1d,
@@ -914,7 +1013,7 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
     int* vout = v1;
     for (int p = 0; p < passes; ++p) {
       k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(kin, M, 8 * p, nblocks, hist);
-      k_scan<<<1, 1024, 0, s>>>(hist, int64_t(256) * nblocks, nullptr);
+      launch_scan(hist, int64_t(256) * nblocks, nullptr, bsum, s);
       k_radix_scatter<<<nblocks, kSortThreads, 0, s>>>(kin, vin, M, 8 * p, nblocks, hist, kout, vout);
       std::swap(kin, kout);
       std::swap(vin, vout);
@@ -926,7 +1025,7 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
     // two this equals block * tiles_per_block + tile
     k_tile_bounds<<<int((M + tb - 1) / tb), tb, 0, s>>>(kin, M, 2 * lb, tstart, tend);
     k_chunk_counts<<<(ntiles + tb - 1) / tb, tb, 0, s>>>(tstart, tend, ntiles, chunk, cnt);
-    k_scan<<<1, 1024, 0, s>>>(cnt, ntiles, total);
+    launch_scan(cnt, ntiles, total, bsum, s);
     fail(cudaMemcpyAsync(&h_total, total, sizeof(int), cudaMemcpyDeviceToHost, s));
     fail(cudaStreamSynchronize(s));
     fail(cudaGetLastError());
@@ -954,6 +1053,7 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
   cudaFree(k1);
   cudaFree(v1);
   cudaFree(hist);
+  cudaFree(bsum);
   cudaFree(tstart);
   cudaFree(tend);
   cudaFree(cnt);
