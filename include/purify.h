@@ -74,7 +74,7 @@ int purify_op_create(const double* uv, int64_t M, int n, int oversample, int J,
 
 /* Work decomposition of the gridding kernels (0 = default). */
 typedef struct {
-  int tile;   /* uv tile side in grid cells: 8 or 16 (default) */
+  int tile;   /* uv tile side in grid cells: 8 (default) or 16 */
   int chunk;  /* visibilities per work item, 64..8192 (default 1024) */
 } purify_op_options;
 
@@ -86,7 +86,8 @@ int purify_op_create_ex(const double* uv, int64_t M, int n, int oversample, int 
  * purify_autotune -- time Phi + Phi^H as the solver applies them (visibilities
  * in the operator's sorted order; `reps` pairs after one warm-up) for every
  * tile in {8, 16} and chunk in {256, 512, 1024, 2048} on this uv coverage and
- * return the fastest options (and their time per pair in ms).
+ * return the fastest options (and their time per pair in ms); candidates
+ * within 2% of the fastest count as ties, won by the largest chunk.
  * Builds and frees one operator per candidate; synchronises `stream`.
  */
 int purify_autotune(const double* uv, int64_t M, int n, int dwt_levels, int precision, int reps,

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <mutex>
 #include <initializer_list>
 #include <new>
 #include <vector>
@@ -66,6 +67,59 @@ int map_err(cudaError_t e, int line = 0) {
     cudaError_t e_ = (call);                              \
     if (e_ != cudaSuccess) return map_err(e_, __LINE__);  \
   } while (0)
+
+// Kernel attributes (dynamic shared-memory limits) are per device, so they
+// are set once per device and precision, not per operator.
+template <typename T> cudaError_t configure_once() {
+  static std::mutex mu;
+  static uint64_t done = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
+  if (bit && (done & bit)) return cudaSuccess;
+  e = configure_fft<T>();
+  if (e == cudaSuccess) e = configure_nufft<T>();
+  if (e == cudaSuccess) e = configure_sara<T>();
+  if (e == cudaSuccess) done |= bit;
+  return e;
+}
+
+// Pinned host mirrors of the device scalars (kNumScalars doubles each, for the
+// asynchronous copies of the resumable solver), carved from 64 KB pinned
+// pages: creating an operator does not pay a pinned allocation.
+class PinnedSlots {
+ public:
+  static constexpr size_t kSlot = 16;  // doubles per slot (>= kNumScalars)
+  double* get() {
+    std::lock_guard<std::mutex> lk(mu_);
+    if (free_.empty()) {
+      void* page = nullptr;
+      if (cudaMallocHost(&page, 65536) != cudaSuccess) return nullptr;
+      pages_.push_back(page);
+      for (size_t k = 0; k < 65536 / (kSlot * sizeof(double)); ++k)
+        free_.push_back(static_cast<double*>(page) + k * kSlot);
+    }
+    double* p = free_.back();
+    free_.pop_back();
+    return p;
+  }
+  void put(double* p) {
+    std::lock_guard<std::mutex> lk(mu_);
+    free_.push_back(p);
+  }
+
+ private:
+  std::mutex mu_;
+  std::vector<void*> pages_;  // kept for the life of the process
+  std::vector<double*> free_;
+};
+static_assert(PinnedSlots::kSlot >= size_t(kNumScalars), "slot holds the scalars");
+PinnedSlots& pinned_slots() {
+  static PinnedSlots* p = new PinnedSlots();
+  return *p;
+}
 
 template <typename T> class OpImpl : public purify_op {
   typedef typename cplx_t<T>::type C;
@@ -179,7 +233,7 @@ template <typename T> class OpImpl : public purify_op {
     if (ev_join) cudaEventDestroy(ev_join);
     if (own) cudaStreamDestroy(own);
     if (aux) cudaStreamDestroy(aux);
-    if (h_sc) cudaFreeHost(h_sc);
+    if (h_sc) pinned_slots().put(h_sc);
   }
 
   template <typename U> int alloc(U** ptr, size_t count) {
@@ -217,12 +271,17 @@ template <typename T> class OpImpl : public purify_op {
   }
   size_t grid_bytes() const { return size_t(g.KP) * g.KP * sizeof(C); }
 
-  int create(const double* uv, int64_t M, int n, int L, cudaStream_t s, int tile = 0, int chunk_opt = 0) {
+  // light: gridding-only operator (Phi^H; no forward grid, no uv copy), as
+  // the PSF set-up of the convolution form needs.
+  bool light = false;
+  int create(const double* uv, int64_t M, int n, int L, cudaStream_t s, int tile = 0, int chunk_opt = 0,
+             bool light_only = false) {
+    light = light_only;
     g.n = n;
     g.K = 2 * n;
     g.KP = g.K + kJ;
     g.pad_lo = kJ / 2 - 1;
-    g.TB = tile > 0 ? tile : 16;
+    g.TB = tile > 0 ? tile : 8;
     if (g.TB > g.K) g.TB = g.K;
     g.ntile1d = g.K / g.TB;
     g.M = M;
@@ -234,9 +293,7 @@ template <typename T> class OpImpl : public purify_op {
     CK(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
-    CK(configure_fft<T>());
-    CK(configure_nufft<T>());
-    CK(configure_sara<T>());
+    CK(configure_once<T>());
     // tables: deapodisation, twiddles, kernel polynomial, filters (host, double)
     const double beta = kb_beta(kJ, 2.0);
     std::vector<T> hs(n);
@@ -265,26 +322,29 @@ template <typename T> class OpImpl : public purify_op {
     if ((rc = alloc(&deapod, n))) return rc;
     if ((rc = alloc(&tw, g.K))) return rc;
     if ((rc = alloc(&pos, M))) return rc;
-    if ((rc = alloc(&uv_keep, 2 * size_t(M)))) return rc;
-    CK(cudaMemcpyAsync(uv_keep, uv, 2 * size_t(M) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (!light) {
+      if ((rc = alloc(&uv_keep, 2 * size_t(M)))) return rc;
+      CK(cudaMemcpyAsync(uv_keep, uv, 2 * size_t(M) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
     if ((rc = alloc(&perm, M))) return rc;
     if ((rc = alloc(&gridA, size_t(n) * g.K))) return rc;
-    if ((rc = alloc(&gridP, size_t(g.KP) * g.KP))) return rc;
+    if (!light && (rc = alloc(&gridP, size_t(g.KP) * g.KP))) return rc;
     if ((rc = alloc(&gridQ, size_t(g.KP) * g.KP))) return rc;
     if ((rc = alloc(&sc, kNumScalars))) return rc;
     if ((rc = alloc(&err, 1))) return rc;
     sara.n = n;
     sara.levels = L;
     sara_select(sara, kSaraAll);
-    if ((rc = alloc(&sara.s0, 8 * N() / 4))) return rc;
-    if ((rc = alloc(&sara.s1, 8 * N() / 4))) return rc;
-    if ((rc = alloc(&sara.cs, 9 * N()))) return rc;
-    CK(cudaMallocHost(&h_sc, kNumScalars * sizeof(double)));
+    h_sc = pinned_slots().get();
+    if (!h_sc) {
+      note_error("pinned host memory", __LINE__, "no pinned slot for the device scalars");
+      return PURIFY_ERR_NOMEM;
+    }
     CK(cudaMemcpyAsync(deapod, hs.data(), n * sizeof(T), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(tw, htw.data(), g.K * sizeof(C), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(err, 0, sizeof(int), s));
     CK(cudaMemsetAsync(sc, 0, kNumScalars * sizeof(double), s));
-    CK(cudaMemsetAsync(gridP, 0, grid_bytes(), s));
+    if (!light) CK(cudaMemsetAsync(gridP, 0, grid_bytes(), s));
     rc = build_bins<T>(uv, M, g, chunk, pos, perm, &items, &n_items, s);
     if (rc) {
       note_error("uv binning failed", __LINE__, cudaGetErrorName(cudaGetLastError()));
@@ -296,6 +356,7 @@ template <typename T> class OpImpl : public purify_op {
     if ((rc = alloc(&cg_part, 5 * kCgPart))) return rc;
     if ((rc = alloc(&tickets, 4))) return rc;
     CK(cudaMemsetAsync(tickets, 0, 4 * sizeof(unsigned int), s));
+    if (light) return check(s, true);
     // TMA descriptor of the padded forward grid, 8-byte elements
     EncodeTiledFn enc = encode_fn();
     if (!enc) {
@@ -381,14 +442,15 @@ template <typename T> class OpImpl : public purify_op {
     if ((rc = alloc(&khat_l, size_t(g.K / 2 + 1) * g.K))) return rc;
     {
       OpImpl<T> big;
-      rc = big.create(uv_keep, g.M, 2 * g.n, 1, s);
+      rc = big.create(uv_keep, g.M, 2 * g.n, 1, s, 0, 0, true);
       if (rc) return rc;
       C* y1 = nullptr;
       T* psf = nullptr;
       C* X = nullptr;
-      cudaError_t e = cudaMalloc(&y1, size_t(g.M) * sizeof(C));
-      if (e == cudaSuccess) e = cudaMalloc(&psf, size_t(g.K) * g.K * sizeof(T));
-      if (e == cudaSuccess) e = cudaMalloc(&X, size_t(g.K) * g.K * sizeof(C));
+      // temporaries from the stream-ordered pool
+      cudaError_t e = cudaMallocAsync(&y1, size_t(g.M) * sizeof(C), s);
+      if (e == cudaSuccess) e = cudaMallocAsync(&psf, size_t(g.K) * g.K * sizeof(T), s);
+      if (e == cudaSuccess) e = cudaMallocAsync(&X, size_t(g.K) * g.K * sizeof(C), s);
       if (e == cudaSuccess) {
         C one;
         one.x = T(1);
@@ -396,13 +458,10 @@ template <typename T> class OpImpl : public purify_op {
         launch_fill<C>(y1, size_t(g.M), one, s);
       }
       if (e == cudaSuccess) rc = big.phi_adj(y1, psf, s);
-      if (e == cudaSuccess && rc == 0) {
-        build_psf_spectrum<T>(psf, g.n, khat_l, X, tw, s);
-        e = cudaStreamSynchronize(s);
-      }
-      cudaFree(y1);
-      cudaFree(psf);
-      cudaFree(X);
+      if (e == cudaSuccess && rc == 0) build_psf_spectrum<T>(psf, g.n, khat_l, X, tw, s);
+      for (void* t : {static_cast<void*>(y1), static_cast<void*>(psf), static_cast<void*>(X)})
+        if (t) cudaFreeAsync(t, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) return map_err(e, __LINE__);
       if (rc) return rc;
     }
@@ -482,11 +541,23 @@ template <typename T> class OpImpl : public purify_op {
     return check(s, false);
   }
 
+  // SARA scratch (bands and prox output), allocated on first use: an operator
+  // used only for Phi / Phi^H (e.g. the PSF set-up) never needs it.
+  int ensure_sara() {
+    if (sara.cs) return PURIFY_OK;
+    int rc;
+    if ((rc = alloc(&sara.s0, 8 * N() / 4)) || (rc = alloc(&sara.s1, 8 * N() / 4)) || (rc = alloc(&sara.cs, 9 * N())))
+      return rc;
+    return PURIFY_OK;
+  }
+
   int sara_fwd(const void* x, void* c, cudaStream_t s) override {
+    if (const int rc = ensure_sara()) return rc;
     PROF(KK_SARA_ANA, s, sara_analysis<T>(sara, static_cast<const T*>(x), static_cast<T*>(c), s));
     return check(s, false);
   }
   int sara_adj(const void* c, void* x, cudaStream_t s) override {
+    if (const int rc = ensure_sara()) return rc;
     PROF(KK_SARA_SYN, s, sara_synthesis<T>(sara, static_cast<const T*>(c), static_cast<T*>(x), s));
     return check(s, false);
   }
@@ -495,6 +566,7 @@ template <typename T> class OpImpl : public purify_op {
   int ensure_solver() {
     if (xh) return PURIFY_OK;
     int rc;
+    if ((rc = ensure_sara())) return rc;
     const size_t n2 = N();
     if ((rc = alloc(&xh, n2)) || (rc = alloc(&xs, n2)) || (rc = alloc(&r, n2)) || (rc = alloc(&p, n2)) ||
         (rc = alloc(&Ap, n2)) || (rc = alloc(&z1, 9 * n2)) || (rc = alloc(&z2, n2)) || (rc = alloc(&w, 9 * n2)) ||
@@ -997,6 +1069,8 @@ int purify_autotune(const double* uv, int64_t M, int n, int dwt_levels, int prec
   int rc = e == cudaSuccess ? PURIFY_OK : PURIFY_ERR_CUDA;
   double best_t = 1e300;
   purify_op_options bo{16, 1024};
+  struct Timed { purify_op_options o; double ms; };
+  std::vector<Timed> times;
   const int tiles[2] = {8, 16};
   const int chunks[4] = {256, 512, 1024, 2048};
   for (int ti = 0; ti < 2 && !rc; ++ti) {
@@ -1015,12 +1089,8 @@ int purify_autotune(const double* uv, int64_t M, int n, int dwt_levels, int prec
       for (int k = 0; k < reps && !r; ++k) r = op->sorted_pair(x, y, x, s);
       cudaEventRecord(e1, s);
       float ms = 0.f;
-      if (!r && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
-        if (ms / reps < best_t) {
-          best_t = ms / reps;
-          bo = o;
-        }
-      }
+      if (!r && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+        times.push_back({o, double(ms) / reps});
       delete op;
       if (r) rc = r;
     }
@@ -1030,6 +1100,18 @@ int purify_autotune(const double* uv, int64_t M, int n, int dwt_levels, int prec
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (rc) return rc;
+  // fastest pair; among candidates within 2% of it (timing noise), the one
+  // with the largest chunk (fewer work items, fewer flushes and atomics)
+  const Timed* pick = nullptr;
+  for (const Timed& c : times)
+    if (!pick || c.ms < pick->ms) pick = &c;
+  if (pick) {
+    const double lim = 1.02 * pick->ms;
+    for (const Timed& c : times)
+      if (c.ms <= lim && (c.o.chunk > pick->o.chunk || (c.o.chunk == pick->o.chunk && c.ms < pick->ms))) pick = &c;
+    bo = pick->o;
+    best_t = pick->ms;
+  }
   *best = bo;
   if (best_ms) *best_ms = best_t;
   return PURIFY_OK;

@@ -21,6 +21,8 @@
 #include <cstring>
 #include <vector>
 
+#include <initializer_list>
+
 #include "internal.h"
 
 namespace purify {
@@ -994,15 +996,17 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
   auto fail = [&](cudaError_t e) {
     if (e != cudaSuccess && rc == 0) rc = (e == cudaErrorMemoryAllocation) ? -2 : -3;
   };
-  fail(cudaMalloc(&k0, M * sizeof(uint32_t)));
-  fail(cudaMalloc(&k1, M * sizeof(uint32_t)));
-  fail(cudaMalloc(&v1, M * sizeof(int)));
-  fail(cudaMalloc(&hist, size_t(256) * nblocks * sizeof(int)));
-  fail(cudaMalloc(&tstart, size_t(ntiles) * sizeof(int)));
-  fail(cudaMalloc(&tend, size_t(ntiles) * sizeof(int)));
-  fail(cudaMalloc(&cnt, size_t(ntiles) * sizeof(int)));
-  fail(cudaMalloc(&total, sizeof(int)));
-  fail(cudaMalloc(&bsum, 1024 * sizeof(int)));
+  // temporaries from the stream-ordered pool (no device-wide synchronisation
+  // on release, reused across operator creations)
+  fail(cudaMallocAsync(&k0, M * sizeof(uint32_t), s));
+  fail(cudaMallocAsync(&k1, M * sizeof(uint32_t), s));
+  fail(cudaMallocAsync(&v1, M * sizeof(int), s));
+  fail(cudaMallocAsync(&hist, size_t(256) * nblocks * sizeof(int), s));
+  fail(cudaMallocAsync(&tstart, size_t(ntiles) * sizeof(int), s));
+  fail(cudaMallocAsync(&tend, size_t(ntiles) * sizeof(int), s));
+  fail(cudaMallocAsync(&cnt, size_t(ntiles) * sizeof(int), s));
+  fail(cudaMallocAsync(&total, sizeof(int), s));
+  fail(cudaMallocAsync(&bsum, 1024 * sizeof(int), s));
   if (rc == 0) {
     const int tb = 256;
     k_bin_keys<<<int((M + tb - 1) / tb), tb, 0, s>>>(uv, R > 1 ? blocks : nullptr, M, g.K, g.TB, lb, g.ntile1d,
@@ -1040,24 +1044,21 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
       fail(cudaGetLastError());
       // largest items first (stable): whole-warp items then finish together
       if (rc == 0 && h_total > 1) {
-        std::vector<WorkItem> h(h_total);
+        std::vector<WorkItem> h(h_total), o(h_total);
         fail(cudaMemcpy(h.data(), items, h.size() * sizeof(WorkItem), cudaMemcpyDeviceToHost));
-        std::stable_sort(h.begin(), h.end(), [](const WorkItem& a, const WorkItem& b) {
-          return (a.end - a.begin) > (b.end - b.begin);
-        });
-        fail(cudaMemcpy(items, h.data(), h.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+        // stable counting sort by length, longest first (lengths <= chunk)
+        std::vector<int> first(size_t(chunk) + 2, 0);
+        for (const WorkItem& w : h) first[size_t(chunk - (w.end - w.begin)) + 1] += 1;
+        for (size_t k = 1; k < first.size(); ++k) first[k] += first[k - 1];
+        for (const WorkItem& w : h) o[size_t(first[size_t(chunk - (w.end - w.begin))]++)] = w;
+        fail(cudaMemcpy(items, o.data(), o.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
       }
     }
   }
-  cudaFree(k0);
-  cudaFree(k1);
-  cudaFree(v1);
-  cudaFree(hist);
-  cudaFree(bsum);
-  cudaFree(tstart);
-  cudaFree(tend);
-  cudaFree(cnt);
-  cudaFree(total);
+  for (void* t : {static_cast<void*>(k0), static_cast<void*>(k1), static_cast<void*>(v1), static_cast<void*>(hist),
+                  static_cast<void*>(bsum), static_cast<void*>(tstart), static_cast<void*>(tend),
+                  static_cast<void*>(cnt), static_cast<void*>(total)})
+    if (t) cudaFreeAsync(t, s);
   if (rc != 0) {
     cudaFree(items);
     return rc;
