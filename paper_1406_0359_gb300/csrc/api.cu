@@ -274,9 +274,12 @@ template <typename T> class OpImpl : public purify_op {
   // light: gridding-only operator (Phi^H; no forward grid, no uv copy), as
   // the PSF set-up of the convolution form needs.
   bool light = false;
+  // refine: light operator on the grid of twice the resolution of `refine`
+  // (tile 8 there, 16 here), reusing its binning (items, order) instead of
+  // sorting the visibilities again.
   int create(const double* uv, int64_t M, int n, int L, cudaStream_t s, int tile = 0, int chunk_opt = 0,
-             bool light_only = false) {
-    light = light_only;
+             bool light_only = false, const OpImpl* refine = nullptr) {
+    light = light_only || refine;
     g.n = n;
     g.K = 2 * n;
     g.KP = g.K + kJ;
@@ -326,7 +329,7 @@ template <typename T> class OpImpl : public purify_op {
       if ((rc = alloc(&uv_keep, 2 * size_t(M)))) return rc;
       CK(cudaMemcpyAsync(uv_keep, uv, 2 * size_t(M) * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
-    if ((rc = alloc(&perm, M))) return rc;
+    if (!refine && (rc = alloc(&perm, M))) return rc;
     if ((rc = alloc(&gridA, size_t(n) * g.K))) return rc;
     if (!light && (rc = alloc(&gridP, size_t(g.KP) * g.KP))) return rc;
     if ((rc = alloc(&gridQ, size_t(g.KP) * g.KP))) return rc;
@@ -345,7 +348,14 @@ template <typename T> class OpImpl : public purify_op {
     CK(cudaMemsetAsync(err, 0, sizeof(int), s));
     CK(cudaMemsetAsync(sc, 0, kNumScalars * sizeof(double), s));
     if (!light) CK(cudaMemsetAsync(gridP, 0, grid_bytes(), s));
-    rc = build_bins<T>(uv, M, g, chunk, pos, perm, &items, &n_items, s);
+    if (refine) {
+      n_items = refine->n_items;
+      CK(cudaMalloc(&items, size_t(n_items > 0 ? n_items : 1) * sizeof(WorkItem)));
+      CK(cudaMemcpyAsync(items, refine->items, size_t(n_items) * sizeof(WorkItem), cudaMemcpyDeviceToDevice, s));
+      launch_encode_x2<T>(refine->uv_keep, refine->perm, M, refine->g.K, g.TB, pos, s);
+    } else {
+      rc = build_bins<T>(uv, M, g, chunk, pos, perm, &items, &n_items, s);
+    }
     if (rc) {
       note_error("uv binning failed", __LINE__, cudaGetErrorName(cudaGetLastError()));
       return rc;
@@ -442,7 +452,9 @@ template <typename T> class OpImpl : public purify_op {
     if ((rc = alloc(&khat_l, size_t(g.K / 2 + 1) * g.K))) return rc;
     {
       OpImpl<T> big;
-      rc = big.create(uv_keep, g.M, 2 * g.n, 1, s, 0, 0, true);
+      const bool reuse = g.TB == 8;  // this binning serves the 2n operator (tiles 16 on its grid)
+      rc = reuse ? big.create(uv_keep, g.M, 2 * g.n, 1, s, 16, chunk, true, this)
+                 : big.create(uv_keep, g.M, 2 * g.n, 1, s, 0, 0, true);
       if (rc) return rc;
       C* y1 = nullptr;
       T* psf = nullptr;
@@ -457,7 +469,7 @@ template <typename T> class OpImpl : public purify_op {
         one.y = T(0);
         launch_fill<C>(y1, size_t(g.M), one, s);
       }
-      if (e == cudaSuccess) rc = big.phi_adj(y1, psf, s);
+      if (e == cudaSuccess) rc = big.adjoint_sorted(y1, psf, s);
       if (e == cudaSuccess && rc == 0) build_psf_spectrum<T>(psf, g.n, khat_l, X, tw, s);
       for (void* t : {static_cast<void*>(y1), static_cast<void*>(psf), static_cast<void*>(X)})
         if (t) cudaFreeAsync(t, s);
@@ -537,6 +549,21 @@ template <typename T> class OpImpl : public purify_op {
     RowEp<T> ep{};
     ep.mode = EP_STORE;
     ep.out = static_cast<T*>(x);
+    row_ep(ep, s);
+    return check(s, false);
+  }
+
+  // Re Phi^H y for y in the operator's sorted visibility order.
+  int adjoint_sorted(const C* y, T* x, cudaStream_t s) {
+    zero_q(s);
+    GridPro<C> pro{};
+    pro.mode = GP_SORTED;
+    pro.y = y;
+    grid(pro, s);
+    col_inv(s);
+    RowEp<T> ep{};
+    ep.mode = EP_STORE;
+    ep.out = x;
     row_ep(ep, s);
     return check(s, false);
   }

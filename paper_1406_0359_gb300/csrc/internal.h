@@ -193,6 +193,10 @@ void launch_gram(const Geometry& g, const CUtensorMap& map, const WorkItem* item
 // With R > 1 visibility blocks (device int32 block index per visibility, in
 // caller order), visibilities are binned by (block, tile, cell) and every work
 // item lies in one block (its `pad` field).
+// Positions for the grid of twice the resolution of a binning of the Kc grid
+// (fine tiles TB = 2 x the coarse tiles): the coarse items and order serve.
+template <typename T>
+void launch_encode_x2(const double* uv, const int* perm, int64_t M, int Kc, int TB, Pos<T>* pos, cudaStream_t s);
 template <typename T>
 int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>* pos, int* perm,
                WorkItem** items_out, int* n_items_out, cudaStream_t s, const int* blocks = nullptr, int R = 1);

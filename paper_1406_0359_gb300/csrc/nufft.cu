@@ -918,6 +918,44 @@ __global__ void k_encode<double>(const double* __restrict__ uv, const int* __res
   pos[i] = p;
 }
 
+// Positions on the grid of twice the resolution (K = 2 Kc) from the cells of
+// the Kc grid: t = 2 (cell_c + f_c) exactly, so that tile (cell / TB) of the
+// fine grid equals tile (cell_c / (TB/2)) of the coarse one and the coarse
+// binning's items and order serve the fine grid unchanged.
+template <typename T>
+__global__ void k_encode_x2(const double* __restrict__ uv, const int* __restrict__ perm, int64_t M, int Kc, int TB,
+                            Pos<T>* __restrict__ pos) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const int64_t m = perm[i];
+  int cell[2];
+  double fr[2];
+  for (int a = 0; a < 2; ++a) {
+    int cc;
+    double fc;
+    grid_cell(uv[2 * m + a], Kc, cc, fc);
+    const double t2 = 2.0 * fc;  // exact
+    const double up = t2 >= 1.0 ? 1.0 : 0.0;
+    cell[a] = (2 * cc + int(up)) % TB;
+    fr[a] = t2 - up;
+  }
+  Pos<T> p;
+  if constexpr (sizeof(T) == 4) {
+    uint32_t e[2];
+    for (int a = 0; a < 2; ++a) {
+      uint32_t q = uint32_t(fr[a] * 16777216.0);
+      if (q > 0xFFFFFFu) q = 0xFFFFFFu;
+      e[a] = (uint32_t(cell[a]) << 24) | q;
+    }
+    p.u = e[0];
+    p.v = e[1];
+  } else {
+    p.u = fmin(double(cell[0]) + fr[0], nextafter(double(cell[0] + 1), 0.0));
+    p.v = fmin(double(cell[1]) + fr[1], nextafter(double(cell[1] + 1), 0.0));
+  }
+  pos[i] = p;
+}
+
 }  // namespace
 
 template <typename T> cudaError_t configure_nufft() {
@@ -971,6 +1009,12 @@ void launch_gram(const Geometry& g, const CUtensorMap& map, const WorkItem* item
   DegridEp<typename cplx_t<T>::type> ep{};
   GridPro<typename cplx_t<T>::type> gp{};
   k_tile<T, TM_GRAM><<<n_items, kThreads, sm, s>>>(g, map, items, pos, nullptr, kb, ep, gp, Q, err);
+}
+
+template <typename T>
+void launch_encode_x2(const double* uv, const int* perm, int64_t M, int Kc, int TB, Pos<T>* pos, cudaStream_t s) {
+  const int tb = 256;
+  k_encode_x2<T><<<int((M + tb - 1) / tb), tb, 0, s>>>(uv, perm, M, Kc, TB, pos);
 }
 
 template <typename T>
@@ -1077,6 +1121,7 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
                                cudaStream_t);                                                                  \
   template void launch_gram<T>(const Geometry&, const CUtensorMap&, const WorkItem*, int, const Pos<T>*,        \
                                const KbPoly<T>&, cplx_t<T>::type*, int*, cudaStream_t);                         \
+  template void launch_encode_x2<T>(const double*, const int*, int64_t, int, int, Pos<T>*, cudaStream_t);     \
   template int build_bins<T>(const double*, int64_t, const Geometry&, int, Pos<T>*, int*, WorkItem**, int*,     \
                              cudaStream_t, const int*, int);
 INST(float)
