@@ -134,10 +134,11 @@ def algorithmic_bytes(kind: str, n: int, M: int, rsize: int = 4) -> float:
         "gram": 4 * N * c * 2 + 8 * M,          # read grid, write grid accumulator, read positions
         "degrid": 4 * N * c + 8 * M + 3 * c * M,  # grid + positions + (z read, y read, z write)
         "grid": 4 * N * c + 8 * M + 3 * c * M,    # grid write + positions + (z, y read, z write)
-        "row_fwd": N * rsize + 2 * N * c,         # image in, n x 2n compact rows out
-        "col_fwd": 2 * N * c + 4 * N * c,         # compact rows in, full grid out
-        "col_inv": 4 * N * c + 2 * N * c,
-        "row_inv": 2 * N * c + 2 * N * rsize,
+        # Phi / Phi^H in real form: half-spectrum rows n x n complex
+        "row_fwd": N * rsize + N * c,             # image in, half-spectrum rows out
+        "col_fwd": N * c + 4 * N * c,             # half-spectrum rows in, full grid out
+        "col_inv": 4 * N * c + N * c,             # accumulator in, half-spectrum rows out
+        "row_inv": N * c + 2 * N * rsize,         # half-spectrum rows in, image in/out (epilogue)
         # convolution form (real image, half spectra n x n complex)
         "row_fwd_h": 3 * N * rsize + N * c,       # r, p in, p out (CG direction), half-spectrum rows out
         "col_conv": N * c + 2 * N * rsize + N * c,  # half-spectrum rows in, PSF half spectrum, rows out

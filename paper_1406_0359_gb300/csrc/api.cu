@@ -330,7 +330,7 @@ template <typename T> class OpImpl : public purify_op {
       CK(cudaMemcpyAsync(uv_keep, uv, 2 * size_t(M) * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
     if (!refine && (rc = alloc(&perm, M))) return rc;
-    if ((rc = alloc(&gridA, size_t(n) * g.K))) return rc;
+    if ((rc = alloc(&gridA, size_t(n) * (g.K / 2)))) return rc;  // half-spectrum rows
     if (!light && (rc = alloc(&gridP, size_t(g.KP) * g.KP))) return rc;
     if ((rc = alloc(&gridQ, size_t(g.KP) * g.KP))) return rc;
     if ((rc = alloc(&sc, kNumScalars))) return rc;
@@ -403,12 +403,16 @@ template <typename T> class OpImpl : public purify_op {
   }
 
   // ---- operator building blocks (enqueue only)
+  // F Z S in real form (the image is real): row pairs to half spectra, then
+  // the half-spectrum columns to the full padded grid with their mirrors.
   void fwd_grid(const RowPro<T>& pro, cudaStream_t s) {
-    PROF(KK_ROW_FWD, s, launch_row_fwd<T>(g, pro, deapod, gridA, tw, s));
-    PROF(KK_COL_FWD, s, launch_col_fwd<T>(g, gridA, gridP, tw, s));
+    PROF(KK_ROW_FWD, s, launch_row_fwd_h<T>(g, pro, deapod, gridA, tw, s));
+    PROF(KK_COL_FWD, s, launch_col_fwd_h<T>(g, gridA, gridP, tw, s));
   }
   void zero_q(cudaStream_t s) { PROF(KK_MEMSET, s, cudaMemsetAsync(gridQ, 0, grid_bytes(), s)); }
-  void col_inv(cudaStream_t s) { PROF(KK_COL_INV, s, launch_col_inv<T>(g, gridQ, gridA, tw, s)); }
+  // Re F^H of the gridded accumulator: the half-spectrum columns of its
+  // Hermitian part (the row pass follows in row_ep / normal_back).
+  void col_inv(cudaStream_t s) { PROF(KK_COL_INV, s, launch_col_inv_h<T>(g, gridQ, gridA, tw, s)); }
   void degrid(const DegridEp<C>& ep, cudaStream_t s) {
     PROF(KK_DEGRID, s, launch_degrid<T>(g, tmap, items, n_items, pos, perm, kb, ep, err, s));
   }
@@ -431,9 +435,11 @@ template <typename T> class OpImpl : public purify_op {
     PROF(KK_GRAM, s, launch_gram<T>(g, tmap, items, n_items, pos, kb, gridQ, err, s));
     col_inv(s);
   }
-  int row_ep(const RowEp<T>& ep, cudaStream_t s) {
+  int row_ep(const RowEp<T>& ep_in, cudaStream_t s) {
+    RowEp<T> ep = ep_in;
+    if (!ep.err) ep.err = err;
     int np = 0;
-    PROF(KK_ROW_INV, s, np = launch_row_inv<T>(g, gridA, deapod, ep, tw, s));
+    PROF(KK_ROW_INV, s, np = launch_row_inv_h<T>(g, gridA, deapod, ep, tw, s));
     return np;
   }
 
@@ -485,7 +491,7 @@ template <typename T> class OpImpl : public purify_op {
   // NUFFT (G^H G per application) or by the precomputed convolution.
   void normal_front(const RowPro<T>& pro, cudaStream_t s) {
     if (toep) {
-      PROF(KK_ROW_FWD_H, s, launch_row_fwd_h<T>(g, pro, gridA, tw, s));
+      PROF(KK_ROW_FWD_H, s, launch_row_fwd_h<T>(g, pro, nullptr, gridA, tw, s));
       PROF(KK_COL_CONV, s, launch_col_conv_h<T>(g, gridA, khat, tw, s));
     } else {
       gram_front(pro, s);
@@ -495,8 +501,8 @@ template <typename T> class OpImpl : public purify_op {
     RowEp<T> ep = ep_in;
     if (!ep.err) ep.err = err;
     int np = 0;
-    if (toep) PROF(KK_ROW_INV_H, s, np = launch_row_inv_h<T>(g, gridA, ep, tw, s));
-    else PROF(KK_ROW_INV, s, np = launch_row_inv<T>(g, gridA, deapod, ep, tw, s));
+    if (toep) PROF(KK_ROW_INV_H, s, np = launch_row_inv_h<T>(g, gridA, nullptr, ep, tw, s));
+    else PROF(KK_ROW_INV, s, np = launch_row_inv_h<T>(g, gridA, deapod, ep, tw, s));
     return np;
   }
 

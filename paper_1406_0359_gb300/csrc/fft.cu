@@ -1,22 +1,27 @@
 // Oversampled 2D FFT passes of the NUFFT (operator F of Phi = G F Z S, Section 4).
 //
 // Each length-K transform (K = 2n, a power of two) is a Stockham sequence of
-// register radix-16 stages (one radix-8/4/2 stage last when log2 K is not a
-// multiple of 4).  A thread always holds the 16 elements t + m K/16 of its
-// sequence: the first stage reads them straight from global memory, the last
-// writes its outputs straight to global memory, and the stages in between
-// exchange through shared memory (padded every 16 elements against bank
-// conflicts) -- two shared round trips for K = 2048.
+// register radix-E stages (E = 8 or 16; one smaller stage last when log2 K
+// is not a multiple of log2 E).  A thread always holds the E elements
+// t + m K/E of its sequence: the first stage reads them straight from global
+// memory, the last writes its outputs straight to global memory, and the
+// stages in between exchange through shared memory (padded every 16
+// elements against bank conflicts).
 //
-// Forward (Phi):   row pass over the n non-zero image rows, fused with the
-//                  deapodisation S and zero-padding Z (only the n non-zero
-//                  inputs are read); column pass over all K columns, reading
-//                  only the n non-zero rows and writing the padded grid (with
-//                  its periodic J-wide halo) that degridding stages by TMA.
-// Adjoint (Phi^H): column pass reading the padded gridding accumulator, folding
-//                  its halo back onto the torus, writing only the n rows the
-//                  crop Z^T keeps; row pass fused with the crop, the
-//                  deapodisation and the solver epilogues.
+// The image is real, so every pass works in real form: two image rows a, b
+// travel as one complex row x_a + i x_b, and only the half spectra (columns
+// 0..K/2 of the row transforms) are kept, n x K/2 complex values.
+// Forward (Phi):   row pass over the n non-zero image rows (pairs), fused with
+//                  the deapodisation S and zero-padding Z; column pass over
+//                  the K/2 half-spectrum columns, writing each grid column
+//                  and its conjugate mirror into the padded grid (with its
+//                  periodic J-wide halo) that degridding stages by TMA.
+// Adjoint (Phi^H): column pass reading the padded gridding accumulator,
+//                  folding its halo back onto the torus and taking its
+//                  Hermitian part (Re of the image is all Phi^H keeps),
+//                  writing only the n rows the crop Z^T keeps; row pass
+//                  fused with the crop, the deapodisation and the solver
+//                  epilogues.
 #include "internal.h"
 #include "solver_kernels.h"
 
@@ -203,13 +208,10 @@ template <int LOGN, int E = 16> PD int last_pos(int t, int cnt) {
 
 constexpr int kRowCta = 256;
 constexpr int kRowE = 8;  // elements per thread in the real-form row passes
+// ... unless a row of K / 8 threads would not fit one CTA (K = 4096): 16 there.
+template <int LOGN> constexpr int row_e() { return (1 << LOGN) / kRowE <= kRowCta ? kRowE : 16; }
+inline int row_e_host(int K) { return K / kRowE <= kRowCta ? kRowE : 16; }
 
-inline int row_nseq(const Geometry& g) {
-  int s = kRowCta / (g.K / 16);
-  if (s < 1) s = 1;
-  if (s > g.n) s = g.n;
-  return s;
-}
 template <typename T> inline int col_width() { return 32 / int(sizeof(typename cplx_t<T>::type)); }
 __host__ __device__ inline size_t padded(int N) { return size_t(N) + size_t(N) / 16 + 1; }
 
@@ -266,45 +268,6 @@ PD void row_ep_store(const RowEp<T>& ep, size_t idx, T val, EpOpd<T> opd, EpAcc<
 template <int LOGN, int E = 16> PD int ep_col(int t, int m) {
   constexpr int K = 1 << LOGN;
   return (last_pos<LOGN, E>(t, m) + K / 4) & (K - 1);
-}
-// Outputs val[r][m] (the final stage's values in sink order) of image rows
-// row0[r], in chunks of CH outputs: operands of the chunk first, then its
-// stores.
-template <int LOGN, int MODE, int NR, int E, typename T>
-PD EpAcc<T> row_ep_run_mode(const RowEp<T>& ep, const T (&val)[NR][E], int t, const size_t (&row0)[NR]) {
-  constexpr int CH = MODE == EP_CG_AP ? E / 2 : E, n = (1 << LOGN) / 2;
-  EpAcc<T> part;
-#pragma unroll
-  for (int c0 = 0; c0 < E; c0 += CH) {
-    EpOpd<T> opd[NR][CH];
-#pragma unroll
-    for (int m = 0; m < CH; ++m) {
-      const int i2 = ep_col<LOGN, E>(t, c0 + m);
-#pragma unroll
-      for (int r = 0; r < NR; ++r)
-        opd[r][m] = i2 < n ? row_ep_operand<MODE>(ep, row0[r] + i2) : EpOpd<T>{T(0), T(0)};
-    }
-#pragma unroll
-    for (int m = 0; m < CH; ++m) {
-      const int i2 = ep_col<LOGN, E>(t, c0 + m);
-      if (i2 < n) {
-#pragma unroll
-        for (int r = 0; r < NR; ++r) row_ep_store<MODE>(ep, row0[r] + i2, val[r][c0 + m], opd[r][m], part);
-      }
-    }
-  }
-  return part;
-}
-template <int LOGN, int NR, int E, typename T>
-PD EpAcc<T> row_ep_run(const RowEp<T>& ep, const T (&val)[NR][E], int t, const size_t (&row0)[NR]) {
-  switch (ep.mode) {
-    case EP_CG_AP: return row_ep_run_mode<LOGN, EP_CG_AP>(ep, val, t, row0);
-    case EP_CG_R0: return row_ep_run_mode<LOGN, EP_CG_R0>(ep, val, t, row0);
-    case EP_POWER: return row_ep_run_mode<LOGN, EP_POWER>(ep, val, t, row0);
-    case EP_XS_ADD: return row_ep_run_mode<LOGN, EP_XS_ADD>(ep, val, t, row0);
-    case EP_QX: return row_ep_run_mode<LOGN, EP_QX>(ep, val, t, row0);
-    default: return row_ep_run_mode<LOGN, EP_STORE>(ep, val, t, row0);
-  }
 }
 
 // Register slot m of the j-th of the E/2 grid columns of a thread that hold
@@ -465,124 +428,6 @@ template <typename T, int LOGN> struct ColThreads {
   static constexpr int value = (32 / int(sizeof(typename cplx_t<T>::type))) * ((1 << LOGN) / 16);
 };
 
-template <typename T, int LOGN>
-__global__ void __launch_bounds__(kRowCta) k_row_fwd(Geometry g, RowPro<T> pro, const T* __restrict__ deapod,
-                                                  typename cplx_t<T>::type* __restrict__ A,
-                                                  const typename cplx_t<T>::type* __restrict__ tw, int nseq) {
-  typedef typename cplx_t<T>::type C;
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int K = g.K, n = g.n;
-  const int seq = threadIdx.x / Plan<LOGN>::T, t = threadIdx.x - seq * Plan<LOGN>::T;
-  const int i1 = blockIdx.x * nseq + seq;
-  C* s = reinterpret_cast<C*>(sm_raw) + seq * padded(K);
-  const size_t row0[1] = {size_t(i1) * n};
-  T val[1][8];
-  int i2[8];
-  row_prologue<LOGN, 1, 16>(pro, row0, t, val, i2);
-  const T s1 = deapod[i1];
-  C v[16];
-#pragma unroll
-  for (int m = 0; m < 16; ++m) v[m] = cz<C>();
-#pragma unroll
-  for (int j = 0; j < 8; ++j) v[j < 4 ? j : j + 8] = cmk<C>(val[0][j] * s1 * deapod[i2[j]], T(0));
-  C* out = A + size_t(i1) * K;
-  auto store = [&](int q, C x) { out[q] = x; };
-  run_stages<LOGN, 0>(v, t, 1, s, 1, tw, -1, store);
-}
-
-template <typename T, int LOGN>
-__global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN>::value <= 512 ? 2 : 1) k_col_fwd(Geometry g, const typename cplx_t<T>::type* __restrict__ A,
-                                                  typename cplx_t<T>::type* __restrict__ Pg,
-                                                  const typename cplx_t<T>::type* __restrict__ tw, int cw) {
-  typedef typename cplx_t<T>::type C;
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int K = g.K, n = g.n, half = n / 2, pl = g.pad_lo, KP = g.KP;
-  const int cc = threadIdx.x % cw, t = threadIdx.x / cw;
-  const int c = blockIdx.x * cw + cc;
-  C* s = reinterpret_cast<C*>(sm_raw) + cc;  // cw interleaved columns
-  auto load = [&](int m) -> C {
-    const int q = t + m * Plan<LOGN>::T;  // grid row
-    const int i1 = (q + half) & (K - 1);
-    return i1 < n ? A[size_t(i1) * K + c] : cz<C>();
-  };
-  const int jhi = kJ - pl;  // grid indices < jhi repeat past the end
-  int cols[2] = {c + pl, -1};
-  if (c >= K - pl) cols[1] = c + pl - K;
-  else if (c < jhi) cols[1] = c + pl + K;
-  auto store = [&](int q, C v) {
-    int rows[2] = {q + pl, -1};
-    if (q >= K - pl) rows[1] = q + pl - K;
-    else if (q < jhi) rows[1] = q + pl + K;
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int b = 0; b < 2; ++b)
-        if (rows[a] >= 0 && cols[b] >= 0) Pg[size_t(rows[a]) * KP + cols[b]] = v;
-  };
-  fft_seq<LOGN>(t, s, cw, tw, -1, load, store);
-}
-
-template <typename T, int LOGN>
-__global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN>::value <= 512 ? 2 : 1) k_col_inv(Geometry g, const typename cplx_t<T>::type* __restrict__ Q,
-                                                  typename cplx_t<T>::type* __restrict__ A,
-                                                  const typename cplx_t<T>::type* __restrict__ tw, int cw) {
-  typedef typename cplx_t<T>::type C;
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int K = g.K, n = g.n, half = n / 2, pl = g.pad_lo, KP = g.KP;
-  const int cc = threadIdx.x % cw, t = threadIdx.x / cw;
-  const int c = blockIdx.x * cw + cc;
-  C* s = reinterpret_cast<C*>(sm_raw) + cc;  // cw interleaved columns
-  const int jhi = kJ - pl;
-  int cols[2] = {c + pl, -1};
-  if (c >= K - pl) cols[1] = c + pl - K;
-  else if (c < jhi) cols[1] = c + pl + K;
-  auto load = [&](int m) -> C {
-    const int q = t + m * Plan<LOGN>::T;
-    int rows[2] = {q + pl, -1};
-    if (q >= K - pl) rows[1] = q + pl - K;
-    else if (q < jhi) rows[1] = q + pl + K;
-    C v = cz<C>();
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int b = 0; b < 2; ++b)
-        if (rows[a] >= 0 && cols[b] >= 0) v = cadd(v, Q[size_t(rows[a]) * KP + cols[b]]);
-    return v;
-  };
-  auto store = [&](int q, C v) {
-    const int i1 = (q + half) & (K - 1);
-    if (i1 < n) A[size_t(i1) * K + c] = v;
-  };
-  fft_seq<LOGN>(t, s, cw, tw, +1, load, store);
-}
-
-template <typename T, int LOGN>
-__global__ void __launch_bounds__(kRowCta) k_row_inv(Geometry g, const typename cplx_t<T>::type* __restrict__ A,
-                                                  const T* __restrict__ deapod, RowEp<T> ep,
-                                                  const typename cplx_t<T>::type* __restrict__ tw, int nseq) {
-  typedef typename cplx_t<T>::type C;
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  __shared__ double red[5 * 32];
-  const int K = g.K, n = g.n;
-  const int seq = threadIdx.x / Plan<LOGN>::T, t = threadIdx.x - seq * Plan<LOGN>::T;
-  const int i1 = blockIdx.x * nseq + seq;
-  C* s = reinterpret_cast<C*>(sm_raw) + seq * padded(K);
-  const C* in = A + size_t(i1) * K;
-  auto load = [&](int m) -> C { return in[t + m * Plan<LOGN>::T]; };
-  T val[1][16];
-  int cnt = 0;
-  auto stash = [&](int, C v) { val[0][cnt++] = v.x; };  // sink order, see last_pos
-  fft_seq<LOGN>(t, s, 1, tw, +1, load, stash);
-  const T s1 = deapod[i1];
-#pragma unroll
-  for (int m = 0; m < 16; ++m) {
-    const int i2 = ep_col<LOGN>(t, m);
-    if (i2 < n) val[0][m] *= s1 * deapod[i2];
-  }
-  const size_t row0[1] = {size_t(i1) * n};
-  row_ep_finish(ep, row_ep_run<LOGN>(ep, val, t, row0), red);
-}
-
 // Composite operator by convolution (Section 3: precompute Phi^H Phi), in its
 // real form.  The image is real and the PSF spectrum real and even, so only
 // the half spectrum k2 in [0, K/2] of each image row is carried: two rows a, b
@@ -594,7 +439,7 @@ __global__ void __launch_bounds__(kRowCta) k_row_inv(Geometry g, const typename 
 // Forward row pass of the real form: rows 2 pr and 2 pr + 1 of the prologue's
 // image, zero-padded to K columns, to their half spectra.
 template <typename T, int LOGN, int E>
-__global__ void __launch_bounds__(kRowCta) k_row_fwd_h(Geometry g, RowPro<T> pro,
+__global__ void __launch_bounds__(kRowCta) k_row_fwd_h(Geometry g, RowPro<T> pro, const T* __restrict__ deapod,
                                                     typename cplx_t<T>::type* __restrict__ B,
                                                     const typename cplx_t<T>::type* __restrict__ tw, int nseq) {
   typedef typename cplx_t<T>::type C;
@@ -611,8 +456,17 @@ __global__ void __launch_bounds__(kRowCta) k_row_fwd_h(Geometry g, RowPro<T> pro
   C v[E];
 #pragma unroll
   for (int m = 0; m < E; ++m) v[m] = cz<C>();
+  if (deapod) {  // S: deapodisation of both rows (the Phi form; the convolution form has none)
+    const T da = deapod[ia], db = deapod[ib];
 #pragma unroll
-  for (int j = 0; j < E / 2; ++j) v[kept_slot<E>(j)] = cmk<C>(val[0][j], val[1][j]);
+    for (int j = 0; j < E / 2; ++j) {
+      const T dc = deapod[i2[j]];
+      v[kept_slot<E>(j)] = cmk<C>(val[0][j] * da * dc, val[1][j] * db * dc);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < E / 2; ++j) v[kept_slot<E>(j)] = cmk<C>(val[0][j], val[1][j]);
+  }
   auto to_smem = [&](int q, C x) { s[sidx(q)] = x; };
   run_stages<LOGN, 0, E>(v, t, 1, s, 1, tw, -1, to_smem);
   __syncthreads();
@@ -698,8 +552,8 @@ __global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN
 // row epilogue.
 template <typename T, int LOGN, int E>
 __global__ void __launch_bounds__(kRowCta, 2) k_row_inv_h(Geometry g, const typename cplx_t<T>::type* __restrict__ B,
-                                                       RowEp<T> ep, const typename cplx_t<T>::type* __restrict__ tw,
-                                                       int nseq) {
+                                                       const T* __restrict__ deapod, RowEp<T> ep,
+                                                       const typename cplx_t<T>::type* __restrict__ tw, int nseq) {
   typedef typename cplx_t<T>::type C;
   constexpr int TT = Plan<LOGN, E>::T;
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -746,12 +600,122 @@ __global__ void __launch_bounds__(kRowCta, 2) k_row_inv_h(Geometry g, const type
     ++cnt;
   };
   fft_seq<LOGN, E>(t, s, 1, tw, +1, load, stash);
+  if (deapod) {  // S^T after the crop (the Phi^H form)
+    const T da = deapod[ia], db = deapod[ib];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int i2 = ep_col<LOGN, E>(t, m);
+      if (i2 < n) {
+        const T dc = deapod[i2];
+        val[0][m] *= da * dc;
+        val[1][m] *= db * dc;
+      }
+    }
+  }
   const size_t row0[2] = {size_t(ia) * n, size_t(ib) * n};
   bool ok = true;
   if (nop > 0) ok = mbar_wait_bounded(&bar, 0, ep.err);
   EpAcc<T> part;
   if (ok) part = row_ep_staged<LOGN>(ep, val, t, row0, ops_all + size_t(seq) * 4 * n);
   row_ep_finish(ep, part, red);
+}
+
+// Real-form column passes of Phi and Phi^H on the padded grid (K + J per side,
+// periodic halo of J cells).  Grid cell (q, c) sits at padded row/column
+// q + pad_lo and also, near the edges, at its periodic image.
+PD int halo_images(int q, int K, int pl, int (&at)[2]) {
+  const int jhi = kJ - pl;  // grid indices < jhi repeat past the end
+  at[0] = q + pl;
+  at[1] = q >= K - pl ? q + pl - K : (q < jhi ? q + pl + K : -1);
+  return at[1] >= 0 ? 2 : 1;
+}
+
+// Phi: cw half-spectrum columns c per CTA.  For the image rows' half spectra
+// X(., c), c < K/2, the column FFT gives grid column c, and column K - c is
+// its conjugate mirror, G(q, K - c) = conj G(-q, c) (a real image).  Column 0
+// carries X(., 0) + i X(., K/2): its transform P gives grid column 0 as
+// (P(q) + conj P(-q)) / 2 and column K/2 as -i (P(q) - conj P(-q)) / 2.
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN>::value <= 512 ? 2 : 1)
+    k_col_fwd_h(Geometry g, const typename cplx_t<T>::type* __restrict__ B, typename cplx_t<T>::type* __restrict__ Pg,
+                const typename cplx_t<T>::type* __restrict__ tw, int cw) {
+  typedef typename cplx_t<T>::type C;
+  constexpr int TT = Plan<LOGN>::T;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int K = g.K, n = g.n, half = n / 2, H = K / 2, pl = g.pad_lo, KP = g.KP;
+  const int cc = threadIdx.x % cw, t = threadIdx.x / cw;
+  const int c = blockIdx.x * cw + cc;
+  C* s = reinterpret_cast<C*>(sm_raw) + cc;
+  auto load = [&](int m) -> C {
+    const int i1 = (t + m * TT + half) & (K - 1);
+    return i1 < n ? B[size_t(i1) * H + c] : cz<C>();
+  };
+  auto to_smem = [&](int q, C v) { s[sidx(q) * cw] = v; };
+  fft_seq<LOGN>(t, s, cw, tw, -1, load, to_smem);
+  __syncthreads();
+  auto put = [&](int q, int col, C v) {
+    int rows[2], cols[2];
+    const int nr = halo_images(q, K, pl, rows), nc = halo_images(col, K, pl, cols);
+    for (int a = 0; a < nr; ++a)
+      for (int b = 0; b < nc; ++b) Pg[size_t(rows[a]) * KP + cols[b]] = v;
+  };
+#pragma unroll 4
+  for (int m = 0; m < 16; ++m) {
+    const int q = t + m * TT, qm = (K - q) & (K - 1);
+    const C P = s[sidx(q) * cw];
+    if (c != 0) {
+      put(q, c, P);
+      put(qm, K - c, cmk<C>(P.x, -P.y));
+    } else {
+      const C Pm = s[sidx(qm) * cw];
+      put(q, 0, cmk<C>(T(0.5) * (P.x + Pm.x), T(0.5) * (P.y - Pm.y)));
+      // -i (P - conj Pm) / 2
+      put(q, H, cmk<C>(T(0.5) * (P.y + Pm.y), T(0.5) * (Pm.x - P.x)));
+    }
+  }
+}
+
+// Phi^H: Re of the inverse transform of the gridded accumulator Q is the
+// inverse transform of its Hermitian part Qh(q, c) = (Q(q, c) + conj Q(-q, -c)) / 2,
+// so only columns c <= K/2 are transformed: cw half-spectrum columns per
+// CTA (halo folded on load), inverse column FFT, the n cropped rows into the
+// half-spectrum rows B; column 0 packs the two Hermitian columns 0 and K/2 as
+// Qh(., 0) + i Qh(., K/2), whose transforms are real.
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN>::value <= 512 ? 2 : 1)
+    k_col_inv_h(Geometry g, const typename cplx_t<T>::type* __restrict__ Q, typename cplx_t<T>::type* __restrict__ B,
+                const typename cplx_t<T>::type* __restrict__ tw, int cw) {
+  typedef typename cplx_t<T>::type C;
+  constexpr int TT = Plan<LOGN>::T;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int K = g.K, n = g.n, half = n / 2, H = K / 2, pl = g.pad_lo, KP = g.KP;
+  const int cc = threadIdx.x % cw, t = threadIdx.x / cw;
+  const int c = blockIdx.x * cw + cc;
+  C* s = reinterpret_cast<C*>(sm_raw) + cc;
+  auto fold = [&](int q, int col) -> C {
+    int rows[2], cols[2];
+    const int nr = halo_images(q, K, pl, rows), nc = halo_images(col, K, pl, cols);
+    C v = cz<C>();
+    for (int a = 0; a < nr; ++a)
+      for (int b = 0; b < nc; ++b) v = cadd(v, Q[size_t(rows[a]) * KP + cols[b]]);
+    return v;
+  };
+  auto load = [&](int m) -> C {
+    const int q = t + m * TT, qm = (K - q) & (K - 1);
+    if (c != 0) {
+      const C a = fold(q, c), b = fold(qm, K - c);
+      return cmk<C>(T(0.5) * (a.x + b.x), T(0.5) * (a.y - b.y));
+    }
+    const C a0 = fold(q, 0), b0 = fold(qm, 0), aH = fold(q, H), bH = fold(qm, H);
+    const C h0 = cmk<C>(T(0.5) * (a0.x + b0.x), T(0.5) * (a0.y - b0.y));
+    const C hH = cmk<C>(T(0.5) * (aH.x + bH.x), T(0.5) * (aH.y - bH.y));
+    return cmk<C>(h0.x - hH.y, h0.y + hH.x);  // h0 + i hH
+  };
+  auto store = [&](int q, C v) {
+    const int i1 = (q + half) & (K - 1);
+    if (i1 < n) B[size_t(i1) * H + c] = v;
+  };
+  fft_seq<LOGN>(t, s, cw, tw, +1, load, store);
 }
 
 // Plain in-place transforms of a K x K complex array (set-up of the PSF spectrum).
@@ -799,7 +763,6 @@ __global__ void __launch_bounds__(ColThreads<T, LOGN>::value) k_cols_plain(typen
 
 }  // namespace
 
-int row_inv_blocks(const Geometry& g) { return g.n / row_nseq(g); }
 
 // Row pairs per CTA of the real-form row passes (E elements per thread).
 inline int row_pair_nseq(const Geometry& g, int E) {
@@ -808,6 +771,9 @@ inline int row_pair_nseq(const Geometry& g, int E) {
   if (s > g.n / 2) s = g.n / 2;
   return s;
 }
+
+// CTAs of one inverse row pass (its epilogue's partial sums).
+int row_inv_blocks(const Geometry& g) { return g.n / 2 / row_pair_nseq(g, row_e_host(g.K)); }
 
 #define PURIFY_LOGN_SWITCH(K, BODY)     \
   switch (K) {                          \
@@ -822,13 +788,11 @@ inline int row_pair_nseq(const Geometry& g, int E) {
   }
 
 template <typename T, int L> cudaError_t configure_one() {
-  cudaError_t e = raise_smem_limit(k_row_fwd<T, L>);
-  if (e == cudaSuccess) e = raise_smem_limit(k_row_inv<T, L>);
-  if (e == cudaSuccess) e = raise_smem_limit(k_col_fwd<T, L>);
-  if (e == cudaSuccess) e = raise_smem_limit(k_col_inv<T, L>);
-  if (e == cudaSuccess) e = raise_smem_limit(k_row_fwd_h<T, L, kRowE>);
+  cudaError_t e = raise_smem_limit(k_row_fwd_h<T, L, row_e<L>()>);
   if (e == cudaSuccess) e = raise_smem_limit(k_col_conv_h<T, L>);
-  if (e == cudaSuccess) e = raise_smem_limit(k_row_inv_h<T, L, kRowE>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_col_fwd_h<T, L>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_col_inv_h<T, L>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_row_inv_h<T, L, row_e<L>()>);
   if (e == cudaSuccess) e = raise_smem_limit(k_rows_plain<T, L>);
   if (e == cudaSuccess) e = raise_smem_limit(k_cols_plain<T, L>);
   return e;
@@ -843,43 +807,6 @@ template <typename T> cudaError_t configure_fft() {
 }
 template cudaError_t configure_fft<float>();
 template cudaError_t configure_fft<double>();
-
-template <typename T>
-void launch_row_fwd(const Geometry& g, const RowPro<T>& pro, const T* deapod, typename cplx_t<T>::type* A,
-                    const typename cplx_t<T>::type* tw, cudaStream_t s) {
-  typedef typename cplx_t<T>::type C;
-  const int nseq = row_nseq(g);
-  const size_t sm = nseq * padded(g.K) * sizeof(C);
-  PURIFY_LOGN_SWITCH(g.K, (k_row_fwd<T, L><<<g.n / nseq, nseq * Plan<L>::T, sm, s>>>(g, pro, deapod, A, tw, nseq)));
-}
-
-template <typename T>
-void launch_col_fwd(const Geometry& g, const typename cplx_t<T>::type* A, typename cplx_t<T>::type* Pg,
-                    const typename cplx_t<T>::type* tw, cudaStream_t s) {
-  typedef typename cplx_t<T>::type C;
-  const int cw = col_width<T>();
-  const size_t sm = cw * padded(g.K) * sizeof(C);
-  PURIFY_LOGN_SWITCH(g.K, (k_col_fwd<T, L><<<g.K / cw, cw * Plan<L>::T, sm, s>>>(g, A, Pg, tw, cw)));
-}
-
-template <typename T>
-void launch_col_inv(const Geometry& g, const typename cplx_t<T>::type* Q, typename cplx_t<T>::type* A,
-                    const typename cplx_t<T>::type* tw, cudaStream_t s) {
-  typedef typename cplx_t<T>::type C;
-  const int cw = col_width<T>();
-  const size_t sm = cw * padded(g.K) * sizeof(C);
-  PURIFY_LOGN_SWITCH(g.K, (k_col_inv<T, L><<<g.K / cw, cw * Plan<L>::T, sm, s>>>(g, Q, A, tw, cw)));
-}
-
-template <typename T>
-int launch_row_inv(const Geometry& g, const typename cplx_t<T>::type* A, const T* deapod, const RowEp<T>& ep,
-                   const typename cplx_t<T>::type* tw, cudaStream_t s) {
-  typedef typename cplx_t<T>::type C;
-  const int nseq = row_nseq(g);
-  const size_t sm = nseq * padded(g.K) * sizeof(C);
-  PURIFY_LOGN_SWITCH(g.K, (k_row_inv<T, L><<<g.n / nseq, nseq * Plan<L>::T, sm, s>>>(g, A, deapod, ep, tw, nseq)));
-  return g.n / nseq;
-}
 
 template <typename T>
 __global__ void k_embed_psf(const T* __restrict__ psf, int n, typename cplx_t<T>::type* __restrict__ X) {
@@ -918,12 +845,12 @@ void build_psf_spectrum(const T* psf, int n, T* khat, typename cplx_t<T>::type* 
 }
 
 template <typename T>
-void launch_row_fwd_h(const Geometry& g, const RowPro<T>& pro, typename cplx_t<T>::type* B,
+void launch_row_fwd_h(const Geometry& g, const RowPro<T>& pro, const T* deapod, typename cplx_t<T>::type* B,
                       const typename cplx_t<T>::type* tw, cudaStream_t s) {
   typedef typename cplx_t<T>::type C;
-  const int nseq = row_pair_nseq(g, kRowE);
+  const int nseq = row_pair_nseq(g, row_e_host(g.K));
   const size_t sm = nseq * padded(g.K) * sizeof(C);
-  PURIFY_LOGN_SWITCH(g.K, (k_row_fwd_h<T, L, kRowE><<<g.n / 2 / nseq, nseq * Plan<L, kRowE>::T, sm, s>>>(g, pro, B, tw, nseq)));
+  PURIFY_LOGN_SWITCH(g.K, (k_row_fwd_h<T, L, row_e<L>()><<<g.n / 2 / nseq, nseq * Plan<L, row_e<L>()>::T, sm, s>>>(g, pro, deapod, B, tw, nseq)));
 }
 
 template <typename T>
@@ -937,13 +864,31 @@ void launch_col_conv_h(const Geometry& g, typename cplx_t<T>::type* B, const T* 
 }
 
 template <typename T>
-int launch_row_inv_h(const Geometry& g, const typename cplx_t<T>::type* B, const RowEp<T>& ep,
+void launch_col_fwd_h(const Geometry& g, const typename cplx_t<T>::type* B, typename cplx_t<T>::type* Pg,
+                      const typename cplx_t<T>::type* tw, cudaStream_t s) {
+  typedef typename cplx_t<T>::type C;
+  const int cw = col_width<T>();
+  const size_t sm = cw * padded(g.K) * sizeof(C);
+  PURIFY_LOGN_SWITCH(g.K, (k_col_fwd_h<T, L><<<g.K / 2 / cw, cw * Plan<L>::T, sm, s>>>(g, B, Pg, tw, cw)));
+}
+
+template <typename T>
+void launch_col_inv_h(const Geometry& g, const typename cplx_t<T>::type* Q, typename cplx_t<T>::type* B,
+                      const typename cplx_t<T>::type* tw, cudaStream_t s) {
+  typedef typename cplx_t<T>::type C;
+  const int cw = col_width<T>();
+  const size_t sm = cw * padded(g.K) * sizeof(C);
+  PURIFY_LOGN_SWITCH(g.K, (k_col_inv_h<T, L><<<g.K / 2 / cw, cw * Plan<L>::T, sm, s>>>(g, Q, B, tw, cw)));
+}
+
+template <typename T>
+int launch_row_inv_h(const Geometry& g, const typename cplx_t<T>::type* B, const T* deapod, const RowEp<T>& ep,
                      const typename cplx_t<T>::type* tw, cudaStream_t s) {
   typedef typename cplx_t<T>::type C;
-  const int nseq = row_pair_nseq(g, kRowE);
+  const int nseq = row_pair_nseq(g, row_e_host(g.K));
   const size_t sm = align16(nseq * padded(g.K) * sizeof(C)) + size_t(nseq) * 4 * g.n * sizeof(T);
   const int nb = g.n / 2 / nseq;
-  PURIFY_LOGN_SWITCH(g.K, (k_row_inv_h<T, L, kRowE><<<nb, nseq * Plan<L, kRowE>::T, sm, s>>>(g, B, ep, tw, nseq)));
+  PURIFY_LOGN_SWITCH(g.K, (k_row_inv_h<T, L, row_e<L>()><<<nb, nseq * Plan<L, row_e<L>()>::T, sm, s>>>(g, B, deapod, ep, tw, nseq)));
   return nb;
 }
 
@@ -962,21 +907,17 @@ void launch_fft2_plain(int K, typename cplx_t<T>::type* X, const typename cplx_t
 }
 
 #define INST(T)                                                                                              \
-  template void launch_row_fwd<T>(const Geometry&, const RowPro<T>&, const T*, cplx_t<T>::type*,                \
-                                  const cplx_t<T>::type*, cudaStream_t);                                        \
-  template void launch_col_fwd<T>(const Geometry&, const cplx_t<T>::type*, cplx_t<T>::type*,                   \
-                                  const cplx_t<T>::type*, cudaStream_t);                                        \
-  template void launch_col_inv<T>(const Geometry&, const cplx_t<T>::type*, cplx_t<T>::type*,                   \
-                                  const cplx_t<T>::type*, cudaStream_t);                                        \
-  template int launch_row_inv<T>(const Geometry&, const cplx_t<T>::type*, const T*, const RowEp<T>&,            \
-                                 const cplx_t<T>::type*, cudaStream_t);                                        \
-  template void launch_row_fwd_h<T>(const Geometry&, const RowPro<T>&, cplx_t<T>::type*, const cplx_t<T>::type*, \
-                                    cudaStream_t);                                                             \
+  template void launch_row_fwd_h<T>(const Geometry&, const RowPro<T>&, const T*, cplx_t<T>::type*,             \
+                                    const cplx_t<T>::type*, cudaStream_t);                                     \
   template void launch_col_conv_h<T>(const Geometry&, cplx_t<T>::type*, const T*, const cplx_t<T>::type*,       \
                                      cudaStream_t);                                                            \
-  template int launch_row_inv_h<T>(const Geometry&, const cplx_t<T>::type*, const RowEp<T>&,                    \
+  template int launch_row_inv_h<T>(const Geometry&, const cplx_t<T>::type*, const T*, const RowEp<T>&,          \
                                    const cplx_t<T>::type*, cudaStream_t);                                      \
   template void launch_fft2_plain<T>(int, cplx_t<T>::type*, const cplx_t<T>::type*, int, cudaStream_t);     \
+  template void launch_col_fwd_h<T>(const Geometry&, const cplx_t<T>::type*, cplx_t<T>::type*,                \
+                                    const cplx_t<T>::type*, cudaStream_t);                                     \
+  template void launch_col_inv_h<T>(const Geometry&, const cplx_t<T>::type*, cplx_t<T>::type*,                \
+                                    const cplx_t<T>::type*, cudaStream_t);                                     \
   template void build_psf_spectrum<T>(const T*, int, T*, cplx_t<T>::type*, const cplx_t<T>::type*, cudaStream_t);
 INST(float)
 INST(double)

@@ -136,34 +136,33 @@ template <typename T> cudaError_t configure_fft();
 template <typename T> cudaError_t configure_nufft();
 template <typename T> cudaError_t configure_sara();
 
-template <typename T>
-void launch_row_fwd(const Geometry& g, const RowPro<T>& pro, const T* deapod, typename cplx_t<T>::type* A,
-                    const typename cplx_t<T>::type* tw, cudaStream_t s);
-template <typename T>
-void launch_col_fwd(const Geometry& g, const typename cplx_t<T>::type* A, typename cplx_t<T>::type* P,
-                    const typename cplx_t<T>::type* tw, cudaStream_t s);
-template <typename T>
-void launch_col_inv(const Geometry& g, const typename cplx_t<T>::type* Q, typename cplx_t<T>::type* A,
-                    const typename cplx_t<T>::type* tw, cudaStream_t s);
-// Returns the number of partial sums written (one per CTA).
-template <typename T>
-int launch_row_inv(const Geometry& g, const typename cplx_t<T>::type* A, const T* deapod, const RowEp<T>& ep,
-                   const typename cplx_t<T>::type* tw, cudaStream_t s);
+// CTAs of one inverse row pass (the partial sums its epilogue writes).
 int row_inv_blocks(const Geometry& g);
 // Composite operator Phi^H Phi as a convolution, in real form: the image
 // rows' half spectra (n x K/2 complex in B, entry 0 = X(0) + i X(K/2)).
 // Forward row pass (prologue, zero-padding, row FFT of row pairs):
+// deapod: S applied to both rows (Phi), or null (the convolution form).
 template <typename T>
-void launch_row_fwd_h(const Geometry& g, const RowPro<T>& pro, typename cplx_t<T>::type* B,
+void launch_row_fwd_h(const Geometry& g, const RowPro<T>& pro, const T* deapod, typename cplx_t<T>::type* B,
                       const typename cplx_t<T>::type* tw, cudaStream_t s);
 // Column pass: forward column FFT, multiply by the real PSF spectrum khat
 // ([K/2/cw][K][cw], then column K/2 as K values), inverse FFT, crop (in place).
 template <typename T>
 void launch_col_conv_h(const Geometry& g, typename cplx_t<T>::type* B, const T* khat,
                        const typename cplx_t<T>::type* tw, cudaStream_t s);
-// Inverse row pass with the row epilogue; returns the number of partial sums.
+// Real-form column passes of Phi (half-spectrum rows B -> the full padded
+// grid, mirrored columns included) and Phi^H (padded accumulator Q -> the
+// half-spectrum rows of its Hermitian part).
 template <typename T>
-int launch_row_inv_h(const Geometry& g, const typename cplx_t<T>::type* B, const RowEp<T>& ep,
+void launch_col_fwd_h(const Geometry& g, const typename cplx_t<T>::type* B, typename cplx_t<T>::type* Pg,
+                      const typename cplx_t<T>::type* tw, cudaStream_t s);
+template <typename T>
+void launch_col_inv_h(const Geometry& g, const typename cplx_t<T>::type* Q, typename cplx_t<T>::type* B,
+                      const typename cplx_t<T>::type* tw, cudaStream_t s);
+// Inverse row pass with the row epilogue (deapod: S^T, or null); returns the
+// number of partial sums.
+template <typename T>
+int launch_row_inv_h(const Geometry& g, const typename cplx_t<T>::type* B, const T* deapod, const RowEp<T>& ep,
                      const typename cplx_t<T>::type* tw, cudaStream_t s);
 // Real spectrum of the convolution kernel from the PSF image (2n x 2n real,
 // pixel offsets [-n, n)^2): circulant embedding on the K = 2n grid, forward

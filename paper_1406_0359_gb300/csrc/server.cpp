@@ -54,7 +54,7 @@ extern "C" int purify_estimate_bytes(int64_t M, int n, int dwt_levels, int preci
   const double N = double(n) * n, K = 2.0 * n, KP = K + 8;
   double b = 0;
   b += M * (2 * r + 4 + 16);                 // positions, permutation, kept uv
-  b += double(n) * K * c + 2 * KP * KP * c;  // compact rows, forward grid, gridding grid
+  b += double(n) * (K / 2) * c + 2 * KP * KP * c;  // half-spectrum rows, forward grid, gridding grid
   b += 2 * 8 * (N / 4) * r + 9 * N * r;      // wavelet scratch bands, prox output
   b += 6 * N * r + 18 * N * r + 2 * M * c;   // solver vectors, z1 and weights, z3 and sorted y
   b += (M / 1024.0 + 4.0 * K * K / 256) * 16;  // work items (bound) and partial sums

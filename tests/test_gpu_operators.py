@@ -115,6 +115,23 @@ def test_full_size_phi_sampled_and_adjoint_identity():
     assert abs(lhs - rhs) / abs(lhs) < 1e-5
 
 
+def test_largest_grid_phi_sampled_and_adjoint_identity():
+    """2048^2 image on the 4096^2 grid (the largest transform size): sampled
+    visibilities against the oracle and the adjoint identity."""
+    n, M = 2048, 65536
+    uv = synth.uv_coverage(M, n, 6)
+    op = make_op(uv, n, 2, "fp32")
+    x = synth.sky(n, 6, 12, 320)
+    yg = host(op.phi(to_dev(x, "fp32")))
+    idx = np.random.default_rng(1).choice(M, 500, replace=False)
+    assert rel(yg[idx], NUFFT(uv[idx], n).phi(x)) < TOL["fp32"]
+    y = synth.random_vis(M, 7)
+    xg = host(op.phi_adj(to_dev(y, "fp32")))
+    lhs = float(np.real(np.vdot(y, yg)))
+    rhs = float(np.sum(x * xg))
+    assert abs(lhs - rhs) / abs(lhs) < 1e-5
+
+
 @pytest.mark.parametrize("prec,tile,chunk", [("fp32", 8, 256), ("fp32", 16, 2048), ("fp64", 8, 512)])
 def test_tile_options_keep_parity(prec, tile, chunk):
     from paper_1406_0359_gb300.binding import Operator
