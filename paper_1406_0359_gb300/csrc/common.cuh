@@ -140,9 +140,20 @@ template <int NT, typename T> __device__ Acc<T> block_merge(Acc<T> a, double* sh
   return a;
 }
 // Merge of n stored partials by one block of NT threads; result in thread 0.
+// Each thread merges p[tid], p[tid + NT], ... in that order; the loads are
+// issued eight at a time so that their latencies overlap.
 template <int NT, typename T> __device__ Acc<T> merge_array(const Acc<T>* p, int n, double* sh) {
+  constexpr int U = 8;
   Acc<T> a;
-  for (int i = threadIdx.x; i < n; i += NT) acc_merge(a, p[i]);
+  int i = threadIdx.x;
+  for (; i + (U - 1) * NT < n; i += U * NT) {
+    Acc<T> v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = p[i + u * NT];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc_merge(a, v[u]);
+  }
+  for (; i < n; i += NT) acc_merge(a, p[i]);
   return block_merge<NT>(a, sh);
 }
 template <int NT> __device__ double block_max(double v, double* sh) {

@@ -346,7 +346,23 @@ template <typename T> PD void row_ep_finish(const RowEp<T>& ep, EpAcc<T> part, d
   if (!ep.ticket || !last_block_done_t0(ep.ticket)) return;
   // last block: merge all blocks' partials (fixed order), FP64 only at the end
   EpAcc<T> tot;
-  for (int i = threadIdx.x; i < int(gridDim.x); i += blockDim.x)
+  int i = threadIdx.x;
+  for (; i + int(blockDim.x) < int(gridDim.x); i += 2 * blockDim.x) {  // two CTAs' partials in flight
+    Acc<T> v[2][5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      if (k < nsum) {
+        v[0][k] = P[size_t(k) * ep.pstride + i];
+        v[1][k] = P[size_t(k) * ep.pstride + i + blockDim.x];
+      }
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      if (k < nsum) {
+        acc_merge(tot.a[k], v[0][k]);
+        acc_merge(tot.a[k], v[1][k]);
+      }
+  }
+  for (; i < int(gridDim.x); i += blockDim.x)
     for (int k = 0; k < nsum; ++k) acc_merge(tot.a[k], P[size_t(k) * ep.pstride + i]);
   for (int k = 0; k < nsum; ++k) {
     warp_merge(tot.a[k]);
@@ -512,21 +528,34 @@ __global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN
   auto to_smem = [&](int q, C v) { s[sidx(q) * cw] = v; };
   fft_seq<LOGN>(t, s, cw, tw, -1, load, to_smem);
   __syncthreads();
-  if (c == 0) {
-    // column 0: the pair (q, -q) per thread, in place; ev(-q) = conj ev(q),
-    // od(-q) = -conj od(q)
-    for (int m = 0; m <= 8; ++m) {
-      const int q = m < 8 ? t + m * TT : H;
-      if (m == 8 && t != 0) break;
-      const int qm = (K - q) & (K - 1);
-      const C P = s[sidx(q) * cw], Pm = s[sidx(qm) * cw];
-      const T evx = T(0.5) * (P.x + Pm.x), evy = T(0.5) * (P.y - Pm.y);
-      const T odx = T(0.5) * (P.x - Pm.x), ody = T(0.5) * (P.y + Pm.y);
-      const T h0 = khat[size_t(q) * cw], hn = knyq[q];
-      s[sidx(q) * cw] = cmk<C>(h0 * evx + hn * odx, h0 * evy + hn * ody);
-      if (qm != q) {
-        const T h0m = khat[size_t(qm) * cw], hnm = knyq[qm];
-        s[sidx(qm) * cw] = cmk<C>(h0m * evx - hnm * odx, hnm * ody - h0m * evy);
+  if (blockIdx.x == 0) {
+    // column 0 (this CTA's first): the pairs (q, -q), q = 0..K/2, in place,
+    // spread over all the CTA's threads with their spectrum values loaded
+    // first; ev(-q) = conj ev(q), od(-q) = -conj od(q)
+    C* s0 = reinterpret_cast<C*>(sm_raw);
+    const int nt = blockDim.x;
+    for (int q0 = 0; q0 <= H; q0 += 4 * nt) {
+      T h0[4], hn[4], h0m[4], hnm[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * nt + int(threadIdx.x), qm = (K - q) & (K - 1);
+        if (q <= H) {
+          h0[u] = khat[size_t(q) * cw];
+          hn[u] = knyq[q];
+          h0m[u] = khat[size_t(qm) * cw];
+          hnm[u] = knyq[qm];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * nt + int(threadIdx.x), qm = (K - q) & (K - 1);
+        if (q <= H) {
+          const C P = s0[sidx(q) * cw], Pm = s0[sidx(qm) * cw];
+          const T evx = T(0.5) * (P.x + Pm.x), evy = T(0.5) * (P.y - Pm.y);
+          const T odx = T(0.5) * (P.x - Pm.x), ody = T(0.5) * (P.y + Pm.y);
+          s0[sidx(q) * cw] = cmk<C>(h0[u] * evx + hn[u] * odx, h0[u] * evy + hn[u] * ody);
+          if (qm != q) s0[sidx(qm) * cw] = cmk<C>(h0m[u] * evx - hnm[u] * odx, hnm[u] * ody - h0m[u] * evy);
+        }
       }
     }
   }

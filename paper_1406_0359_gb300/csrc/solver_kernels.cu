@@ -8,6 +8,7 @@ namespace purify {
 
 namespace {
 constexpr int kT = 256;
+constexpr int kFinT = 1024;  // the single-block merge of the per-item partials
 
 // 16-byte vectors of the CG update.
 template <typename T> struct Vec16;
@@ -68,25 +69,44 @@ __global__ void __launch_bounds__(kT) k_finalize(const double* __restrict__ pa, 
 // min(1, nu eps_b / ||v - nu y||_b), the total residual and the worst
 // feasibility ratio max_b ||y_b - Phi_b x|| / eps_b.
 template <typename T>
-__global__ void __launch_bounds__(kT) k_finalize_blocks(const double* __restrict__ part0,
-                                                        const double* __restrict__ part1,
-                                                        const int* __restrict__ item_block, int n_items, int R,
-                                                        double nu, const double* __restrict__ eps_b,
-                                                        double* __restrict__ scale_b, double* __restrict__ sc) {
-  __shared__ double red[32];
+__global__ void __launch_bounds__(kFinT) k_finalize_blocks(const double* __restrict__ part0,
+                                                           const double* __restrict__ part1,
+                                                           const int* __restrict__ item_block, int n_items, int R,
+                                                           double nu, const double* __restrict__ eps_b,
+                                                           double* __restrict__ scale_b, double* __restrict__ sc) {
+  __shared__ double red[2 * 32];  // one Acc<T> per warp
   const Acc<T>* p0 = reinterpret_cast<const Acc<T>*>(part0);
   const Acc<T>* p1 = reinterpret_cast<const Acc<T>*>(part1);
   double tot1 = 0.0, worst = 0.0;
+  constexpr int U = 4;  // loads in flight per thread and array
   for (int b = 0; b < R; ++b) {
     Acc<T> a, c;
-    for (int i = threadIdx.x; i < n_items; i += kT) {
-      if (R == 1 || item_block[4 * i] == b) {  // WorkItem::pad
+    int i = threadIdx.x;
+    for (; i + (U - 1) * kFinT < n_items; i += U * kFinT) {
+      Acc<T> x[U], y[U];
+      bool in[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int j = i + u * kFinT;
+        in[u] = R == 1 || item_block[4 * j] == b;  // WorkItem::pad
+        x[u] = p0[j];
+        y[u] = p1[j];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (in[u]) {
+          acc_merge(a, x[u]);
+          acc_merge(c, y[u]);
+        }
+    }
+    for (; i < n_items; i += kFinT) {
+      if (R == 1 || item_block[4 * i] == b) {
         acc_merge(a, p0[i]);
         acc_merge(c, p1[i]);
       }
     }
-    const double av = block_merge<kT>(a, red).value();
-    const double cv = block_merge<kT>(c, red).value();
+    const double av = block_merge<kFinT>(a, red).value();
+    const double cv = block_merge<kFinT>(c, red).value();
     if (threadIdx.x == 0) {
       const double s = sqrt(av), rad = nu * eps_b[b];
       scale_b[b] = s <= rad ? 1.0 : rad / s;
@@ -193,7 +213,7 @@ int launch_reduce(const T* v, size_t N, int op, const double* sc, double* partia
 template <typename T>
 void launch_finalize_blocks(const double* part0, const double* part1, const int* items_as_int, int n_items, int R,
                             double nu, const double* eps_b, double* scale_b, double* sc, cudaStream_t s) {
-  k_finalize_blocks<T><<<1, kT, 0, s>>>(part0, part1, items_as_int + 3, n_items, R, nu, eps_b, scale_b, sc);
+  k_finalize_blocks<T><<<1, kFinT, 0, s>>>(part0, part1, items_as_int + 3, n_items, R, nu, eps_b, scale_b, sc);
 }
 
 void launch_max_partials(const double* p, int np, double* sc, cudaStream_t s) {
