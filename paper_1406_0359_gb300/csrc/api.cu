@@ -299,22 +299,22 @@ template <typename T> class OpImpl : public purify_op {
     CK(configure_once<T>());
     // tables: deapodisation, twiddles, kernel polynomial, filters (host, double)
     const double beta = kb_beta(kJ, 2.0);
-    std::vector<T> hs(n);
-    for (int i = 0; i < n; ++i) hs[i] = T(1.0 / kb_fourier(double(i - n / 2) / g.K, kJ, beta));
+    std::vector<double> hd;
+    kb_deapod_table(n, g.K, kJ, beta, hd);
+    std::vector<T> hs(hd.begin(), hd.end());
     std::vector<C> htw(g.K);
     for (int m = 0; m < g.K; ++m) {
       const double a = -2.0 * M_PI * double(m) / g.K;
       htw[m].x = T(std::cos(a));
       htw[m].y = T(std::sin(a));
     }
-    std::vector<double> coef;
     constexpr int D = KbDeg<T>::value;
-    kb_poly_fit(kJ, beta, D, coef);
+    const std::vector<double>& coef = kb_poly_cached(kJ, beta, D);
     for (int a = 0; a < kJ; ++a)
       for (int d = 0; d <= D; ++d) kb.c[a][d] = T(coef[size_t(a) * (D + 1) + d]);
     std::memset(&sara.f, 0, sizeof(sara.f));
     for (int k = 1; k <= kMaxDb; ++k) {
-      const std::vector<double> h = daubechies_lowpass(k);
+      const std::vector<double>& h = daubechies_lowpass_cached(k);
       const int F = 2 * k;
       for (int m = 0; m < F; ++m) {
         sara.f.h[k - 1][m] = T(h[m]);

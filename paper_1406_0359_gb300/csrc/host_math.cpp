@@ -3,7 +3,10 @@
 
 #include <cmath>
 #include <complex>
+#include <map>
+#include <mutex>
 #include <stdexcept>
+#include <tuple>
 
 namespace purify {
 
@@ -170,6 +173,50 @@ std::vector<double> daubechies_lowpass(int K) {
   }
   for (double& v : out) v *= std::sqrt(2.0) / s;
   return out;
+}
+
+namespace {
+std::mutex g_table_mutex;
+}  // namespace
+
+const std::vector<double>& kb_poly_cached(int J, double beta, int deg) {
+  static std::map<std::tuple<int, double, int>, std::vector<double>> cache;
+  std::lock_guard<std::mutex> lock(g_table_mutex);
+  auto it = cache.find(std::make_tuple(J, beta, deg));
+  if (it == cache.end()) {
+    std::vector<double> coef;
+    kb_poly_fit(J, beta, deg, coef);
+    it = cache.emplace(std::make_tuple(J, beta, deg), std::move(coef)).first;
+  }
+  return it->second;
+}
+
+const std::vector<double>& daubechies_lowpass_cached(int K) {
+  static std::map<int, std::vector<double>> cache;
+  std::lock_guard<std::mutex> lock(g_table_mutex);
+  auto it = cache.find(K);
+  if (it == cache.end()) it = cache.emplace(K, daubechies_lowpass(K)).first;
+  return it->second;
+}
+
+void kb_deapod_table(int n, int K, int J, double beta, std::vector<double>& out) {
+  const double scale = J / bessel_i0(beta);
+  out.resize(size_t(n));
+  for (int i = 0; i < n; ++i) {
+    const double t = M_PI * J * double(i - n / 2) / K;
+    const double d = beta * beta - t * t;
+    double v;
+    if (d > 1e-12) {
+      const double r = std::sqrt(d);
+      v = std::sinh(r) / r;
+    } else if (d < -1e-12) {
+      const double r = std::sqrt(-d);
+      v = std::sin(r) / r;
+    } else {
+      v = 1.0;
+    }
+    out[size_t(i)] = 1.0 / (v * scale);
+  }
 }
 
 }  // namespace purify

@@ -1,7 +1,7 @@
 // Host-side tables for the CUDA path: Kaiser-Bessel kernel, its Fourier
 // transform for deapodisation, the piecewise-polynomial kernel used by the
-// FP32 kernels, and the Daubechies filters.  Computed in double on the host
-// once per operator.
+// FP32 kernels, and the Daubechies filters.  Computed in double on the host;
+// the kernel polynomial and the filters once per process.
 #pragma once
 #include <vector>
 
@@ -25,5 +25,13 @@ double kb_poly_fit(int J, double beta, int deg, std::vector<double>& coef);
 // DbK low-pass analysis filter (length 2K) by spectral factorisation with
 // the minimum-phase root choice, normalised to sum sqrt(2).
 std::vector<double> daubechies_lowpass(int K);
+
+// The two tables above computed once per process and kept (thread-safe).
+const std::vector<double>& kb_poly_cached(int J, double beta, int deg);
+const std::vector<double>& daubechies_lowpass_cached(int K);
+
+// Deapodisation weights 1 / kb_fourier((i - n/2) / K), i < n, with I0(beta)
+// evaluated once.
+void kb_deapod_table(int n, int K, int J, double beta, std::vector<double>& out);
 
 }  // namespace purify

@@ -599,7 +599,7 @@ int static_scratch(float** out) {
   }
   if (!g_static_filters_ready) {
     for (int k = 1; k <= kMaxDb; ++k) {
-      const std::vector<double> h = daubechies_lowpass(k);
+      const std::vector<double>& h = daubechies_lowpass_cached(k);
       const int F = 2 * k;
       for (int m = 0; m < kMaxTaps; ++m) {
         g_static_filters.h[k - 1][m] = m < F ? float(h[m]) : 0.0f;

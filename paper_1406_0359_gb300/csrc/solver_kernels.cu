@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kFinT) k_finalize_blocks(const double* __restr
   const Acc<T>* p0 = reinterpret_cast<const Acc<T>*>(part0);
   const Acc<T>* p1 = reinterpret_cast<const Acc<T>*>(part1);
   double tot1 = 0.0, worst = 0.0;
-  constexpr int U = 4;  // loads in flight per thread and array
+  constexpr int U = 8;  // loads in flight per thread and array
   for (int b = 0; b < R; ++b) {
     Acc<T> a, c;
     int i = threadIdx.x;
