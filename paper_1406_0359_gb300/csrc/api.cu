@@ -27,6 +27,39 @@
 
 namespace purify {
 
+cudaError_t setup_alloc(void** p, size_t bytes, cudaStream_t s) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaMallocAsync(p, bytes, s);
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+      cudaMemPoolProps props;
+      std::memset(&props, 0, sizeof(props));
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      cudaMemPool_t np = nullptr;
+      if (cudaMemPoolCreate(&np, &props) == cudaSuccess) {
+        uint64_t keep = kSetupPoolKeep;
+        cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = np;
+      } else {
+        cudaGetLastError();  // fall back to the device's default pool
+        e = cudaDeviceGetDefaultMemPool(&np, dev);
+        if (e != cudaSuccess) return e;
+        pools[dev] = np;
+      }
+    }
+    pool = pools[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
 thread_local char g_last_error[256] = "";
 void set_last_error(const char* msg) { std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
 
@@ -160,6 +193,10 @@ template <typename T> class OpImpl : public purify_op {
   double* scale_dev = nullptr;  // projection scale per block (R)
   int64_t bytes = 0;
   std::vector<void*> allocs;
+  // Set-up (light) operator: buffers from the set-up pool on this stream, the
+  // only stream that uses them; released in stream order.
+  cudaStream_t pool_stream = nullptr;
+  bool items_pooled = false;  // items from the set-up pool (refined operator)
   cudaStream_t own = nullptr;  // solver stream (capturable, non-blocking)
   cudaStream_t aux = nullptr;  // second branch of an SDMM iteration (ball block)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr, ev_join = nullptr;
@@ -224,8 +261,13 @@ template <typename T> class OpImpl : public purify_op {
     run_release();
     prof_release();
     if (own) cudaStreamSynchronize(own);
-    cudaFree(items);
-    for (void* a : allocs) cudaFree(a);
+    if (items_pooled) cudaFreeAsync(items, pool_stream);
+    else cudaFree(items);
+    if (pool_stream) {  // set-up operator: every use was on pool_stream
+      for (void* a : allocs) cudaFreeAsync(a, pool_stream);
+    } else {
+      for (void* a : allocs) cudaFree(a);
+    }
     if (aux) cudaStreamSynchronize(aux);
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
@@ -239,7 +281,8 @@ template <typename T> class OpImpl : public purify_op {
   template <typename U> int alloc(U** ptr, size_t count) {
     void* a = nullptr;
     const size_t b = count * sizeof(U) > 0 ? count * sizeof(U) : 16;
-    CK(cudaMalloc(&a, b));
+    if (pool_stream) CK(setup_alloc(&a, b, pool_stream));
+    else CK(cudaMalloc(&a, b));
     allocs.push_back(a);
     bytes += int64_t(b);
     *ptr = static_cast<U*>(a);
@@ -280,6 +323,7 @@ template <typename T> class OpImpl : public purify_op {
   int create(const double* uv, int64_t M, int n, int L, cudaStream_t s, int tile = 0, int chunk_opt = 0,
              bool light_only = false, const OpImpl* refine = nullptr) {
     light = light_only || refine;
+    if (light) pool_stream = s;
     g.n = n;
     g.K = 2 * n;
     g.KP = g.K + kJ;
@@ -350,7 +394,8 @@ template <typename T> class OpImpl : public purify_op {
     if (!light) CK(cudaMemsetAsync(gridP, 0, grid_bytes(), s));
     if (refine) {
       n_items = refine->n_items;
-      CK(cudaMalloc(&items, size_t(n_items > 0 ? n_items : 1) * sizeof(WorkItem)));
+      CK(setup_alloc(&items, size_t(n_items > 0 ? n_items : 1) * sizeof(WorkItem), s));
+      items_pooled = true;
       CK(cudaMemcpyAsync(items, refine->items, size_t(n_items) * sizeof(WorkItem), cudaMemcpyDeviceToDevice, s));
       launch_encode_x2<T>(refine->uv_keep, refine->perm, M, refine->g.K, g.TB, pos, s);
     } else {
@@ -465,10 +510,10 @@ template <typename T> class OpImpl : public purify_op {
       C* y1 = nullptr;
       T* psf = nullptr;
       C* X = nullptr;
-      // temporaries from the stream-ordered pool
-      cudaError_t e = cudaMallocAsync(&y1, size_t(g.M) * sizeof(C), s);
-      if (e == cudaSuccess) e = cudaMallocAsync(&psf, size_t(g.K) * g.K * sizeof(T), s);
-      if (e == cudaSuccess) e = cudaMallocAsync(&X, size_t(g.K) * g.K * sizeof(C), s);
+      // temporaries from the set-up pool
+      cudaError_t e = setup_alloc(&y1, size_t(g.M) * sizeof(C), s);
+      if (e == cudaSuccess) e = setup_alloc(&psf, size_t(g.K) * g.K * sizeof(T), s);
+      if (e == cudaSuccess) e = setup_alloc(&X, size_t(g.K) * g.K * sizeof(C), s);
       if (e == cudaSuccess) {
         C one;
         one.x = T(1);

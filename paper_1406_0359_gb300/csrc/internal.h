@@ -188,6 +188,16 @@ template <typename T>
 void launch_gram(const Geometry& g, const CUtensorMap& map, const WorkItem* items, int n_items, const Pos<T>* pos,
                  const KbPoly<T>& kb, typename cplx_t<T>::type* Q, int* err, cudaStream_t s);
 
+// Stream-ordered memory for set-up temporaries (binning scratch, the PSF
+// operator and its buffers): one pool per device that keeps up to
+// kSetupPoolKeep bytes of released memory mapped, so that repeated operator
+// creations reuse it instead of mapping new memory each time.
+constexpr uint64_t kSetupPoolKeep = uint64_t(1) << 30;
+cudaError_t setup_alloc(void** p, size_t bytes, cudaStream_t s);
+template <typename U> cudaError_t setup_alloc(U** p, size_t bytes, cudaStream_t s) {
+  return setup_alloc(reinterpret_cast<void**>(p), bytes, s);
+}
+
 // uv binning (once per operator).  Fills pos/perm and returns the work list.
 // With R > 1 visibility blocks (device int32 block index per visibility, in
 // caller order), visibilities are binned by (block, tile, cell) and every work

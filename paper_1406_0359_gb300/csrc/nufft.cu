@@ -1040,17 +1040,17 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
   auto fail = [&](cudaError_t e) {
     if (e != cudaSuccess && rc == 0) rc = (e == cudaErrorMemoryAllocation) ? -2 : -3;
   };
-  // temporaries from the stream-ordered pool (no device-wide synchronisation
-  // on release, reused across operator creations)
-  fail(cudaMallocAsync(&k0, M * sizeof(uint32_t), s));
-  fail(cudaMallocAsync(&k1, M * sizeof(uint32_t), s));
-  fail(cudaMallocAsync(&v1, M * sizeof(int), s));
-  fail(cudaMallocAsync(&hist, size_t(256) * nblocks * sizeof(int), s));
-  fail(cudaMallocAsync(&tstart, size_t(ntiles) * sizeof(int), s));
-  fail(cudaMallocAsync(&tend, size_t(ntiles) * sizeof(int), s));
-  fail(cudaMallocAsync(&cnt, size_t(ntiles) * sizeof(int), s));
-  fail(cudaMallocAsync(&total, sizeof(int), s));
-  fail(cudaMallocAsync(&bsum, 1024 * sizeof(int), s));
+  // temporaries from the set-up pool (no device-wide synchronisation on
+  // release, reused across operator creations)
+  fail(setup_alloc(&k0, M * sizeof(uint32_t), s));
+  fail(setup_alloc(&k1, M * sizeof(uint32_t), s));
+  fail(setup_alloc(&v1, M * sizeof(int), s));
+  fail(setup_alloc(&hist, size_t(256) * nblocks * sizeof(int), s));
+  fail(setup_alloc(&tstart, size_t(ntiles) * sizeof(int), s));
+  fail(setup_alloc(&tend, size_t(ntiles) * sizeof(int), s));
+  fail(setup_alloc(&cnt, size_t(ntiles) * sizeof(int), s));
+  fail(setup_alloc(&total, sizeof(int), s));
+  fail(setup_alloc(&bsum, 1024 * sizeof(int), s));
   if (rc == 0) {
     const int tb = 256;
     k_bin_keys<<<int((M + tb - 1) / tb), tb, 0, s>>>(uv, R > 1 ? blocks : nullptr, M, g.K, g.TB, lb, g.ntile1d,
