@@ -334,12 +334,14 @@ template <typename T> class OpImpl : public purify_op {
     g.M = M;
     levels = L;
     chunk = chunk_opt > 0 ? chunk_opt : 1024;
-    CK(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
-    CK(cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking));
-    CK(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+    if (!light) {  // a set-up operator runs only on the caller's stream
+      CK(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+      CK(cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+    }
     CK(configure_once<T>());
     // tables: deapodisation, twiddles, kernel polynomial, filters (host, double)
     const double beta = kb_beta(kJ, 2.0);
@@ -411,7 +413,7 @@ template <typename T> class OpImpl : public purify_op {
     if ((rc = alloc(&cg_part, 5 * kCgPart))) return rc;
     if ((rc = alloc(&tickets, 4))) return rc;
     CK(cudaMemsetAsync(tickets, 0, 4 * sizeof(unsigned int), s));
-    if (light) return check(s, true);
+    if (light) return check(s, false);  // its user synchronises s
     // TMA descriptor of the padded forward grid, 8-byte elements
     EncodeTiledFn enc = encode_fn();
     if (!enc) {
