@@ -68,6 +68,9 @@ enum purify_status {
  *   out         receives the new operator; untouched on error.
  * The operator owns device copies of the sorted uv tiles and tables and is
  * released by purify_op_destroy.  Synchronises `stream` before returning.
+ * Set-up temporaries (binning scratch; later, the PSF operator of the
+ * convolution form) come from a per-device memory pool of the library that
+ * keeps up to 1 GiB of released memory mapped for the next creation.
  */
 int purify_op_create(const double* uv, int64_t M, int n, int oversample, int J,
                      int dwt_levels, int precision, void* stream, purify_op** out);
