@@ -534,7 +534,7 @@ template <typename T> class OpImpl : public purify_op {
     return PURIFY_OK;
   }
 
-  // Front half of Re(Phi^H Phi) x: up to the compact rows in gridA, by the
+  // Front half of Re(Phi^H Phi) x: up to the half-spectrum rows in gridA, by the
   // NUFFT (G^H G per application) or by the precomputed convolution.
   void normal_front(const RowPro<T>& pro, cudaStream_t s) {
     if (toep) {

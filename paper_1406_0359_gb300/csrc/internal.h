@@ -4,8 +4,10 @@
 //   pos    [M]        visibility positions in uv-tile order (Pos<T>)
 //   perm   [M]        sorted slot -> caller's visibility index
 //   items  [n_items]  work items: (tile, first slot, end slot), <= chunk slots each
-//   gridA  [n][K]     compact rows: image rows after the row FFT (forward) or
-//                     before the inverse row FFT (adjoint)
+//   gridA  [n][K/2]   half-spectrum rows: the row FFTs of image row pairs
+//                     x_a + i x_b split into the half spectra of rows a and b
+//                     (entry 0 = X(0) + i X(K/2)), after the forward row pass
+//                     or before the inverse one
 //   gridP  [KP][KP]   forward oversampled grid with a J-wide periodic halo,
 //                     read in (TB+J)^2 patches by TMA for degridding
 //   gridQ  [KP][KP]   gridding accumulator with the same halo (folded on read)
