@@ -91,20 +91,6 @@ PD double warp_max(double v) {
   return v;
 }
 
-// Deterministic block sum (fixed tree order); result valid in thread 0.
-template <int NT> __device__ double block_sum(double v, double* sh /*[32]*/) {
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (w == 0) {
-    r = (lane < NT / 32) ? sh[lane] : 0.0;
-    r = warp_sum(r);
-  }
-  __syncthreads();
-  return r;
-}
 // Merging of compensated partials.  Per-block partial sums are stored as
 // Acc<T> (8 bytes, in double-sized slots) and merged in the same compensated
 // FP32 form, so the only FP64 arithmetic of a reduction is the final value:
@@ -202,19 +188,6 @@ __device__ __forceinline__ bool last_block_done_t0(unsigned int* ticket) {
   return last;
 }
 
-// Fixed-order sum of n partials by one block (any blockDim multiple of 32).
-__device__ __forceinline__ double block_sum_array(const double* p, int n, double* sh) {
-  double a = 0.0;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) a += p[k];
-  a = warp_sum(a);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) sh[w] = a;
-  __syncthreads();
-  double t = 0.0;
-  for (int k = 0; k < int((blockDim.x + 31) >> 5); ++k) t += sh[k];
-  __syncthreads();
-  return t;
-}
 
 // ---------------------------------------------------------------- mbarrier + TMA
 PD uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -223,7 +196,6 @@ PD void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 PD void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-PD void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 PD void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");

@@ -217,26 +217,11 @@ __host__ __device__ inline size_t padded(int N) { return size_t(N) + size_t(N) /
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-// Row-pass epilogues (see RowEpMode), split so that every operand an output
-// needs is loaded (for a chunk of a thread's outputs) before the first output
-// of the chunk is stored: the stores may alias the operands, which would
-// otherwise serialise one memory round trip per output.
+// Row-pass epilogues (see RowEpMode): per output, its operands (EpOpd, from
+// the rows staged in shared memory) and the stores and partial sums of the
+// mode.
 template <typename T> struct EpOpd { T a, b; };
 template <typename T> struct EpAcc { Acc<T> a[5]; };
-template <int MODE, typename T> PD EpOpd<T> row_ep_operand(const RowEp<T>& ep, size_t idx) {
-  EpOpd<T> o{T(0), T(0)};
-  if constexpr (MODE == EP_CG_AP) {
-    o.a = ep.p[idx];
-    o.b = ep.r[idx];
-  } else if constexpr (MODE == EP_QX) {
-    o.a = ep.p[idx];
-  } else if constexpr (MODE == EP_CG_R0) {
-    o.a = ep.b[idx] - T(2) * ep.p[idx];
-  } else if constexpr (MODE == EP_XS_ADD) {
-    o.a = ep.b[idx];
-  }
-  return o;
-}
 template <int MODE, typename T>
 PD void row_ep_store(const RowEp<T>& ep, size_t idx, T val, EpOpd<T> opd, EpAcc<T>& part) {
   if constexpr (MODE == EP_CG_AP) {
