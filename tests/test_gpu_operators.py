@@ -154,3 +154,24 @@ def test_autotuner_returns_a_valid_choice():
     uv = torch.as_tensor(synth.uv_coverage(M, n, 2)).cuda()
     tile, chunk, ms = purify_autotune(uv, n, 3)
     assert tile in (8, 16) and chunk in (256, 512, 1024, 2048) and ms > 0
+
+
+def test_repeated_creation_reuses_set_up_memory_deterministically():
+    """Operators built one after another (their binning scratch and PSF set-up
+    buffers come from the library's set-up pool, reused between creations)
+    give the same Phi bit for bit (a gather) and the same Phi^H and
+    convolution-form Phi^H Phi up to the order of the gridding's global
+    atomic adds."""
+    n, M = 128, 20000
+    uv = synth.uv_coverage(M, n, 11)
+    x = to_dev(synth.sky(n, 11, 3, 10), "fp32")
+    y = to_dev(synth.random_vis(M, 12), "fp32")
+    outs = []
+    for _ in range(3):
+        op = make_op(uv, n, 3, "fp32")
+        outs.append((host(op.phi(x)), host(op.phi_adj(y)), host(op.gram(x, mode=1))))
+        op.close()
+    for later in outs[1:]:
+        assert np.array_equal(outs[0][0], later[0])
+        assert rel(later[1], outs[0][1]) < 1e-6
+        assert rel(later[2], outs[0][2]) < 1e-6
