@@ -173,7 +173,8 @@ template <typename T> class OpImpl : public purify_op {
   SaraPlan<T> sara{};
   double* partials = nullptr;
   double* cg_part = nullptr;        // CG partial sums (row pass, CG update)
-  unsigned int* tickets = nullptr;  // last-block tickets of the CG reductions
+  unsigned int* tickets = nullptr;  // last-block tickets: CG reductions (0, 1), ball scalars (2)
+  double* fin_part = nullptr;       // per-CTA partials of the ball-scalar merge (2 x kFinCtas)
   static constexpr int kCgPart = 4096;
   double* sc = nullptr;
   double* h_sc = nullptr;
@@ -412,6 +413,7 @@ template <typename T> class OpImpl : public purify_op {
     if ((rc = alloc(&eps_dev, 64)) || (rc = alloc(&scale_dev, 64))) return rc;
     if ((rc = alloc(&cg_part, 5 * kCgPart))) return rc;
     if ((rc = alloc(&tickets, 4))) return rc;
+    if ((rc = alloc(&fin_part, 2 * kFinCtas))) return rc;
     CK(cudaMemsetAsync(tickets, 0, 4 * sizeof(unsigned int), s));
     if (light) return check(s, false);  // its user synchronises s
     // TMA descriptor of the padded forward grid, 8-byte elements
@@ -797,7 +799,7 @@ template <typename T> class OpImpl : public purify_op {
     dep.part1 = bpart + n_items;
     degrid(dep, b3);
     PROF(KK_VEC, b3, launch_finalize_blocks<T>(bpart, bpart + n_items, reinterpret_cast<const int*>(items), n_items,
-                                                nblocks, nu, eps_dev, scale_dev, sc, b3));
+                                                nblocks, nu, eps_dev, scale_dev, sc, fin_part, tickets + 2, b3));
     zero_q(b3);
     GridPro<C> gp{};
     gp.mode = GP_BALL;

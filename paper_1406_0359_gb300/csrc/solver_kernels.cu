@@ -122,6 +122,60 @@ __global__ void __launch_bounds__(kFinT) k_finalize_blocks(const double* __restr
   }
 }
 
+// The same scalars for one visibility block (R = 1) in two levels: kFinCtas
+// CTAs each merge a contiguous slice of the items' partials (fixed order),
+// the last CTA to finish (ticket) merges the CTAs' partials in index order.
+template <typename T>
+__global__ void __launch_bounds__(kT) k_finalize_ball1(const double* __restrict__ part0,
+                                                       const double* __restrict__ part1, int n_items, double nu,
+                                                       const double* __restrict__ eps_b, double* __restrict__ scale_b,
+                                                       double* __restrict__ sc, double* __restrict__ cpart,
+                                                       unsigned int* __restrict__ ticket) {
+  __shared__ double red[32];
+  const Acc<T>* p0 = reinterpret_cast<const Acc<T>*>(part0);
+  const Acc<T>* p1 = reinterpret_cast<const Acc<T>*>(part1);
+  Acc<T>* c0 = reinterpret_cast<Acc<T>*>(cpart);
+  Acc<T>* c1 = c0 + gridDim.x;
+  const int per = (n_items + int(gridDim.x) - 1) / int(gridDim.x);
+  const int lo = int(blockIdx.x) * per, hi = min(n_items, lo + per);
+  constexpr int U = 4;
+  Acc<T> a, c;
+  int i = lo + int(threadIdx.x);
+  for (; i + (U - 1) * kT < hi; i += U * kT) {
+    Acc<T> x[U], y[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      x[u] = p0[i + u * kT];
+      y[u] = p1[i + u * kT];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      acc_merge(a, x[u]);
+      acc_merge(c, y[u]);
+    }
+  }
+  for (; i < hi; i += kT) {
+    acc_merge(a, p0[i]);
+    acc_merge(c, p1[i]);
+  }
+  a = block_merge<kT>(a, red);
+  c = block_merge<kT>(c, red);
+  if (threadIdx.x == 0) {
+    c0[blockIdx.x] = a;
+    c1[blockIdx.x] = c;
+  }
+  if (!last_block_done(ticket)) return;
+  const double av = merge_array<kT>(c0, int(gridDim.x), red).value();
+  const double cv = merge_array<kT>(c1, int(gridDim.x), red).value();
+  if (threadIdx.x == 0) {
+    const double s = sqrt(av), rad = nu * eps_b[0];
+    scale_b[0] = s <= rad ? 1.0 : rad / s;
+    sc[S_RESID] = sqrt(cv);
+    sc[S_FEAS] = sqrt(cv) / eps_b[0];
+    sc[S_BALLSCALE] = scale_b[0];
+  }
+}
+
 // Per-block partials of a reduction over v: compensated sums (RED_SUM, RED_VAR
 // about sc[S_MEAN], RED_SQ) stored as Acc<T>; RED_MAXABS stores the block
 // maximum as a double.
@@ -212,8 +266,15 @@ int launch_reduce(const T* v, size_t N, int op, const double* sc, double* partia
 
 template <typename T>
 void launch_finalize_blocks(const double* part0, const double* part1, const int* items_as_int, int n_items, int R,
-                            double nu, const double* eps_b, double* scale_b, double* sc, cudaStream_t s) {
-  k_finalize_blocks<T><<<1, kFinT, 0, s>>>(part0, part1, items_as_int + 3, n_items, R, nu, eps_b, scale_b, sc);
+                            double nu, const double* eps_b, double* scale_b, double* sc, double* cpart,
+                            unsigned int* ticket, cudaStream_t s) {
+  if (R == 1 && cpart && ticket) {
+    int nb = (n_items + 4 * kT - 1) / (4 * kT);
+    nb = nb < 1 ? 1 : (nb > kFinCtas ? kFinCtas : nb);
+    k_finalize_ball1<T><<<nb, kT, 0, s>>>(part0, part1, n_items, nu, eps_b, scale_b, sc, cpart, ticket);
+  } else {
+    k_finalize_blocks<T><<<1, kFinT, 0, s>>>(part0, part1, items_as_int + 3, n_items, R, nu, eps_b, scale_b, sc);
+  }
 }
 
 void launch_max_partials(const double* p, int np, double* sc, cudaStream_t s) {
@@ -237,7 +298,8 @@ template <typename C> void launch_gather(const C* src, const int* perm, size_t M
   template void launch_axpy<T>(T*, const T*, const double*, int, size_t, cudaStream_t);                \
   template void launch_finalize<T>(const double*, int, int, double, double*, cudaStream_t);             \
   template void launch_finalize_blocks<T>(const double*, const double*, const int*, int, int, double,           \
-                                          const double*, double*, double*, cudaStream_t);                      \
+                                          const double*, double*, double*, double*, unsigned int*,             \
+                                          cudaStream_t);                                                       \
   template int launch_reduce<T>(const T*, size_t, int, const double*, double*, cudaStream_t);           \
   template void launch_reweight<T>(T*, size_t, double, cudaStream_t);                                   \
   template void launch_fill<T>(T*, size_t, T, cudaStream_t);                                            \

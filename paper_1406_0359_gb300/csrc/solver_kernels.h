@@ -24,10 +24,14 @@ template <typename T>
 int launch_reduce(const T* v, size_t N, int op, const double* sc, double* partials, cudaStream_t s);
 void launch_max_partials(const double* p, int np, double* sc, cudaStream_t s);
 // Ball scalars per visibility block; items_as_int points at the WorkItem array
-// (four ints per item, the block in the fourth).
+// (four ints per item, the block in the fourth).  With R = 1, cpart (2 x
+// kFinCtas doubles) and a zeroed ticket, the merge runs on up to kFinCtas
+// CTAs in two levels; otherwise on one CTA.
+constexpr int kFinCtas = 64;
 template <typename T>
 void launch_finalize_blocks(const double* part0, const double* part1, const int* items_as_int, int n_items, int R,
-                            double nu, const double* eps_b, double* scale_b, double* sc, cudaStream_t s);
+                            double nu, const double* eps_b, double* scale_b, double* sc, double* cpart,
+                            unsigned int* ticket, cudaStream_t s);
 template <typename T> void launch_reweight(T* w, size_t N, double delta, cudaStream_t s);
 template <typename T> void launch_fill(T* v, size_t N, T val, cudaStream_t s);
 template <typename T> void launch_scale(T* v, size_t N, const double* sc, int idx, double mul, cudaStream_t s);
