@@ -291,7 +291,11 @@ def run_ours(args, ws, rank, local):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(uv_h, x_h, n, L, reps=1)
+        y1 = op.phi(xt)
+        gpu_out = {"phi": y1.cpu().numpy().astype(np.complex128),
+                   "phi_adj_phi": op.phi_adj(y1).cpu().numpy().astype(np.float64),
+                   "psi_h": op.sara_fwd(xt).cpu().numpy().astype(np.float64)}
+        cpu = cpu_baseline(uv_h, x_h, n, L, reps=1, gpu=gpu_out)
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": K,
@@ -325,9 +329,10 @@ def run_ours(args, ws, rank, local):
 
 
 # ----------------------------------------------------------------- oracle timing
-def oracle_sample_times(uv, x, n, L, reps):
+def oracle_sample_times(uv, x, n, L, reps, keep=False):
     """Time the oracle's Phi + Phi^H pair (reps times) and one Psi^H + Psi pair at
-    full size; returns (median pair s, psi s, build s)."""
+    full size; returns (median pair s, psi s, build s, outputs): outputs holds the
+    last pair's Phi x and Re Phi^H Phi x and Psi^H x when keep is set."""
     import numpy as np
 
     from oracle import sara
@@ -339,21 +344,33 @@ def oracle_sample_times(uv, x, n, L, reps):
     pairs = []
     for _ in range(reps):
         t = time.perf_counter()
-        op.phi_adj_real(op.phi(x))
+        yx = op.phi(x)
+        gx = op.phi_adj_real(yx)
         pairs.append(time.perf_counter() - t)
     t = time.perf_counter()
-    sara.synthesis(sara.analysis(x, L), L)
+    cx = sara.analysis(x, L)
+    sara.synthesis(cx, L)
     psi = time.perf_counter() - t
-    return statistics.median(pairs), psi, build
+    outs = {"phi": yx, "phi_adj_phi": gx, "psi_h": cx} if keep else None
+    return statistics.median(pairs), psi, build, outs
 
 
-def cpu_baseline(uv, x, n, L, reps=1):
-    pair, psi, build = oracle_sample_times(uv, x, n, L, reps)
+def cpu_baseline(uv, x, n, L, reps=1, gpu=None):
+    """The oracle leg: its time per SDMM iteration and, when the GPU path's FP32
+    outputs for the same x are given (gpu: phi, phi_adj_phi, psi_h as NumPy
+    arrays), their relative L2 errors against the oracle's outputs."""
+    import numpy as np
+
+    pair, psi, build, outs = oracle_sample_times(uv, x, n, L, reps, keep=gpu is not None)
     it = 12 * pair + psi  # 11 Re Phi^H Phi (CG) + Phi and Phi^H (ball block) + Psi^H, Psi
-    return {"value": round(1.0 / it, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{reps} oracle Phi+Phi^H pair(s) and one Psi^H+Psi at full size, SDMM iteration "
-                      f"extrapolated as 12 pairs + 1 Psi pair ({pair:.2f} s per pair, {psi:.2f} s Psi; "
-                      f"operator build {build:.1f} s untimed); NumPy/SciPy single-threaded"}
+    out = {"value": round(1.0 / it, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{reps} oracle Phi+Phi^H pair(s) and one Psi^H+Psi at full size, SDMM iteration "
+                     f"extrapolated as 12 pairs + 1 Psi pair ({pair:.2f} s per pair, {psi:.2f} s Psi; "
+                     f"operator build {build:.1f} s untimed); NumPy/SciPy single-threaded"}
+    if gpu is not None:
+        out["fp32_vs_oracle"] = {k: float(np.linalg.norm(gpu[k] - outs[k]) / np.linalg.norm(outs[k]))
+                                 for k in ("phi", "phi_adj_phi", "psi_h")}
+    return out
 
 
 def run_reference(args, ws, rank):
