@@ -54,3 +54,35 @@ def test_memory_estimate_is_monotone_without_gpu():
     assert binding.purify_estimate_bytes(200_000, 256, 4) > a
     assert binding.purify_estimate_bytes(100_000, 512, 4) > a
     assert binding.purify_estimate_bytes(100_000, 256, 4, binding.PURIFY_FP64) > a
+
+
+def test_invalid_arguments_are_rejected_before_any_device_work():
+    """Argument checks of the C-ABI run before any CUDA call, so they can be
+    exercised without a GPU: every bad size, option or null pointer returns
+    PURIFY_ERR_INVALID (the uv pointer below is never dereferenced)."""
+    from paper_1406_0359_gb300 import binding, build
+
+    build.build()
+    L = binding.lib()
+    INV = -1  # PURIFY_ERR_INVALID
+    fake = ctypes.c_void_p(256)
+    h = ctypes.c_void_p()
+    F32 = binding.PURIFY_FP32
+
+    def create(uv=fake, M=4096, n=64, over=2, J=8, levels=3, prec=F32, out=True):
+        return L.purify_op_create(uv, M, n, over, J, levels, prec, None, ctypes.byref(h) if out else None)
+
+    bad = [dict(uv=None), dict(M=0), dict(M=1 << 31), dict(n=8), dict(n=100), dict(n=4096), dict(over=3),
+           dict(J=6), dict(levels=0), dict(n=16, levels=4), dict(prec=7), dict(out=False)]
+    for kw in bad:
+        assert create(**kw) == INV, kw
+    assert h.value is None
+    opt = binding.purify_op_options(tile=12, chunk=0)
+    assert L.purify_op_create_ex(fake, 4096, 64, 2, 8, 3, F32, ctypes.byref(opt), None, ctypes.byref(h)) == INV
+    opt = binding.purify_op_options(tile=8, chunk=32)
+    assert L.purify_op_create_ex(fake, 4096, 64, 2, 8, 3, F32, ctypes.byref(opt), None, ctypes.byref(h)) == INV
+    for f in ("purify_phi", "purify_phi_adj", "purify_sara_fwd", "purify_sara_adj"):
+        assert getattr(L, f)(None, fake, fake, None) == INV, f
+    assert L.purify_gram(None, fake, fake, 1, None) == INV
+    assert L.purify_op_set_dictionary(None, 1) == INV
+    assert L.purify_op_destroy(None) == 0
