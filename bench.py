@@ -122,7 +122,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "window": "the same SDMM iterations for ~0.6 s, then the timed region"}
 
 
 def algorithmic_bytes(kind: str, n: int, M: int, rsize: int = 4) -> float:
@@ -201,6 +201,13 @@ def run_ours(args, ws, rank, local):
     kw["t_max"] = K
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        # nvidia-smi samples every 200 ms, longer than a short timed region:
+        # keep the GPU on the same iterations for ~0.6 s first, so that the
+        # samples describe the clocks under this load up to the timed region
+        t_load = time.perf_counter() + 0.6
+        while time.perf_counter() < t_load:
+            op.solve(y, eps, **dict(kw, t_max=max(K, 20)))
+            torch.cuda.synchronize()
         barrier()
         e0.record()
         res = op.solve(y, eps, **kw)
