@@ -106,3 +106,29 @@ def test_full_small_config_matches_oracle(prec):
     xg = host(res.x)
     assert rel(xg, x_ref) < IMG_TOL[prec]
     assert abs(simulate.snr_db(P["x_true"], xg) - simulate.snr_db(P["x_true"], x_ref)) < 0.05
+
+
+def test_full_size_sara_and_fp32_solve_against_references():
+    """1024^2 sky, 4,194,304 uv points, 4 levels (the bench workload): Psi^H
+    and Psi against the oracle over the whole image, and three SDMM
+    iterations of the FP32 path (graph, convolution-form CG) against the same
+    iterations in FP64 on the GPU (NUFFT-form CG)."""
+    from oracle import sara as osara
+    from paper_1406_0359_gb300.binding import Operator
+
+    w = synth.WORKLOADS["large_1024"]
+    n, M, L = w.n, w.M, w.levels
+    uv = synth.uv_coverage(M, n, w.seed)
+    x = synth.sky(n, w.seed, w.n_blobs, w.n_points)
+    op = Operator(torch.as_tensor(uv).cuda(), n, L, "fp32")
+    c = op.sara_fwd(to_dev(x, "fp32"))
+    c_ref = osara.analysis(x, L)
+    assert rel(host(c), c_ref) < 1e-5
+    assert rel(host(op.sara_adj(c)), osara.synthesis(c_ref, L)) < 1e-5
+    y = op.phi(to_dev(x, "fp32"))
+    eps = 0.05 * float(torch.linalg.vector_norm(y))
+    r32 = op.solve(y, eps, t_max=3, cg_iters=w.cg_iters)
+    op64 = Operator(torch.as_tensor(uv).cuda(), n, L, "fp64")
+    r64 = op64.solve(y.to(torch.complex128), eps, t_max=3, cg_iters=w.cg_iters, nu=r32.stats["nu"],
+                     gamma=r32.stats["gamma"], gram=0, use_graph=False)
+    assert rel(host(r32.x), host(r64.x)) < 1e-4
