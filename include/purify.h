@@ -195,8 +195,9 @@ int purify_op_set_blocks(purify_op* op, const int* block_ids, int R, void* strea
  *           (from the NUFFT adjoint of unit visibilities on a 2n x 2n image)
  *           applied as a circular convolution on the 2n grid; needs n <= 1024.
  *           It equals the exact (NUDFT) normal operator up to the NUFFT error
- *           of the PSF.  The first call builds and keeps the spectrum
- *           (K^2 reals of operator memory; synchronises `stream`).
+ *           of the PSF.  The first call builds and keeps the real half
+ *           spectrum ((K/2 + 1) K reals of operator memory; its set-up
+ *           buffers come from the set-up pool; synchronises `stream`).
  *   x, out  device, real[n][n].
  */
 int purify_gram(purify_op* op, const void* x, void* out, int mode, void* stream);
