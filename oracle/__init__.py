@@ -22,7 +22,9 @@ Modules:
   simulate       input-SNR noise rule, epsilon rule, SNR metric
 
 Parity status: every function here is pinned by a test under tests/ against
-a closed form, a brute-force computation or a library routine, except the
-SARA reweighting schedule (the paper gives only its shape; "parity
-unpinned" for the delta schedule, see sdmm.delta_schedule).
+a closed form, a brute-force computation, a certificate or a library
+routine.  The SARA weight rule and the reweighting loop are pinned as a
+majorise-minimise descent at fixed delta; the delta schedule itself
+(sdmm.delta_schedule) is a reading the paper does not fix: "parity unpinned"
+for it.
 """

@@ -1,8 +1,8 @@
 """Kaiser-Bessel interpolation kernel (oracle, FP64, test infrastructure only).
 
-The paper's measurement operator is a non-uniform FFT that maps a discrete
-image to continuous visibilities (Section 4); the kernel is Kaiser-Bessel
-with support J and 2x oversampling.  The paper does not give beta; the
+Section 4 computes the measurement operator with an NUFFT (image pixels to
+visibilities at off-grid uv points); here its interpolation kernel is
+Kaiser-Bessel with support J and 2x oversampling.  The paper does not give beta; the
 reading used is the Beatty et al. (2005) rule
     beta = pi * sqrt((J/alpha)^2 (alpha - 1/2)^2 - 0.8),
 which is 18.639 for J = 8, alpha = 2.

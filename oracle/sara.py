@@ -1,8 +1,8 @@
 """SARA dictionary Psi = [Psi_1, ..., Psi_9] and its sub-dictionaries
 (oracle, FP64, test infrastructure only).
 
-Section 2.2: the dictionary concatenates the Dirac basis and the first eight
-orthonormal Daubechies bases (q = 9, D = 9N).  The paper does not write the
+Section 2.2: q = 9 bases side by side -- the identity (Dirac) and the
+orthonormal Daubechies wavelets Db1 to Db8 (D = 9N coefficients).  The paper does not write the
 normalisation; Section 3 uses Psi Psi^H = I (the composite operator
 sum_i L_i^H L_i = Phi^H Phi + 2I), which holds when every one of the q bases
 is scaled by 1/sqrt(q) (reading; 1/3 for SARA).  Coefficients are stored

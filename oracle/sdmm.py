@@ -160,7 +160,8 @@ def sdmm(op, psi, y, eps, gamma, w, t_max, cg_iters, nu, x0=None, xi=0.0, blocks
 
 
 def delta_schedule(alpha0: np.ndarray, k: int, decay: float = 0.1, delta0=None, delta_min=None) -> float:
-    """Reweighting parameter for round k >= 1 (reading; parity unpinned):
+    """Reweighting parameter for round k >= 1 (reading; parity unpinned: the
+    paper fixes no schedule, and no identity constrains one):
     delta_1 = std of the round-0 coefficients (or delta0 when given, 1 when
     the coefficients are all zero), delta_k = max(decay^(k-1) delta_1, delta_min),
     delta_min defaulting to 1e-4 delta_1."""
@@ -172,8 +173,11 @@ def delta_schedule(alpha0: np.ndarray, k: int, decay: float = 0.1, delta0=None, 
 
 
 def reweight(alpha: np.ndarray, delta: float) -> np.ndarray:
-    """SARA weights w_j = delta / (delta + |alpha_j|) (Section 2.2: weights are
-    essentially the inverse of the previous solution's coefficients)."""
+    """SARA weights w_j = delta / (delta + |alpha_j|) (Section 2.2: each round's
+    weight on a coefficient falls off as the inverse of that coefficient's
+    magnitude in the previous solution; delta keeps it finite).  Pinned as a
+    majorise-minimise step: at fixed delta the rounds descend
+    sum_j log(delta + |alpha_j|) (tests/test_oracle_solver.py)."""
     return delta / (delta + np.abs(alpha))
 
 

@@ -217,6 +217,73 @@ def test_reweighting_rule():
     assert w[2] == pytest.approx(0.5 / 3.5)
 
 
+# ------------------------------------------------ reweighting as majorise-minimise
+# Section 2.2 replaces the l0 prior by a sequence of weighted l1 problems whose
+# weights come from the previous solution.  With w_j = delta / (delta + |a_j|)
+# each round minimises, over the feasible set of problem (3), the linearisation
+# at the previous solution of the concave penalty P(x) = sum_j log(delta +
+# |(Psi^H x)_j|) (up to the constant factor delta).  Its tangent majorises P,
+# so at a fixed delta every round that is solved to optimality cannot increase
+# P (Candes, Wakin & Boyd 2008).  The pin runs the oracle's own SARA loop with a
+# constant delta (decay 1, delta_min = delta0), certifies each round's optimality
+# against the weights of the round before, and checks that P never rises.
+def _mm_rounds(rounds, iters, reweight=None, monkeypatch=None):
+    T = tiny_problem()
+    gamma = 10.0 * S.default_gamma(T["dop"], T["dpsi"], T["y"], T["nu"])
+    x0 = S.sdmm(T["dop"], T["dpsi"], T["y"], T["eps"], gamma, np.ones(9 * 64), iters, 20, T["nu"]).x
+    delta = float(np.std(T["dpsi"].analysis(x0)))
+    if reweight is not None:
+        monkeypatch.setattr(S, "reweight", reweight)
+    _, sts = S.sara_solve(T["dop"], T["dpsi"], T["y"], T["eps"], gamma, iters, 20, T["nu"], rounds,
+                          decay=1.0, delta0=delta, delta_min=delta)
+    pen = [float(np.sum(np.log(delta + np.abs(T["dpsi"].analysis(st.x))))) for st in sts]
+    return T, gamma, delta, sts, np.array(pen)
+
+
+@pytest.mark.slow
+def test_reweighted_rounds_descend_the_log_penalty():
+    T, gamma, delta, sts, pen = _mm_rounds(3, 1500)
+    assert np.all(np.diff(pen) < 1e-7 * np.abs(pen[0]))  # P never rises
+    assert pen[1] < pen[0] - 1e-3  # the first reweighting makes real progress
+    for k in range(1, len(sts)):
+        # round k is optimal for the weights taken from round k - 1's solution
+        w = S.reweight(T["dpsi"].analysis(sts[k - 1].x), delta)
+        gap, resid = _duality_gap(T, sts[k], w, gamma)
+        assert abs(gap) < 1e-7 and resid < 1e-6
+        assert np.linalg.norm(T["y"] - T["dop"].phi(sts[k].x)) <= T["eps"] * (1 + 1e-6)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("plant", ["signed", "inverted", "squared"])
+def test_planted_reweighting_mistakes_break_the_descent(plant, monkeypatch):
+    """Plausible slips in the weight rule: the sign of the coefficient kept
+    (no absolute value), the weight inverted, the denominator squared.  Each
+    lets the log-penalty rise between rounds, which the pin above forbids."""
+    bad = {"signed": lambda a, d: d / (d + a),
+           "inverted": lambda a, d: (d + np.abs(a)) / d,
+           "squared": lambda a, d: d / (d + np.abs(a)) ** 2}[plant]
+    _, _, _, _, pen = _mm_rounds(3, 1500, bad, monkeypatch)
+    assert np.max(np.diff(pen)) > 1e-3
+
+
+@pytest.mark.slow
+def test_stale_reweighting_coefficients_fail_the_certificate(monkeypatch):
+    """Weights computed once from the first solution and reused (the wrong
+    round's coefficients) leave later rounds optimal for stale weights: the
+    certificate against the previous round's weights no longer closes."""
+    rule = S.reweight
+    first = {}
+
+    def stale(a, d):
+        first.setdefault("a", np.array(a, copy=True))
+        return rule(first["a"], d)
+
+    T, gamma, delta, sts, _ = _mm_rounds(2, 1500, stale, monkeypatch)
+    w = rule(T["dpsi"].analysis(sts[1].x), delta)
+    gap, _ = _duality_gap(T, sts[2], w, gamma)
+    assert abs(gap) > 1e-5
+
+
 def test_sara_outer_loop_runs_and_is_feasible():
     T = tiny_problem()
     gamma = 10.0 * S.default_gamma(T["dop"], T["dpsi"], T["y"], T["nu"])
