@@ -6,7 +6,8 @@ on Psi^H x (analysis with the fused prox), the positivity block, the l2-ball
 block (Phi, projection, Phi^H) -- every kernel of the hot path.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
-on the host cores instead (bounded sample, extrapolated; see ``sample``).
+on the host cores instead: real oracle SDMM iterations of the same workload,
+as many as fit a bounded time (``steps`` reports how many were timed).
 Under torchrun every rank runs its own independent solve (replicas, weak
 scaling); the time is the maximum over ranks.
 """
@@ -125,12 +126,26 @@ class ClockSampler:
                 "samples": len(sm), "window": "the same SDMM iterations for ~0.6 s, then the timed region"}
 
 
-def algorithmic_bytes(kind: str, n: int, M: int, rsize: int = 4) -> float:
+def workload_string(name: str, w) -> str:
+    """The workload description both arms print in config.workload."""
+    return (f"{name}: {w.n}x{w.n} sky, M={w.M} uv points, {2 * w.n}^2 grid, J=8, SARA {w.levels} levels, "
+            f"{w.cg_iters} CG steps per iteration")
+
+
+def algorithmic_bytes(kind: str, n: int, M: int, rsize: int = 4, levels: int = 4, cg: int = 10) -> float:
     """Bytes each kernel kind must move per launch (FP32: 4-byte reals, 8-byte
-    complex).  N = n^2 pixels; the oversampled grid holds 4N complex cells."""
+    complex).  N = n^2 pixels; the oversampled grid holds 4N complex cells.
+    The SARA sets count one launch set (all levels) in their SDMM form:
+    analysis with the l1 prox (x in; z_1, w in, z_1 and 2r - v out for the
+    9N coefficients; LL scratch bands out and in level by level), synthesis
+    with the positivity block (2r - v in, scratch bands, x_hat and z_2 in,
+    z_2 and x_1 + x_2 out)."""
     N = n * n
     c = 2 * rsize
+    band = sum(8 * (N >> (2 * lev)) for lev in range(1, levels))  # 8 filters' LL bands of levels 1..L-1
     table = {
+        "sara_analysis": N * rsize + 9 * N * 4 * rsize + 2 * band * rsize,
+        "sara_synthesis": 9 * N * rsize + 2 * band * rsize + 4 * N * rsize,
         "gram": 4 * N * c * 2 + 8 * M,          # read grid, write grid accumulator, read positions
         "degrid": 4 * N * c + 8 * M + 3 * c * M,  # grid + positions + (z read, y read, z write)
         "grid": 4 * N * c + 8 * M + 3 * c * M,    # grid write + positions + (z, y read, z write)
@@ -139,10 +154,14 @@ def algorithmic_bytes(kind: str, n: int, M: int, rsize: int = 4) -> float:
         "col_fwd": N * c + 4 * N * c,             # half-spectrum rows in, full grid out
         "col_inv": 4 * N * c + N * c,             # accumulator in, half-spectrum rows out
         "row_inv": N * c + 2 * N * rsize,         # half-spectrum rows in, image in/out (epilogue)
-        # convolution form (real image, half spectra n x n complex)
-        "row_fwd_h": 3 * N * rsize + N * c,       # r, p in, p out (CG direction), half-spectrum rows out
+        # convolution form (real image, half spectra n x n complex), averaged
+        # over the cg + 1 launches of one CG: the first two forward passes
+        # read one image (x_hat, then p), the other cg - 1 apply the CG update
+        # (x, r, p, Ap in; x, r, p out); the first inverse pass forms r and p
+        # (b, x_hat in; r, p out), the other cg form Ap (p, r in; Ap out)
+        "row_fwd_h": (2 * (N * rsize + N * c) + (cg - 1) * (7 * N * rsize + N * c)) / (cg + 1),
         "col_conv": N * c + 2 * N * rsize + N * c,  # half-spectrum rows in, PSF half spectrum, rows out
-        "row_inv_h": N * c + 2 * N * rsize,       # half-spectrum rows in, p in, image out
+        "row_inv_h": ((N * c + 4 * N * rsize) + cg * (N * c + 3 * N * rsize)) / (cg + 1),
     }
     return float(table.get(kind, 0))
 
@@ -226,12 +245,18 @@ def run_ours(args, ws, rank, local):
     dom = max(busy, key=lambda k: busy[k][0])
     dom_ms, dom_n = busy[dom]
     hbm, peak_kind = peaks()
-    bytes_launch = algorithmic_bytes(dom, n, M)
+    bytes_launch = algorithmic_bytes(dom, n, M, levels=L, cg=w.cg_iters)
     achieved = bytes_launch / (dom_ms / dom_n / 1e3) / 1e9
     kernels_per_call = {"sara_analysis": 1 + L, "sara_synthesis": L}
     launches = sum(v[1] * kernels_per_call.get(k, 1) for k, v in kt.items() if k != "memset")
-    per_kernel = {k: {"ms_per_launch": round(v[0] / v[1], 4), "launches": v[1],
-                      "share": round(v[0] / total_busy, 4)} for k, v in busy.items()}
+    per_kernel = {}
+    for k, v in busy.items():
+        e = {"ms_per_launch": round(v[0] / v[1], 4), "launches": v[1], "share": round(v[0] / total_busy, 4)}
+        b = algorithmic_bytes(k, n, M, levels=L, cg=w.cg_iters)
+        if b > 0:  # achieved algorithmic GB/s and its fraction of the measured HBM copy peak
+            gbs = b / (v[0] / v[1] / 1e3) / 1e9
+            e.update({"bytes_per_launch": b, "gbs": round(gbs, 1), "frac_of_hbm_peak": round(gbs / hbm, 4)})
+        per_kernel[k] = e
 
     # Phi + Phi^H throughput (visibilities per second)
     reps = max(3, K // 2)
@@ -302,14 +327,13 @@ def run_ours(args, ws, rank, local):
         gpu_out = {"phi": y1.cpu().numpy().astype(np.complex128),
                    "phi_adj_phi": op.phi_adj(y1).cpu().numpy().astype(np.float64),
                    "psi_h": op.sara_fwd(xt).cpu().numpy().astype(np.float64)}
-        cpu = cpu_baseline(uv_h, x_h, n, L, reps=1, gpu=gpu_out)
+        cpu = cpu_baseline(args.workload, gpu=gpu_out)
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(ms / K, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (compensated reductions, FP64 finals)", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {n}x{n} sky, M={M} uv points, 2048^2 grid, J=8, "
-                               f"SARA {L} levels, {w.cg_iters} CG steps per iteration",
+        "config": {"workload": workload_string(args.workload, w),
                    "global_batch": ws, "parallelism": f"replicas x{ws}",
                    "l2": "per-iteration working set ~0.4 GB > 129 MB L2 (no flush needed)"},
         "phi_phiH_vis_per_s": round(vis_per_s, 1),
@@ -336,85 +360,118 @@ def run_ours(args, ws, rank, local):
 
 
 # ----------------------------------------------------------------- oracle timing
-def oracle_sample_times(uv, x, n, L, reps, keep=False):
-    """Time the oracle's Phi + Phi^H pair (reps times) and one Psi^H + Psi pair at
-    full size; returns (median pair s, psi s, build s, outputs): outputs holds the
-    last pair's Phi x and Re Phi^H Phi x and Psi^H x when keep is set."""
+def _oracle_setup(name, seed_offset=0):
+    """The oracle's operator, dictionary and a measured problem of the named
+    workload (same synthetic inputs as the GPU arm); build time untimed."""
     import numpy as np
 
-    from oracle import sara
+    from oracle import sdmm as osdmm
+    from oracle import simulate
     from oracle.nufft import NUFFT
+    from paper_1406_0359_gb300 import synth
 
+    w = synth.WORKLOADS[name]
+    seed = w.seed + seed_offset
+    uv = synth.uv_coverage(w.M, w.n, seed)
+    x = synth.sky(w.n, seed, w.n_blobs, w.n_points)
     t = time.perf_counter()
-    op = NUFFT(uv, n)
+    op = NUFFT(uv, w.n)
     build = time.perf_counter() - t
-    pairs = []
-    for _ in range(reps):
-        t = time.perf_counter()
-        yx = op.phi(x)
-        gx = op.phi_adj_real(yx)
-        pairs.append(time.perf_counter() - t)
+    a, b = synth.noise_draws(w.M, seed)
+    y, sigma = simulate.add_noise(op.phi(x), w.isnr_db, a, b)
+    psi = osdmm.SaraDictionary(w.levels)
+    nu = 1.0 / math.sqrt(osdmm.operator_norm_sq(op, 3))  # any nu > 0 leaves problem (3) unchanged
+    gamma = osdmm.default_gamma(op, psi, y, nu)
+    return dict(w=w, op=op, psi=psi, x=x, y=y, eps=simulate.epsilon(sigma, w.M), nu=nu, gamma=gamma,
+                build_s=build, weights=np.ones((9, w.n, w.n)))
+
+
+def _oracle_iteration(S, st):
+    """One real oracle SDMM iteration (Algorithm 1 steps 5-10, 10 CG steps), timed."""
+    from oracle import sdmm as osdmm
+
+    w = S["w"]
     t = time.perf_counter()
-    cx = sara.analysis(x, L)
-    sara.synthesis(cx, L)
-    psi = time.perf_counter() - t
-    outs = {"phi": yx, "phi_adj_phi": gx, "psi_h": cx} if keep else None
-    return statistics.median(pairs), psi, build, outs
+    osdmm.sdmm_iteration(st, S["op"], S["psi"], S["y"], S["eps"], S["gamma"], S["weights"], w.cg_iters, S["nu"])
+    return time.perf_counter() - t
 
 
-def cpu_baseline(uv, x, n, L, reps=1, gpu=None):
-    """The oracle leg: its time per SDMM iteration and, when the GPU path's FP32
-    outputs for the same x are given (gpu: phi, phi_adj_phi, psi_h as NumPy
-    arrays), their relative L2 errors against the oracle's outputs."""
+def _oracle_threads() -> str:
+    return (f"scipy.fft on all {os.cpu_count()} host cores (workers=-1); sparse gridding/degridding and "
+            f"elementwise NumPy single-threaded")
+
+
+def cpu_baseline(name, gpu=None):
+    """The oracle leg of the GPU arm: ONE real oracle SDMM iteration of the
+    bench workload timed on the host cores, the extrapolation from one
+    Phi + Phi^H pair beside it as a labelled cross-check, and -- when the GPU
+    path's FP32 outputs for the same sky are given (gpu: phi, phi_adj_phi,
+    psi_h) -- their relative L2 errors against the oracle's."""
     import numpy as np
 
-    pair, psi, build, outs = oracle_sample_times(uv, x, n, L, reps, keep=gpu is not None)
-    it = 12 * pair + psi  # 11 Re Phi^H Phi (CG) + Phi and Phi^H (ball block) + Psi^H, Psi
-    out = {"value": round(1.0 / it, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"{reps} oracle Phi+Phi^H pair(s) and one Psi^H+Psi at full size, SDMM iteration "
-                     f"extrapolated as 12 pairs + 1 Psi pair ({pair:.2f} s per pair, {psi:.2f} s Psi; "
-                     f"operator build {build:.1f} s untimed); NumPy/SciPy single-threaded"}
+    from oracle import sara as osara
+    from oracle import sdmm as osdmm
+
+    S = _oracle_setup(name)
+    op, x, L = S["op"], S["x"], S["w"].levels
+    st = osdmm.sdmm_init(op, S["psi"], np.zeros_like(x), S["nu"])
+    it_s = _oracle_iteration(S, st)
+    t = time.perf_counter()
+    yx = op.phi(x)
+    gx = op.phi_adj_real(yx)
+    pair = time.perf_counter() - t
+    t = time.perf_counter()
+    cx = osara.analysis(x, L)
+    osara.synthesis(cx, L)
+    psi = time.perf_counter() - t
+    out = {"value": round(1.0 / it_s, 5), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"one full oracle SDMM iteration of the bench workload ({w_iter(S)}), {it_s:.1f} s; "
+                     f"{_oracle_threads()}; operator build {S['build_s']:.1f} s untimed",
+           "extrapolated_cross_check": {"iters_per_s": round(1.0 / (12 * pair + psi), 5),
+                                        "from": f"12 Phi+Phi^H pairs ({pair:.2f} s each) + one Psi^H+Psi ({psi:.2f} s)"}}
     if gpu is not None:
+        outs = {"phi": yx, "phi_adj_phi": gx, "psi_h": cx}
         out["fp32_vs_oracle"] = {k: float(np.linalg.norm(gpu[k] - outs[k]) / np.linalg.norm(outs[k]))
                                  for k in ("phi", "phi_adj_phi", "psi_h")}
     return out
 
 
+def w_iter(S) -> str:
+    w = S["w"]
+    return f"{w.cg_iters} CG steps, l1, positivity and l2-ball blocks"
+
+
 def run_reference(args, ws, rank):
+    """The reference arm: the FP64 oracle on the host cores, each timed step
+    one real SDMM iteration of the bench workload.  Iterations run until
+    `steps` are timed or the time cap is reached; `steps` reports how many
+    were timed (one iteration takes tens of seconds on the CPU)."""
     if rank != 0:
         return
-    from paper_1406_0359_gb300 import synth
-
-    w = synth.WORKLOADS[args.workload]
-    n, M, L = w.n, w.M, w.levels
-    uv = synth.uv_coverage(M, n, w.seed)
-    x = synth.sky(n, w.seed, w.n_blobs, w.n_points)
     import numpy as np
 
-    from oracle import sara
-    from oracle.nufft import NUFFT
+    from oracle import sdmm as osdmm
+    from paper_1406_0359_gb300 import synth
 
-    op = NUFFT(uv, n)
-    t = time.perf_counter()
-    sara.synthesis(sara.analysis(x, L), L)
-    psi = time.perf_counter() - t
-    for _ in range(args.warmup):
-        op.phi_adj_real(op.phi(x))
+    cap_s = float(os.environ.get("PURIFY_REFERENCE_SECONDS", "120"))
+    S = _oracle_setup(args.workload)
+    st = osdmm.sdmm_init(S["op"], S["psi"], np.zeros_like(S["x"]), S["nu"])
     times = []
-    for _ in range(args.steps):
-        t = time.perf_counter()
-        op.phi_adj_real(op.phi(x))
-        times.append(time.perf_counter() - t)
-    pair = statistics.median(times)
-    step = 12 * pair + psi
-    value = 1.0 / step
-    sample = (f"each step one oracle Phi+Phi^H pair at full size; SDMM iteration extrapolated as 12 pairs "
-              f"+ one Psi^H+Psi ({pair:.2f} s per pair, {psi:.2f} s Psi); NumPy/SciPy single-threaded")
-    out = {"metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": round(step * 1e3, 1), "higher_is_better": True,
+    while len(times) < args.steps and sum(times) < cap_s:
+        times.append(_oracle_iteration(S, st))
+    total = sum(times)
+    value = len(times) / total
+    w = synth.WORKLOADS[args.workload]
+    sample = (f"{len(times)} real oracle SDMM iterations of the bench workload from x = 0 ({w_iter(S)}), "
+              f"{total:.1f} s in all (cap {cap_s:.0f} s, {args.steps} requested); {_oracle_threads()}; "
+              f"operator build {S['build_s']:.1f} s and set-up untimed, no warm-up iteration")
+    out = {"metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": ws, "steps": len(times),
+           "steps_requested": args.steps, "warmup": 0, "warmup_requested": args.warmup,
+           "ms_per_step": round(total / len(times) * 1e3, 1), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": f"{args.workload}: {n}x{n} sky, M={M} uv points, 2048^2 grid, J=8, SARA {L} levels"},
-           "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "config": {"workload": workload_string(args.workload, w)},
+           "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": sample},
            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

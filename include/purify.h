@@ -49,7 +49,9 @@ enum purify_status {
   PURIFY_ERR_CUDA = -3,          /* a CUDA runtime call failed */
   PURIFY_ERR_TIMEOUT = -4,       /* a bounded device-side wait gave up */
   PURIFY_ERR_NOT_CONVERGED = -5, /* halting rule not met within t_max (x is still valid) */
-  PURIFY_ERR_BUDGET = -6         /* request exceeds the configured device-memory budget */
+  PURIFY_ERR_BUDGET = -6,        /* request exceeds the configured device-memory budget */
+  PURIFY_ERR_CANCELLED = -7,     /* request cancelled by purify_server_cancel */
+  PURIFY_ERR_NONFINITE = -8      /* the solve's objective or residual became NaN or infinite */
 };
 
 /*
@@ -66,6 +68,7 @@ enum purify_status {
  *   precision   PURIFY_FP32 (float storage, FP64 reductions) or PURIFY_FP64.
  *   stream      stream for the set-up kernels (uv binning, tables).
  *   out         receives the new operator; untouched on error.
+ * PURIFY_ERR_INVALID (purify_last_error says which) for a non-finite uv.
  * The operator owns device copies of the sorted uv tiles and tables and is
  * released by purify_op_destroy.  Synchronises `stream` before returning.
  * Set-up temporaries (binning scratch; later, the PSF operator of the
@@ -150,10 +153,15 @@ int purify_sara_adj(purify_op* op, const void* c, void* x, void* stream);
  * The multi-level scratch lives in one fixed 4 MiB device array per device,
  * held until the process exits.  The first call on a device looks up that
  * array's device address (cudaGetSymbolAddress) with the device current;
- * make that first call before any stream capture.  Every call shares the
- * array, which keeps the last call's contents (each call overwrites what it
- * reads, so nothing needs clearing): calls that overlap on the GPU (other
- * streams, other threads) race and must be serialised by the caller.
+ * with CUDA's lazy module loading that lookup is also what loads this
+ * function's device code and so reserves the 4 MiB: make the first call at
+ * start-up, where that one reservation is acceptable, and before any stream
+ * capture.  Later calls reserve nothing.  Every call shares the array, which
+ * keeps the last call's contents (each call overwrites what it reads, so
+ * nothing needs clearing): calls that overlap on the GPU (other streams,
+ * other threads) race and must be serialised by the caller.  A launch error
+ * is reported through cudaPeekAtLastError, which leaves the error state as
+ * it was (an error pending from earlier work is reported too).
  */
 int purify_sara_fwd_static(const float* x, float* c, int n, int levels, void* stream);
 
@@ -244,10 +252,70 @@ typedef struct {
  *   stats  host, may be NULL.
  * Blocks until the solve has finished on `stream`.  Returns
  * PURIFY_ERR_NOT_CONVERGED (with a valid x_out) when xi > 0 and the halting
- * rule was not met within t_max in the last round.
+ * rule was not met within t_max in the last round; PURIFY_ERR_INVALID for a
+ * y holding NaN or infinity (checked once at the start); PURIFY_ERR_NONFINITE
+ * when the final objective or residual is not finite; PURIFY_ERR_TIMEOUT
+ * when a bounded device wait gave up.
  */
 int purify_sdmm_solve(purify_op* op, const void* y, const purify_params* params,
                       void* x_out, purify_stats* stats, void* stream);
+
+/*
+ * Resumable solve and checkpoints.  purify_sdmm_solve is begin + steps + end
+ * in one call; the three parts are also public so that a caller can stop
+ * between SDMM iterations, save the solver state to host memory, and resume
+ * it later -- in this process or another -- on an operator built from the
+ * same uv coverage, image side, levels, precision, dictionary and blocks.
+ *
+ * purify_solve_begin -- check y, take nu and gamma (computed as in
+ *   purify_sdmm_solve when <= 0), set up round 0; y and params as for
+ *   purify_sdmm_solve (params copied; y read before the call returns).
+ * purify_solve_step -- run up to max_iters SDMM iterations (Algorithm 1 steps
+ *   5-10, rounds advancing as in the SARA loop), then wait for them; *done is
+ *   set to 1 once the last round has finished.  Returns PURIFY_ERR_TIMEOUT if
+ *   a bounded device wait gave up.
+ * purify_solve_end -- copy the last x_hat to x_out (device real[n][n]), fill
+ *   stats, release the solve; statuses as purify_sdmm_solve.
+ * purify_solve_state_bytes -- size of a checkpoint of this operator's solve.
+ * purify_solve_save -- write the state after the last completed iteration to
+ *   `host` (bytes >= purify_solve_state_bytes): a header (format version,
+ *   precision, n, M, dictionary size, blocks, round, iteration counters,
+ *   convergence state, nu, gamma, the first reweighting delta, the last
+ *   objective) followed by x_hat, sum_i x_i, z_1, z_2, the SARA weights W and
+ *   z_3 (reals of the operator's precision; z_3 in the operator's sorted
+ *   visibility order).  CG vectors are not state: every SDMM iteration
+ *   restarts its CG from x_hat.
+ * purify_solve_load -- after purify_solve_begin with the same y and
+ *   parameters, replace the fresh state by a saved one; the next
+ *   purify_solve_step continues where the saved solve stopped.
+ *   PURIFY_ERR_INVALID when the checkpoint does not match the operator.
+ * The resumed solve runs the same kernels in the same order; gridding sums
+ * with atomics, so a resumed and an uninterrupted solve agree to rounding,
+ * not bit for bit.
+ */
+int purify_solve_begin(purify_op* op, const void* y, const purify_params* params, void* stream);
+int purify_solve_step(purify_op* op, int max_iters, int* done);
+int purify_solve_end(purify_op* op, void* x_out, purify_stats* stats, void* stream);
+int purify_solve_state_bytes(const purify_op* op, int64_t* bytes);
+int purify_solve_save(purify_op* op, void* host, int64_t bytes);
+int purify_solve_load(purify_op* op, const void* host, int64_t bytes);
+
+/*
+ * Failure detection (the paper has no counterpart).  Every mbarrier wait of
+ * the library's kernels (TMA patch loads in degridding, bulk operand copies
+ * in the CG row passes) is bounded: after its budget of try-wait spins it
+ * raises a device error flag, lets any copy still in flight land (a second,
+ * fixed budget), skips its work and returns, and the next synchronising call
+ * reports PURIFY_ERR_TIMEOUT; the context stays usable.
+ * purify_set_wait_limit -- set the first-phase budget (spins; 0 restores the
+ *   default 2^24) on the current device, for tests and diagnostics.
+ * purify_wait_selftest -- one CTA arms an mbarrier for 16 bytes and, with
+ *   deliver != 0, brings them by a bulk copy (returns PURIFY_OK); with
+ *   deliver == 0 nothing is ever sent, the wait runs out of its budget and
+ *   the call returns PURIFY_ERR_TIMEOUT.  Blocks on `stream`.
+ */
+int purify_set_wait_limit(uint32_t spins);
+int purify_wait_selftest(int deliver, void* stream);
 
 /*
  * Kernel timing (instrumentation; the paper has no counterpart).  While
@@ -267,14 +335,21 @@ const char* purify_kernel_name(int kind);
 /*
  * Request server (continuous batching; the paper has no counterpart -- it is
  * the serving form of Algorithm 1 for many independent imaging requests).
- * Requests wait in a FIFO queue; each scheduling round admits queued requests
+ * Requests wait in a FIFO queue; each scheduling pass admits queued requests
  * while a slot is free and their estimated device memory
- * (purify_estimate_bytes) fits the budget, keeps each admitted solve's image,
- * dual variables and sorted uv tiles resident on the device, and advances
- * every admitted solve by one SDMM iteration on its own stream so that their
- * kernels overlap.  A finished solve frees its slot and memory for the next
- * round.  The caller drives rounds with purify_server_step; not thread-safe.
- * All solves run on the current device (at create time).
+ * (purify_estimate_bytes) fits the budget, and keeps each admitted solve's
+ * image, dual variables and sorted uv tiles resident on the device.  Every
+ * admitted solve runs one SDMM iteration at a time on its own stream, so
+ * that the solves' kernels overlap; a solve whose iteration has completed
+ * gets its halting test and its next iteration in the next pass, while one
+ * still running is left alone (no lock-step: a large image never holds back
+ * a small one).  A finished solve frees its slot and memory at once.  The
+ * device memory of admitted solves comes from a stream-ordered memory pool
+ * of the server that keeps up to `budget_bytes` mapped, so admitting and
+ * releasing solves never synchronises the device; host inputs are staged
+ * through pinned memory on the server's own stream.  The caller drives the
+ * server with purify_server_step; not thread-safe.  All solves run on the
+ * current device (at create time).
  */
 typedef struct purify_server purify_server;
 int purify_server_create(int64_t budget_bytes, int max_slots, purify_server** out);
@@ -282,11 +357,19 @@ int purify_server_destroy(purify_server* srv);
 /* Work decomposition used for requests of image side n (e.g. from purify_autotune). */
 int purify_server_set_options(purify_server* srv, int n, const purify_op_options* opt);
 /* Copies uv (host double[M][2]) and y (host complex[M] of the precision) and
- * queues the request; PURIFY_ERR_BUDGET if it can never fit the budget. */
+ * queues the request; PURIFY_ERR_BUDGET if it can never fit the budget;
+ * PURIFY_ERR_INVALID (purify_last_error names the array and visibility) if
+ * uv or y holds NaN or infinity -- nothing is queued then. */
 int purify_server_submit(purify_server* srv, const double* uv_host, const void* y_host, int64_t M, int n,
                          int dwt_levels, int precision, const purify_params* params, int* request_id);
-/* One scheduling round; reports how many solves are active and queued after it. */
+/* One scheduling pass; reports how many solves are active and queued after it. */
 int purify_server_step(purify_server* srv, int* n_active, int* n_queued);
+/* Cancel a queued or running request: a queued one leaves the queue; a
+ * running one is stopped between SDMM iterations (the call waits for the
+ * iteration in flight on that solve's stream only) and its memory and slot
+ * are released.  Its result is PURIFY_ERR_CANCELLED afterwards.
+ * PURIFY_ERR_INVALID for an unknown or already finished request. */
+int purify_server_cancel(purify_server* srv, int request_id);
 /* 1 and the image (host real[n][n]), stats, latency (submit to done) and
  * queueing time (submit to admission) when the request has finished; 0 while
  * it is queued or running; its negative status if it failed. */

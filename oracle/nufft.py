@@ -15,7 +15,8 @@ what the paper leaves open:
   kb(t - j), separable in u and v;
 * deapodisation S multiplies pixel p by 1 / (kb_hat(p1/K) kb_hat(p2/K)), the
   analytic kernel transform at the pixel's frequency in cycles per cell;
-* Z places pixel p at grid index p mod K; F is the unnormalised forward DFT.
+* Z places pixel p at grid index p mod K; F is the unnormalised forward DFT
+  (scipy.fft, run on every host core: the transform is the library's).
 
 The adjoint is the exact conjugate transpose of the same matrices; for a
 real image the restricted adjoint is its real part (the problem is posed on
@@ -26,6 +27,7 @@ from __future__ import annotations
 import math
 
 import numpy as np
+import scipy.fft as sfft
 import scipy.sparse as sp
 
 from .kaiser_bessel import beatty_beta, kb, kb_hat
@@ -73,14 +75,14 @@ class NUFFT:
 
     def phi(self, x: np.ndarray) -> np.ndarray:
         """Phi x = G F Z S x for an n x n image (real or complex)."""
-        ghat = np.fft.fft2(self.zs(x))
+        ghat = sfft.fft2(self.zs(x), workers=-1)
         return self.G @ ghat.reshape(-1)
 
     # --- adjoint -----------------------------------------------------------
     def phi_adj(self, y: np.ndarray) -> np.ndarray:
         """Phi^H y = S Z^T F^H G^H y as a complex n x n image."""
         ghat = (self.G.T @ np.asarray(y, dtype=np.complex128)).reshape(self.K, self.K)
-        g = np.fft.ifft2(ghat) * (self.K * self.K)  # unnormalised inverse DFT
+        g = sfft.ifft2(ghat, workers=-1) * (self.K * self.K)  # unnormalised inverse DFT
         return self.S * g[np.ix_(self.q, self.q)]
 
     def phi_adj_real(self, y: np.ndarray) -> np.ndarray:

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libpurify_gb300.so")
 PURIFY_FP32, PURIFY_FP64 = 0, 1
 _STATUS = {0: "ok", -1: "invalid argument", -2: "device allocation failed", -3: "CUDA runtime error",
            -4: "bounded device wait timed out", -5: "halting rule not met within t_max",
-           -6: "device memory budget exceeded"}
+           -6: "device memory budget exceeded", -7: "request cancelled", -8: "solve produced non-finite values"}
 
 
 class PurifyError(RuntimeError):
@@ -59,7 +59,10 @@ EXPORTS = ["purify_op_create", "purify_op_destroy", "purify_op_info", "purify_ph
            "purify_last_error", "purify_sara_fwd_static", "purify_gram", "purify_op_set_blocks",
            "purify_server_create", "purify_server_destroy", "purify_server_submit", "purify_server_step",
            "purify_server_result", "purify_estimate_bytes", "purify_op_create_ex", "purify_autotune",
-           "purify_server_set_options", "purify_op_set_dictionary", "purify_op_dictionary"]
+           "purify_server_set_options", "purify_op_set_dictionary", "purify_op_dictionary",
+           "purify_solve_begin", "purify_solve_step", "purify_solve_end", "purify_solve_state_bytes",
+           "purify_solve_save", "purify_solve_load", "purify_set_wait_limit", "purify_wait_selftest",
+           "purify_server_cancel"]
 KERNEL_KINDS = ["row_fwd", "col_fwd", "degrid", "grid", "gram", "col_inv", "row_inv", "sara_analysis",
                 "sara_synthesis", "vector", "memset", "col_conv", "row_fwd_h", "row_inv_h"]
 
@@ -109,6 +112,15 @@ def lib() -> ctypes.CDLL:
                                       ctypes.POINTER(vp)]
     L.purify_autotune.argtypes = [vp, i64, ci, ci, ci, ci, vp, ctypes.POINTER(purify_op_options),
                                   ctypes.POINTER(ctypes.c_double)]
+    L.purify_solve_begin.argtypes = [vp, vp, ctypes.POINTER(purify_params), vp]
+    L.purify_solve_step.argtypes = [vp, ci, ctypes.POINTER(ci)]
+    L.purify_solve_end.argtypes = [vp, vp, ctypes.POINTER(purify_stats), vp]
+    L.purify_solve_state_bytes.argtypes = [vp, ctypes.POINTER(i64)]
+    L.purify_solve_save.argtypes = [vp, vp, i64]
+    L.purify_solve_load.argtypes = [vp, vp, i64]
+    L.purify_set_wait_limit.argtypes = [ctypes.c_uint32]
+    L.purify_wait_selftest.argtypes = [ci, vp]
+    L.purify_server_cancel.argtypes = [vp, ci]
     L.purify_last_error.argtypes = []
     L.purify_last_error.restype = ctypes.c_char_p
     for f in EXPORTS:
@@ -234,6 +246,50 @@ def purify_sdmm_solve(h, y_ptr, params: purify_params, x_ptr, stream=None) -> tu
     return rc, st
 
 
+def purify_solve_begin(h, y_ptr, params: purify_params, stream=None) -> None:
+    _check(lib().purify_solve_begin(h, y_ptr, ctypes.byref(params), _stream(stream)), "purify_solve_begin")
+
+
+def purify_solve_step(h, max_iters: int) -> bool:
+    """Run up to max_iters SDMM iterations; True once the solve has finished."""
+    done = ctypes.c_int()
+    _check(lib().purify_solve_step(h, max_iters, ctypes.byref(done)), "purify_solve_step")
+    return bool(done.value)
+
+
+def purify_solve_end(h, x_ptr, stream=None) -> tuple[int, purify_stats]:
+    st = purify_stats()
+    rc = lib().purify_solve_end(h, x_ptr, ctypes.byref(st), _stream(stream))
+    _check(rc, "purify_solve_end", allow=(-5,))
+    return rc, st
+
+
+def purify_solve_state_bytes(h) -> int:
+    b = ctypes.c_int64()
+    _check(lib().purify_solve_state_bytes(h, ctypes.byref(b)), "purify_solve_state_bytes")
+    return b.value
+
+
+def purify_solve_save(h) -> bytes:
+    buf = ctypes.create_string_buffer(purify_solve_state_bytes(h))
+    _check(lib().purify_solve_save(h, buf, len(buf)), "purify_solve_save")
+    return buf.raw
+
+
+def purify_solve_load(h, state: bytes) -> None:
+    buf = ctypes.create_string_buffer(state, len(state))
+    _check(lib().purify_solve_load(h, buf, len(state)), "purify_solve_load")
+
+
+def purify_set_wait_limit(spins: int) -> None:
+    _check(lib().purify_set_wait_limit(spins), "purify_set_wait_limit")
+
+
+def purify_wait_selftest(deliver: bool, stream=None) -> int:
+    """Status of the bounded-wait self-test (0, or -4 when the wait gave up)."""
+    return lib().purify_wait_selftest(int(deliver), _stream(stream))
+
+
 def purify_strerror(code: int) -> str:
     return lib().purify_strerror(code).decode()
 
@@ -344,6 +400,38 @@ class Operator:
         purify_sara_adj(self.h, _dptr(c, self.rdtype, (q, n, n)), _dptr(x, self.rdtype, (n, n)), stream)
         return x
 
+    @staticmethod
+    def params(eps: float, t_max: int = 200, cg_iters: int = 10, n_reweight: int = 0, gamma: float = 0.0,
+               nu: float = 0.0, xi: float = 0.0, delta0: float = 0.0, delta_min: float = 0.0,
+               delta_decay: float = 0.1, warm_start: bool = True, power_iters: int = 30, use_graph: bool = True,
+               gram: int = -1) -> purify_params:
+        p = purify_default_params()
+        p.eps, p.gamma, p.nu, p.t_max, p.cg_iters = eps, gamma, nu, t_max, cg_iters
+        p.xi, p.n_reweight, p.delta0, p.delta_min = xi, n_reweight, delta0, delta_min
+        p.delta_decay, p.warm_start, p.power_iters, p.use_graph = delta_decay, int(warm_start), power_iters, int(use_graph)
+        p.gram = gram
+        return p
+
+    def solve_begin(self, y: torch.Tensor, eps: float, stream=None, **kw) -> None:
+        """Start a resumable solve (purify_solve_begin); keyword arguments as solve()."""
+        self._y_keep = y
+        purify_solve_begin(self.h, _dptr(y, self.cdtype, (self.M,)), self.params(eps, **kw), stream)
+
+    def solve_step(self, max_iters: int) -> bool:
+        return purify_solve_step(self.h, max_iters)
+
+    def solve_end(self, out: torch.Tensor | None = None, stream=None) -> SolveResult:
+        n = self.n
+        x = out if out is not None else torch.empty(n, n, dtype=self.rdtype, device="cuda")
+        rc, st = purify_solve_end(self.h, _dptr(x, self.rdtype, (n, n)), stream)
+        return SolveResult(x, st.as_dict(), rc)
+
+    def save_state(self) -> bytes:
+        return purify_solve_save(self.h)
+
+    def load_state(self, state: bytes) -> None:
+        purify_solve_load(self.h, state)
+
     def solve(self, y: torch.Tensor, eps: float, t_max: int = 200, cg_iters: int = 10, n_reweight: int = 0,
               gamma: float = 0.0, nu: float = 0.0, xi: float = 0.0, delta0: float = 0.0,
               delta_min: float = 0.0, delta_decay: float = 0.1, warm_start: bool = True,
@@ -412,6 +500,9 @@ class Server:
     def set_options(self, n: int, tile: int, chunk: int) -> None:
         o = purify_op_options(tile, chunk)
         _check(lib().purify_server_set_options(self.h, n, ctypes.byref(o)), "purify_server_set_options")
+
+    def cancel(self, rid: int) -> None:
+        _check(lib().purify_server_cancel(self.h, rid), "purify_server_cancel")
 
     def step(self) -> tuple[int, int]:
         a, q = ctypes.c_int(), ctypes.c_int()

@@ -198,6 +198,11 @@ template <typename T> class OpImpl : public purify_op {
   // only stream that uses them; released in stream order.
   cudaStream_t pool_stream = nullptr;
   bool items_pooled = false;  // items from the set-up pool (refined operator)
+  // Operator of the request server: every allocation comes from the server's
+  // stream-ordered pool on the operator's own stream and goes back to it in
+  // stream order, so creating and releasing solves never synchronises the
+  // device (cudaMalloc / cudaFree would stall the solves running beside).
+  cudaMemPool_t mem_pool = nullptr;
   cudaStream_t own = nullptr;  // solver stream (capturable, non-blocking)
   cudaStream_t aux = nullptr;  // second branch of an SDMM iteration (ball block)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr, ev_join = nullptr;
@@ -245,12 +250,13 @@ template <typename T> class OpImpl : public purify_op {
     }
     WorkItem* new_items = nullptr;
     int new_n = 0;
-    const int rc = build_bins<T>(uv_keep, g.M, g, chunk, pos, perm, &new_items, &new_n, s, blocks, R);
+    const int rc = build_bins<T>(uv_keep, g.M, g, chunk, pos, perm, &new_items, &new_n, s, blocks, R, mem_pool);
     if (rc) {
       note_error("uv binning failed", __LINE__, cudaGetErrorName(cudaGetLastError()));
       return rc;
     }
-    cudaFree(items);
+    CK(cudaStreamSynchronize(own));
+    free_items();
     items = new_items;
     n_items = new_n;
     nblocks = R;
@@ -258,18 +264,27 @@ template <typename T> class OpImpl : public purify_op {
     return size_partials();
   }
 
+  void free_items() {
+    if (!items) return;
+    if (items_pooled) cudaFreeAsync(items, pool_stream);
+    else if (mem_pool) cudaFreeAsync(items, own);
+    else cudaFree(items);
+    items = nullptr;
+  }
+
   ~OpImpl() override {
     run_release();
     prof_release();
     if (own) cudaStreamSynchronize(own);
-    if (items_pooled) cudaFreeAsync(items, pool_stream);
-    else cudaFree(items);
+    if (aux) cudaStreamSynchronize(aux);
+    free_items();
     if (pool_stream) {  // set-up operator: every use was on pool_stream
       for (void* a : allocs) cudaFreeAsync(a, pool_stream);
+    } else if (mem_pool) {  // server operator: both streams are idle
+      for (void* a : allocs) cudaFreeAsync(a, own);
     } else {
       for (void* a : allocs) cudaFree(a);
     }
-    if (aux) cudaStreamSynchronize(aux);
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
     if (ev_fork) cudaEventDestroy(ev_fork);
@@ -282,8 +297,15 @@ template <typename T> class OpImpl : public purify_op {
   template <typename U> int alloc(U** ptr, size_t count) {
     void* a = nullptr;
     const size_t b = count * sizeof(U) > 0 ? count * sizeof(U) : 16;
-    if (pool_stream) CK(setup_alloc(&a, b, pool_stream));
-    else CK(cudaMalloc(&a, b));
+    if (pool_stream) {
+      CK(setup_alloc(&a, b, pool_stream));
+    } else if (mem_pool) {
+      // complete before return, so that any stream may use it
+      CK(cudaMallocFromPoolAsync(&a, b, mem_pool, own));
+      CK(cudaStreamSynchronize(own));
+    } else {
+      CK(cudaMalloc(&a, b));
+    }
     allocs.push_back(a);
     bytes += int64_t(b);
     *ptr = static_cast<U*>(a);
@@ -322,8 +344,9 @@ template <typename T> class OpImpl : public purify_op {
   // (tile 8 there, 16 here), reusing its binning (items, order) instead of
   // sorting the visibilities again.
   int create(const double* uv, int64_t M, int n, int L, cudaStream_t s, int tile = 0, int chunk_opt = 0,
-             bool light_only = false, const OpImpl* refine = nullptr) {
+             bool light_only = false, const OpImpl* refine = nullptr, cudaMemPool_t pool = nullptr) {
     light = light_only || refine;
+    mem_pool = light ? nullptr : pool;
     if (light) pool_stream = s;
     g.n = n;
     g.K = 2 * n;
@@ -381,7 +404,7 @@ template <typename T> class OpImpl : public purify_op {
     if (!light && (rc = alloc(&gridP, size_t(g.KP) * g.KP))) return rc;
     if ((rc = alloc(&gridQ, size_t(g.KP) * g.KP))) return rc;
     if ((rc = alloc(&sc, kNumScalars))) return rc;
-    if ((rc = alloc(&err, 1))) return rc;
+    if ((rc = alloc(&err, 2))) return rc;  // [0] timed-out wait, [1] non-finite input
     sara.n = n;
     sara.levels = L;
     sara_select(sara, kSaraAll);
@@ -392,8 +415,9 @@ template <typename T> class OpImpl : public purify_op {
     }
     CK(cudaMemcpyAsync(deapod, hs.data(), n * sizeof(T), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(tw, htw.data(), g.K * sizeof(C), cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
     CK(cudaMemsetAsync(sc, 0, kNumScalars * sizeof(double), s));
+    if (!light) launch_check_finite<double>(uv, 2 * size_t(M), err + 1, s);
     if (!light) CK(cudaMemsetAsync(gridP, 0, grid_bytes(), s));
     if (refine) {
       n_items = refine->n_items;
@@ -402,7 +426,7 @@ template <typename T> class OpImpl : public purify_op {
       CK(cudaMemcpyAsync(items, refine->items, size_t(n_items) * sizeof(WorkItem), cudaMemcpyDeviceToDevice, s));
       launch_encode_x2<T>(refine->uv_keep, refine->perm, M, refine->g.K, g.TB, pos, s);
     } else {
-      rc = build_bins<T>(uv, M, g, chunk, pos, perm, &items, &n_items, s);
+      rc = build_bins<T>(uv, M, g, chunk, pos, perm, &items, &n_items, s, nullptr, 1, mem_pool);
     }
     if (rc) {
       note_error("uv binning failed", __LINE__, cudaGetErrorName(cudaGetLastError()));
@@ -438,7 +462,18 @@ template <typename T> class OpImpl : public purify_op {
       return PURIFY_ERR_CUDA;
     }
     CK(cudaStreamSynchronize(s));
+    if ((rc = take_input_flag("purify_op_create", "uv holds a non-finite coordinate"))) return rc;
     return PURIFY_OK;
+  }
+
+  // Read and clear the non-finite-input flag (stream already synchronised).
+  int take_input_flag(const char* who, const char* what) {
+    int h = 0;
+    CK(cudaMemcpy(&h, err + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!h) return PURIFY_OK;
+    CK(cudaMemset(err + 1, 0, sizeof(int)));
+    note_error(who, __LINE__, what);
+    return PURIFY_ERR_INVALID;
   }
 
   void info(int* n, int64_t* M, int* K, int* tile, int* ni, int* prec, int64_t* b) const override {
@@ -578,6 +613,7 @@ template <typename T> class OpImpl : public purify_op {
       CK(cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost));
       if (h) {
         cudaMemset(err, 0, sizeof(int));
+        note_error("bounded device wait", __LINE__, "a TMA or bulk-copy wait gave up");
         return PURIFY_ERR_TIMEOUT;
       }
     }
@@ -887,6 +923,9 @@ template <typename T> class OpImpl : public purify_op {
     if (gmode == 1 && (rc = ensure_toeplitz(s))) return rc;
     toep = gmode == 1;
     launch_gather<C>(static_cast<const C*>(y), perm, M, ys, s);
+    launch_check_finite<T>(reinterpret_cast<const T*>(ys), 2 * M, err + 1, s);
+    CK(cudaStreamSynchronize(s));
+    if ((rc = take_input_flag("purify_sdmm_solve", "y holds a non-finite visibility"))) return rc;
     run.nu = P->nu;
     if (!(run.nu > 0)) {
       double lam = 0;
@@ -899,20 +938,132 @@ template <typename T> class OpImpl : public purify_op {
       if (!(run.gamma > 0)) run.gamma = 1e-12;
     }
     run.decay = P->delta_decay > 0 ? P->delta_decay : 0.1;
-    if (P->use_graph && !prof) {
-      cudaGraph_t graph = nullptr;
-      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      iteration(run.nu, run.gamma, P->eps, P->cg_iters, s);
-      cudaError_t ce = cudaStreamEndCapture(s, &graph);
-      if (ce != cudaSuccess) return map_err(ce, __LINE__);
-      ce = cudaGraphInstantiate(&run.gexec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (ce != cudaSuccess) return map_err(ce, __LINE__);
-    }
+    if ((rc = capture_iteration(s))) return rc;
     launch_fill<T>(w, D(), T(1), s);
     CK(cudaMemsetAsync(xh, 0, n2 * sizeof(T), s));
     run.active = true;
     return check(s, false);
+  }
+
+  // One SDMM iteration captured as a CUDA graph (when the parameters ask for
+  // replay), with the current nu and gamma baked into its kernel arguments.
+  int capture_iteration(cudaStream_t s) {
+    if (run.gexec) {
+      cudaGraphExecDestroy(run.gexec);
+      run.gexec = nullptr;
+    }
+    if (!run.P.use_graph || prof) return PURIFY_OK;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    iteration(run.nu, run.gamma, run.P.eps, run.P.cg_iters, s);
+    cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    if (ce != cudaSuccess) return map_err(ce, __LINE__);
+    ce = cudaGraphInstantiate(&run.gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return map_err(ce, __LINE__);
+    return PURIFY_OK;
+  }
+
+  int run_steps(int max_iters, int* done) override {
+    *done = 0;
+    if (!run.active || max_iters < 0) return PURIFY_ERR_INVALID;
+    int rc = PURIFY_OK;
+    for (int k = 0; k < max_iters && !*done && !rc; ++k) {
+      rc = step_launch();
+      if (!rc) rc = step_check(done);
+    }
+    if (!rc) rc = check(own, true);
+    return rc;
+  }
+
+  // ---- checkpoint: the state an SDMM iteration carries to the next
+  // (Algorithm 1: x_hat, sum_i x_i and the duals z_1, z_2, z_3), the SARA
+  // weights of the round and the loop counters.  CG vectors restart from
+  // x_hat every iteration and are not state.
+  struct StateHeader {
+    uint32_t magic, version;
+    int32_t precision, n;
+    int64_t M;
+    int32_t nbases, nblocks, round, t, total, converged, round_ready, pad;
+    double nu, gamma, delta1, prev;
+  };
+  static constexpr uint32_t kStateMagic = 0x4D445350u;  // "PSDM"
+  int64_t state_bytes() const override {
+    return int64_t(sizeof(StateHeader)) + int64_t((3 * N() + 2 * D() + 2 * size_t(g.M)) * sizeof(T));
+  }
+  // (device array, element count) pairs in checkpoint order.
+  void state_arrays(T* (&a)[6], size_t (&len)[6]) const {
+    T* arr[6] = {xh, xs, z1, z2, w, reinterpret_cast<T*>(z3)};
+    const size_t l[6] = {N(), N(), D(), N(), D(), 2 * size_t(g.M)};
+    for (int k = 0; k < 6; ++k) {
+      a[k] = arr[k];
+      len[k] = l[k];
+    }
+  }
+  int save_state(void* host, int64_t bytes) override {
+    if (!run.active || !host || bytes < state_bytes()) return PURIFY_ERR_INVALID;
+    CK(cudaStreamSynchronize(own));
+    StateHeader h{};
+    h.magic = kStateMagic;
+    h.version = 1;
+    h.precision = sizeof(T) == 4 ? PURIFY_FP32 : PURIFY_FP64;
+    h.n = g.n;
+    h.M = g.M;
+    h.nbases = sara.nbases;
+    h.nblocks = nblocks;
+    h.round = run.round;
+    h.t = run.t;
+    h.total = run.total;
+    h.converged = run.converged;
+    h.round_ready = run.round_ready ? 1 : 0;
+    h.nu = run.nu;
+    h.gamma = run.gamma;
+    h.delta1 = run.delta1;
+    h.prev = run.prev;
+    unsigned char* dst = static_cast<unsigned char*>(host);
+    std::memcpy(dst, &h, sizeof(h));
+    dst += sizeof(h);
+    T* a[6];
+    size_t len[6];
+    state_arrays(a, len);
+    for (int k = 0; k < 6; ++k) {
+      CK(cudaMemcpy(dst, a[k], len[k] * sizeof(T), cudaMemcpyDeviceToHost));
+      dst += len[k] * sizeof(T);
+    }
+    return PURIFY_OK;
+  }
+  int load_state(const void* host, int64_t bytes) override {
+    if (!run.active || !host || bytes < state_bytes()) return PURIFY_ERR_INVALID;
+    StateHeader h;
+    std::memcpy(&h, host, sizeof(h));
+    if (h.magic != kStateMagic || h.version != 1 || h.precision != (sizeof(T) == 4 ? PURIFY_FP32 : PURIFY_FP64) ||
+        h.n != g.n || h.M != g.M || h.nbases != sara.nbases || h.nblocks != nblocks || h.round > run.P.n_reweight) {
+      note_error("purify_solve_load", __LINE__, "checkpoint does not match this operator or solve");
+      return PURIFY_ERR_INVALID;
+    }
+    CK(cudaStreamSynchronize(own));
+    const unsigned char* src = static_cast<const unsigned char*>(host) + sizeof(h);
+    T* a[6];
+    size_t len[6];
+    state_arrays(a, len);
+    for (int k = 0; k < 6; ++k) {
+      CK(cudaMemcpy(a[k], src, len[k] * sizeof(T), cudaMemcpyHostToDevice));
+      src += len[k] * sizeof(T);
+    }
+    run.round = h.round;
+    run.t = h.t;
+    run.total = h.total;
+    run.converged = h.converged;
+    run.round_ready = h.round_ready != 0;
+    run.delta1 = h.delta1;
+    run.prev = h.prev;
+    if (h.nu != run.nu || h.gamma != run.gamma) {
+      run.nu = h.nu;
+      run.gamma = h.gamma;
+      int rc = capture_iteration(own);
+      if (rc) return rc;
+    }
+    return check(own, true);
   }
 
   // Round set-up (Algorithm 1 steps 1-3; SARA weights from the previous round).
@@ -1024,6 +1175,10 @@ template <typename T> class OpImpl : public purify_op {
       st->elapsed_ms = ms;
     }
     const bool not_conv = run.P.xi > 0 && !run.converged;
+    if (!rc && !(std::isfinite(h_sc[S_OBJ]) && std::isfinite(h_sc[S_RESID]))) {
+      note_error("purify_sdmm_solve", __LINE__, "objective or residual is not finite");
+      rc = PURIFY_ERR_NONFINITE;
+    }
     run_release();
     cudaEventRecord(ev_out, s);
     cudaStreamWaitEvent(user, ev_out, 0);
@@ -1070,6 +1225,35 @@ template <typename T> class OpImpl : public purify_op {
 };
 
 }  // namespace
+
+int create_pooled_op(const double* uv, int64_t M, int n, int levels, int precision, const purify_op_options* opt,
+                     cudaMemPool_t pool, cudaStream_t s, purify_op** out) {
+  const int tile = opt ? opt->tile : 0, chunk = opt ? opt->chunk : 0;
+  if (!uv || !out || !pool || M < 1 || M >= (int64_t(1) << 31) || n < 16 || n > 2048 || (n & (n - 1)) ||
+      levels < 1 || (n >> levels) < 2 || (tile != 0 && tile != 8 && tile != 16) || tile > 2 * n ||
+      (chunk != 0 && (chunk < 64 || chunk > 8192)) || (precision != PURIFY_FP32 && precision != PURIFY_FP64))
+    return PURIFY_ERR_INVALID;
+  purify_op* op = nullptr;
+  int rc;
+  if (precision == PURIFY_FP32) {
+    OpImpl<float>* o = new (std::nothrow) OpImpl<float>();
+    if (!o) return PURIFY_ERR_NOMEM;
+    rc = o->create(uv, M, n, levels, s, tile, chunk, false, nullptr, pool);
+    op = o;
+  } else {
+    OpImpl<double>* o = new (std::nothrow) OpImpl<double>();
+    if (!o) return PURIFY_ERR_NOMEM;
+    rc = o->create(uv, M, n, levels, s, tile, chunk, false, nullptr, pool);
+    op = o;
+  }
+  if (rc) {
+    delete op;
+    return rc;
+  }
+  *out = op;
+  return PURIFY_OK;
+}
+
 }  // namespace purify
 
 using purify::OpImpl;
@@ -1300,6 +1484,56 @@ int purify_sdmm_solve(purify_op* op, const void* y, const purify_params* params,
   return op->solve(y, params, x_out, stats, static_cast<cudaStream_t>(stream));
 }
 
+int purify_solve_begin(purify_op* op, const void* y, const purify_params* params, void* stream) {
+  if (!op || !y || !params) return PURIFY_ERR_INVALID;
+  return op->begin(y, params, static_cast<cudaStream_t>(stream));
+}
+
+int purify_solve_step(purify_op* op, int max_iters, int* done) {
+  if (!op || !done) return PURIFY_ERR_INVALID;
+  return op->run_steps(max_iters, done);
+}
+
+int purify_solve_end(purify_op* op, void* x_out, purify_stats* stats, void* stream) {
+  if (!op || !x_out) return PURIFY_ERR_INVALID;
+  return op->end(x_out, stats, static_cast<cudaStream_t>(stream));
+}
+
+int purify_solve_state_bytes(const purify_op* op, int64_t* bytes) {
+  if (!op || !bytes) return PURIFY_ERR_INVALID;
+  *bytes = op->state_bytes();
+  return PURIFY_OK;
+}
+
+int purify_solve_save(purify_op* op, void* host, int64_t bytes) {
+  if (!op) return PURIFY_ERR_INVALID;
+  return op->save_state(host, bytes);
+}
+
+int purify_solve_load(purify_op* op, const void* host, int64_t bytes) {
+  if (!op) return PURIFY_ERR_INVALID;
+  return op->load_state(host, bytes);
+}
+
+int purify_set_wait_limit(uint32_t spins) {
+  const uint32_t s = spins ? spins : purify::kSpinLimit;
+  cudaError_t e = purify::set_wait_spins_fft(s);
+  if (e == cudaSuccess) e = purify::set_wait_spins_nufft(s);
+  if (e == cudaSuccess) e = purify::set_wait_spins_solver(s);
+  return purify::map_err(e, __LINE__);
+}
+
+int purify_wait_selftest(int deliver, void* stream) {
+  int timed_out = 0;
+  const cudaError_t e = purify::wait_selftest(deliver, static_cast<cudaStream_t>(stream), &timed_out);
+  if (e != cudaSuccess) return purify::map_err(e, __LINE__);
+  if (timed_out) {
+    purify::set_last_error("purify_wait_selftest: the bounded wait gave up (nothing was delivered)");
+    return PURIFY_ERR_TIMEOUT;
+  }
+  return PURIFY_OK;
+}
+
 const char* purify_last_error(void) { return purify::g_last_error; }
 
 const char* purify_strerror(int status) {
@@ -1311,6 +1545,8 @@ const char* purify_strerror(int status) {
     case PURIFY_ERR_TIMEOUT: return "bounded device wait timed out";
     case PURIFY_ERR_NOT_CONVERGED: return "halting rule not met within t_max";
     case PURIFY_ERR_BUDGET: return "device memory budget exceeded";
+    case PURIFY_ERR_CANCELLED: return "request cancelled";
+    case PURIFY_ERR_NONFINITE: return "solve produced non-finite values";
     default: return "unknown status";
   }
 }

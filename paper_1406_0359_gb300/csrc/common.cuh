@@ -32,6 +32,16 @@ enum : int { DEV_OK = 0, DEV_TIMEOUT = 1 };
 // Bounded spin budget for mbarrier waits: far beyond any TMA latency, short
 // enough that a lost transaction surfaces as an error instead of a hang.
 constexpr uint32_t kSpinLimit = 1u << 24;
+// The first-phase budget (before a wait is reported as timed out) is a
+// device variable of each compiled module, kSpinLimit unless the host lowers
+// it (purify_set_wait_limit); the drain phase that follows a timeout, which
+// lets copies still in flight land before the CTA exits, always keeps the
+// full kSpinLimit.
+static __device__ uint32_t g_wait_spins = kSpinLimit;
+// Host side: set this module's first-phase budget on the current device.
+static inline cudaError_t set_module_wait_spins(uint32_t spins) {
+  return cudaMemcpyToSymbol(g_wait_spins, &spins, sizeof(spins));
+}
 
 PD void set_error(int* err, int code) {
   if (err) atomicCAS(err, DEV_OK, code);
@@ -212,14 +222,17 @@ PD bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
   return ok != 0;
 }
 // Wait for `phase` of `bar` with a bounded spin; on timeout flag the error,
-// keep waiting (bounded again) so the copy in flight lands before the CTA
-// can exit, and return false.
-PD bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, int* err) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i)
+// keep waiting (bounded again, unless drain is false because nothing is in
+// flight) so the copy in flight lands before the CTA can exit, and return
+// false.
+PD bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, int* err, bool drain = true) {
+  const uint32_t lim = g_wait_spins;
+  for (uint32_t i = 0; i < lim; ++i)
     if (mbar_try_wait(bar, phase)) return true;
   set_error(err, DEV_TIMEOUT);
-  for (uint32_t i = 0; i < kSpinLimit; ++i)
-    if (mbar_try_wait(bar, phase)) break;
+  if (drain)
+    for (uint32_t i = 0; i < kSpinLimit; ++i)
+      if (mbar_try_wait(bar, phase)) break;
   return false;
 }
 // Untiled bulk copy global -> shared: both addresses 16-byte aligned, bytes a

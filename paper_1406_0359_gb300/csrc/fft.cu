@@ -822,6 +822,8 @@ template <typename T> cudaError_t configure_fft() {
 template cudaError_t configure_fft<float>();
 template cudaError_t configure_fft<double>();
 
+cudaError_t set_wait_spins_fft(uint32_t spins) { return set_module_wait_spins(spins); }
+
 template <typename T>
 __global__ void k_embed_psf(const T* __restrict__ psf, int n, typename cplx_t<T>::type* __restrict__ X) {
   typedef typename cplx_t<T>::type C;

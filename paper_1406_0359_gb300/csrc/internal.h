@@ -131,6 +131,16 @@ template <typename C> struct GridPro {
 // Record the detail returned by purify_last_error() on this thread.
 void set_last_error(const char* msg);
 
+// First-phase budget of the bounded mbarrier waits in each compiled module
+// that waits (current device).
+cudaError_t set_wait_spins_fft(uint32_t spins);
+cudaError_t set_wait_spins_nufft(uint32_t spins);
+cudaError_t set_wait_spins_solver(uint32_t spins);
+// Bounded-wait self-test: one CTA arms an mbarrier for 16 bytes and either
+// delivers them by a bulk copy (deliver != 0) or sends nothing; *timed_out
+// receives whether the wait gave up.  Blocks on `s`.
+cudaError_t wait_selftest(int deliver, cudaStream_t s, int* timed_out);
+
 // ----------------------------------------------------------------- launchers
 // Raise the dynamic shared-memory limit of every kernel (once per operator,
 // outside any stream capture).
@@ -208,9 +218,11 @@ template <typename U> cudaError_t setup_alloc(U** p, size_t bytes, cudaStream_t 
 // (fine tiles TB = 2 x the coarse tiles): the coarse items and order serve.
 template <typename T>
 void launch_encode_x2(const double* uv, const int* perm, int64_t M, int Kc, int TB, Pos<T>* pos, cudaStream_t s);
+// items_pool: allocate the work list from this pool on `s` (else cudaMalloc).
 template <typename T>
 int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>* pos, int* perm,
-               WorkItem** items_out, int* n_items_out, cudaStream_t s, const int* blocks = nullptr, int R = 1);
+               WorkItem** items_out, int* n_items_out, cudaStream_t s, const int* blocks = nullptr, int R = 1,
+               cudaMemPool_t items_pool = nullptr);
 
 // SARA dictionary.
 template <typename T>

@@ -968,6 +968,8 @@ template <typename T> cudaError_t configure_nufft() {
 template cudaError_t configure_nufft<float>();
 template cudaError_t configure_nufft<double>();
 
+cudaError_t set_wait_spins_nufft(uint32_t spins) { return set_module_wait_spins(spins); }
+
 size_t tile_smem_bytes(int precision_bytes, int TB, int mode) {
   if (precision_bytes == 4) {
     size_t b = tile_stage_bytes<float>();
@@ -1019,7 +1021,8 @@ void launch_encode_x2(const double* uv, const int* perm, int64_t M, int Kc, int 
 
 template <typename T>
 int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>* pos, int* perm,
-               WorkItem** items_out, int* n_items_out, cudaStream_t s, const int* blocks, int R) {
+               WorkItem** items_out, int* n_items_out, cudaStream_t s, const int* blocks, int R,
+               cudaMemPool_t items_pool) {
   const int tiles_per_block = g.ntile1d * g.ntile1d;
   const int ntiles = tiles_per_block * (R > 1 ? R : 1);  // bins
   int lb = 0;
@@ -1079,7 +1082,9 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
     fail(cudaGetLastError());
   }
   if (rc == 0) {
-    fail(cudaMalloc(&items, size_t(h_total > 0 ? h_total : 1) * sizeof(WorkItem)));
+    const size_t ib = size_t(h_total > 0 ? h_total : 1) * sizeof(WorkItem);
+    fail(items_pool ? cudaMallocFromPoolAsync(reinterpret_cast<void**>(&items), ib, items_pool, s)
+                    : cudaMalloc(&items, ib));
     if (rc == 0) {
       const int tb = 256;
       k_fill_items<<<(ntiles + tb - 1) / tb, tb, 0, s>>>(tstart, tend, cnt, ntiles, tiles_per_block, chunk, items);
@@ -1089,13 +1094,15 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
       // largest items first (stable): whole-warp items then finish together
       if (rc == 0 && h_total > 1) {
         std::vector<WorkItem> h(h_total), o(h_total);
-        fail(cudaMemcpy(h.data(), items, h.size() * sizeof(WorkItem), cudaMemcpyDeviceToHost));
+        fail(cudaMemcpyAsync(h.data(), items, h.size() * sizeof(WorkItem), cudaMemcpyDeviceToHost, s));
+        fail(cudaStreamSynchronize(s));
         // stable counting sort by length, longest first (lengths <= chunk)
         std::vector<int> first(size_t(chunk) + 2, 0);
         for (const WorkItem& w : h) first[size_t(chunk - (w.end - w.begin)) + 1] += 1;
         for (size_t k = 1; k < first.size(); ++k) first[k] += first[k - 1];
         for (const WorkItem& w : h) o[size_t(first[size_t(chunk - (w.end - w.begin))]++)] = w;
-        fail(cudaMemcpy(items, o.data(), o.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+        fail(cudaMemcpyAsync(items, o.data(), o.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
+        fail(cudaStreamSynchronize(s));
       }
     }
   }
@@ -1104,7 +1111,8 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
                   static_cast<void*>(cnt), static_cast<void*>(total)})
     if (t) cudaFreeAsync(t, s);
   if (rc != 0) {
-    cudaFree(items);
+    if (items_pool) cudaFreeAsync(items, s);
+    else cudaFree(items);
     return rc;
   }
   *items_out = items;
@@ -1123,7 +1131,7 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
                                const KbPoly<T>&, cplx_t<T>::type*, int*, cudaStream_t);                         \
   template void launch_encode_x2<T>(const double*, const int*, int64_t, int, int, Pos<T>*, cudaStream_t);     \
   template int build_bins<T>(const double*, int64_t, const Geometry&, int, Pos<T>*, int*, WorkItem**, int*,     \
-                             cudaStream_t, const int*, int);
+                             cudaStream_t, const int*, int, cudaMemPool_t);
 INST(float)
 INST(double)
 #undef INST

@@ -24,6 +24,13 @@ struct purify_op {
   virtual int step_launch() = 0;
   virtual int step_check(int* done) = 0;
   virtual int end(void* x, purify_stats* st, cudaStream_t user) = 0;
+  // Up to max_iters iterations of the resumable solve, then a synchronous
+  // check of the device error flag; *done = 1 once the last round finished.
+  virtual int run_steps(int max_iters, int* done) = 0;
+  // Solver state between iterations (checkpoint / resume).
+  virtual int64_t state_bytes() const = 0;
+  virtual int save_state(void* host, int64_t bytes) = 0;
+  virtual int load_state(const void* host, int64_t bytes) = 0;
   virtual cudaStream_t stream() const = 0;
   // Phi then Phi^H in the solver's sorted visibility order (autotuner timing).
   virtual int sorted_pair(const void* x, void* y, void* out, cudaStream_t s) = 0;
@@ -86,3 +93,12 @@ struct purify_op {
   }
 };
 
+namespace purify {
+// Operator whose device memory all comes from `pool` (stream-ordered, never
+// synchronising the device on release): the request server's operators.
+// Arguments as purify_op_create_ex; `opt` may be null.
+int create_pooled_op(const double* uv, int64_t M, int n, int levels, int precision, const purify_op_options* opt,
+                     cudaMemPool_t pool, cudaStream_t s, purify_op** out);
+// Record the detail returned by purify_last_error() on this thread.
+void set_last_error(const char* msg);
+}  // namespace purify

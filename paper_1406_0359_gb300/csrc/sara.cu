@@ -640,7 +640,7 @@ extern "C" int purify_sara_fwd_static(const float* x, float* c, int n, int level
   P.f = g_static_filters;
   sara_select(P, kSaraAll);
   sara_analysis<float>(P, x, c, static_cast<cudaStream_t>(stream));
-  const cudaError_t e = cudaGetLastError();
+  const cudaError_t e = cudaPeekAtLastError();
   if (e != cudaSuccess) {
     char buf[160];
     std::snprintf(buf, sizeof(buf), "purify_sara_fwd_static: launch failed: %s", cudaGetErrorName(e));

@@ -1,17 +1,29 @@
 // Request server: continuous batching of SARA-SDMM solves on one GPU.
 //
 // Requests (host uv, host visibilities, image side, parameters) wait in a
-// FIFO queue.  A scheduling round admits queued requests while a slot is free
-// and their estimated device memory fits the budget (operator creation: uv
-// binning, tables; the solve's state then stays resident), then advances every
-// admitted solve by one SDMM iteration (Algorithm 1), each on its operator's
-// own stream so that the solves' kernels overlap on the device.  A finished
-// solve's image is copied back, its memory is released and the next request
-// can take its slot in the following round.  The caller drives the rounds and
-// collects results; the server is not thread-safe.
+// FIFO queue.  Each scheduling call admits queued requests while a slot is
+// free and their estimated device memory fits the budget (operator creation:
+// uv binning, tables; the solve's state then stays resident), and keeps every
+// admitted solve moving one SDMM iteration (Algorithm 1) at a time on its
+// operator's own stream, so that the solves' kernels overlap on the device.
+// A solve whose iteration has completed (its event has fired) gets its
+// halting test and its next iteration at once; one whose iteration is still
+// running is left alone, so a large image never holds back a small one.  A
+// finished solve's image is copied back, its memory returns to the pool and
+// the next request can take its slot.
+//
+// Device memory of admitted solves (operators, state, staging of uv and y)
+// comes from one stream-ordered memory pool of the server that keeps up to
+// the budget mapped: admitting and releasing solves never calls cudaMalloc or
+// cudaFree, which would synchronise the whole device.  Host inputs reach the
+// device through a pinned staging buffer on the server's admission stream.
+//
+// The caller drives the server (purify_server_step) and collects results;
+// the server is not thread-safe.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -36,8 +48,9 @@ struct Request {
   purify_params P{};
   int64_t est = 0;
   purify_op* op = nullptr;
-  void* y_dev = nullptr;
   void* x_dev = nullptr;
+  cudaEvent_t ev = nullptr;  // end of the iteration in flight
+  bool inflight = false;
   std::vector<unsigned char> x;
   purify_stats st{};
   int status = 1;  // 1 queued/active, 0 done, < 0 error, -5 done without convergence
@@ -45,6 +58,18 @@ struct Request {
 };
 
 size_t real_bytes(int precision) { return precision == PURIFY_FP32 ? 4 : 8; }
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return PURIFY_OK;
+  return e == cudaErrorMemoryAllocation ? PURIFY_ERR_NOMEM : PURIFY_ERR_CUDA;
+}
+
+// Index of the first non-finite value among n, or -1.
+template <typename T> int64_t first_nonfinite(const T* v, int64_t n) {
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return i;
+  return -1;
+}
 
 }  // namespace
 
@@ -58,6 +83,7 @@ extern "C" int purify_estimate_bytes(int64_t M, int n, int dwt_levels, int preci
   b += 2 * 8 * (N / 4) * r + 9 * N * r;      // wavelet scratch bands, prox output
   b += 6 * N * r + 18 * N * r + 2 * M * c;   // solver vectors, z1 and weights, z3 and sorted y
   b += (M / 1024.0 + 4.0 * K * K / 256) * 16;  // work items (bound) and partial sums
+  b += M * (16 + c) + N * r;                 // the server's staging of uv and y, the result image
   if (n <= 1024) {
     // composite operator: spectrum kept; while it is built, a 2n operator,
     // a unit-visibility vector and two K^2 buffers live for a moment
@@ -75,101 +101,194 @@ struct purify_server {
   int max_slots = 1;
   int64_t in_use = 0;
   int next_id = 1;
+  int device = 0;
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t adm = nullptr;  // admission copies and operator set-up
+  void* pin = nullptr;         // pinned staging of one request's uv and y
+  size_t pin_bytes = 0;
   std::deque<Request*> queue;
   std::vector<Request*> active;
   std::map<int, Request*> all;
   std::map<int, purify_op_options> opts;  // per image side (from the autotuner)
+
+  int init(int64_t budget_bytes, int slots) {
+    budget = budget_bytes;
+    max_slots = slots;
+    if (cudaGetDevice(&device) != cudaSuccess) return PURIFY_ERR_CUDA;
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaError_t e = cudaMemPoolCreate(&pool, &props);
+    if (e == cudaSuccess) {
+      uint64_t keep = uint64_t(budget);
+      e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&adm, cudaStreamNonBlocking);
+    return cuda_status(e);
+  }
 
   ~purify_server() {
     for (auto& kv : all) {
       release(kv.second);
       delete kv.second;
     }
+    if (adm) cudaStreamSynchronize(adm);
+    if (adm) cudaStreamDestroy(adm);
+    if (pin) cudaFreeHost(pin);
+    if (pool) cudaMemPoolDestroy(pool);
   }
 
+  // Return a solve's memory to the pool (its streams are idle afterwards).
   void release(Request* r) {
-    if (r->op) purify_op_destroy(r->op);
-    if (r->y_dev) cudaFree(r->y_dev);
-    if (r->x_dev) cudaFree(r->x_dev);
+    if (r->op) {
+      cudaStreamSynchronize(r->op->stream());
+      if (r->x_dev) cudaFreeAsync(r->x_dev, r->op->stream());
+      purify_op_destroy(r->op);
+    }
+    if (r->ev) cudaEventDestroy(r->ev);
     r->op = nullptr;
-    r->y_dev = r->x_dev = nullptr;
+    r->x_dev = nullptr;
+    r->ev = nullptr;
+    r->inflight = false;
   }
 
-  void fail(Request* r, int rc) {
-    r->status = rc;
+  void finish(Request* r, int status) {
+    r->status = status;
     r->t_done = now_s();
     release(r);
     in_use -= r->est;
   }
 
+  int stage(size_t bytes) {
+    if (bytes <= pin_bytes) return PURIFY_OK;
+    if (pin) {
+      cudaStreamSynchronize(adm);
+      cudaFreeHost(pin);
+      pin = nullptr;
+      pin_bytes = 0;
+    }
+    if (cudaMallocHost(&pin, bytes) != cudaSuccess) return PURIFY_ERR_NOMEM;
+    pin_bytes = bytes;
+    return PURIFY_OK;
+  }
+
+  // Set up one admitted request: stage uv and y, build its operator from the
+  // pool, start its solve.  uv and y copies return to the pool once the
+  // solve has taken its own copy of y.
+  int setup(Request* r) {
+    const size_t uvb = r->uv.size() * sizeof(double), yb = r->y.size();
+    int rc = stage(uvb + yb);
+    if (rc) return rc;
+    unsigned char* h = static_cast<unsigned char*>(pin);
+    cudaError_t e = cudaStreamSynchronize(adm);  // the staging buffer is free again
+    if (e != cudaSuccess) return cuda_status(e);
+    std::memcpy(h, r->uv.data(), uvb);
+    std::memcpy(h + uvb, r->y.data(), yb);
+    void *uv_dev = nullptr, *y_dev = nullptr;
+    e = cudaMallocFromPoolAsync(&uv_dev, uvb, pool, adm);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&y_dev, yb, pool, adm);
+    if (e == cudaSuccess)
+      e = cudaMallocFromPoolAsync(&r->x_dev, size_t(r->n) * r->n * real_bytes(r->precision), pool, adm);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(uv_dev, h, uvb, cudaMemcpyHostToDevice, adm);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y_dev, h + uvb, yb, cudaMemcpyHostToDevice, adm);
+    rc = cuda_status(e);
+    if (!rc) {
+      auto oi = opts.find(r->n);
+      rc = purify::create_pooled_op(static_cast<const double*>(uv_dev), r->M, r->n, r->levels, r->precision,
+                                    oi == opts.end() ? nullptr : &oi->second, pool, adm, &r->op);
+    }
+    if (!rc) rc = r->op->begin(y_dev, &r->P, adm);  // returns once y is gathered into the solve's state
+    if (!rc) rc = cuda_status(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
+    if (uv_dev) cudaFreeAsync(uv_dev, adm);
+    if (y_dev) cudaFreeAsync(y_dev, adm);
+    return rc;
+  }
+
   // Admission: FIFO, a free slot and the estimated memory within the budget.
-  int admit() {
+  void admit() {
     while (!queue.empty() && int(active.size()) < max_slots) {
       Request* r = queue.front();
       if (in_use + r->est > budget && !active.empty()) break;  // wait for memory
       queue.pop_front();
       in_use += r->est;
       r->t_admit = now_s();
-      const size_t cb = 2 * real_bytes(r->precision);
-      double* uv_dev = nullptr;
-      cudaError_t e = cudaMalloc(&uv_dev, r->uv.size() * sizeof(double));
-      if (e == cudaSuccess) e = cudaMalloc(&r->y_dev, size_t(r->M) * cb);
-      if (e == cudaSuccess) e = cudaMalloc(&r->x_dev, size_t(r->n) * r->n * real_bytes(r->precision));
-      if (e == cudaSuccess)
-        e = cudaMemcpy(uv_dev, r->uv.data(), r->uv.size() * sizeof(double), cudaMemcpyHostToDevice);
-      if (e == cudaSuccess) e = cudaMemcpy(r->y_dev, r->y.data(), r->y.size(), cudaMemcpyHostToDevice);
-      int rc = e == cudaSuccess ? PURIFY_OK : (e == cudaErrorMemoryAllocation ? PURIFY_ERR_NOMEM : PURIFY_ERR_CUDA);
-      if (!rc) {
-        auto oi = opts.find(r->n);
-        rc = purify_op_create_ex(uv_dev, r->M, r->n, 2, 8, r->levels, r->precision,
-                                 oi == opts.end() ? nullptr : &oi->second, nullptr, &r->op);
-      }
-      cudaFree(uv_dev);
-      if (!rc) rc = r->op->begin(r->y_dev, &r->P, r->op->stream());
+      const int rc = setup(r);
       if (rc) {
-        fail(r, rc);
+        finish(r, rc);
         continue;
       }
       active.push_back(r);
     }
+  }
+
+  // A finished solve: its image to host memory, its memory back to the pool.
+  void complete(Request* r) {
+    cudaStream_t s = r->op->stream();
+    int rc = r->op->end(r->x_dev, &r->st, s);
+    const size_t xb = size_t(r->n) * r->n * real_bytes(r->precision);
+    r->x.resize(xb);
+    cudaError_t e = cudaMemcpyAsync(r->x.data(), r->x_dev, xb, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if ((rc == PURIFY_OK || rc == PURIFY_ERR_NOT_CONVERGED) && e != cudaSuccess) rc = cuda_status(e);
+    finish(r, rc);
+  }
+
+  // One scheduling pass: admit; for every solve whose iteration in flight has
+  // completed, apply the halting test and launch its next iteration (or
+  // complete it); solves still running are left alone.
+  int step() {
+    admit();
+    std::vector<Request*> keep;
+    for (Request* r : active) {
+      if (r->inflight) {
+        const cudaError_t q = cudaEventQuery(r->ev);
+        if (q == cudaErrorNotReady) {
+          keep.push_back(r);
+          continue;
+        }
+        r->inflight = false;
+        int done = 0;
+        int rc = q == cudaSuccess ? r->op->step_check(&done) : cuda_status(q);
+        if (rc) {
+          finish(r, rc);
+          continue;
+        }
+        if (done) {
+          complete(r);
+          continue;
+        }
+      }
+      int rc = r->op->step_launch();
+      if (!rc) rc = cuda_status(cudaEventRecord(r->ev, r->op->stream()));
+      if (rc) {
+        finish(r, rc);
+        continue;
+      }
+      r->inflight = true;
+      keep.push_back(r);
+    }
+    active.swap(keep);
     return PURIFY_OK;
   }
 
-  // One scheduling round: admit, launch one iteration of every admitted solve
-  // (each on its own stream), then check them; finished solves release their
-  // memory and slot.
-  int step() {
-    admit();
-    for (Request* r : active) {
-      const int rc = r->op->step_launch();
-      if (rc) r->status = rc;
-    }
-    std::vector<Request*> keep;
-    for (Request* r : active) {
-      int done = 0;
-      if (r->status == 1) {
-        const int rc = r->op->step_check(&done);
-        if (rc) r->status = rc;
-      }
-      if (r->status != 1) {
-        fail(r, r->status);
-        continue;
-      }
-      if (!done) {
-        keep.push_back(r);
-        continue;
-      }
-      const size_t xb = size_t(r->n) * r->n * real_bytes(r->precision);
-      int rc = r->op->end(r->x_dev, &r->st, r->op->stream());
-      r->x.resize(xb);
-      const int rc2 = cudaMemcpy(r->x.data(), r->x_dev, xb, cudaMemcpyDeviceToHost) == cudaSuccess ? 0 : -3;
-      if (rc == PURIFY_OK || rc == PURIFY_ERR_NOT_CONVERGED) rc = rc2 ? rc2 : rc;
-      r->status = rc;
+  int cancel(int id) {
+    auto it = all.find(id);
+    if (it == all.end()) return PURIFY_ERR_INVALID;
+    Request* r = it->second;
+    if (r->status != 1) return PURIFY_ERR_INVALID;  // already finished
+    auto q = std::find(queue.begin(), queue.end(), r);
+    if (q != queue.end()) {
+      queue.erase(q);
+      r->status = PURIFY_ERR_CANCELLED;
       r->t_done = now_s();
-      release(r);
-      in_use -= r->est;
+      return PURIFY_OK;
     }
-    active.swap(keep);
+    auto a = std::find(active.begin(), active.end(), r);
+    if (a == active.end()) return PURIFY_ERR_INVALID;
+    active.erase(a);
+    finish(r, PURIFY_ERR_CANCELLED);  // waits for the iteration in flight, then releases
     return PURIFY_OK;
   }
 };
@@ -180,8 +299,11 @@ int purify_server_create(int64_t budget_bytes, int max_slots, purify_server** ou
   if (!out || budget_bytes <= 0 || max_slots < 1) return PURIFY_ERR_INVALID;
   purify_server* s = new (std::nothrow) purify_server();
   if (!s) return PURIFY_ERR_NOMEM;
-  s->budget = budget_bytes;
-  s->max_slots = max_slots;
+  const int rc = s->init(budget_bytes, max_slots);
+  if (rc) {
+    delete s;
+    return rc;
+  }
   *out = s;
   return PURIFY_OK;
 }
@@ -202,6 +324,21 @@ int purify_server_submit(purify_server* srv, const double* uv_host, const void* 
   if (!srv || !uv_host || !y_host || !params || !request_id || M < 1 || n < 16 || n > 2048 || (n & (n - 1)) ||
       dwt_levels < 1 || (n >> dwt_levels) < 2 || (precision != PURIFY_FP32 && precision != PURIFY_FP64))
     return PURIFY_ERR_INVALID;
+  // inputs are checked here, before they can reach the device
+  int64_t bad = first_nonfinite(uv_host, 2 * M);
+  const char* what = "uv";
+  if (bad < 0) {
+    bad = precision == PURIFY_FP32 ? first_nonfinite(static_cast<const float*>(y_host), 2 * M)
+                                   : first_nonfinite(static_cast<const double*>(y_host), 2 * M);
+    what = "y";
+  }
+  if (bad >= 0) {
+    char buf[128];
+    std::snprintf(buf, sizeof(buf), "purify_server_submit: %s holds a non-finite value (visibility %lld)", what,
+                  static_cast<long long>(bad / 2));
+    purify::set_last_error(buf);
+    return PURIFY_ERR_INVALID;
+  }
   Request* r = new (std::nothrow) Request();
   if (!r) return PURIFY_ERR_NOMEM;
   r->id = srv->next_id++;
@@ -233,6 +370,11 @@ int purify_server_step(purify_server* srv, int* n_active, int* n_queued) {
   if (n_active) *n_active = int(srv->active.size());
   if (n_queued) *n_queued = int(srv->queue.size());
   return rc;
+}
+
+int purify_server_cancel(purify_server* srv, int request_id) {
+  if (!srv) return PURIFY_ERR_INVALID;
+  return srv->cancel(request_id);
 }
 
 int purify_server_result(purify_server* srv, int request_id, void* x_host, purify_stats* stats, double* latency_s,

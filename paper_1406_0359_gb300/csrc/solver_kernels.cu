@@ -233,6 +233,34 @@ __global__ void k_scale(T* __restrict__ v, size_t N, const double* __restrict__ 
   for (size_t i = size_t(blockIdx.x) * kT + threadIdx.x; i < N; i += size_t(gridDim.x) * kT) v[i] *= s;
 }
 
+template <typename T>
+__global__ void k_check_finite(const T* __restrict__ v, size_t N, int* __restrict__ flag) {
+  bool bad = false;
+  for (size_t i = size_t(blockIdx.x) * kT + threadIdx.x; i < N; i += size_t(gridDim.x) * kT)
+    bad |= !isfinite(v[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
+}
+
+// Self-test of the bounded mbarrier wait: thread 0 arms the barrier for 16
+// bytes; with deliver set a bulk copy brings them, otherwise nothing is ever
+// sent and the wait runs out of its budget (no copy is in flight, so there
+// is nothing to drain).  The outcome goes to the module's flag.
+static __device__ int g_selftest_flag;
+static __device__ __align__(16) unsigned char g_selftest_src[16];
+__global__ void k_wait_selftest(int deliver) {
+  __shared__ __align__(16) unsigned char dst[16];
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    g_selftest_flag = DEV_OK;
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+    mbar_arrive_expect_tx(&bar, 16u);
+    if (deliver) bulk_load(dst, g_selftest_src, 16u, &bar);
+  }
+  __syncthreads();
+  mbar_wait_bounded(&bar, 0, &g_selftest_flag, deliver != 0);
+}
+
 template <typename C>
 __global__ void k_gather(const C* __restrict__ src, const int* __restrict__ perm, size_t M, C* __restrict__ dst) {
   for (size_t i = size_t(blockIdx.x) * kT + threadIdx.x; i < M; i += size_t(gridDim.x) * kT) dst[i] = src[perm[i]];
@@ -292,6 +320,23 @@ template <typename T> void launch_scale(T* v, size_t N, const double* sc, int id
 }
 template <typename C> void launch_gather(const C* src, const int* perm, size_t M, C* dst, cudaStream_t s) {
   k_gather<C><<<nblk(M), kT, 0, s>>>(src, perm, M, dst);
+}
+template <typename T> void launch_check_finite(const T* v, size_t n, int* flag, cudaStream_t s) {
+  k_check_finite<T><<<nblk(n), kT, 0, s>>>(v, n, flag);
+}
+template void launch_check_finite<float>(const float*, size_t, int*, cudaStream_t);
+template void launch_check_finite<double>(const double*, size_t, int*, cudaStream_t);
+
+cudaError_t set_wait_spins_solver(uint32_t spins) { return set_module_wait_spins(spins); }
+
+cudaError_t wait_selftest(int deliver, cudaStream_t s, int* timed_out) {
+  k_wait_selftest<<<1, 32, 0, s>>>(deliver);
+  cudaError_t e = cudaGetLastError();
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbolAsync(&h, g_selftest_flag, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) *timed_out = h != DEV_OK;
+  return e;
 }
 
 #define INST(T)                                                                                       \

@@ -36,5 +36,7 @@ template <typename T> void launch_reweight(T* w, size_t N, double delta, cudaStr
 template <typename T> void launch_fill(T* v, size_t N, T val, cudaStream_t s);
 template <typename T> void launch_scale(T* v, size_t N, const double* sc, int idx, double mul, cudaStream_t s);
 template <typename C> void launch_gather(const C* src, const int* perm, size_t M, C* dst, cudaStream_t s);
+// Device flag set when any of the n values is not finite (NaN or infinity).
+template <typename T> void launch_check_finite(const T* v, size_t n, int* flag, cudaStream_t s);
 
 }  // namespace purify

@@ -1,5 +1,6 @@
-"""Continuous-batching request server: results alone vs. in the mix, budget
-admission, and the device-memory estimate."""
+"""Continuous-batching request server: results alone vs. in the mix (images
+from 64^2 to 2048^2), budget admission, cancellation, input checks, and the
+device-memory estimate."""
 import math
 
 import numpy as np
@@ -11,7 +12,8 @@ from tests._gpu import need_gpu, rel
 
 pytestmark = pytest.mark.gpu
 
-MIX = [(64, 3000, 11), (128, 20000, 12), (256, 60000, 13), (64, 5000, 14), (128, 9000, 15), (256, 130000, 16)]
+MIX = [(64, 3000, 11), (128, 20000, 12), (256, 60000, 13), (64, 5000, 14), (128, 9000, 15), (256, 130000, 16),
+       (2048, 65536, 17)]
 
 
 def problem(n, M, seed):
@@ -87,3 +89,47 @@ def test_estimate_bounds_operator_memory():
         op.solve(torch.as_tensor(y, dtype=torch.complex64).cuda(), eps, t_max=2, cg_iters=2)
         assert op.info()["device_bytes"] <= purify_estimate_bytes(M, n, 3)
         op.close()
+
+
+def test_cancel_queued_and_running_requests():
+    need_gpu()
+    from paper_1406_0359_gb300.binding import PurifyError, Server
+
+    reqs = [(128, *problem(128, 20000, s)) for s in (31, 32, 33)]
+    srv = Server(int(40e9), 1)
+    ids = [srv.submit(uv, y, n, 3, eps, t_max=200, cg_iters=8) for (n, uv, y, eps) in reqs]
+    for _ in range(5):  # request 0 admitted and a few iterations in
+        srv.step()
+    srv.cancel(ids[1])  # still queued
+    srv.cancel(ids[0])  # running: stopped between iterations
+    with pytest.raises(PurifyError):
+        srv.cancel(ids[0])  # already finished
+    for _ in range(100000):
+        a, q = srv.step()
+        if a == 0 and q == 0:
+            break
+    for rid in ids[:2]:
+        with pytest.raises(PurifyError) as e:
+            srv.result(rid)
+        assert e.value.code == -7
+    x, st, lat, qs = srv.result(ids[2])  # the one left runs to the end
+    assert st["iterations"] == 200 and np.all(np.isfinite(x))
+    srv.close()
+
+
+def test_nonfinite_request_is_refused_at_submit():
+    need_gpu()
+    from paper_1406_0359_gb300.binding import PurifyError, Server
+
+    n, (uv, y, eps) = 64, problem(64, 3000, 41)
+    srv = Server(int(40e9), 2)
+    y = np.array(y, copy=True)
+    y[123] = np.nan
+    with pytest.raises(PurifyError) as e:
+        srv.submit(uv, y, n, 3, eps)
+    assert e.value.code == -1 and "visibility 123" in str(e.value)
+    uv = np.array(uv, copy=True)
+    uv[7, 0] = np.inf
+    with pytest.raises(PurifyError):
+        srv.submit(uv, np.zeros(3000, np.complex64), n, 3, eps)
+    srv.close()

@@ -86,3 +86,24 @@ def test_invalid_arguments_are_rejected_before_any_device_work():
     assert L.purify_gram(None, fake, fake, 1, None) == INV
     assert L.purify_op_set_dictionary(None, 1) == INV
     assert L.purify_op_destroy(None) == 0
+
+
+def test_resume_and_diagnostic_calls_reject_bad_arguments_without_gpu():
+    from paper_1406_0359_gb300 import binding, build
+
+    build.build()
+    L = binding.lib()
+    fake = ctypes.c_void_p(256)
+    done = ctypes.c_int()
+    b = ctypes.c_int64()
+    p = binding.purify_default_params()
+    assert L.purify_solve_begin(None, fake, ctypes.byref(p), None) == -1
+    assert L.purify_solve_begin(fake, None, ctypes.byref(p), None) == -1
+    assert L.purify_solve_step(None, 1, ctypes.byref(done)) == -1
+    assert L.purify_solve_end(None, fake, None, None) == -1
+    assert L.purify_solve_state_bytes(None, ctypes.byref(b)) == -1
+    assert L.purify_solve_save(None, fake, 16) == -1
+    assert L.purify_solve_load(None, fake, 16) == -1
+    assert L.purify_server_cancel(None, 1) == -1
+    assert binding.purify_strerror(-7) == "request cancelled"
+    assert "non-finite" in binding.purify_strerror(-8)
