@@ -181,6 +181,29 @@ int purify_op_set_dictionary(purify_op* op, unsigned mask);
 int purify_op_dictionary(const purify_op* op, unsigned* mask, int* n_bases);
 
 /*
+ * purify_op_set_prior -- the prior of purify_sdmm_solve's first block.
+ * Section 4 solves the same constrained problem with total variation in
+ * place of the l1 analysis prior ("TV"; with n_reweight > 0 the reweighted
+ * "RWTV").
+ *   prior 0: ||W Psi^H x||_1 over the dictionary of purify_op_set_dictionary
+ *            (the default; SARA and its sub-dictionaries).
+ *   prior 1: TV_W(x) = sum_ij w_ij |(grad x)_ij|, the weighted isotropic total
+ *            variation with forward differences and a zero difference past the
+ *            last row and column; L_1 = I, so the composite operator is still
+ *            Phi^H Phi + 2I.  Its proximity operator (Eq. 7) is computed on
+ *            the dual: prox(v) = v + div q, q from `tv_iters` projected-gradient
+ *            steps q <- P(q + (1/8) grad(v + div q)) onto |q_ij| <= gamma w_ij,
+ *            warm-started from the previous SDMM iteration's q (zero at the
+ *            start of every round).  RWTV weights w_i = delta / (delta +
+ *            |grad x_hat|_i), delta from the same schedule as SARA's applied
+ *            to the gradient magnitudes.  The default gamma is
+ *            1e-3 ||nu^2 Re Phi^H y||_inf; the objective reported is TV_W.
+ *   tv_iters 1..100000 (prior 1; ignored for prior 0).
+ * PURIFY_ERR_INVALID for other values or while a resumable solve is active.
+ */
+int purify_op_set_prior(purify_op* op, int prior, int tv_iters);
+
+/*
  * purify_op_set_blocks -- partition the visibilities into R blocks (Eq. 4):
  * the solver then imposes one constraint ||y_b - Phi_b x||_2 <= eps_b per
  * block (Eq. 5), i.e. S = R + 2 functions in Eq. 6, each block with its own
@@ -325,9 +348,10 @@ int purify_wait_selftest(int deliver, void* stream);
  * profiling was enabled.  Kinds: 0 row_fwd, 1 col_fwd, 2 degrid, 3 grid,
  * 4 gram, 5 col_inv, 6 row_inv, 7 sara_analysis, 8 sara_synthesis,
  * 9 vector (CG updates and scalar finalisation), 10 memset, 11 col_conv,
- * 12 row_fwd_h, 13 row_inv_h (the row passes of the convolution form).
+ * 12 row_fwd_h, 13 row_inv_h (the row passes of the convolution form),
+ * 14 tv (the TV block of purify_op_set_prior).
  */
-enum { PURIFY_NUM_KERNEL_KINDS = 14 };
+enum { PURIFY_NUM_KERNEL_KINDS = 15 };
 int purify_profile(purify_op* op, int enable);
 int purify_profile_read(purify_op* op, int kind, double* total_ms, int64_t* launches);
 const char* purify_kernel_name(int kind);

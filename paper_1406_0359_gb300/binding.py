@@ -62,9 +62,9 @@ EXPORTS = ["purify_op_create", "purify_op_destroy", "purify_op_info", "purify_ph
            "purify_server_set_options", "purify_op_set_dictionary", "purify_op_dictionary",
            "purify_solve_begin", "purify_solve_step", "purify_solve_end", "purify_solve_state_bytes",
            "purify_solve_save", "purify_solve_load", "purify_set_wait_limit", "purify_wait_selftest",
-           "purify_server_cancel"]
+           "purify_server_cancel", "purify_op_set_prior"]
 KERNEL_KINDS = ["row_fwd", "col_fwd", "degrid", "grid", "gram", "col_inv", "row_inv", "sara_analysis",
-                "sara_synthesis", "vector", "memset", "col_conv", "row_fwd_h", "row_inv_h"]
+                "sara_synthesis", "vector", "memset", "col_conv", "row_fwd_h", "row_inv_h", "tv"]
 
 _lib = None
 
@@ -121,6 +121,7 @@ def lib() -> ctypes.CDLL:
     L.purify_set_wait_limit.argtypes = [ctypes.c_uint32]
     L.purify_wait_selftest.argtypes = [ci, vp]
     L.purify_server_cancel.argtypes = [vp, ci]
+    L.purify_op_set_prior.argtypes = [vp, ci, ci]
     L.purify_last_error.argtypes = []
     L.purify_last_error.restype = ctypes.c_char_p
     for f in EXPORTS:
@@ -383,6 +384,10 @@ class Operator:
     def set_dictionary(self, mask: int) -> None:
         """Bases of Psi: bit 0 Dirac, bit K DbK (default 0x1FF, SARA)."""
         purify_op_set_dictionary(self.h, mask)
+
+    def set_prior(self, prior: str = "l1", tv_iters: int = 20) -> None:
+        """First SDMM block: "l1" (analysis over the dictionary) or "tv"."""
+        _check(lib().purify_op_set_prior(self.h, {"l1": 0, "tv": 1}[prior], tv_iters), "purify_op_set_prior")
 
     def dictionary(self) -> tuple[int, int]:
         """(mask, number of bases q) of Psi."""

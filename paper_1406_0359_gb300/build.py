@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpurify_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "fft.cu", "nufft.cu", "sara.cu", "solver_kernels.cu", "host_math.cpp", "server.cpp"]
+SOURCES = ["api.cu", "fft.cu", "nufft.cu", "sara.cu", "solver_kernels.cu", "tv.cu", "host_math.cpp", "server.cpp"]
 
 
 def _nvcc() -> str:

@@ -192,6 +192,11 @@ template <typename T> class OpImpl : public purify_op {
   std::vector<int64_t> block_sizes;
   double* eps_dev = nullptr;    // nu-independent radii eps_b (R)
   double* scale_dev = nullptr;  // projection scale per block (R)
+  // prior of the f_1 block: 0 the l1 analysis prior over the dictionary
+  // (SARA and its sub-dictionaries), 1 TV (Section 4's TV / RWTV)
+  int prior = 0;
+  int tv_iters = 20;
+  T* tvq = nullptr;  // the TV prox's dual: two buffers of 2N
   int64_t bytes = 0;
   std::vector<void*> allocs;
   // Set-up (light) operator: buffers from the set-up pool on this stream, the
@@ -212,7 +217,7 @@ template <typename T> class OpImpl : public purify_op {
   int partials_cap = 0;
   int size_partials() {
     const int np = std::max({2 * n_items, row_inv_blocks(g), sara_partials_capacity(g.n, levels),
-                             vec_blocks(9 * N()), 1});
+                             vec_blocks(9 * N()), tv_partials(g.n), 1});
     if (2 * n_items > bpart_cap) {
       double* bnew = nullptr;
       const int rc = alloc(&bnew, size_t(std::max(2 * n_items, 1)));
@@ -313,7 +318,22 @@ template <typename T> class OpImpl : public purify_op {
   }
 
   size_t N() const { return size_t(g.n) * g.n; }
-  size_t D() const { return size_t(sara.nbases) * N(); }  // dictionary coefficients
+  // coefficients of the f_1 block: the dictionary's, or one per pixel for TV
+  size_t D() const { return prior == 1 ? N() : size_t(sara.nbases) * N(); }
+
+  int set_prior(int pr, int iters) override {
+    if (run.active) {
+      note_error("purify_op_set_prior", __LINE__, "a solve is in progress on this operator");
+      return PURIFY_ERR_INVALID;
+    }
+    if ((pr != 0 && pr != 1) || (pr == 1 && (iters < 1 || iters > 100000))) {
+      note_error("purify_op_set_prior", __LINE__, "prior must be 0 (l1 analysis) or 1 (TV, 1 <= tv_iters <= 1e5)");
+      return PURIFY_ERR_INVALID;
+    }
+    prior = pr;
+    if (pr == 1) tv_iters = iters;
+    return PURIFY_OK;
+  }
 
   // Dictionary of the l1 block: the SARA bases in `mask` (bit 0 Dirac, bit K DbK).
   int set_dictionary(unsigned mask) override {
@@ -692,6 +712,10 @@ template <typename T> class OpImpl : public purify_op {
       return rc;
     return PURIFY_OK;
   }
+  int ensure_tv() {
+    if (tvq) return PURIFY_OK;
+    return alloc(&tvq, 4 * N());
+  }
 
   int read_scalars(cudaStream_t s) {
     CK(cudaMemcpyAsync(h_sc, sc, kNumScalars * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -727,7 +751,8 @@ template <typename T> class OpImpl : public purify_op {
     return PURIFY_OK;
   }
 
-  // 1e-3 ||Psi^H (nu^2 Re Phi^H y)||_inf with y the sorted visibilities.
+  // 1e-3 ||Psi^H (nu^2 Re Phi^H y)||_inf with y the sorted visibilities
+  // (Psi^H = I for the TV prior).
   int default_gamma(double nu, double* gamma, cudaStream_t s) {
     zero_q(s);
     GridPro<C> pro{};
@@ -739,8 +764,12 @@ template <typename T> class OpImpl : public purify_op {
     ep.mode = EP_STORE;
     ep.out = Ap;
     row_ep(ep, s);
-    sara_analysis<T>(sara, Ap, z1, s);
-    const int np = launch_reduce<T>(z1, D(), RED_MAXABS, sc, partials, s);
+    const T* coef = Ap;  // TV: the back-projection itself (L_1 = I)
+    if (prior == 0) {
+      sara_analysis<T>(sara, Ap, z1, s);
+      coef = z1;
+    }
+    const int np = launch_reduce<T>(coef, D(), RED_MAXABS, sc, partials, s);
     launch_max_partials(partials, np, sc, s);
     int rc = check(s, true);
     if (rc) return rc;
@@ -749,9 +778,11 @@ template <typename T> class OpImpl : public purify_op {
     return PURIFY_OK;
   }
 
-  // Population standard deviation of Psi^H x_hat (reweighting delta_1).
+  // Population standard deviation of Psi^H x_hat (reweighting delta_1), or
+  // of the gradient magnitudes |grad x_hat| for the TV prior.
   int coef_std(double* out, cudaStream_t s) {
-    sara_analysis<T>(sara, xh, z1, s);
+    if (prior == 1) tv_magnitude<T>(xh, z1, g.n, s);
+    else sara_analysis<T>(sara, xh, z1, s);
     const size_t D = this->D();
     int np = launch_reduce<T>(z1, D, RED_SUM, sc, partials, s);
     launch_finalize<T>(partials, np, FIN_MEAN, double(D), sc, s);
@@ -848,17 +879,38 @@ template <typename T> class OpImpl : public purify_op {
     grid(gp, b3);
     col_inv(b3);
     if (b3 != s) cudaEventRecord(ev_join, b3);
-    // block 1 (l1 on Psi^H x_hat) fused into the analysis, block 2 (positivity)
-    // fused into the synthesis: xs = x_1 + x_2
-    L1Block<T> b1{};
-    b1.z1 = z1;
-    b1.w = w;
-    b1.gamma = gamma;
-    b1.partials = partials;
-    int npo = 0;
-    PROF(KK_SARA_ANA, s, npo = sara_analysis_prox<T>(sara, xh, b1, s));
-    fin(partials, npo, FIN_OBJ, 0.0, s);
-    PROF(KK_SARA_SYN, s, sara_synthesis_pos<T>(sara, xh, z2, xs, s));
+    if (prior == 1) {
+      // block 1 (weighted TV, L_1 = I) with block 2 (positivity) in its
+      // epilogue: xs = x_1 + x_2
+      TvBlock<T> tb{};
+      tb.n = g.n;
+      tb.iters = tv_iters;
+      tb.gamma = gamma;
+      tb.xh = xh;
+      tb.z1 = z1;
+      tb.z2 = z2;
+      tb.w = w;
+      tb.v = sara.cs;
+      tb.qa = tvq;
+      tb.qb = tvq + 2 * n2;
+      tb.xs = xs;
+      tb.partials = partials;
+      int npo = 0;
+      PROF(KK_TV, s, npo = tv_block<T>(tb, s));
+      fin(partials, npo, FIN_OBJ, 0.0, s);
+    } else {
+      // block 1 (l1 on Psi^H x_hat) fused into the analysis, block 2 (positivity)
+      // fused into the synthesis: xs = x_1 + x_2
+      L1Block<T> b1{};
+      b1.z1 = z1;
+      b1.w = w;
+      b1.gamma = gamma;
+      b1.partials = partials;
+      int npo = 0;
+      PROF(KK_SARA_ANA, s, npo = sara_analysis_prox<T>(sara, xh, b1, s));
+      fin(partials, npo, FIN_OBJ, 0.0, s);
+      PROF(KK_SARA_SYN, s, sara_synthesis_pos<T>(sara, xh, z2, xs, s));
+    }
     // join: xs += nu Re Phi^H (2 r_3 - v_3)
     if (b3 != s) cudaStreamWaitEvent(s, ev_join, 0);
     RowEp<T> ep{};
@@ -900,6 +952,7 @@ template <typename T> class OpImpl : public purify_op {
       return PURIFY_ERR_INVALID;
     if (run.active) run_release();
     int rc = ensure_solver();
+    if (!rc && prior == 1) rc = ensure_tv();
     if (rc) return rc;
     cudaStream_t s = own;
     CK(cudaEventRecord(ev_in, user));
@@ -984,21 +1037,23 @@ template <typename T> class OpImpl : public purify_op {
     uint32_t magic, version;
     int32_t precision, n;
     int64_t M;
-    int32_t nbases, nblocks, round, t, total, converged, round_ready, pad;
+    int32_t nbases, nblocks, round, t, total, converged, round_ready, prior;
     double nu, gamma, delta1, prev;
   };
   static constexpr uint32_t kStateMagic = 0x4D445350u;  // "PSDM"
   int64_t state_bytes() const override {
-    return int64_t(sizeof(StateHeader)) + int64_t((3 * N() + 2 * D() + 2 * size_t(g.M)) * sizeof(T));
+    const size_t tv = prior == 1 ? 2 * N() : 0;  // the TV prox's warm-started dual
+    return int64_t(sizeof(StateHeader)) + int64_t((3 * N() + 2 * D() + 2 * size_t(g.M) + tv) * sizeof(T));
   }
-  // (device array, element count) pairs in checkpoint order.
-  void state_arrays(T* (&a)[6], size_t (&len)[6]) const {
-    T* arr[6] = {xh, xs, z1, z2, w, reinterpret_cast<T*>(z3)};
-    const size_t l[6] = {N(), N(), D(), N(), D(), 2 * size_t(g.M)};
-    for (int k = 0; k < 6; ++k) {
+  // (device array, element count) pairs in checkpoint order; returns their number.
+  int state_arrays(T* (&a)[7], size_t (&len)[7]) const {
+    T* arr[7] = {xh, xs, z1, z2, w, reinterpret_cast<T*>(z3), tvq};
+    const size_t l[7] = {N(), N(), D(), N(), D(), 2 * size_t(g.M), 2 * N()};
+    for (int k = 0; k < 7; ++k) {
       a[k] = arr[k];
       len[k] = l[k];
     }
+    return prior == 1 ? 7 : 6;
   }
   int save_state(void* host, int64_t bytes) override {
     if (!run.active || !host || bytes < state_bytes()) return PURIFY_ERR_INVALID;
@@ -1016,6 +1071,7 @@ template <typename T> class OpImpl : public purify_op {
     h.total = run.total;
     h.converged = run.converged;
     h.round_ready = run.round_ready ? 1 : 0;
+    h.prior = prior;
     h.nu = run.nu;
     h.gamma = run.gamma;
     h.delta1 = run.delta1;
@@ -1023,10 +1079,10 @@ template <typename T> class OpImpl : public purify_op {
     unsigned char* dst = static_cast<unsigned char*>(host);
     std::memcpy(dst, &h, sizeof(h));
     dst += sizeof(h);
-    T* a[6];
-    size_t len[6];
-    state_arrays(a, len);
-    for (int k = 0; k < 6; ++k) {
+    T* a[7];
+    size_t len[7];
+    const int na = state_arrays(a, len);
+    for (int k = 0; k < na; ++k) {
       CK(cudaMemcpy(dst, a[k], len[k] * sizeof(T), cudaMemcpyDeviceToHost));
       dst += len[k] * sizeof(T);
     }
@@ -1037,16 +1093,17 @@ template <typename T> class OpImpl : public purify_op {
     StateHeader h;
     std::memcpy(&h, host, sizeof(h));
     if (h.magic != kStateMagic || h.version != 1 || h.precision != (sizeof(T) == 4 ? PURIFY_FP32 : PURIFY_FP64) ||
-        h.n != g.n || h.M != g.M || h.nbases != sara.nbases || h.nblocks != nblocks || h.round > run.P.n_reweight) {
+        h.n != g.n || h.M != g.M || h.nbases != sara.nbases || h.nblocks != nblocks || h.prior != prior ||
+        h.round > run.P.n_reweight) {
       note_error("purify_solve_load", __LINE__, "checkpoint does not match this operator or solve");
       return PURIFY_ERR_INVALID;
     }
     CK(cudaStreamSynchronize(own));
     const unsigned char* src = static_cast<const unsigned char*>(host) + sizeof(h);
-    T* a[6];
-    size_t len[6];
-    state_arrays(a, len);
-    for (int k = 0; k < 6; ++k) {
+    T* a[7];
+    size_t len[7];
+    const int na = state_arrays(a, len);
+    for (int k = 0; k < na; ++k) {
       CK(cudaMemcpy(a[k], src, len[k] * sizeof(T), cudaMemcpyHostToDevice));
       src += len[k] * sizeof(T);
     }
@@ -1082,10 +1139,12 @@ template <typename T> class OpImpl : public purify_op {
       }
       const double dmin = P.delta_min > 0 ? P.delta_min : 1e-4 * run.delta1;
       const double delta = std::max(std::pow(run.decay, run.round - 1) * run.delta1, dmin);
-      sara_analysis<T>(sara, xh, w, s);
+      if (prior == 1) tv_magnitude<T>(xh, w, g.n, s);  // RWTV: delta / (delta + |grad x_hat|)
+      else sara_analysis<T>(sara, xh, w, s);
       launch_reweight<T>(w, D(), delta, s);
     }
     cudaMemsetAsync(z1, 0, D() * sizeof(T), s);
+    if (prior == 1) cudaMemsetAsync(tvq, 0, 2 * n2 * sizeof(T), s);
     cudaMemsetAsync(z2, 0, n2 * sizeof(T), s);
     cudaMemsetAsync(z3, 0, M * sizeof(C), s);
     if (run.round > 0 && P.warm_start) {
@@ -1431,6 +1490,11 @@ int purify_op_dictionary(const purify_op* op, unsigned* mask, int* n_bases) {
   return PURIFY_OK;
 }
 
+int purify_op_set_prior(purify_op* op, int prior, int tv_iters) {
+  if (!op) return PURIFY_ERR_INVALID;
+  return op->set_prior(prior, tv_iters);
+}
+
 int purify_gram(purify_op* op, const void* x, void* out, int mode, void* stream) {
   if (!op || !x || !out) return PURIFY_ERR_INVALID;
   return op->gram(x, out, mode, static_cast<cudaStream_t>(stream));
@@ -1454,7 +1518,7 @@ int purify_profile_read(purify_op* op, int kind, double* total_ms, int64_t* laun
 const char* purify_kernel_name(int kind) {
   static const char* names[] = {"row_fwd", "col_fwd", "degrid", "grid", "gram", "col_inv",
                                 "row_inv", "sara_analysis", "sara_synthesis", "vector", "memset", "col_conv",
-                                "row_fwd_h", "row_inv_h"};
+                                "row_fwd_h", "row_inv_h", "tv"};
   if (kind < 0 || kind >= PURIFY_NUM_KERNEL_KINDS) return "unknown";
   return names[kind];
 }

@@ -265,4 +265,25 @@ template <typename T>
 void sara_synthesis_pos(const SaraPlan<T>& P, const T* xh, T* z2, T* xs, cudaStream_t s);
 int sara_partials_capacity(int n, int levels);
 
+// TV prior (Section 4's TV / RWTV): the SDMM TV block with the positivity
+// block fused into its epilogue (tv.cu).  v: n x n scratch; qa, qb: the
+// dual's two buffers (2 n^2 each; the dual enters and leaves in qa).
+template <typename T> struct TvBlock {
+  int n, iters;
+  double gamma;
+  const T* xh;
+  T* z1;
+  T* z2;
+  const T* w;  // may be null (w = 1)
+  T* v;
+  T* qa;
+  T* qb;
+  T* xs;
+  double* partials;  // per-CTA objective partials (tv_partials(n) of them)
+};
+template <typename T> int tv_block(const TvBlock<T>& b, cudaStream_t s);
+// |grad x| per pixel (forward differences, zero past the last row / column).
+template <typename T> void tv_magnitude(const T* x, T* out, int n, cudaStream_t s);
+int tv_partials(int n);
+
 }  // namespace purify

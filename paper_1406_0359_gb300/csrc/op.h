@@ -18,6 +18,7 @@ struct purify_op {
   virtual int gram(const void* x, void* out, int mode, cudaStream_t s) = 0;
   virtual int set_blocks(const int* blocks, int R, cudaStream_t s) = 0;
   virtual int set_dictionary(unsigned mask) = 0;
+  virtual int set_prior(int prior, int tv_iters) = 0;
   virtual unsigned dictionary(int* nbases) const = 0;
   // resumable solve (request server)
   virtual int begin(const void* y, const purify_params* p, cudaStream_t user) = 0;
@@ -38,7 +39,7 @@ struct purify_op {
 
   // ---- kernel timing (instrumentation)
   enum Kind { KK_ROW_FWD = 0, KK_COL_FWD, KK_DEGRID, KK_GRID, KK_GRAM, KK_COL_INV, KK_ROW_INV, KK_SARA_ANA,
-              KK_SARA_SYN, KK_VEC, KK_MEMSET, KK_COL_CONV, KK_ROW_FWD_H, KK_ROW_INV_H, KK_COUNT };
+              KK_SARA_SYN, KK_VEC, KK_MEMSET, KK_COL_CONV, KK_ROW_FWD_H, KK_ROW_INV_H, KK_TV, KK_COUNT };
   bool prof = false;
   struct Pending { int kind; cudaEvent_t a, b; };
   std::vector<Pending> pending;
