@@ -32,7 +32,7 @@ UNIT = "iters/s"
 WORKLOAD = "large_1024"
 # DRAM bytes (read + write) per launch from the committed ncu capture of each
 # kernel at this workload (profiles/); kernels changed since have no entry.
-MEASURED_TRAFFIC = {"col_conv": 16.847616e6 + 0.945664e6}
+MEASURED_TRAFFIC = {}
 
 
 # ----------------------------------------------------------------- helpers
@@ -321,6 +321,11 @@ def run_ours(args, ws, rank, local):
                      "reference": "same operators and solver in FP64 on the GPU"}
         op64.close()
 
+    batch = None
+    if rank == 0 and not args.no_batch_summary:
+        batch = batch_study(16, 20, seed=40, plain_arm=False)
+        batch["note"] = "reduced form of the 64-instance batch (bench.py --batch); solves/s of 16 instances x 20 iterations"
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         y1 = op.phi(xt)
@@ -352,6 +357,7 @@ def run_ours(args, ws, rank, local):
         "solver": {"objective": res.stats["objective"], "residual_over_eps": res.stats["residual"] / eps,
                    "nu": nu, "gamma": gamma, "op_device_bytes": info["device_bytes"], "work_items": info["n_items"]},
         "cpu_baseline": cpu,
+        "batch_16x20": batch,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -524,63 +530,108 @@ def _drain(srv, ids, arrivals=None, reqs=None, params=None):
     return wall, res
 
 
-def run_batch(args):
-    """64 uneven instances (images 128/256/512 square, M uniform in [0.5N, 3N])
-    advanced together by the request server (all admitted at once), against
-    the same instances solved one at a time.  Tile/chunk per image size come
-    from the autotuner."""
+def batch_study(count, iters, seed=4, server_arm=False, plain_arm=True):
+    """`count` uneven instances (images 128/256/512 square, M uniform in
+    [0.5N, 3N], seeded skies and coverages): the batched solver
+    (purify_batch_solve: one launch per pass per image side, one graph per
+    iteration) against the same instances solved one at a time in FP32 and by
+    the plain FP64 GPU solver (no graph replay), each with `iters` SDMM
+    iterations.  nu and gamma are taken once per instance and given to every
+    arm; operators are built before timing.  Tile/chunk per image side from
+    the autotuner."""
     import numpy as np
     import torch
 
-    from paper_1406_0359_gb300 import build as _build
-    from paper_1406_0359_gb300.binding import Server, purify_autotune
+    from paper_1406_0359_gb300.binding import Operator, Server, batch_solve, purify_autotune
 
-    _build.build()
     dev = torch.device("cuda", 0)
-    rng = np.random.default_rng(4)
+    rng = np.random.default_rng(seed)
     reqs = []
-    for i in range(args.batch_size):
+    for i in range(count):
         n = int(rng.choice([128, 256, 512]))
         M = int(rng.uniform(0.5, 3.0) * n * n)
-        reqs.append(_make_request(n, M, 4 + i, dev))
+        reqs.append(_make_request(n, M, seed + i, dev))
     tuned = {}
-    for n in (128, 256, 512):
+    for n in sorted({r["n"] for r in reqs}):
         r = next(q for q in reqs if q["n"] == n)
         tuned[n] = purify_autotune(torch.as_tensor(r["uv"], device=dev), n, 3)
-    params = dict(t_max=args.batch_iters, cg_iters=10)
-    # batched FP32 (all admitted), FP32 one at a time, and the plain GPU solver:
-    # FP64, no graph replay, one at a time
-    arms = (("batched", len(reqs), "fp32", {}), ("sequential", 1, "fp32", {}),
-            ("plain_fp64", 1, "fp64", {"use_graph": 0}))
-    out = {}
-    for label, slots, prec, extra in arms:
-        srv = Server(int(150e9), slots)
+
+    def ops_for(prec):
+        return [Operator(torch.as_tensor(r["uv"], device=dev), r["n"], 3, prec, tile=tuned[r["n"]][0],
+                         chunk=tuned[r["n"]][1]) for r in reqs]
+
+    ops = ops_for("fp32")
+    ys = [torch.as_tensor(r["y"], dtype=torch.complex64, device=dev) for r in reqs]
+    eps = [r["eps"] for r in reqs]
+    # nu, gamma by the library's rules, once per instance (also builds each CG operator)
+    first = batch_solve(ops, ys, eps, t_max=1, cg_iters=1)
+    nus, gammas = [r.stats["nu"] for r in first], [r.stats["gamma"] for r in first]
+    kw = dict(t_max=iters, cg_iters=10)
+    batch_solve(ops, ys, eps, nu=nus, gamma=gammas, **kw)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res_b = batch_solve(ops, ys, eps, nu=nus, gamma=gammas, **kw)
+    torch.cuda.synchronize()
+    t_b = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    res_s = [op.solve(y, e, nu=nu, gamma=g, **kw) for op, y, e, nu, g in zip(ops, ys, eps, nus, gammas)]
+    torch.cuda.synchronize()
+    t_s = time.perf_counter() - t0
+    out = {"instances": count, "iterations_per_solve": iters,
+           "batched_solves_per_s": round(count / t_b, 3), "sequential_fp32_solves_per_s": round(count / t_s, 3),
+           "speedup_vs_sequential_fp32": round(t_s / t_b, 3),
+           "max_rel_diff_batched_vs_alone": max(float(torch.linalg.vector_norm(a.x - b.x) / torch.linalg.vector_norm(b.x))
+                                                for a, b in zip(res_b, res_s)),
+           "autotuned": {str(k): {"tile": v[0], "chunk": v[1]} for k, v in tuned.items()}}
+    xb = [r.x.cpu().numpy().astype(np.float64) for r in res_b]
+    out["snr_db_mean"] = round(float(np.mean([_snr_db(r["x"], x) for r, x in zip(reqs, xb)])), 4)
+    for o in ops:
+        o.close()
+    if plain_arm:
+        ops64 = ops_for("fp64")
+        ys64 = [y.to(torch.complex128) for y in ys]
+        ops64[0].solve(ys64[0], eps[0], nu=nus[0], gamma=gammas[0], t_max=1, cg_iters=1, use_graph=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res_p = [op.solve(y, e, nu=nu, gamma=g, use_graph=False, **kw)
+                 for op, y, e, nu, g in zip(ops64, ys64, eps, nus, gammas)]
+        torch.cuda.synchronize()
+        t_p = time.perf_counter() - t0
+        xp = [r.x.cpu().numpy() for r in res_p]
+        snr_p = [_snr_db(r["x"], x) for r, x in zip(reqs, xp)]
+        out.update({"plain_fp64_solves_per_s": round(count / t_p, 3), "speedup_vs_plain_fp64": round(t_p / t_b, 3),
+                    "max_rel_diff_vs_plain_fp64": max(float(np.linalg.norm(a - b) / np.linalg.norm(b))
+                                                      for a, b in zip(xb, xp)),
+                    "snr_db_mean_plain_fp64": round(float(np.mean(snr_p)), 4),
+                    "max_abs_snr_diff_db": round(float(np.max(np.abs(np.array(
+                        [_snr_db(r["x"], x) for r, x in zip(reqs, xb)]) - np.array(snr_p)))), 6)})
+        for o in ops64:
+            o.close()
+    if server_arm:  # the request server with every instance admitted at once (one stream per solve)
+        srv = Server(int(150e9), count)
         for n, (tile, chunk, _) in tuned.items():
             srv.set_options(n, tile, chunk)
-        ids = [srv.submit(r["uv"], r["y"], r["n"], 3, r["eps"], precision=prec, **params, **extra) for r in reqs]
-        wall, res = _drain(srv, ids)
+        ids = [srv.submit(r["uv"], r["y"], r["n"], 3, r["eps"], nu=nu, gamma=g, **kw)
+               for r, nu, g in zip(reqs, nus, gammas)]
+        wall, _ = _drain(srv, ids)
         srv.close()
-        out[label] = (wall, res)
-    xb = [r[0] for r in out["batched"][1]]
-    xs = [r[0] for r in out["sequential"][1]]
-    xp = [r[0] for r in out["plain_fp64"][1]]
-    worst = max(float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(xb, xs))
-    worst64 = max(float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(xb, xp))
-    snr_b = [_snr_db(r["x"], x) for r, x in zip(reqs, xb)]
-    snr_p = [_snr_db(r["x"], x) for r, x in zip(reqs, xp)]
-    line = {"metric": "batched SARA-SDMM solves/s, 64 uneven instances (128..512 square, M in [0.5N, 3N])",
-            "value": round(len(reqs) / out["batched"][0], 3), "unit": "solves/s", "higher_is_better": True,
-            "sequential_fp32_solves_per_s": round(len(reqs) / out["sequential"][0], 3),
-            "plain_fp64_solves_per_s": round(len(reqs) / out["plain_fp64"][0], 3),
-            "speedup_vs_sequential_fp32": round(out["sequential"][0] / out["batched"][0], 3),
-            "speedup_vs_plain_fp64": round(out["plain_fp64"][0] / out["batched"][0], 3),
-            "iterations_per_solve": args.batch_iters, "dtype": "f32 (compensated reductions, FP64 finals)",
-            "data": "synthetic",
-            "max_rel_diff_batched_vs_alone": worst, "max_rel_diff_vs_plain_fp64": worst64,
-            "snr_db_mean": round(float(np.mean(snr_b)), 4), "snr_db_mean_plain_fp64": round(float(np.mean(snr_p)), 4),
-            "max_abs_snr_diff_db": round(float(np.max(np.abs(np.array(snr_b) - np.array(snr_p)))), 6),
-            "autotuned": {str(k): {"tile": v[0], "chunk": v[1], "phi_phiH_ms": round(v[2], 4)} for k, v in tuned.items()},
-            "config": {"workload": "64 independent solves, seeds 4+i", "mode": "request server, all admitted"}}
+        out["server_all_admitted_solves_per_s"] = round(count / wall, 3)
+    return out
+
+
+def run_batch(args):
+    """C4: 64 uneven instances through the batched solver against one at a
+    time (FP32 graph replay; plain FP64), and the request server's form."""
+    from paper_1406_0359_gb300 import build as _build
+
+    _build.build()
+    res = batch_study(args.batch_size, args.batch_iters, server_arm=True)
+    line = {"metric": f"batched SARA-SDMM solves/s, {args.batch_size} uneven instances (128..512 square, "
+                      "M in [0.5N, 3N])", "value": res["batched_solves_per_s"], "unit": "solves/s",
+            "higher_is_better": True, "dtype": "f32 (compensated reductions, FP64 finals)", "data": "synthetic",
+            "config": {"workload": f"{args.batch_size} independent solves, seeds 4+i",
+                       "mode": "purify_batch_solve: one launch per pass per image side, one graph per iteration"}}
+    line.update(res)
     print(json.dumps(line), flush=True)
 
 
@@ -653,6 +704,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-batch-summary", action="store_true")
     ap.add_argument("--batch", action="store_true", help="64 uneven instances: batched vs one at a time")
     ap.add_argument("--batch-size", type=int, default=64)
     ap.add_argument("--batch-iters", type=int, default=50)

@@ -284,6 +284,33 @@ int purify_sdmm_solve(purify_op* op, const void* y, const purify_params* params,
                       void* x_out, purify_stats* stats, void* stream);
 
 /*
+ * purify_batch_solve -- many independent SARA solves (Eq. 3 by Algorithm 1,
+ * as purify_sdmm_solve; e.g. frequency channels or fields) advanced
+ * together.  Instances are grouped by image side; within a group every pass
+ * of an SDMM iteration (CG passes, degridding, gridding, projections, SARA
+ * levels, vector steps) is one kernel launch over all of the group's
+ * instances, reading each instance's arguments from a device table, and one
+ * SDMM iteration of the whole batch is one captured CUDA graph in which the
+ * groups run side by side.
+ *   count   number of instances (>= 1).
+ *   ops     count distinct operators of one precision, image sides 64..1024,
+ *           one visibility block, the l1 prior (any dictionary).
+ *   y       count device pointers, each instance's visibilities (caller order).
+ *   params  count parameter sets: each instance's eps, gamma, nu (<= 0:
+ *           computed per instance as in purify_sdmm_solve), delta rules; t_max,
+ *           cg_iters and n_reweight equal for all, xi = 0 (fixed counts); the
+ *           CG operator is the precomputed convolution form (gram 0 refused).
+ *   x_out   count device pointers, real[n_i][n_i].
+ *   stats   host, count entries, may be NULL.
+ * Each instance's result equals its purify_sdmm_solve up to rounding (the
+ * gridding atomics and the order of partial sums).  Blocks until done;
+ * PURIFY_ERR_INVALID (purify_last_error says which rule) for instances the
+ * batch cannot group.
+ */
+int purify_batch_solve(int count, purify_op* const* ops, const void* const* y, const purify_params* params,
+                       void* const* x_out, purify_stats* stats, void* stream);
+
+/*
  * Resumable solve and checkpoints.  purify_sdmm_solve is begin + steps + end
  * in one call; the three parts are also public so that a caller can stop
  * between SDMM iterations, save the solver state to host memory, and resume

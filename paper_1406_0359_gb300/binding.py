@@ -62,7 +62,7 @@ EXPORTS = ["purify_op_create", "purify_op_destroy", "purify_op_info", "purify_ph
            "purify_server_set_options", "purify_op_set_dictionary", "purify_op_dictionary",
            "purify_solve_begin", "purify_solve_step", "purify_solve_end", "purify_solve_state_bytes",
            "purify_solve_save", "purify_solve_load", "purify_set_wait_limit", "purify_wait_selftest",
-           "purify_server_cancel", "purify_op_set_prior"]
+           "purify_server_cancel", "purify_op_set_prior", "purify_batch_solve"]
 KERNEL_KINDS = ["row_fwd", "col_fwd", "degrid", "grid", "gram", "col_inv", "row_inv", "sara_analysis",
                 "sara_synthesis", "vector", "memset", "col_conv", "row_fwd_h", "row_inv_h", "tv"]
 
@@ -122,6 +122,8 @@ def lib() -> ctypes.CDLL:
     L.purify_wait_selftest.argtypes = [ci, vp]
     L.purify_server_cancel.argtypes = [vp, ci]
     L.purify_op_set_prior.argtypes = [vp, ci, ci]
+    L.purify_batch_solve.argtypes = [ci, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(purify_params),
+                                     ctypes.POINTER(vp), ctypes.POINTER(purify_stats), vp]
     L.purify_last_error.argtypes = []
     L.purify_last_error.restype = ctypes.c_char_p
     for f in EXPORTS:
@@ -456,6 +458,26 @@ class Operator:
         rc, st = purify_sdmm_solve(self.h, _dptr(y, self.cdtype, (self.M,)), p, _dptr(x, self.rdtype, (n, n)),
                                    stream)
         return SolveResult(x, st.as_dict(), rc)
+
+
+def batch_solve(ops: list, ys: list, eps: list, stream=None, **kw) -> list:
+    """purify_batch_solve over Operators `ops` with visibilities `ys` and
+    per-instance bounds `eps`; keyword arguments (shared, or a list per
+    instance for gamma / nu) as Operator.solve.  Returns SolveResults."""
+    count = len(ops)
+    per = {k: kw.pop(k) for k in ("gamma", "nu") if isinstance(kw.get(k), (list, tuple))}
+    P = (purify_params * count)()
+    st = (purify_stats * count)()
+    xs = [torch.empty(o.n, o.n, dtype=o.rdtype, device="cuda") for o in ops]
+    for i, o in enumerate(ops):
+        extra = {k: v[i] for k, v in per.items()}
+        P[i] = Operator.params(float(eps[i]), **kw, **extra)
+    H = (ctypes.c_void_p * count)(*[o.h for o in ops])
+    Y = (ctypes.c_void_p * count)(*[_dptr(y, o.cdtype, (o.M,)).value for y, o in zip(ys, ops)])
+    X = (ctypes.c_void_p * count)(*[x.data_ptr() for x in xs])
+    rc = lib().purify_batch_solve(count, H, Y, P, X, st, _stream(stream))
+    _check(rc, "purify_batch_solve", allow=(-5,))
+    return [SolveResult(x, s.as_dict(), rc) for x, s in zip(xs, st)]
 
 
 def purify_estimate_bytes(M: int, n: int, levels: int, precision: int = PURIFY_FP32) -> int:

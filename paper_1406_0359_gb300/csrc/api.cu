@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <initializer_list>
 #include <new>
@@ -213,6 +214,34 @@ template <typename T> class OpImpl : public purify_op {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr, ev_join = nullptr;
   double* bpart = nullptr;     // ball-block partials (2 per work item), apart from the l1 block's
   int bpart_cap = 0;
+  CUtensorMap* tmap_dev = nullptr;  // device copy of tmap (batched degridding reads it there)
+
+  // ---- recording of one SDMM iteration for the batched solver: with `rec`
+  // set, the pass helpers append their launch arguments instead of
+  // launching (branch 1 = the ball block's stream).
+  enum RecKind { R_RF, R_CC, R_RI, R_CF, R_CI, R_DG, R_GR, R_B1, R_ZERO, R_AXPY, R_FIN, R_SARA, R_FORK, R_JOIN };
+  struct PassRec {
+    int kind = 0, branch = 0;
+    RowFwdArgs<T> rf{};
+    ColConvArgs<T> cc{};
+    RowInvArgs<T> ri{};
+    ColFwdArgs<T> cf{};
+    ColInvArgs<T> ci{};
+    DegridArgs<T> dg{};
+    GridArgs<T> gr{};
+    Ball1Args b1{};
+    ZeroArgs z{};
+    AxpyArgs<T> ax{};
+    FinArgs fin{};
+    SaraBatchInst<T> sara{};
+  };
+  std::vector<PassRec>* rec = nullptr;
+  PassRec& record(int kind, cudaStream_t s) {
+    rec->emplace_back();
+    rec->back().kind = kind;
+    rec->back().branch = (s == aux && aux != own) ? 1 : 0;
+    return rec->back();
+  }
 
   int partials_cap = 0;
   int size_partials() {
@@ -481,6 +510,8 @@ template <typename T> class OpImpl : public purify_op {
       note_error("cuTensorMapEncodeTiled failed", __LINE__, buf);
       return PURIFY_ERR_CUDA;
     }
+    if ((rc = alloc(&tmap_dev, 1))) return rc;
+    CK(cudaMemcpyAsync(tmap_dev, &tmap, sizeof(CUtensorMap), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     if ((rc = take_input_flag("purify_op_create", "uv holds a non-finite coordinate"))) return rc;
     return PURIFY_OK;
@@ -510,20 +541,49 @@ template <typename T> class OpImpl : public purify_op {
   // F Z S in real form (the image is real): row pairs to half spectra, then
   // the half-spectrum columns to the full padded grid with their mirrors.
   void fwd_grid(const RowPro<T>& pro, cudaStream_t s) {
+    if (rec) {
+      record(R_RF, s).rf = RowFwdArgs<T>{g, pro, deapod, gridA, tw, row_pass_nseq(g)};
+      record(R_CF, s).cf = ColFwdArgs<T>{g, gridA, gridP, tw, col_pass_width<T>()};
+      return;
+    }
     PROF(KK_ROW_FWD, s, launch_row_fwd_h<T>(g, pro, deapod, gridA, tw, s));
     PROF(KK_COL_FWD, s, launch_col_fwd_h<T>(g, gridA, gridP, tw, s));
   }
-  void zero_q(cudaStream_t s) { PROF(KK_MEMSET, s, cudaMemsetAsync(gridQ, 0, grid_bytes(), s)); }
+  void zero_q(cudaStream_t s) {
+    if (rec) {
+      record(R_ZERO, s).z = ZeroArgs{gridQ, grid_bytes()};
+      return;
+    }
+    PROF(KK_MEMSET, s, cudaMemsetAsync(gridQ, 0, grid_bytes(), s));
+  }
   // Re F^H of the gridded accumulator: the half-spectrum columns of its
   // Hermitian part (the row pass follows in row_ep / normal_back).
-  void col_inv(cudaStream_t s) { PROF(KK_COL_INV, s, launch_col_inv_h<T>(g, gridQ, gridA, tw, s)); }
+  void col_inv(cudaStream_t s) {
+    if (rec) {
+      record(R_CI, s).ci = ColInvArgs<T>{g, gridQ, gridA, tw, col_pass_width<T>()};
+      return;
+    }
+    PROF(KK_COL_INV, s, launch_col_inv_h<T>(g, gridQ, gridA, tw, s));
+  }
   void degrid(const DegridEp<C>& ep, cudaStream_t s) {
+    if (rec) {
+      record(R_DG, s).dg = DegridArgs<T>{g, tmap_dev, items, n_items, pos, perm, ep, err};
+      return;
+    }
     PROF(KK_DEGRID, s, launch_degrid<T>(g, tmap, items, n_items, pos, perm, kb, ep, err, s));
   }
   void grid(const GridPro<C>& pro, cudaStream_t s) {
+    if (rec) {
+      record(R_GR, s).gr = GridArgs<T>{g, items, n_items, pos, perm, pro, gridQ};
+      return;
+    }
     PROF(KK_GRID, s, launch_grid<T>(g, items, n_items, pos, perm, kb, pro, gridQ, s));
   }
   void fin(const double* pa, int na, int op, double arg, cudaStream_t s) {
+    if (rec) {
+      record(R_FIN, s).fin = FinArgs{pa, na, op, arg, sc};
+      return;
+    }
     PROF(KK_VEC, s, launch_finalize<T>(pa, na, op, arg, sc, s));
   }
   RowPro<T> plain(const T* x) const {
@@ -542,6 +602,10 @@ template <typename T> class OpImpl : public purify_op {
   int row_ep(const RowEp<T>& ep_in, cudaStream_t s) {
     RowEp<T> ep = ep_in;
     if (!ep.err) ep.err = err;
+    if (rec) {
+      record(R_RI, s).ri = RowInvArgs<T>{g, gridA, deapod, ep, tw, row_pass_nseq(g), row_inv_blocks(g)};
+      return row_inv_blocks(g);
+    }
     int np = 0;
     PROF(KK_ROW_INV, s, np = launch_row_inv_h<T>(g, gridA, deapod, ep, tw, s));
     return np;
@@ -594,6 +658,11 @@ template <typename T> class OpImpl : public purify_op {
   // Front half of Re(Phi^H Phi) x: up to the half-spectrum rows in gridA, by the
   // NUFFT (G^H G per application) or by the precomputed convolution.
   void normal_front(const RowPro<T>& pro, cudaStream_t s) {
+    if (rec) {  // the batched solver takes the convolution form only
+      record(R_RF, s).rf = RowFwdArgs<T>{g, pro, nullptr, gridA, tw, row_pass_nseq(g)};
+      record(R_CC, s).cc = ColConvArgs<T>{g, gridA, khat, khat + size_t(g.K / 2) * g.K, tw, col_pass_width<T>()};
+      return;
+    }
     if (toep) {
       PROF(KK_ROW_FWD_H, s, launch_row_fwd_h<T>(g, pro, nullptr, gridA, tw, s));
       PROF(KK_COL_CONV, s, launch_col_conv_h<T>(g, gridA, khat, tw, s));
@@ -604,6 +673,10 @@ template <typename T> class OpImpl : public purify_op {
   int normal_back(const RowEp<T>& ep_in, cudaStream_t s) {
     RowEp<T> ep = ep_in;
     if (!ep.err) ep.err = err;
+    if (rec) {
+      record(R_RI, s).ri = RowInvArgs<T>{g, gridA, nullptr, ep, tw, row_pass_nseq(g), row_inv_blocks(g)};
+      return row_inv_blocks(g);
+    }
     int np = 0;
     if (toep) PROF(KK_ROW_INV_H, s, np = launch_row_inv_h<T>(g, gridA, nullptr, ep, tw, s));
     else PROF(KK_ROW_INV, s, np = launch_row_inv_h<T>(g, gridA, deapod, ep, tw, s));
@@ -843,7 +916,10 @@ template <typename T> class OpImpl : public purify_op {
       ep.ticket = tickets + 1;
       normal_back(ep, s);
     }
-    if (cg_iters > 0) PROF(KK_VEC, s, launch_axpy<T>(xh, p, sc, S_ALPHA, n2, s));  // last step: x += alpha p
+    if (cg_iters > 0) {  // last step: x += alpha p
+      if (rec) record(R_AXPY, s).ax = AxpyArgs<T>{xh, p, sc, S_ALPHA, n2};
+      else PROF(KK_VEC, s, launch_axpy<T>(xh, p, sc, S_ALPHA, n2, s));
+    }
     // The three proximal blocks (steps 6-8) are independent until their sum:
     // the ball block's degridding, projection and gridding run on the second
     // stream beside the l1 and positivity blocks, and the join feeds its last
@@ -851,7 +927,9 @@ template <typename T> class OpImpl : public purify_op {
     // (With kernel timing enabled both branches stay on one stream, so that
     // every kernel's time is its own.)
     cudaStream_t b3 = prof ? s : aux;
-    if (b3 != s) {
+    if (rec) {
+      record(R_FORK, s);
+    } else if (b3 != s) {
       cudaEventRecord(ev_fork, s);
       cudaStreamWaitEvent(b3, ev_fork, 0);
     }
@@ -865,8 +943,11 @@ template <typename T> class OpImpl : public purify_op {
     dep.part0 = bpart;
     dep.part1 = bpart + n_items;
     degrid(dep, b3);
-    PROF(KK_VEC, b3, launch_finalize_blocks<T>(bpart, bpart + n_items, reinterpret_cast<const int*>(items), n_items,
-                                                nblocks, nu, eps_dev, scale_dev, sc, fin_part, tickets + 2, b3));
+    if (rec)
+      record(R_B1, b3).b1 = Ball1Args{bpart, bpart + n_items, n_items, nu, eps_dev, scale_dev, sc, fin_part, tickets + 2};
+    else
+      PROF(KK_VEC, b3, launch_finalize_blocks<T>(bpart, bpart + n_items, reinterpret_cast<const int*>(items), n_items,
+                                                  nblocks, nu, eps_dev, scale_dev, sc, fin_part, tickets + 2, b3));
     zero_q(b3);
     GridPro<C> gp{};
     gp.mode = GP_BALL;
@@ -878,7 +959,8 @@ template <typename T> class OpImpl : public purify_op {
     gp.block_scale = scale_dev;
     grid(gp, b3);
     col_inv(b3);
-    if (b3 != s) cudaEventRecord(ev_join, b3);
+    if (rec) record(R_JOIN, s);
+    else if (b3 != s) cudaEventRecord(ev_join, b3);
     if (prior == 1) {
       // block 1 (weighted TV, L_1 = I) with block 2 (positivity) in its
       // epilogue: xs = x_1 + x_2
@@ -898,6 +980,9 @@ template <typename T> class OpImpl : public purify_op {
       int npo = 0;
       PROF(KK_TV, s, npo = tv_block<T>(tb, s));
       fin(partials, npo, FIN_OBJ, 0.0, s);
+    } else if (rec) {
+      record(R_SARA, s).sara = SaraBatchInst<T>{&sara, xh, z1, w, gamma, partials, z2, xs};
+      fin(partials, sara_prox_partials<T>(sara), FIN_OBJ, 0.0, s);
     } else {
       // block 1 (l1 on Psi^H x_hat) fused into the analysis, block 2 (positivity)
       // fused into the synthesis: xs = x_1 + x_2
@@ -912,7 +997,7 @@ template <typename T> class OpImpl : public purify_op {
       PROF(KK_SARA_SYN, s, sara_synthesis_pos<T>(sara, xh, z2, xs, s));
     }
     // join: xs += nu Re Phi^H (2 r_3 - v_3)
-    if (b3 != s) cudaStreamWaitEvent(s, ev_join, 0);
+    if (!rec && b3 != s) cudaStreamWaitEvent(s, ev_join, 0);
     RowEp<T> ep{};
     ep.mode = EP_XS_ADD;
     ep.out = xs;
@@ -1283,6 +1368,288 @@ template <typename T> class OpImpl : public purify_op {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Batched solver: many independent SARA-SDMM instances (different images, uv
+// coverages and visibility counts) advanced together.  Instances are grouped
+// by image side; for each group every pass of an SDMM iteration -- the CG
+// passes, the ball block, the SARA blocks, the vector steps -- is ONE launch
+// over all of the group's instances, its arguments read from a device table
+// (one entry per instance, recorded from each instance's own iteration so
+// that the batched passes are exactly the single-instance ones).  One SDMM
+// iteration of the whole batch is one captured CUDA graph whose groups run
+// as parallel branches.
+template <typename T> class BatchImpl {
+  typedef typename OpImpl<T>::PassRec Rec;
+
+ public:
+  struct Group {
+    std::vector<int> idx;              // instances (indices into ops)
+    std::vector<int> kinds, branches;  // the recorded pass sequence
+    std::vector<size_t> off;           // offset of each pass's table in the group's buffer
+    void* dev = nullptr;
+    SaraBatch<T>* sara = nullptr;
+    int max_items = 0, max_tb = 8;
+    size_t max_q = 0;
+    cudaStream_t main = nullptr, aux = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, done = nullptr;
+  };
+  std::vector<OpImpl<T>*> ops;
+  std::vector<Group> groups;
+  cudaStream_t bs = nullptr;
+  cudaEvent_t ev0 = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+
+  ~BatchImpl() {
+    if (bs) cudaStreamSynchronize(bs);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    for (Group& gr : groups) {
+      if (gr.dev) cudaFree(gr.dev);
+      sara_batch_destroy(gr.sara);
+      const cudaEvent_t evs[3] = {gr.fork, gr.join, gr.done};
+      for (cudaEvent_t e : evs)
+        if (e) cudaEventDestroy(e);
+      if (gr.main) cudaStreamDestroy(gr.main);
+      if (gr.aux) cudaStreamDestroy(gr.aux);
+    }
+    if (ev0) cudaEventDestroy(ev0);
+    if (bs) cudaStreamDestroy(bs);
+  }
+
+  // Record every instance's iteration, group by image side, upload the tables.
+  int build() {
+    CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming));
+    std::vector<std::vector<Rec>> recs(ops.size());
+    for (size_t i = 0; i < ops.size(); ++i) {
+      OpImpl<T>* o = ops[i];
+      o->rec = &recs[i];
+      o->iteration(o->run.nu, o->run.gamma, o->run.P.eps, o->run.P.cg_iters, o->own);
+      o->rec = nullptr;
+    }
+    std::map<int, int> gid;
+    for (size_t i = 0; i < ops.size(); ++i) {
+      auto it = gid.find(ops[i]->g.n);
+      if (it == gid.end()) {
+        gid[ops[i]->g.n] = int(groups.size());
+        groups.emplace_back();
+        it = gid.find(ops[i]->g.n);
+      }
+      groups[it->second].idx.push_back(int(i));
+    }
+    for (Group& gr : groups) {
+      const std::vector<Rec>& r0 = recs[gr.idx[0]];
+      for (const Rec& r : r0) {
+        gr.kinds.push_back(r.kind);
+        gr.branches.push_back(r.branch);
+      }
+      for (int i : gr.idx) {
+        if (recs[i].size() != r0.size()) return invalid("instances of one image side differ in their passes");
+        for (size_t k = 0; k < r0.size(); ++k)
+          if (recs[i][k].kind != r0[k].kind) return invalid("instances of one image side differ in their passes");
+        gr.max_items = std::max(gr.max_items, ops[i]->n_items);
+        gr.max_tb = std::max(gr.max_tb, ops[i]->g.TB);
+        gr.max_q = std::max(gr.max_q, ops[i]->grid_bytes());
+      }
+      // tables: one entry per instance for every pass with arguments
+      const int cnt = int(gr.idx.size());
+      size_t total = 0;
+      for (int kind : gr.kinds) {
+        gr.off.push_back(total);
+        total += (entry_bytes(kind) * cnt + 255) & ~size_t(255);
+      }
+      std::vector<unsigned char> host(total > 0 ? total : 1);
+      std::vector<SaraBatchInst<T>> sara_in;
+      for (size_t k = 0; k < gr.kinds.size(); ++k)
+        for (int j = 0; j < cnt; ++j) {
+          const Rec& r = recs[gr.idx[j]][k];
+          unsigned char* d = host.data() + gr.off[k] + entry_bytes(r.kind) * j;
+          switch (r.kind) {
+            case OpImpl<T>::R_RF: std::memcpy(d, &r.rf, sizeof(r.rf)); break;
+            case OpImpl<T>::R_CC: std::memcpy(d, &r.cc, sizeof(r.cc)); break;
+            case OpImpl<T>::R_RI: std::memcpy(d, &r.ri, sizeof(r.ri)); break;
+            case OpImpl<T>::R_CF: std::memcpy(d, &r.cf, sizeof(r.cf)); break;
+            case OpImpl<T>::R_CI: std::memcpy(d, &r.ci, sizeof(r.ci)); break;
+            case OpImpl<T>::R_DG: std::memcpy(d, &r.dg, sizeof(r.dg)); break;
+            case OpImpl<T>::R_GR: std::memcpy(d, &r.gr, sizeof(r.gr)); break;
+            case OpImpl<T>::R_B1: std::memcpy(d, &r.b1, sizeof(r.b1)); break;
+            case OpImpl<T>::R_ZERO: std::memcpy(d, &r.z, sizeof(r.z)); break;
+            case OpImpl<T>::R_AXPY: std::memcpy(d, &r.ax, sizeof(r.ax)); break;
+            case OpImpl<T>::R_FIN: std::memcpy(d, &r.fin, sizeof(r.fin)); break;
+            case OpImpl<T>::R_SARA: sara_in.push_back(r.sara); break;
+            default: break;
+          }
+        }
+      CK(cudaMalloc(&gr.dev, host.size()));
+      CK(cudaMemcpy(gr.dev, host.data(), host.size(), cudaMemcpyHostToDevice));
+      if (!sara_in.empty()) {
+        int np = 0;
+        const int rc = sara_batch_create<T>(sara_in, &gr.sara, &np);
+        if (rc) return rc;
+      }
+      CK(cudaStreamCreateWithFlags(&gr.main, cudaStreamNonBlocking));
+      CK(cudaStreamCreateWithFlags(&gr.aux, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&gr.fork, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&gr.join, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&gr.done, cudaEventDisableTiming));
+    }
+    return capture();
+  }
+
+  static size_t entry_bytes(int kind) {
+    switch (kind) {
+      case OpImpl<T>::R_RF: return sizeof(RowFwdArgs<T>);
+      case OpImpl<T>::R_CC: return sizeof(ColConvArgs<T>);
+      case OpImpl<T>::R_RI: return sizeof(RowInvArgs<T>);
+      case OpImpl<T>::R_CF: return sizeof(ColFwdArgs<T>);
+      case OpImpl<T>::R_CI: return sizeof(ColInvArgs<T>);
+      case OpImpl<T>::R_DG: return sizeof(DegridArgs<T>);
+      case OpImpl<T>::R_GR: return sizeof(GridArgs<T>);
+      case OpImpl<T>::R_B1: return sizeof(Ball1Args);
+      case OpImpl<T>::R_ZERO: return sizeof(ZeroArgs);
+      case OpImpl<T>::R_AXPY: return sizeof(AxpyArgs<T>);
+      case OpImpl<T>::R_FIN: return sizeof(FinArgs);
+      default: return 0;
+    }
+  }
+
+  int invalid(const char* why) {
+    note_error("purify_batch_solve", __LINE__, why);
+    return PURIFY_ERR_INVALID;
+  }
+
+  // One SDMM iteration of every instance as one graph: per group, the
+  // recorded passes as batched launches on the group's main stream, the ball
+  // block between the fork and the join on its second stream.
+  int capture() {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
+    cudaEventRecord(ev0, bs);
+    for (Group& gr : groups) {
+      cudaStreamWaitEvent(gr.main, ev0, 0);
+      const int cnt = int(gr.idx.size());
+      const Geometry& g = ops[gr.idx[0]]->g;
+      const size_t N = size_t(g.n) * g.n;
+      unsigned char* d = static_cast<unsigned char*>(gr.dev);
+      for (size_t k = 0; k < gr.kinds.size(); ++k) {
+        cudaStream_t s = gr.branches[k] ? gr.aux : gr.main;
+        const void* tab = d + gr.off[k];
+        switch (gr.kinds[k]) {
+          case OpImpl<T>::R_RF: launch_row_fwd_h_batch<T>(g, static_cast<const RowFwdArgs<T>*>(tab), cnt, s); break;
+          case OpImpl<T>::R_CC: launch_col_conv_h_batch<T>(g, static_cast<const ColConvArgs<T>*>(tab), cnt, s); break;
+          case OpImpl<T>::R_RI: launch_row_inv_h_batch<T>(g, static_cast<const RowInvArgs<T>*>(tab), cnt, s); break;
+          case OpImpl<T>::R_CF: launch_col_fwd_h_batch<T>(g, static_cast<const ColFwdArgs<T>*>(tab), cnt, s); break;
+          case OpImpl<T>::R_CI: launch_col_inv_h_batch<T>(g, static_cast<const ColInvArgs<T>*>(tab), cnt, s); break;
+          case OpImpl<T>::R_DG:
+            launch_degrid_batch<T>(static_cast<const DegridArgs<T>*>(tab), cnt, gr.max_items, gr.max_tb,
+                                   ops[gr.idx[0]]->kb, s);
+            break;
+          case OpImpl<T>::R_GR:
+            launch_grid_batch<T>(static_cast<const GridArgs<T>*>(tab), cnt, gr.max_items, gr.max_tb,
+                                 ops[gr.idx[0]]->kb, s);
+            break;
+          case OpImpl<T>::R_B1: launch_finalize_ball1_batch<T>(static_cast<const Ball1Args*>(tab), cnt, s); break;
+          case OpImpl<T>::R_ZERO: launch_zero_batch(static_cast<const ZeroArgs*>(tab), cnt, gr.max_q, s); break;
+          case OpImpl<T>::R_AXPY: launch_axpy_batch<T>(static_cast<const AxpyArgs<T>*>(tab), cnt, N, s); break;
+          case OpImpl<T>::R_FIN: launch_finalize_batch<T>(static_cast<const FinArgs*>(tab), cnt, s); break;
+          case OpImpl<T>::R_SARA: sara_batch_launch<T>(gr.sara, s); break;
+          case OpImpl<T>::R_FORK:
+            cudaEventRecord(gr.fork, gr.main);
+            cudaStreamWaitEvent(gr.aux, gr.fork, 0);
+            break;
+          case OpImpl<T>::R_JOIN:
+            cudaEventRecord(gr.join, gr.aux);
+            cudaStreamWaitEvent(gr.main, gr.join, 0);
+            break;
+          default: break;
+        }
+      }
+      cudaEventRecord(gr.done, gr.main);
+      cudaStreamWaitEvent(bs, gr.done, 0);
+    }
+    cudaError_t ce = cudaStreamEndCapture(bs, &graph);
+    if (ce != cudaSuccess) return map_err(ce, __LINE__);
+    ce = cudaGraphInstantiate(&gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return map_err(ce, __LINE__);
+    return PURIFY_OK;
+  }
+};
+
+// purify_batch_solve: begin every instance (nu, gamma, round 0 on its own
+// stream), record and capture the batched iteration, then run the rounds in
+// lock step -- the round set-ups per instance, the iterations as graph
+// replays -- and end every instance.
+template <typename T>
+int batch_solve(int count, purify_op* const* ops_in, const void* const* y, const purify_params* params,
+                void* const* x_out, purify_stats* stats, cudaStream_t user) {
+  BatchImpl<T> b;
+  for (int i = 0; i < count; ++i) {
+    OpImpl<T>* o = dynamic_cast<OpImpl<T>*>(ops_in[i]);
+    if (!o || !y[i] || !x_out[i]) return PURIFY_ERR_INVALID;
+    const purify_params& P = params[i];
+    const purify_params& P0 = params[0];
+    if (P.xi != 0.0 || P.t_max != P0.t_max || P.cg_iters != P0.cg_iters || P.n_reweight != P0.n_reweight ||
+        o->nblocks != 1 || o->prior != 0 || o->g.n < 64 || o->g.n > 1024 || P.gram == 0) {
+      note_error("purify_batch_solve", __LINE__,
+                 "instances need xi = 0, equal t_max, cg_iters and n_reweight, one visibility block, the l1 prior, "
+                 "64 <= n <= 1024 and the convolution form of the CG operator");
+      return PURIFY_ERR_INVALID;
+    }
+    for (int j = 0; j < i; ++j)
+      if (ops_in[j] == ops_in[i]) return PURIFY_ERR_INVALID;
+    b.ops.push_back(o);
+  }
+  // every instance's set-up (its CG operator, nu, gamma, state) on its own stream
+  for (int i = 0; i < count; ++i) {
+    purify_params P = params[i];
+    P.use_graph = 0;
+    P.gram = 1;
+    const int rc = b.ops[i]->begin(y[i], &P, user);
+    if (rc) {
+      for (int j = 0; j <= i; ++j) b.ops[j]->run_release();
+      return rc;
+    }
+  }
+  int rc = b.build();
+  cudaStream_t bs = b.bs;
+  if (!rc) {
+    for (OpImpl<T>* o : b.ops) {
+      cudaEventRecord(o->ev_out, o->own);
+      cudaStreamWaitEvent(bs, o->ev_out, 0);
+    }
+  }
+  bool done = rc != 0;
+  while (!done && !rc) {
+    for (OpImpl<T>* o : b.ops)
+      if (!rc && !o->run.round_ready) rc = o->start_round(bs);
+    if (rc) break;
+    cudaError_t e = cudaGraphLaunch(b.gexec, bs);
+    if (e != cudaSuccess) rc = map_err(e, __LINE__);
+    int all = 1;
+    for (OpImpl<T>* o : b.ops) {
+      int d = 0;
+      if (!rc) rc = o->step_check(&d);
+      all &= d;
+    }
+    done = all != 0;
+  }
+  if (!rc) {
+    cudaError_t e = cudaStreamSynchronize(bs);
+    if (e != cudaSuccess) rc = map_err(e, __LINE__);
+  }
+  int first = rc;
+  for (int i = 0; i < count; ++i) {
+    OpImpl<T>* o = b.ops[i];
+    if (rc) {
+      o->run_release();
+      continue;
+    }
+    const int r = o->end(x_out[i], stats ? &stats[i] : nullptr, user);
+    if (r && !first) first = r;
+  }
+  return first;
+}
+
 }  // namespace
 
 int create_pooled_op(const double* uv, int64_t M, int n, int levels, int precision, const purify_op_options* opt,
@@ -1546,6 +1913,22 @@ int purify_sdmm_solve(purify_op* op, const void* y, const purify_params* params,
                       void* stream) {
   if (!op || !y || !params || !x_out) return PURIFY_ERR_INVALID;
   return op->solve(y, params, x_out, stats, static_cast<cudaStream_t>(stream));
+}
+
+int purify_batch_solve(int count, purify_op* const* ops, const void* const* y, const purify_params* params,
+                       void* const* x_out, purify_stats* stats, void* stream) {
+  if (count < 1 || !ops || !y || !params || !x_out) return PURIFY_ERR_INVALID;
+  int prec = -1;
+  for (int i = 0; i < count; ++i) {
+    if (!ops[i]) return PURIFY_ERR_INVALID;
+    int p = 0;
+    ops[i]->info(nullptr, nullptr, nullptr, nullptr, nullptr, &p, nullptr);
+    if (prec >= 0 && p != prec) return PURIFY_ERR_INVALID;
+    prec = p;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (prec == PURIFY_FP32) return purify::batch_solve<float>(count, ops, y, params, x_out, stats, s);
+  return purify::batch_solve<double>(count, ops, y, params, x_out, stats, s);
 }
 
 int purify_solve_begin(purify_op* op, const void* y, const purify_params* params, void* stream) {

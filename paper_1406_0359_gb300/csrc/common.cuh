@@ -169,13 +169,14 @@ template <int NT> __device__ double block_max(double v, double* sh) {
 // Last-block reduction: every block has written partials[blockIdx.x]; the
 // block that finishes last (atomic ticket, no waiting) returns true in all
 // its threads, after which it may read all partials.  It resets the ticket.
-__device__ __forceinline__ bool last_block_done(unsigned int* ticket) {
+__device__ __forceinline__ bool last_block_done(unsigned int* ticket,
+                                                unsigned int count = gridDim.x * gridDim.y * gridDim.z) {
   __shared__ bool last;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned int t = atomicAdd(ticket, 1u);
-    last = (t == gridDim.x * gridDim.y * gridDim.z - 1);
+    last = (t == count - 1);
     if (last) *ticket = 0u;
   }
   __syncthreads();
@@ -184,19 +185,38 @@ __device__ __forceinline__ bool last_block_done(unsigned int* ticket) {
 }
 
 // As last_block_done, for blocks whose global results for the last block
-// were all written by thread 0 (only thread 0 fences before the ticket).
-__device__ __forceinline__ bool last_block_done_t0(unsigned int* ticket) {
+// were all written by thread 0 (only thread 0 fences before the ticket);
+// `count` blocks take part (one instance's blocks of a batched launch).
+__device__ __forceinline__ bool last_block_done_t0(unsigned int* ticket, unsigned int count) {
   __shared__ bool last;
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned int t = atomicAdd(ticket, 1u);
-    last = (t == gridDim.x * gridDim.y * gridDim.z - 1);
+    last = (t == count - 1);
     if (last) *ticket = 0u;
   }
   __syncthreads();
   if (last) __threadfence();
   return last;
 }
+
+// Kernel arguments: by value for one operator (ArgVal, kernel parameter
+// space), or from a device table for a batch of independent instances of the
+// same size (ArgTab: instance blockIdx.y, every instance the same grid).
+template <typename A> struct ArgVal {
+  static constexpr bool kTable = false;
+  A a;
+  PD const A& get() const { return a; }
+  PD const A& get_at(int) const { return a; }
+  PD int inst() const { return 0; }
+};
+template <typename A> struct ArgTab {
+  static constexpr bool kTable = true;
+  const A* t;
+  PD A get() const { return t[blockIdx.y]; }
+  PD A get_at(int i) const { return t[i]; }
+  PD int inst() const { return int(blockIdx.y); }
+};
 
 
 // ---------------------------------------------------------------- mbarrier + TMA
@@ -242,6 +262,12 @@ PD void bulk_load(void* smem_dst, const void* gsrc, uint32_t bytes, uint64_t* ba
                    smem_u32(smem_dst)),
                "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
+}
+// Before the first TMA use of a tensor map that lives in global memory
+// (written there by a host copy): order the generic-proxy write before the
+// tensor-map proxy's read.
+PD void tensormap_acquire(const CUtensorMap* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
 }
 PD void tma_load_2d(void* smem_dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
   asm volatile(

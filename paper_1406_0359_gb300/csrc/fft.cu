@@ -313,7 +313,8 @@ PD void row_prologue(const RowPro<T>& pro, const size_t (&row0)[NR], int t, T (&
 //             <r,r> / <p,Ap> in exact arithmetic); the next residual norm by
 //             ||r - alpha Ap||^2 = <r,r> - 2 alpha <r,Ap> + alpha^2 <Ap,Ap>
 //             (clamped at 0); beta = ||r_new||^2 / <r,r>.
-template <typename T> PD void row_ep_finish(const RowEp<T>& ep, EpAcc<T> part, double* red /*[5*32]*/) {
+template <typename T>
+PD void row_ep_finish(const RowEp<T>& ep, EpAcc<T> part, double* red /*[5*32]*/, int bid, int nblocks) {
   if (!ep.partials) return;
   const int nsum = ep.mode == EP_CG_AP ? 5 : 1;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = int((blockDim.x + 31) >> 5);
@@ -328,14 +329,14 @@ template <typename T> PD void row_ep_finish(const RowEp<T>& ep, EpAcc<T> part, d
     for (int k = 0; k < nsum; ++k) {
       Acc<T> b = lane < nw ? st[k * 32 + lane] : Acc<T>();
       warp_merge(b);
-      if (lane == 0) P[size_t(k) * ep.pstride + blockIdx.x] = b;
+      if (lane == 0) P[size_t(k) * ep.pstride + bid] = b;
     }
   }
-  if (!ep.ticket || !last_block_done_t0(ep.ticket)) return;
+  if (!ep.ticket || !last_block_done_t0(ep.ticket, unsigned(nblocks))) return;
   // last block: merge all blocks' partials (fixed order), FP64 only at the end
   EpAcc<T> tot;
   int i = threadIdx.x;
-  for (; i + int(blockDim.x) < int(gridDim.x); i += 2 * blockDim.x) {  // two CTAs' partials in flight
+  for (; i + int(blockDim.x) < nblocks; i += 2 * blockDim.x) {  // two CTAs' partials in flight
     Acc<T> v[2][5];
 #pragma unroll
     for (int k = 0; k < 5; ++k)
@@ -350,7 +351,7 @@ template <typename T> PD void row_ep_finish(const RowEp<T>& ep, EpAcc<T> part, d
         acc_merge(tot.a[k], v[1][k]);
       }
   }
-  for (; i < int(gridDim.x); i += blockDim.x)
+  for (; i < nblocks; i += blockDim.x)
     for (int k = 0; k < nsum; ++k) acc_merge(tot.a[k], P[size_t(k) * ep.pstride + i]);
   for (int k = 0; k < nsum; ++k) {
     warp_merge(tot.a[k]);
@@ -442,11 +443,16 @@ template <typename T, int LOGN> struct ColThreads {
 
 // Forward row pass of the real form: rows 2 pr and 2 pr + 1 of the prologue's
 // image, zero-padded to K columns, to their half spectra.
-template <typename T, int LOGN, int E>
-__global__ void __launch_bounds__(kRowCta) k_row_fwd_h(Geometry g, RowPro<T> pro, const T* __restrict__ deapod,
-                                                    typename cplx_t<T>::type* __restrict__ B,
-                                                    const typename cplx_t<T>::type* __restrict__ tw, int nseq) {
+template <typename T, int LOGN, int E, typename Src>
+__global__ void __launch_bounds__(kRowCta) k_row_fwd_h(Src src) {
   typedef typename cplx_t<T>::type C;
+  decltype(auto) a = src.get();
+  const Geometry& g = a.g;
+  const RowPro<T>& pro = a.pro;
+  const T* __restrict__ deapod = a.deapod;
+  C* __restrict__ B = a.B;
+  const C* __restrict__ tw = a.tw;
+  const int nseq = a.nseq;
   constexpr int TT = Plan<LOGN, E>::T;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int K = g.K, n = g.n, H = K / 2;
@@ -501,11 +507,17 @@ __global__ void __launch_bounds__(kRowCta) k_row_fwd_h(Geometry g, RowPro<T> pro
 // One CTA per SM and the full register file per thread: the radix-16
 // stages then run spill-free, which measured faster (22.6 against 24.8 us per
 // launch at K = 2048) than two spilling CTAs per SM, despite the second wave.
-template <typename T, int LOGN>
+template <typename T, int LOGN, typename Src>
 __global__ void __launch_bounds__(ColThreads<T, LOGN>::value, 1)
-    k_col_conv_h(Geometry g, typename cplx_t<T>::type* __restrict__ B, const T* __restrict__ khat,
-                 const T* __restrict__ knyq, const typename cplx_t<T>::type* __restrict__ tw, int cw) {
+    k_col_conv_h(Src src) {
   typedef typename cplx_t<T>::type C;
+  decltype(auto) a = src.get();
+  const Geometry& g = a.g;
+  C* __restrict__ B = a.B;
+  const T* __restrict__ khat = a.khat;
+  const T* __restrict__ knyq = a.knyq;
+  const C* __restrict__ tw = a.tw;
+  const int cw = a.cw;
   constexpr int TT = Plan<LOGN>::T;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int K = g.K, n = g.n, half = n / 2, H = K / 2;
@@ -570,11 +582,16 @@ __global__ void __launch_bounds__(ColThreads<T, LOGN>::value, 1)
 // b = 2 pr + 1 rebuilt into Z = Y_a + i Y_b over all K frequencies
 // (Y(K - k) = conj Y(k)), one inverse FFT, Re -> row a, Im -> row b, crop and
 // row epilogue.
-template <typename T, int LOGN, int E>
-__global__ void __launch_bounds__(kRowCta, 2) k_row_inv_h(Geometry g, const typename cplx_t<T>::type* __restrict__ B,
-                                                       const T* __restrict__ deapod, RowEp<T> ep,
-                                                       const typename cplx_t<T>::type* __restrict__ tw, int nseq) {
+template <typename T, int LOGN, int E, typename Src>
+__global__ void __launch_bounds__(kRowCta, 2) k_row_inv_h(Src src) {
   typedef typename cplx_t<T>::type C;
+  decltype(auto) a = src.get();
+  const Geometry& g = a.g;
+  const C* __restrict__ B = a.B;
+  const T* __restrict__ deapod = a.deapod;
+  const RowEp<T>& ep = a.ep;
+  const C* __restrict__ tw = a.tw;
+  const int nseq = a.nseq;
   constexpr int TT = Plan<LOGN, E>::T;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ double red[5 * 32];
@@ -586,8 +603,8 @@ __global__ void __launch_bounds__(kRowCta, 2) k_row_inv_h(Geometry g, const type
   // The epilogue's operand rows (ops[seq][k][row][n]) arrive by bulk copies
   // while the transform runs.
   T* ops_all = reinterpret_cast<T*>(sm_raw + align16(nseq * padded(K) * sizeof(C)));
-  const T* src[2] = {nullptr, nullptr};
-  const int nop = ep_staged(ep, src);
+  const T* opd[2] = {nullptr, nullptr};
+  const int nop = ep_staged(ep, opd);
   if (nop > 0 && threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_barrier_init();
@@ -597,7 +614,7 @@ __global__ void __launch_bounds__(kRowCta, 2) k_row_inv_h(Geometry g, const type
       const int r0 = 2 * (blockIdx.x * nseq + q);
       for (int k = 0; k < nop; ++k)
         for (int r = 0; r < 2; ++r)
-          bulk_load(ops_all + ((size_t(q) * 2 + k) * 2 + r) * n, src[k] + size_t(r0 + r) * n, row_bytes, &bar);
+          bulk_load(ops_all + ((size_t(q) * 2 + k) * 2 + r) * n, opd[k] + size_t(r0 + r) * n, row_bytes, &bar);
     }
   }
   __syncthreads();
@@ -637,7 +654,7 @@ __global__ void __launch_bounds__(kRowCta, 2) k_row_inv_h(Geometry g, const type
   if (nop > 0) ok = mbar_wait_bounded(&bar, 0, ep.err);
   EpAcc<T> part;
   if (ok) part = row_ep_staged<LOGN>(ep, val, t, row0, ops_all + size_t(seq) * 4 * n);
-  row_ep_finish(ep, part, red);
+  row_ep_finish(ep, part, red, int(blockIdx.x), a.nblocks);
 }
 
 // Real-form column passes of Phi and Phi^H on the padded grid (K + J per side,
@@ -655,11 +672,16 @@ PD int halo_images(int q, int K, int pl, int (&at)[2]) {
 // its conjugate mirror, G(q, K - c) = conj G(-q, c) (a real image).  Column 0
 // carries X(., 0) + i X(., K/2): its transform P gives grid column 0 as
 // (P(q) + conj P(-q)) / 2 and column K/2 as -i (P(q) - conj P(-q)) / 2.
-template <typename T, int LOGN>
+template <typename T, int LOGN, typename Src>
 __global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN>::value <= 512 ? 2 : 1)
-    k_col_fwd_h(Geometry g, const typename cplx_t<T>::type* __restrict__ B, typename cplx_t<T>::type* __restrict__ Pg,
-                const typename cplx_t<T>::type* __restrict__ tw, int cw) {
+    k_col_fwd_h(Src src) {
   typedef typename cplx_t<T>::type C;
+  decltype(auto) a = src.get();
+  const Geometry& g = a.g;
+  const C* __restrict__ B = a.B;
+  C* __restrict__ Pg = a.Pg;
+  const C* __restrict__ tw = a.tw;
+  const int cw = a.cw;
   constexpr int TT = Plan<LOGN>::T;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int K = g.K, n = g.n, half = n / 2, H = K / 2, pl = g.pad_lo, KP = g.KP;
@@ -701,11 +723,16 @@ __global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN
 // CTA (halo folded on load), inverse column FFT, the n cropped rows into the
 // half-spectrum rows B; column 0 packs the two Hermitian columns 0 and K/2 as
 // Qh(., 0) + i Qh(., K/2), whose transforms are real.
-template <typename T, int LOGN>
+template <typename T, int LOGN, typename Src>
 __global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN>::value <= 512 ? 2 : 1)
-    k_col_inv_h(Geometry g, const typename cplx_t<T>::type* __restrict__ Q, typename cplx_t<T>::type* __restrict__ B,
-                const typename cplx_t<T>::type* __restrict__ tw, int cw) {
+    k_col_inv_h(Src src) {
   typedef typename cplx_t<T>::type C;
+  decltype(auto) a = src.get();
+  const Geometry& g = a.g;
+  const C* __restrict__ Q = a.Q;
+  C* __restrict__ B = a.B;
+  const C* __restrict__ tw = a.tw;
+  const int cw = a.cw;
   constexpr int TT = Plan<LOGN>::T;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int K = g.K, n = g.n, half = n / 2, H = K / 2, pl = g.pad_lo, KP = g.KP;
@@ -794,6 +821,10 @@ inline int row_pair_nseq(const Geometry& g, int E) {
 
 // CTAs of one inverse row pass (its epilogue's partial sums).
 int row_inv_blocks(const Geometry& g) { return g.n / 2 / row_pair_nseq(g, row_e_host(g.K)); }
+int row_pass_nseq(const Geometry& g) { return row_pair_nseq(g, row_e_host(g.K)); }
+template <typename T> int col_pass_width() { return col_width<T>(); }
+template int col_pass_width<float>();
+template int col_pass_width<double>();
 
 #define PURIFY_LOGN_SWITCH(K, BODY)     \
   switch (K) {                          \
@@ -807,12 +838,30 @@ int row_inv_blocks(const Geometry& g) { return g.n / 2 / row_pair_nseq(g, row_e_
     default: { constexpr int L = 12; BODY; } break;  \
   }
 
+// Grid sides of the batched passes (image sides 64..1024).
+#define PURIFY_LOGN_SWITCH_BATCH(K, BODY)                 \
+  switch (K) {                                            \
+    case 128: { constexpr int L = 7; BODY; } break;       \
+    case 256: { constexpr int L = 8; BODY; } break;       \
+    case 512: { constexpr int L = 9; BODY; } break;       \
+    case 1024: { constexpr int L = 10; BODY; } break;     \
+    case 2048: { constexpr int L = 11; BODY; } break;     \
+    default: break;                                       \
+  }
+
 template <typename T, int L> cudaError_t configure_one() {
-  cudaError_t e = raise_smem_limit(k_row_fwd_h<T, L, row_e<L>()>);
-  if (e == cudaSuccess) e = raise_smem_limit(k_col_conv_h<T, L>);
-  if (e == cudaSuccess) e = raise_smem_limit(k_col_fwd_h<T, L>);
-  if (e == cudaSuccess) e = raise_smem_limit(k_col_inv_h<T, L>);
-  if (e == cudaSuccess) e = raise_smem_limit(k_row_inv_h<T, L, row_e<L>()>);
+  cudaError_t e = raise_smem_limit(k_row_fwd_h<T, L, row_e<L>(), ArgVal<RowFwdArgs<T>>>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_col_conv_h<T, L, ArgVal<ColConvArgs<T>>>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_col_fwd_h<T, L, ArgVal<ColFwdArgs<T>>>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_col_inv_h<T, L, ArgVal<ColInvArgs<T>>>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_row_inv_h<T, L, row_e<L>(), ArgVal<RowInvArgs<T>>>);
+  if constexpr (L >= 7 && L <= 11) {
+    if (e == cudaSuccess) e = raise_smem_limit(k_row_fwd_h<T, L, row_e<L>(), ArgTab<RowFwdArgs<T>>>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_col_conv_h<T, L, ArgTab<ColConvArgs<T>>>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_col_fwd_h<T, L, ArgTab<ColFwdArgs<T>>>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_col_inv_h<T, L, ArgTab<ColInvArgs<T>>>);
+    if (e == cudaSuccess) e = raise_smem_limit(k_row_inv_h<T, L, row_e<L>(), ArgTab<RowInvArgs<T>>>);
+  }
   if (e == cudaSuccess) e = raise_smem_limit(k_rows_plain<T, L>);
   if (e == cudaSuccess) e = raise_smem_limit(k_cols_plain<T, L>);
   return e;
@@ -866,52 +915,96 @@ void build_psf_spectrum(const T* psf, int n, T* khat, typename cplx_t<T>::type* 
   k_spectrum_layout<T><<<int((tot + tb - 1) / tb), tb, 0, s>>>(X, K, col_width<T>(), 1.0 / (double(K) * K), khat);
 }
 
+// Launch shapes of the real-form passes for grid side K (image side n = K/2).
+inline int row_pass_ctas(const Geometry& g) { return g.n / 2 / row_pair_nseq(g, row_e_host(g.K)); }
+template <typename T> inline size_t row_fwd_smem(const Geometry& g) {
+  return row_pair_nseq(g, row_e_host(g.K)) * padded(g.K) * sizeof(typename cplx_t<T>::type);
+}
+template <typename T> inline size_t row_inv_smem(const Geometry& g) {
+  const int nseq = row_pair_nseq(g, row_e_host(g.K));
+  return align16(nseq * padded(g.K) * sizeof(typename cplx_t<T>::type)) + size_t(nseq) * 4 * g.n * sizeof(T);
+}
+template <typename T> inline size_t col_smem(const Geometry& g) {
+  return col_width<T>() * padded(g.K) * sizeof(typename cplx_t<T>::type);
+}
+
 template <typename T>
 void launch_row_fwd_h(const Geometry& g, const RowPro<T>& pro, const T* deapod, typename cplx_t<T>::type* B,
                       const typename cplx_t<T>::type* tw, cudaStream_t s) {
-  typedef typename cplx_t<T>::type C;
   const int nseq = row_pair_nseq(g, row_e_host(g.K));
-  const size_t sm = nseq * padded(g.K) * sizeof(C);
-  PURIFY_LOGN_SWITCH(g.K, (k_row_fwd_h<T, L, row_e<L>()><<<g.n / 2 / nseq, nseq * Plan<L, row_e<L>()>::T, sm, s>>>(g, pro, deapod, B, tw, nseq)));
+  ArgVal<RowFwdArgs<T>> src{RowFwdArgs<T>{g, pro, deapod, B, tw, nseq}};
+  PURIFY_LOGN_SWITCH(g.K, (k_row_fwd_h<T, L, row_e<L>()><<<row_pass_ctas(g), nseq * Plan<L, row_e<L>()>::T,
+                                                           row_fwd_smem<T>(g), s>>>(src)));
 }
 
 template <typename T>
 void launch_col_conv_h(const Geometry& g, typename cplx_t<T>::type* B, const T* khat,
                        const typename cplx_t<T>::type* tw, cudaStream_t s) {
-  typedef typename cplx_t<T>::type C;
   const int cw = col_width<T>();
-  const size_t sm = cw * padded(g.K) * sizeof(C);
-  const T* knyq = khat + size_t(g.K / 2) * g.K;
-  PURIFY_LOGN_SWITCH(g.K, (k_col_conv_h<T, L><<<g.K / 2 / cw, cw * Plan<L>::T, sm, s>>>(g, B, khat, knyq, tw, cw)));
+  ArgVal<ColConvArgs<T>> src{ColConvArgs<T>{g, B, khat, khat + size_t(g.K / 2) * g.K, tw, cw}};
+  PURIFY_LOGN_SWITCH(g.K, (k_col_conv_h<T, L><<<g.K / 2 / cw, cw * Plan<L>::T, col_smem<T>(g), s>>>(src)));
 }
 
 template <typename T>
 void launch_col_fwd_h(const Geometry& g, const typename cplx_t<T>::type* B, typename cplx_t<T>::type* Pg,
                       const typename cplx_t<T>::type* tw, cudaStream_t s) {
-  typedef typename cplx_t<T>::type C;
   const int cw = col_width<T>();
-  const size_t sm = cw * padded(g.K) * sizeof(C);
-  PURIFY_LOGN_SWITCH(g.K, (k_col_fwd_h<T, L><<<g.K / 2 / cw, cw * Plan<L>::T, sm, s>>>(g, B, Pg, tw, cw)));
+  ArgVal<ColFwdArgs<T>> src{ColFwdArgs<T>{g, B, Pg, tw, cw}};
+  PURIFY_LOGN_SWITCH(g.K, (k_col_fwd_h<T, L><<<g.K / 2 / cw, cw * Plan<L>::T, col_smem<T>(g), s>>>(src)));
 }
 
 template <typename T>
 void launch_col_inv_h(const Geometry& g, const typename cplx_t<T>::type* Q, typename cplx_t<T>::type* B,
                       const typename cplx_t<T>::type* tw, cudaStream_t s) {
-  typedef typename cplx_t<T>::type C;
   const int cw = col_width<T>();
-  const size_t sm = cw * padded(g.K) * sizeof(C);
-  PURIFY_LOGN_SWITCH(g.K, (k_col_inv_h<T, L><<<g.K / 2 / cw, cw * Plan<L>::T, sm, s>>>(g, Q, B, tw, cw)));
+  ArgVal<ColInvArgs<T>> src{ColInvArgs<T>{g, Q, B, tw, cw}};
+  PURIFY_LOGN_SWITCH(g.K, (k_col_inv_h<T, L><<<g.K / 2 / cw, cw * Plan<L>::T, col_smem<T>(g), s>>>(src)));
 }
 
 template <typename T>
 int launch_row_inv_h(const Geometry& g, const typename cplx_t<T>::type* B, const T* deapod, const RowEp<T>& ep,
                      const typename cplx_t<T>::type* tw, cudaStream_t s) {
-  typedef typename cplx_t<T>::type C;
   const int nseq = row_pair_nseq(g, row_e_host(g.K));
-  const size_t sm = align16(nseq * padded(g.K) * sizeof(C)) + size_t(nseq) * 4 * g.n * sizeof(T);
-  const int nb = g.n / 2 / nseq;
-  PURIFY_LOGN_SWITCH(g.K, (k_row_inv_h<T, L, row_e<L>()><<<nb, nseq * Plan<L, row_e<L>()>::T, sm, s>>>(g, B, deapod, ep, tw, nseq)));
+  const int nb = row_pass_ctas(g);
+  ArgVal<RowInvArgs<T>> src{RowInvArgs<T>{g, B, deapod, ep, tw, nseq, nb}};
+  PURIFY_LOGN_SWITCH(g.K, (k_row_inv_h<T, L, row_e<L>()><<<nb, nseq * Plan<L, row_e<L>()>::T, row_inv_smem<T>(g),
+                                                           s>>>(src)));
   return nb;
+}
+
+// Batched passes: `count` instances of one grid side (g gives the shared
+// shape), arguments in a device table, instance = blockIdx.y.
+template <typename T>
+void launch_row_fwd_h_batch(const Geometry& g, const RowFwdArgs<T>* tab, int count, cudaStream_t s) {
+  const int nseq = row_pair_nseq(g, row_e_host(g.K));
+  ArgTab<RowFwdArgs<T>> src{tab};
+  PURIFY_LOGN_SWITCH_BATCH(g.K, (k_row_fwd_h<T, L, row_e<L>()><<<dim3(row_pass_ctas(g), count),
+                                                           nseq * Plan<L, row_e<L>()>::T, row_fwd_smem<T>(g), s>>>(src)));
+}
+template <typename T>
+void launch_col_conv_h_batch(const Geometry& g, const ColConvArgs<T>* tab, int count, cudaStream_t s) {
+  const int cw = col_width<T>();
+  ArgTab<ColConvArgs<T>> src{tab};
+  PURIFY_LOGN_SWITCH_BATCH(g.K, (k_col_conv_h<T, L><<<dim3(g.K / 2 / cw, count), cw * Plan<L>::T, col_smem<T>(g), s>>>(src)));
+}
+template <typename T>
+void launch_col_fwd_h_batch(const Geometry& g, const ColFwdArgs<T>* tab, int count, cudaStream_t s) {
+  const int cw = col_width<T>();
+  ArgTab<ColFwdArgs<T>> src{tab};
+  PURIFY_LOGN_SWITCH_BATCH(g.K, (k_col_fwd_h<T, L><<<dim3(g.K / 2 / cw, count), cw * Plan<L>::T, col_smem<T>(g), s>>>(src)));
+}
+template <typename T>
+void launch_col_inv_h_batch(const Geometry& g, const ColInvArgs<T>* tab, int count, cudaStream_t s) {
+  const int cw = col_width<T>();
+  ArgTab<ColInvArgs<T>> src{tab};
+  PURIFY_LOGN_SWITCH_BATCH(g.K, (k_col_inv_h<T, L><<<dim3(g.K / 2 / cw, count), cw * Plan<L>::T, col_smem<T>(g), s>>>(src)));
+}
+template <typename T>
+void launch_row_inv_h_batch(const Geometry& g, const RowInvArgs<T>* tab, int count, cudaStream_t s) {
+  const int nseq = row_pair_nseq(g, row_e_host(g.K));
+  ArgTab<RowInvArgs<T>> src{tab};
+  PURIFY_LOGN_SWITCH_BATCH(g.K, (k_row_inv_h<T, L, row_e<L>()><<<dim3(row_pass_ctas(g), count),
+                                                           nseq * Plan<L, row_e<L>()>::T, row_inv_smem<T>(g), s>>>(src)));
 }
 
 template <typename T>
@@ -940,7 +1033,12 @@ void launch_fft2_plain(int K, typename cplx_t<T>::type* X, const typename cplx_t
                                     const cplx_t<T>::type*, cudaStream_t);                                     \
   template void launch_col_inv_h<T>(const Geometry&, const cplx_t<T>::type*, cplx_t<T>::type*,                \
                                     const cplx_t<T>::type*, cudaStream_t);                                     \
-  template void build_psf_spectrum<T>(const T*, int, T*, cplx_t<T>::type*, const cplx_t<T>::type*, cudaStream_t);
+  template void build_psf_spectrum<T>(const T*, int, T*, cplx_t<T>::type*, const cplx_t<T>::type*, cudaStream_t); \
+  template void launch_row_fwd_h_batch<T>(const Geometry&, const RowFwdArgs<T>*, int, cudaStream_t);         \
+  template void launch_col_conv_h_batch<T>(const Geometry&, const ColConvArgs<T>*, int, cudaStream_t);       \
+  template void launch_col_fwd_h_batch<T>(const Geometry&, const ColFwdArgs<T>*, int, cudaStream_t);         \
+  template void launch_col_inv_h_batch<T>(const Geometry&, const ColInvArgs<T>*, int, cudaStream_t);         \
+  template void launch_row_inv_h_batch<T>(const Geometry&, const RowInvArgs<T>*, int, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

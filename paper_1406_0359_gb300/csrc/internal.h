@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace purify {
@@ -128,6 +130,71 @@ template <typename C> struct GridPro {
   const double* block_scale;  // per visibility block (R > 1), else null
 };
 
+// Arguments of the real-form FFT passes (one operator; a batch passes a
+// device table of them, one per instance).
+template <typename T> struct RowFwdArgs {
+  Geometry g;
+  RowPro<T> pro;
+  const T* deapod;
+  typename cplx_t<T>::type* B;
+  const typename cplx_t<T>::type* tw;
+  int nseq;
+};
+template <typename T> struct ColConvArgs {
+  Geometry g;
+  typename cplx_t<T>::type* B;
+  const T* khat;
+  const T* knyq;
+  const typename cplx_t<T>::type* tw;
+  int cw;
+};
+template <typename T> struct RowInvArgs {
+  Geometry g;
+  const typename cplx_t<T>::type* B;
+  const T* deapod;
+  RowEp<T> ep;
+  const typename cplx_t<T>::type* tw;
+  int nseq;
+  int nblocks;  // CTAs of the instance (its epilogue partials, its ticket)
+};
+template <typename T> struct ColFwdArgs {
+  Geometry g;
+  const typename cplx_t<T>::type* B;
+  typename cplx_t<T>::type* Pg;
+  const typename cplx_t<T>::type* tw;
+  int cw;
+};
+template <typename T> struct ColInvArgs {
+  Geometry g;
+  const typename cplx_t<T>::type* Q;
+  typename cplx_t<T>::type* B;
+  const typename cplx_t<T>::type* tw;
+  int cw;
+};
+
+// Arguments of the warp-per-item degridding / gridding (one operator; a batch
+// passes a device table; the kernel polynomial is shared).  map: the TMA
+// descriptor of the padded forward grid in global memory (batch only).
+template <typename T> struct DegridArgs {
+  Geometry g;
+  const CUtensorMap* map;
+  const WorkItem* items;
+  int n_items;
+  const Pos<T>* pos;
+  const int* perm;
+  DegridEp<typename cplx_t<T>::type> dep;
+  int* err;
+};
+template <typename T> struct GridArgs {
+  Geometry g;
+  const WorkItem* items;
+  int n_items;
+  const Pos<T>* pos;
+  const int* perm;
+  GridPro<typename cplx_t<T>::type> gpro;
+  typename cplx_t<T>::type* Q;
+};
+
 // Record the detail returned by purify_last_error() on this thread.
 void set_last_error(const char* msg);
 
@@ -150,6 +217,10 @@ template <typename T> cudaError_t configure_sara();
 
 // CTAs of one inverse row pass (the partial sums its epilogue writes).
 int row_inv_blocks(const Geometry& g);
+// Row pairs per CTA of the row passes; interleaved columns per CTA of the
+// column passes.
+int row_pass_nseq(const Geometry& g);
+template <typename T> int col_pass_width();
 // Composite operator Phi^H Phi as a convolution, in real form: the image
 // rows' half spectra (n x K/2 complex in B, entry 0 = X(0) + i X(K/2)).
 // Forward row pass (prologue, zero-padding, row FFT of row pairs):
@@ -176,6 +247,14 @@ void launch_col_inv_h(const Geometry& g, const typename cplx_t<T>::type* Q, type
 template <typename T>
 int launch_row_inv_h(const Geometry& g, const typename cplx_t<T>::type* B, const T* deapod, const RowEp<T>& ep,
                      const typename cplx_t<T>::type* tw, cudaStream_t s);
+// Batched real-form passes: `count` instances of the grid side g.K (image
+// sides 64..1024), one launch, arguments from a device table (instance =
+// blockIdx.y); every instance has g's launch shape.
+template <typename T> void launch_row_fwd_h_batch(const Geometry& g, const RowFwdArgs<T>* tab, int count, cudaStream_t s);
+template <typename T> void launch_col_conv_h_batch(const Geometry& g, const ColConvArgs<T>* tab, int count, cudaStream_t s);
+template <typename T> void launch_col_fwd_h_batch(const Geometry& g, const ColFwdArgs<T>* tab, int count, cudaStream_t s);
+template <typename T> void launch_col_inv_h_batch(const Geometry& g, const ColInvArgs<T>* tab, int count, cudaStream_t s);
+template <typename T> void launch_row_inv_h_batch(const Geometry& g, const RowInvArgs<T>* tab, int count, cudaStream_t s);
 // Real spectrum of the convolution kernel from the PSF image (2n x 2n real,
 // pixel offsets [-n, n)^2): circulant embedding on the K = 2n grid, forward
 // FFT, scaled by 1/K^2, columns [0, K/2] stored in launch_col_conv_h's layout
@@ -196,6 +275,14 @@ template <typename T>
 void launch_grid(const Geometry& g, const WorkItem* items, int n_items, const Pos<T>* pos, const int* perm,
                  const KbPoly<T>& kb, const GridPro<typename cplx_t<T>::type>& pro, typename cplx_t<T>::type* Q,
                  cudaStream_t s);
+// Batched: `count` instances (their tiles may differ), one launch; the grid
+// covers the largest instance's items (max_items) and the rest exit early.
+template <typename T>
+void launch_degrid_batch(const DegridArgs<T>* tab, int count, int max_items, int max_tb, const KbPoly<T>& kb,
+                         cudaStream_t s);
+template <typename T>
+void launch_grid_batch(const GridArgs<T>* tab, int count, int max_items, int max_tb, const KbPoly<T>& kb,
+                       cudaStream_t s);
 template <typename T>
 void launch_gram(const Geometry& g, const CUtensorMap& map, const WorkItem* items, int n_items, const Pos<T>* pos,
                  const KbPoly<T>& kb, typename cplx_t<T>::type* Q, int* err, cudaStream_t s);
@@ -264,6 +351,29 @@ int sara_analysis_prox(const SaraPlan<T>& P, const T* xh, const L1Block<T>& b, c
 template <typename T>
 void sara_synthesis_pos(const SaraPlan<T>& P, const T* xh, T* z2, T* xs, cudaStream_t s);
 int sara_partials_capacity(int n, int levels);
+
+// Batched SDMM blocks 1 and 2 (sara.cu): instances of one image side,
+// wavelet levels and dictionary, every analysis / synthesis launch covering
+// all of them.  Per instance: its plan (bands, filters, prox output cs), x_hat,
+// z_1, the weights, gamma, its objective partials, z_2 and the output xs.
+template <typename T> struct SaraBatchInst {
+  const SaraPlan<T>* P;
+  const T* xh;
+  T* z1;
+  const T* w;
+  double gamma;
+  double* partials;
+  T* z2;
+  T* xs;
+};
+template <typename T> struct SaraBatch;
+// Builds the device argument tables; *np receives the objective partials
+// each instance writes.
+template <typename T> int sara_batch_create(const std::vector<SaraBatchInst<T>>& in, SaraBatch<T>** out, int* np);
+template <typename T> void sara_batch_launch(const SaraBatch<T>* b, cudaStream_t s);
+template <typename T> void sara_batch_destroy(SaraBatch<T>* b);
+// Objective partials the fused analysis of P writes.
+template <typename T> int sara_prox_partials(const SaraPlan<T>& P);
 
 // TV prior (Section 4's TV / RWTV): the SDMM TV block with the positivity
 // block fused into its epilogue (tv.cu).  v: n x n scratch; qa, qb: the

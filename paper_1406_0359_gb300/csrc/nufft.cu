@@ -387,13 +387,18 @@ PD bool warp_stage_patch(C* patch, uint64_t* bar, const CUtensorMap* map, int tu
   return __all_sync(0xffffffffu, ok) != 0;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_degrid_w(Geometry g, const __grid_constant__ CUtensorMap map,
-                                                       const WorkItem* __restrict__ items, int n_items,
-                                                       const Pos<T>* __restrict__ pos, const int* __restrict__ perm,
-                                                       KbPoly<T> kb, DegridEp<typename cplx_t<T>::type> dep,
-                                                       int* err) {
+template <typename T, typename Src>
+__global__ void __launch_bounds__(kThreads) k_degrid_w(Src src, KbPoly<T> kb, const __grid_constant__ CUtensorMap map0) {
   typedef typename cplx_t<T>::type C;
+  decltype(auto) a = src.get();
+  const Geometry& g = a.g;
+  const WorkItem* __restrict__ items = a.items;
+  const int n_items = a.n_items;
+  const Pos<T>* __restrict__ pos = a.pos;
+  const int* __restrict__ perm = a.perm;
+  const DegridEp<C>& dep = a.dep;
+  int* err = a.err;
+  const CUtensorMap* map = Src::kTable ? a.map : &map0;
   extern __shared__ __align__(128) unsigned char sm_raw[];
   __shared__ __align__(8) uint64_t bars[kWItems];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -405,7 +410,8 @@ __global__ void __launch_bounds__(kThreads) k_degrid_w(Geometry g, const __grid_
   const size_t pe = warp_patch_elems<T>(g.TB);
   C* patch = reinterpret_cast<C*>(sm_raw) + warp * pe;
   T* wst = reinterpret_cast<T*>(reinterpret_cast<C*>(sm_raw) + kWItems * pe) + warp * 32 * kDgStage;
-  if (!warp_stage_patch(patch, &bars[warp], &map, tu, tv, g.TB, PW, lane, err)) return;
+  if (Src::kTable && lane == 0) tensormap_acquire(map);
+  if (!warp_stage_patch(patch, &bars[warp], map, tu, tv, g.TB, PW, lane, err)) return;
   const int grp = lane >> 2, k = lane & 3;
   Acc<T> p0, p1;
   for (int base = it.begin; base < it.end; base += 32) {
@@ -519,12 +525,17 @@ template <typename T> PD void kahan_cell_add(KCell<T>* cell, T vx, T vy) {
   *cell = k;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_grid_w(Geometry g, const WorkItem* __restrict__ items, int n_items,
-                                                     const Pos<T>* __restrict__ pos, const int* __restrict__ perm,
-                                                     KbPoly<T> kb, GridPro<typename cplx_t<T>::type> gpro,
-                                                     typename cplx_t<T>::type* __restrict__ Q) {
+template <typename T, typename Src>
+__global__ void __launch_bounds__(kThreads) k_grid_w(Src src, KbPoly<T> kb) {
   typedef typename cplx_t<T>::type C;
+  decltype(auto) a = src.get();
+  const Geometry& g = a.g;
+  const WorkItem* __restrict__ items = a.items;
+  const int n_items = a.n_items;
+  const Pos<T>* __restrict__ pos = a.pos;
+  const int* __restrict__ perm = a.perm;
+  const GridPro<C>& gpro = a.gpro;
+  C* __restrict__ Q = a.Q;
   extern __shared__ __align__(128) unsigned char sm_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int item = blockIdx.x * kWItems + warp;
@@ -960,8 +971,10 @@ __global__ void k_encode_x2(const double* __restrict__ uv, const int* __restrict
 
 template <typename T> cudaError_t configure_nufft() {
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = raise_smem_limit(k_degrid_w<T>);
-  if (e == cudaSuccess) e = raise_smem_limit(k_grid_w<T>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_degrid_w<T, ArgVal<DegridArgs<T>>>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_grid_w<T, ArgVal<GridArgs<T>>>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_degrid_w<T, ArgTab<DegridArgs<T>>>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_grid_w<T, ArgTab<GridArgs<T>>>);
   if (e == cudaSuccess) e = raise_smem_limit(k_tile<T, TM_GRAM>);
   return e;
 }
@@ -989,8 +1002,19 @@ void launch_degrid(const Geometry& g, const CUtensorMap& map, const WorkItem* it
                    cudaStream_t s) {
   if (n_items <= 0) return;
   const size_t sm = kWItems * (warp_patch_elems<T>(g.TB) * sizeof(typename cplx_t<T>::type) + 32 * kDgStage * sizeof(T));
-  k_degrid_w<T><<<(n_items + kWItems - 1) / kWItems, kThreads, sm, s>>>(g, map, items, n_items, pos, perm, kb, ep,
-                                                                       err);
+  ArgVal<DegridArgs<T>> src{DegridArgs<T>{g, nullptr, items, n_items, pos, perm, ep, err}};
+  k_degrid_w<T><<<(n_items + kWItems - 1) / kWItems, kThreads, sm, s>>>(src, kb, map);
+}
+
+template <typename T>
+void launch_degrid_batch(const DegridArgs<T>* tab, int count, int max_items, int max_tb, const KbPoly<T>& kb,
+                         cudaStream_t s) {
+  if (max_items <= 0 || count <= 0) return;
+  const size_t sm = kWItems * (warp_patch_elems<T>(max_tb) * sizeof(typename cplx_t<T>::type) + 32 * kDgStage * sizeof(T));
+  CUtensorMap unused;
+  std::memset(&unused, 0, sizeof(unused));
+  ArgTab<DegridArgs<T>> src{tab};
+  k_degrid_w<T><<<dim3((max_items + kWItems - 1) / kWItems, count), kThreads, sm, s>>>(src, kb, unused);
 }
 
 template <typename T>
@@ -1000,7 +1024,18 @@ void launch_grid(const Geometry& g, const WorkItem* items, int n_items, const Po
   if (n_items <= 0) return;
   const size_t PW = size_t(g.TB + kJ);
   const size_t sm = kWItems * (PW * PW * sizeof(KCell<T>) + 32 * kStage * sizeof(T));
-  k_grid_w<T><<<(n_items + kWItems - 1) / kWItems, kThreads, sm, s>>>(g, items, n_items, pos, perm, kb, pro, Q);
+  ArgVal<GridArgs<T>> src{GridArgs<T>{g, items, n_items, pos, perm, pro, Q}};
+  k_grid_w<T><<<(n_items + kWItems - 1) / kWItems, kThreads, sm, s>>>(src, kb);
+}
+
+template <typename T>
+void launch_grid_batch(const GridArgs<T>* tab, int count, int max_items, int max_tb, const KbPoly<T>& kb,
+                       cudaStream_t s) {
+  if (max_items <= 0 || count <= 0) return;
+  const size_t PW = size_t(max_tb + kJ);
+  const size_t sm = kWItems * (PW * PW * sizeof(KCell<T>) + 32 * kStage * sizeof(T));
+  ArgTab<GridArgs<T>> src{tab};
+  k_grid_w<T><<<dim3((max_items + kWItems - 1) / kWItems, count), kThreads, sm, s>>>(src, kb);
 }
 
 template <typename T>
@@ -1127,6 +1162,8 @@ int build_bins(const double* uv, int64_t M, const Geometry& g, int chunk, Pos<T>
   template void launch_grid<T>(const Geometry&, const WorkItem*, int, const Pos<T>*, const int*,                \
                                const KbPoly<T>&, const GridPro<cplx_t<T>::type>&, cplx_t<T>::type*,             \
                                cudaStream_t);                                                                  \
+  template void launch_degrid_batch<T>(const DegridArgs<T>*, int, int, int, const KbPoly<T>&, cudaStream_t);    \
+  template void launch_grid_batch<T>(const GridArgs<T>*, int, int, int, const KbPoly<T>&, cudaStream_t);        \
   template void launch_gram<T>(const Geometry&, const CUtensorMap&, const WorkItem*, int, const Pos<T>*,        \
                                const KbPoly<T>&, cplx_t<T>::type*, int*, cudaStream_t);                         \
   template void launch_encode_x2<T>(const double*, const int*, int64_t, int, int, Pos<T>*, cudaStream_t);     \

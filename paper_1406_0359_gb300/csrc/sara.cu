@@ -21,7 +21,9 @@
 // epilogue applies the positivity block and writes x_1 + x_2.
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "../../include/purify.h"
@@ -182,16 +184,20 @@ __device__ void ana_body(const AnaArgs<T>& A, const T* __restrict__ h, const T* 
   if (A.partials) {
     const Acc<T> t = block_merge<kThr>(part, red);
     if (threadIdx.x == 0)
-      reinterpret_cast<Acc<T>*>(A.partials)[(size_t(blockIdx.z) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
+      reinterpret_cast<Acc<T>*>(A.partials)[(size_t(z) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThr) k_ana_level(AnaArgs<T> A, DbFilters<T> f) {
+// One analysis level; blockIdx.z = instance * nf + filter slot (one
+// instance: nf = gridDim.z).
+template <typename T, typename Src>
+__global__ void __launch_bounds__(kThr) k_ana_level(Src src, int nf, DbFilters<T> f) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ double red[32];
   T* sm = reinterpret_cast<T*>(sm_raw);
-  const int z = blockIdx.z, k = A.fid[z];
+  const int inst = int(blockIdx.z) / nf, z = int(blockIdx.z) - inst * nf;
+  const AnaArgs<T> A = src.get_at(inst);
+  const int k = A.fid[z];
   const T* h = f.h[k];
   const T* g = f.g[k];
   switch (k) {
@@ -207,10 +213,22 @@ __global__ void __launch_bounds__(kThr) k_ana_level(AnaArgs<T> A, DbFilters<T> f
 }
 
 // Dirac block: c_0 = x / sqrt(q) (with the prox epilogue when fused).
-template <typename T>
-__global__ void __launch_bounds__(kThr) k_dirac(const T* __restrict__ x, size_t N, T scale, CoefOut<T> out,
-                                                double* partials) {
+template <typename T> struct DiracArgs {
+  const T* x;
+  size_t N;
+  T scale;
+  CoefOut<T> out;
+  double* partials;
+};
+template <typename T, typename Src>
+__global__ void __launch_bounds__(kThr) k_dirac(Src src) {
   __shared__ double red[32];
+  decltype(auto) a = src.get();
+  const T* __restrict__ x = a.x;
+  const size_t N = a.N;
+  const T scale = a.scale;
+  const CoefOut<T>& out = a.out;
+  double* partials = a.partials;
   Acc<T> part;
   const size_t i = size_t(blockIdx.x) * kThr + threadIdx.x;
   if (i < N) emit(out, i, x[i] * scale, part);
@@ -343,19 +361,23 @@ __device__ void syn_dispatch(const SynArgs<T>& S, const DbFilters<T>& f, int z, 
   }
 }
 
-// Intermediate synthesis level: blockIdx.z = filter slot, output band -> scratch.
-template <typename T>
-__global__ void __launch_bounds__(kThr) k_syn_level(SynArgs<T> S, DbFilters<T> f) {
+// Intermediate synthesis level: blockIdx.z = instance * nf + filter slot,
+// output band -> scratch.
+template <typename T, typename Src>
+__global__ void __launch_bounds__(kThr) k_syn_level(Src src, int nf, DbFilters<T> f) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sm = reinterpret_cast<T*>(sm_raw);
+  const int inst = int(blockIdx.z) / nf, z = int(blockIdx.z) - inst * nf;
+  const SynArgs<T> S = src.get_at(inst);
   T acc[kTO * kTO / kThr];
-  syn_dispatch(S, f, blockIdx.z, S.fid[blockIdx.z], sm, blockIdx.y * kTO, blockIdx.x * kTO, acc, false);
+  syn_dispatch(S, f, z, S.fid[z], sm, blockIdx.y * kTO, blockIdx.x * kTO, acc, false);
 }
 
 // Finest level: all selected filters and the Dirac block summed into the
 // image (ALL: the eight filters in slots 0..7, unrolled).
-template <typename T, bool ALL>
-__global__ void __launch_bounds__(kThr) k_syn_final(SynArgs<T> S, DbFilters<T> f) {
+template <typename T, bool ALL, typename Src>
+__global__ void __launch_bounds__(kThr) k_syn_final(Src src, DbFilters<T> f) {
+  const SynArgs<T> S = src.get_at(int(blockIdx.z));
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sm = reinterpret_cast<T*>(sm_raw);
   const int i0 = blockIdx.y * kTO, j0 = blockIdx.x * kTO;
@@ -398,25 +420,34 @@ template <typename T> size_t syn_smem(int F) {
 
 inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
-// Runs the analysis levels; returns partial sums written (prox mode).
+// Launch plan of one analysis (Dirac block, then one launch per level) and
+// one synthesis (coarse levels, then the fused finest level), shared by the
+// single-operator path (arguments by value) and the batch (device tables).
+template <typename T> struct AnaPlan {
+  bool dirac;
+  DiracArgs<T> d;
+  int nb0;
+  int levels;
+  AnaArgs<T> a[16];
+  dim3 grid[16];  // z = filter slots
+  int np;         // objective partials written
+};
 template <typename T>
-int run_analysis(const SaraPlan<T>& P, const T* x, const CoefOut<T>& out, double* partials, cudaStream_t s) {
+AnaPlan<T> plan_analysis(const SaraPlan<T>& P, const T* x, const CoefOut<T>& out, double* partials) {
+  AnaPlan<T> pl{};
   const int n = P.n;
   const size_t N = size_t(n) * n;
-  int np = 0;
-  if (P.dirac) {
-    const int nb0 = int((N + kThr - 1) / kThr);
-    k_dirac<T><<<nb0, kThr, 0, s>>>(x, N, P.scale, out, partials ? partials : nullptr);
-    if (partials) np += nb0;
-  }
-  if (P.nf == 0) return np;
-  const size_t sm = ana_smem<T>(16);
+  pl.dirac = P.dirac != 0;
+  pl.nb0 = int((N + kThr - 1) / kThr);
+  pl.d = DiracArgs<T>{x, N, P.scale, out, partials};
+  int np = pl.dirac && partials ? pl.nb0 : 0;
+  pl.levels = P.nf > 0 ? P.levels : 0;
   const T* in = x;
   size_t in_stride = 0;
   T* bufs[2] = {P.s0, P.s1};
-  for (int lev = 1; lev <= P.levels; ++lev) {
+  for (int lev = 1; lev <= pl.levels; ++lev) {
     const int L = n >> (lev - 1), H = L / 2;
-    AnaArgs<T> A;
+    AnaArgs<T>& A = pl.a[lev - 1];
     A.in = in;
     A.in_stride = in_stride;
     A.L = L;
@@ -428,19 +459,27 @@ int run_analysis(const SaraPlan<T>& P, const T* x, const CoefOut<T>& out, double
     A.scale = P.scale;
     A.out = out;
     A.partials = partials ? partials + np : nullptr;
-    dim3 grid(cdiv(H, kTH), cdiv(H, kTH), P.nf);
-    k_ana_level<T><<<grid, kThr, sm, s>>>(A, P.f);
-    if (partials) np += int(grid.x * grid.y * grid.z);
+    pl.grid[lev - 1] = dim3(cdiv(H, kTH), cdiv(H, kTH), P.nf);
+    if (partials) np += int(pl.grid[lev - 1].x * pl.grid[lev - 1].y * pl.grid[lev - 1].z);
     in = A.s_out;
     in_stride = size_t(H) * H;
   }
-  return np;
+  pl.np = np;
+  return pl;
 }
 
+template <typename T> struct SynPlan {
+  int levels;  // coarse levels (launches before the final one)
+  SynArgs<T> a[16];
+  dim3 grid[16];
+  SynArgs<T> fin;
+  dim3 fgrid;
+  bool all;  // the eight filters: the unrolled final kernel
+};
 template <typename T>
-void run_synthesis(const SaraPlan<T>& P, const T* c, T* x, int pos_block, const T* xh, T* z2, cudaStream_t s) {
+SynPlan<T> plan_synthesis(const SaraPlan<T>& P, const T* c, T* x, int pos_block, const T* xh, T* z2) {
+  SynPlan<T> pl{};
   const int n = P.n;
-  const size_t sm = syn_smem<T>(16);
   T* bufs[2] = {P.s0, P.s1};
   const T* s_in = nullptr;
   auto select = [&](SynArgs<T>& S) {
@@ -449,20 +488,23 @@ void run_synthesis(const SaraPlan<T>& P, const T* c, T* x, int pos_block, const 
     for (int z = 0; z < kMaxDb; ++z) S.fid[z] = P.fid[z];
     S.scale = P.scale;
   };
-  for (int lev = P.levels; lev >= 2 && P.nf > 0; --lev) {
+  int k = 0;
+  for (int lev = P.levels; lev >= 2 && P.nf > 0; --lev, ++k) {
     const int H = n >> lev, L = 2 * H;
-    SynArgs<T> S{};
+    SynArgs<T>& S = pl.a[k];
+    S = SynArgs<T>{};
     S.c = c;
     S.s_in = s_in;
     S.H = H;
     S.n = n;
     S.s_out = bufs[lev & 1];
     select(S);
-    dim3 grid(cdiv(L, kTO), cdiv(L, kTO), P.nf);
-    k_syn_level<T><<<grid, kThr, sm, s>>>(S, P.f);
+    pl.grid[k] = dim3(cdiv(L, kTO), cdiv(L, kTO), P.nf);
     s_in = S.s_out;
   }
-  SynArgs<T> S{};
+  pl.levels = k;
+  SynArgs<T>& S = pl.fin;
+  S = SynArgs<T>{};
   S.c = c;
   S.s_in = s_in;
   S.H = n / 2;
@@ -473,21 +515,45 @@ void run_synthesis(const SaraPlan<T>& P, const T* c, T* x, int pos_block, const 
   S.x_out = x;
   S.xh = xh;
   S.z2 = z2;
-  dim3 grid(cdiv(n, kTO), cdiv(n, kTO), 1);
-  if (P.nf == kMaxDb)
-    k_syn_final<T, true><<<grid, kThr, sm, s>>>(S, P.f);
+  pl.fgrid = dim3(cdiv(n, kTO), cdiv(n, kTO), 1);
+  pl.all = P.nf == kMaxDb;
+  return pl;
+}
+
+// Runs the analysis levels; returns partial sums written (prox mode).
+template <typename T>
+int run_analysis(const SaraPlan<T>& P, const T* x, const CoefOut<T>& out, double* partials, cudaStream_t s) {
+  const AnaPlan<T> pl = plan_analysis(P, x, out, partials);
+  if (pl.dirac) k_dirac<T><<<pl.nb0, kThr, 0, s>>>(ArgVal<DiracArgs<T>>{pl.d});
+  const size_t sm = ana_smem<T>(16);
+  for (int l = 0; l < pl.levels; ++l)
+    k_ana_level<T><<<pl.grid[l], kThr, sm, s>>>(ArgVal<AnaArgs<T>>{pl.a[l]}, P.nf, P.f);
+  return pl.np;
+}
+
+template <typename T>
+void run_synthesis(const SaraPlan<T>& P, const T* c, T* x, int pos_block, const T* xh, T* z2, cudaStream_t s) {
+  const SynPlan<T> pl = plan_synthesis(P, c, x, pos_block, xh, z2);
+  const size_t sm = syn_smem<T>(16);
+  for (int l = 0; l < pl.levels; ++l) k_syn_level<T><<<pl.grid[l], kThr, sm, s>>>(ArgVal<SynArgs<T>>{pl.a[l]}, P.nf, P.f);
+  if (pl.all)
+    k_syn_final<T, true><<<pl.fgrid, kThr, sm, s>>>(ArgVal<SynArgs<T>>{pl.fin}, P.f);
   else
-    k_syn_final<T, false><<<grid, kThr, sm, s>>>(S, P.f);
+    k_syn_final<T, false><<<pl.fgrid, kThr, sm, s>>>(ArgVal<SynArgs<T>>{pl.fin}, P.f);
 }
 
 }  // namespace
 
 template <typename T> cudaError_t configure_sara() {
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = raise_smem_limit(k_ana_level<T>);
-  if (e == cudaSuccess) e = raise_smem_limit(k_syn_level<T>);
-  if (e == cudaSuccess) e = raise_smem_limit(k_syn_final<T, true>);
-  if (e == cudaSuccess) e = raise_smem_limit(k_syn_final<T, false>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_ana_level<T, ArgVal<AnaArgs<T>>>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_syn_level<T, ArgVal<SynArgs<T>>>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_syn_final<T, true, ArgVal<SynArgs<T>>>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_syn_final<T, false, ArgVal<SynArgs<T>>>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_ana_level<T, ArgTab<AnaArgs<T>>>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_syn_level<T, ArgTab<SynArgs<T>>>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_syn_final<T, true, ArgTab<SynArgs<T>>>);
+  if (e == cudaSuccess) e = raise_smem_limit(k_syn_final<T, false, ArgTab<SynArgs<T>>>);
   return e;
 }
 template cudaError_t configure_sara<float>();
@@ -544,7 +610,122 @@ void sara_synthesis_pos(const SaraPlan<T>& P, const T* xh, T* z2, T* xs, cudaStr
   run_synthesis<T>(P, P.cs, xs, 1, xh, z2, s);
 }
 
+// ---- batched SDMM blocks 1 and 2 (l1 prox on the analysis, positivity on
+// the synthesis) for instances of one image side, levels and dictionary:
+// every launch of the sequence covers all instances (device argument
+// tables, instance in blockIdx.y / blockIdx.z).
+template <typename T> struct SaraBatch {
+  void* dev = nullptr;
+  int count = 0, nf = 0, levels_a = 0, levels_s = 0, nb0 = 0;
+  bool dirac = false, all = false;
+  dim3 agrid[16], sgrid[16], fgrid;
+  const DiracArgs<T>* dtab = nullptr;
+  const AnaArgs<T>* atab[16] = {};
+  const SynArgs<T>* stab[16] = {};
+  const SynArgs<T>* ftab = nullptr;
+  DbFilters<T> f;
+};
+
+template <typename T>
+int sara_batch_create(const std::vector<SaraBatchInst<T>>& in, SaraBatch<T>** out, int* np) {
+  if (in.empty()) return PURIFY_ERR_INVALID;
+  SaraBatch<T>* b = new (std::nothrow) SaraBatch<T>();
+  if (!b) return PURIFY_ERR_NOMEM;
+  const int count = int(in.size());
+  std::vector<AnaPlan<T>> ap(count);
+  std::vector<SynPlan<T>> sp(count);
+  for (int i = 0; i < count; ++i) {
+    const SaraBatchInst<T>& u = in[i];
+    CoefOut<T> co{};
+    co.prox = 1;
+    co.z1 = u.z1;
+    co.w = u.w;
+    co.cs = u.P->cs;
+    co.gamma = T(u.gamma);
+    ap[i] = plan_analysis(*u.P, u.xh, co, u.partials);
+    sp[i] = plan_synthesis(*u.P, u.P->cs, u.xs, 1, u.xh, u.z2);
+  }
+  const SaraPlan<T>& P0 = *in[0].P;
+  b->count = count;
+  b->nf = P0.nf;
+  b->dirac = ap[0].dirac;
+  b->nb0 = ap[0].nb0;
+  b->levels_a = ap[0].levels;
+  b->levels_s = sp[0].levels;
+  b->all = sp[0].all;
+  b->f = P0.f;
+  // one device buffer: Dirac table, analysis tables per level, synthesis tables per level, final table
+  const size_t nd = sizeof(DiracArgs<T>) * count, na = sizeof(AnaArgs<T>) * count, ns = sizeof(SynArgs<T>) * count;
+  const size_t total = nd + na * b->levels_a + ns * (b->levels_s + 1);
+  std::vector<unsigned char> host(total);
+  size_t off = 0;
+  for (int i = 0; i < count; ++i) std::memcpy(&host[off + i * sizeof(DiracArgs<T>)], &ap[i].d, sizeof(DiracArgs<T>));
+  const size_t doff = off;
+  off += nd;
+  size_t aoff[16], soff[16];
+  for (int l = 0; l < b->levels_a; ++l, off += na) {
+    aoff[l] = off;
+    b->agrid[l] = dim3(ap[0].grid[l].x, ap[0].grid[l].y, ap[0].grid[l].z * count);
+    for (int i = 0; i < count; ++i) std::memcpy(&host[off + i * sizeof(AnaArgs<T>)], &ap[i].a[l], sizeof(AnaArgs<T>));
+  }
+  for (int l = 0; l < b->levels_s; ++l, off += ns) {
+    soff[l] = off;
+    b->sgrid[l] = dim3(sp[0].grid[l].x, sp[0].grid[l].y, sp[0].grid[l].z * count);
+    for (int i = 0; i < count; ++i) std::memcpy(&host[off + i * sizeof(SynArgs<T>)], &sp[i].a[l], sizeof(SynArgs<T>));
+  }
+  const size_t foff = off;
+  b->fgrid = dim3(sp[0].fgrid.x, sp[0].fgrid.y, count);
+  for (int i = 0; i < count; ++i) std::memcpy(&host[off + i * sizeof(SynArgs<T>)], &sp[i].fin, sizeof(SynArgs<T>));
+  if (cudaMalloc(&b->dev, total) != cudaSuccess) {
+    delete b;
+    return PURIFY_ERR_NOMEM;
+  }
+  if (cudaMemcpy(b->dev, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(b->dev);
+    delete b;
+    return PURIFY_ERR_CUDA;
+  }
+  unsigned char* d = static_cast<unsigned char*>(b->dev);
+  b->dtab = reinterpret_cast<const DiracArgs<T>*>(d + doff);
+  for (int l = 0; l < b->levels_a; ++l) b->atab[l] = reinterpret_cast<const AnaArgs<T>*>(d + aoff[l]);
+  for (int l = 0; l < b->levels_s; ++l) b->stab[l] = reinterpret_cast<const SynArgs<T>*>(d + soff[l]);
+  b->ftab = reinterpret_cast<const SynArgs<T>*>(d + foff);
+  *np = ap[0].np;
+  *out = b;
+  return PURIFY_OK;
+}
+
+template <typename T> void sara_batch_launch(const SaraBatch<T>* b, cudaStream_t s) {
+  if (b->dirac) k_dirac<T><<<dim3(b->nb0, b->count), kThr, 0, s>>>(ArgTab<DiracArgs<T>>{b->dtab});
+  const size_t sma = ana_smem<T>(16), sms = syn_smem<T>(16);
+  for (int l = 0; l < b->levels_a; ++l)
+    k_ana_level<T><<<b->agrid[l], kThr, sma, s>>>(ArgTab<AnaArgs<T>>{b->atab[l]}, b->nf, b->f);
+  for (int l = 0; l < b->levels_s; ++l)
+    k_syn_level<T><<<b->sgrid[l], kThr, sms, s>>>(ArgTab<SynArgs<T>>{b->stab[l]}, b->nf, b->f);
+  if (b->all)
+    k_syn_final<T, true><<<b->fgrid, kThr, sms, s>>>(ArgTab<SynArgs<T>>{b->ftab}, b->f);
+  else
+    k_syn_final<T, false><<<b->fgrid, kThr, sms, s>>>(ArgTab<SynArgs<T>>{b->ftab}, b->f);
+}
+
+template <typename T> int sara_prox_partials(const SaraPlan<T>& P) {
+  CoefOut<T> co{};
+  co.prox = 1;
+  double dummy = 0;
+  return plan_analysis(P, static_cast<const T*>(nullptr), co, &dummy).np;
+}
+
+template <typename T> void sara_batch_destroy(SaraBatch<T>* b) {
+  if (!b) return;
+  if (b->dev) cudaFree(b->dev);
+  delete b;
+}
+
 #define INST(T)                                                                                 \
+  template int sara_batch_create<T>(const std::vector<SaraBatchInst<T>>&, SaraBatch<T>**, int*);  \
+  template void sara_batch_launch<T>(const SaraBatch<T>*, cudaStream_t);                          \
+  template void sara_batch_destroy<T>(SaraBatch<T>*);                                             \
+  template int sara_prox_partials<T>(const SaraPlan<T>&);                                         \
   template void sara_analysis<T>(const SaraPlan<T>&, const T*, T*, cudaStream_t);                 \
   template void sara_synthesis<T>(const SaraPlan<T>&, const T*, T*, cudaStream_t);                \
   template int sara_analysis_prox<T>(const SaraPlan<T>&, const T*, const L1Block<T>&, cudaStream_t); \

@@ -16,10 +16,15 @@ template <> struct Vec16<float> { typedef float4 type; static constexpr int W = 
 template <> struct Vec16<double> { typedef double2 type; static constexpr int W = 2; };
 
 // x += sc[idx] p on 16-byte vectors (N / W of them, both arrays 16-byte aligned).
-template <typename T>
-__global__ void __launch_bounds__(kT) k_axpy(T* __restrict__ x, const T* __restrict__ p,
-                                             const double* __restrict__ sc, int idx, size_t N) {
+template <typename T, typename Src>
+__global__ void __launch_bounds__(kT) k_axpy(Src src) {
   typedef typename Vec16<T>::type V;
+  decltype(auto) args = src.get();
+  T* __restrict__ x = args.x;
+  const T* __restrict__ p = args.p;
+  const double* __restrict__ sc = args.sc;
+  const int idx = args.idx;
+  const size_t N = args.N;
   constexpr int W = Vec16<T>::W;
   const T a = T(sc[idx]);
   V* xv = reinterpret_cast<V*>(x);
@@ -37,10 +42,14 @@ __global__ void __launch_bounds__(kT) k_axpy(T* __restrict__ x, const T* __restr
 
 // One block: merge the compensated partials (Acc<T>) in a fixed order, then
 // apply `op` (FinOp) in FP64.
-template <typename T>
-__global__ void __launch_bounds__(kT) k_finalize(const double* __restrict__ pa, int na, int op, double arg,
-                                                 double* __restrict__ sc) {
+template <typename T, typename Src>
+__global__ void __launch_bounds__(kT) k_finalize(Src src) {
   __shared__ double red[32];
+  decltype(auto) args = src.get();
+  const double* __restrict__ pa = args.pa;
+  const int na = args.na, op = args.op;
+  const double arg = args.arg;
+  double* __restrict__ sc = args.sc;
   const double a = merge_array<kT>(reinterpret_cast<const Acc<T>*>(pa), na, red).value();
   if (threadIdx.x != 0) return;
   switch (op) {
@@ -125,13 +134,19 @@ __global__ void __launch_bounds__(kFinT) k_finalize_blocks(const double* __restr
 // The same scalars for one visibility block (R = 1) in two levels: kFinCtas
 // CTAs each merge a contiguous slice of the items' partials (fixed order),
 // the last CTA to finish (ticket) merges the CTAs' partials in index order.
-template <typename T>
-__global__ void __launch_bounds__(kT) k_finalize_ball1(const double* __restrict__ part0,
-                                                       const double* __restrict__ part1, int n_items, double nu,
-                                                       const double* __restrict__ eps_b, double* __restrict__ scale_b,
-                                                       double* __restrict__ sc, double* __restrict__ cpart,
-                                                       unsigned int* __restrict__ ticket) {
+template <typename T, typename Src>
+__global__ void __launch_bounds__(kT) k_finalize_ball1(Src src) {
   __shared__ double red[32];
+  decltype(auto) args = src.get();
+  const double* __restrict__ part0 = args.part0;
+  const double* __restrict__ part1 = args.part1;
+  const int n_items = args.n_items;
+  const double nu = args.nu;
+  const double* __restrict__ eps_b = args.eps_b;
+  double* __restrict__ scale_b = args.scale_b;
+  double* __restrict__ sc = args.sc;
+  double* __restrict__ cpart = args.cpart;
+  unsigned int* __restrict__ ticket = args.ticket;
   const Acc<T>* p0 = reinterpret_cast<const Acc<T>*>(part0);
   const Acc<T>* p1 = reinterpret_cast<const Acc<T>*>(part1);
   Acc<T>* c0 = reinterpret_cast<Acc<T>*>(cpart);
@@ -164,7 +179,7 @@ __global__ void __launch_bounds__(kT) k_finalize_ball1(const double* __restrict_
     c0[blockIdx.x] = a;
     c1[blockIdx.x] = c;
   }
-  if (!last_block_done(ticket)) return;
+  if (!last_block_done(ticket, gridDim.x)) return;
   const double av = merge_array<kT>(c0, int(gridDim.x), red).value();
   const double cv = merge_array<kT>(c1, int(gridDim.x), red).value();
   if (threadIdx.x == 0) {
@@ -233,6 +248,14 @@ __global__ void k_scale(T* __restrict__ v, size_t N, const double* __restrict__ 
   for (size_t i = size_t(blockIdx.x) * kT + threadIdx.x; i < N; i += size_t(gridDim.x) * kT) v[i] *= s;
 }
 
+// Zero `bytes` (a multiple of 16) of one instance's buffer.
+__global__ void __launch_bounds__(kT) k_zero(ArgTab<ZeroArgs> src) {
+  const ZeroArgs a = src.get();
+  uint4* p = static_cast<uint4*>(a.p);
+  const size_t n = a.bytes / 16;
+  for (size_t i = size_t(blockIdx.x) * kT + threadIdx.x; i < n; i += size_t(gridDim.x) * kT) p[i] = make_uint4(0, 0, 0, 0);
+}
+
 template <typename T>
 __global__ void k_check_finite(const T* __restrict__ v, size_t N, int* __restrict__ flag) {
   bool bad = false;
@@ -278,11 +301,25 @@ int vec_blocks(size_t N) { return nblk(N); }
 template <typename T> void launch_axpy(T* x, const T* p, const double* sc, int idx, size_t N, cudaStream_t s) {
   // one 16-byte vector per thread; N and the pointers are multiples of 16
   // bytes (n x n images, n >= 16; cudaMalloc'd arrays)
-  k_axpy<T><<<nblk((N + 3) / 4), kT, 0, s>>>(x, p, sc, idx, N);
+  k_axpy<T><<<nblk((N + 3) / 4), kT, 0, s>>>(ArgVal<AxpyArgs<T>>{AxpyArgs<T>{x, p, sc, idx, N}});
+}
+template <typename T> void launch_axpy_batch(const AxpyArgs<T>* tab, int count, size_t N, cudaStream_t s) {
+  k_axpy<T><<<dim3(nblk((N + 3) / 4), count), kT, 0, s>>>(ArgTab<AxpyArgs<T>>{tab});
+}
+template <typename T> void launch_finalize_batch(const FinArgs* tab, int count, cudaStream_t s) {
+  k_finalize<T><<<dim3(1, count), kT, 0, s>>>(ArgTab<FinArgs>{tab});
+}
+template <typename T> void launch_finalize_ball1_batch(const Ball1Args* tab, int count, cudaStream_t s) {
+  k_finalize_ball1<T><<<dim3(kFinCtas, count), kT, 0, s>>>(ArgTab<Ball1Args>{tab});
+}
+void launch_zero_batch(const ZeroArgs* tab, int count, size_t max_bytes, cudaStream_t s) {
+  size_t b = (max_bytes / 16 + kT - 1) / kT;
+  if (b > 2048) b = 2048;
+  k_zero<<<dim3(unsigned(b > 0 ? b : 1), count), kT, 0, s>>>(ArgTab<ZeroArgs>{tab});
 }
 
 template <typename T> void launch_finalize(const double* pa, int na, int op, double arg, double* sc, cudaStream_t s) {
-  k_finalize<T><<<1, kT, 0, s>>>(pa, na, op, arg, sc);
+  k_finalize<T><<<1, kT, 0, s>>>(ArgVal<FinArgs>{FinArgs{pa, na, op, arg, sc}});
 }
 
 template <typename T>
@@ -299,7 +336,8 @@ void launch_finalize_blocks(const double* part0, const double* part1, const int*
   if (R == 1 && cpart && ticket) {
     int nb = (n_items + 4 * kT - 1) / (4 * kT);
     nb = nb < 1 ? 1 : (nb > kFinCtas ? kFinCtas : nb);
-    k_finalize_ball1<T><<<nb, kT, 0, s>>>(part0, part1, n_items, nu, eps_b, scale_b, sc, cpart, ticket);
+    k_finalize_ball1<T><<<nb, kT, 0, s>>>(
+        ArgVal<Ball1Args>{Ball1Args{part0, part1, n_items, nu, eps_b, scale_b, sc, cpart, ticket}});
   } else {
     k_finalize_blocks<T><<<1, kFinT, 0, s>>>(part0, part1, items_as_int + 3, n_items, R, nu, eps_b, scale_b, sc);
   }
@@ -341,6 +379,9 @@ cudaError_t wait_selftest(int deliver, cudaStream_t s, int* timed_out) {
 
 #define INST(T)                                                                                       \
   template void launch_axpy<T>(T*, const T*, const double*, int, size_t, cudaStream_t);                \
+  template void launch_axpy_batch<T>(const AxpyArgs<T>*, int, size_t, cudaStream_t);                   \
+  template void launch_finalize_batch<T>(const FinArgs*, int, cudaStream_t);                            \
+  template void launch_finalize_ball1_batch<T>(const Ball1Args*, int, cudaStream_t);                    \
   template void launch_finalize<T>(const double*, int, int, double, double*, cudaStream_t);             \
   template void launch_finalize_blocks<T>(const double*, const double*, const int*, int, int, double,           \
                                           const double*, double*, double*, double*, unsigned int*,             \

@@ -36,6 +36,28 @@ template <typename T> void launch_reweight(T* w, size_t N, double delta, cudaStr
 template <typename T> void launch_fill(T* v, size_t N, T val, cudaStream_t s);
 template <typename T> void launch_scale(T* v, size_t N, const double* sc, int idx, double mul, cudaStream_t s);
 template <typename C> void launch_gather(const C* src, const int* perm, size_t M, C* dst, cudaStream_t s);
+// Batched vector steps of instances of one size (argument tables in device
+// memory; instance = blockIdx.y, one grid for all).
+template <typename T> struct AxpyArgs { T* x; const T* p; const double* sc; int idx; size_t N; };
+template <typename T> void launch_axpy_batch(const AxpyArgs<T>* tab, int count, size_t N, cudaStream_t s);
+struct FinArgs { const double* pa; int na; int op; double arg; double* sc; };
+template <typename T> void launch_finalize_batch(const FinArgs* tab, int count, cudaStream_t s);
+struct Ball1Args {
+  const double* part0;
+  const double* part1;
+  int n_items;
+  double nu;
+  const double* eps_b;
+  double* scale_b;
+  double* sc;
+  double* cpart;
+  unsigned int* ticket;
+};
+// kFinCtas CTAs per instance (the two-level merge of the R = 1 ball scalars).
+template <typename T> void launch_finalize_ball1_batch(const Ball1Args* tab, int count, cudaStream_t s);
+struct ZeroArgs { void* p; size_t bytes; };  // bytes a multiple of 16
+void launch_zero_batch(const ZeroArgs* tab, int count, size_t max_bytes, cudaStream_t s);
+
 // Device flag set when any of the n values is not finite (NaN or infinity).
 template <typename T> void launch_check_finite(const T* v, size_t n, int* flag, cudaStream_t s);
 
