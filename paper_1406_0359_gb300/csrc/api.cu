@@ -211,7 +211,9 @@ template <typename T> class OpImpl : public purify_op {
   cudaMemPool_t mem_pool = nullptr;
   cudaStream_t own = nullptr;  // solver stream (capturable, non-blocking)
   cudaStream_t aux = nullptr;  // second branch of an SDMM iteration (ball block)
+  cudaStream_t aux2 = nullptr;  // zeroing of the gridding accumulator beside the ball block's first passes
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_zfork = nullptr, ev_zjoin = nullptr;
   double* bpart = nullptr;     // ball-block partials (2 per work item), apart from the l1 block's
   int bpart_cap = 0;
   CUtensorMap* tmap_dev = nullptr;  // device copy of tmap (batched degridding reads it there)
@@ -323,6 +325,10 @@ template <typename T> class OpImpl : public purify_op {
     if (ev_out) cudaEventDestroy(ev_out);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
+    if (ev_zfork) cudaEventDestroy(ev_zfork);
+    if (ev_zjoin) cudaEventDestroy(ev_zjoin);
+    if (aux2) cudaStreamSynchronize(aux2);
+    if (aux2) cudaStreamDestroy(aux2);
     if (own) cudaStreamDestroy(own);
     if (aux) cudaStreamDestroy(aux);
     if (h_sc) pinned_slots().put(h_sc);
@@ -410,6 +416,9 @@ template <typename T> class OpImpl : public purify_op {
     if (!light) {  // a set-up operator runs only on the caller's stream
       CK(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
       CK(cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking));
+      CK(cudaStreamCreateWithFlags(&aux2, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&ev_zfork, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ev_zjoin, cudaEventDisableTiming));
       CK(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
       CK(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
       CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
@@ -933,7 +942,16 @@ template <typename T> class OpImpl : public purify_op {
       cudaEventRecord(ev_fork, s);
       cudaStreamWaitEvent(b3, ev_fork, 0);
     }
-    // block 3 (data fidelity): v = nu Phi x_hat + z_3, project on the ball
+    // block 3 (data fidelity): v = nu Phi x_hat + z_3, project on the ball.
+    // The gridding accumulator is zeroed on a third stream meanwhile (nothing
+    // before the gridding pass touches it).
+    const bool zpar = !rec && b3 != s;
+    if (zpar) {
+      cudaEventRecord(ev_zfork, b3);
+      cudaStreamWaitEvent(aux2, ev_zfork, 0);
+      zero_q(aux2);
+      cudaEventRecord(ev_zjoin, aux2);
+    }
     fwd_grid(plain(xh), b3);
     DegridEp<C> dep{};
     dep.mode = DG_BALL;
@@ -948,7 +966,8 @@ template <typename T> class OpImpl : public purify_op {
     else
       PROF(KK_VEC, b3, launch_finalize_blocks<T>(bpart, bpart + n_items, reinterpret_cast<const int*>(items), n_items,
                                                   nblocks, nu, eps_dev, scale_dev, sc, fin_part, tickets + 2, b3));
-    zero_q(b3);
+    if (zpar) cudaStreamWaitEvent(b3, ev_zjoin, 0);
+    else zero_q(b3);
     GridPro<C> gp{};
     gp.mode = GP_BALL;
     gp.z = z3;
