@@ -328,6 +328,10 @@ def run_ours(args, ws, rank, local):
         batch = batch_study(16, 20, seed=40, plain_arm=False)
         batch["note"] = "reduced form of the 64-instance batch (bench.py --batch); solves/s of 16 instances x 20 iterations"
 
+    serving = None
+    if rank == 0 and not args.no_batch_summary:
+        serving = serving_summary()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         y1 = op.phi(xt)
@@ -360,6 +364,7 @@ def run_ours(args, ws, rank, local):
                    "nu": nu, "gamma": gamma, "op_device_bytes": info["device_bytes"], "work_items": info["n_items"]},
         "cpu_baseline": cpu,
         "batch_16x20": batch,
+        "serving_12": serving,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -635,6 +640,45 @@ def run_batch(args):
                        "mode": "purify_batch_solve: one launch per pass per image side, one graph per iteration"}}
     line.update(res)
     print(json.dumps(line), flush=True)
+
+
+def serving_summary(count=12, seed=7, rate_mult=2.0):
+    """Reduced form of the serving benchmark for the default bench line:
+    `count` requests (images 128^2-512^2, M log-uniform in [16K, 256K], SDMM
+    to xi = 1e-4 or 100 iterations), one at a time through the server, then
+    as Poisson arrivals at `rate_mult` times that rate with 16 slots:
+    solves/s, p50 / p99 latency and the worst difference from the one-at-a-time
+    results."""
+    import numpy as np
+    import torch
+
+    from paper_1406_0359_gb300.binding import Server
+
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(count):
+        n = int(rng.choice([128, 256, 512], p=[0.4, 0.35, 0.25]))
+        M = int(np.exp(rng.uniform(np.log(16384), np.log(1 << 18))))
+        reqs.append(_make_request(n, M, 900 + i, dev))
+    params = dict(t_max=100, cg_iters=10, xi=1e-4)
+    srv = Server(int(150e9), 1)
+    ids = [srv.submit(r["uv"], r["y"], r["n"], 3, r["eps"], **params) for r in reqs]
+    seq_wall, seq_res = _drain(srv, ids)
+    srv.close()
+    lam = rate_mult * count / seq_wall
+    arr = np.cumsum(np.random.default_rng(seed + 1).exponential(1.0 / lam, count))
+    srv = Server(int(150e9), 16)
+    ids = [None] * count
+    wall, res = _drain(srv, ids, list(arr), reqs, params)
+    srv.close()
+    lat = np.array([r[2] for r in res])
+    return {"requests": count, "one_at_a_time_solves_per_s": round(count / seq_wall, 3),
+            "offered_rps": round(lam, 3), "solves_per_s": round(count / wall, 3),
+            "p50_s": round(float(np.percentile(lat, 50)), 4), "p99_s": round(float(np.percentile(lat, 99)), 4),
+            "max_rel_diff_vs_alone": max(float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0]))
+                                         for a, b in zip(res, seq_res)),
+            "note": "reduced form of bench.py --serving: images 128^2-512^2, M 16K-256K, xi = 1e-4 or 100 iterations"}
 
 
 def run_serving(args):
