@@ -74,3 +74,29 @@ def test_gram_forms_agree_at_full_size():
     assert rel(g1, g0) < 1e-5
     gb = host(op.gram(to_dev(b, "fp32"), mode=1))
     assert abs(np.sum(b * g1) - np.sum(a * gb)) < 1e-5 * abs(np.sum(a * g1))
+
+
+@pytest.mark.parametrize("n,M,seed", [(64, 4096, 1), (128, 20000, 5)])
+def test_gram_convolution_matches_cufft(n, M, seed):
+    """Cross-check of the library's FFT passes against cuFFT (torch.fft on the
+    GPU): the composite operator of Section 3 rebuilt from the oracle's PSF
+    k = Re Phi_2n^H(1) on the 2n x 2n image, embedded circulantly on the
+    K = 2n grid (offset d at index d mod K), its spectrum's real part (the
+    even part of k), and the image placed at pixel index p mod K with p the
+    centred pixel coordinate; out = Re F^-1(khat F(x)) cropped back."""
+    uv = synth.uv_coverage(M, n, seed)
+    x = synth.random_image(n, seed)
+    K = 2 * n
+    psf = NUFFT(uv, 2 * n).phi_adj_real(np.ones(M))  # offsets d in [-n, n) at index d + n
+    emb = np.roll(psf, (-n, -n), axis=(0, 1))  # index d mod K
+    dev = torch.device("cuda")
+    khat = torch.fft.fft2(torch.as_tensor(emb, dtype=torch.complex128, device=dev)).real
+    q = (np.arange(n) - n // 2) % K
+    grid = torch.zeros((K, K), dtype=torch.complex128, device=dev)
+    grid[np.ix_(q, q)] = torch.as_tensor(x, dtype=torch.complex128, device=dev)
+    conv = torch.fft.ifft2(khat * torch.fft.fft2(grid)).real[np.ix_(q, q)]
+    ref = conv.cpu().numpy()
+    for prec, tol in (("fp32", 1e-5), ("fp64", 1e-10)):
+        op = make_op(uv, n, prec)
+        assert rel(host(op.gram(to_dev(x, prec), mode=1)), ref) < tol
+        op.close()

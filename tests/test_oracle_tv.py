@@ -8,7 +8,6 @@ import numpy as np
 import pytest
 from scipy.optimize import lsq_linear
 
-from oracle import sdmm as S
 from oracle import tv as TV
 from tests._tiny import tiny_problem
 
