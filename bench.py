@@ -272,6 +272,12 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     pair_ms = e0.elapsed_time(e1) / reps
     vis_per_s = M / (pair_ms / 1e3)
+    # bytes of one Phi + Phi^H pair: the staged count (every pass's reads and
+    # writes, FP32: Phi 196N + 16M, Phi^H 204N + 16M) and the compulsory one
+    # (image in and out, uv positions and visibilities once: 2 (4N + 16M))
+    N = n * n
+    pair_bytes = {"staged": float(400 * N + 32 * M), "compulsory": float(8 * N + 32 * M)}
+    pair_gbs = {k: round(v / (pair_ms / 1e3) / 1e9, 1) for k, v in pair_bytes.items()}
 
     # end to end through the public API from pinned host buffers
     from paper_1406_0359_gb300.binding import Operator as Op2
@@ -348,6 +354,8 @@ def run_ours(args, ws, rank, local):
                    "global_batch": ws, "parallelism": f"replicas x{ws}",
                    "l2": "per-iteration working set ~0.4 GB > 129 MB L2 (no flush needed)"},
         "phi_phiH_vis_per_s": round(vis_per_s, 1),
+        "phi_phiH": {"ms": round(pair_ms, 4), "bytes": pair_bytes, "achieved_gbs": pair_gbs,
+                     "frac_of_hbm_peak": {k: round(v / hbm, 4) for k, v in pair_gbs.items()}},
         "plain_fp64_gpu_iters_per_s": None if plain is None else round(plain, 3),
         "precision_fp32_vs_fp64": precision,
         "autotuned": {"tile": tile, "chunk": chunk, "phi_phiH_ms": round(tune_ms, 4)},
