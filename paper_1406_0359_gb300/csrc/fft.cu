@@ -672,8 +672,11 @@ PD int halo_images(int q, int K, int pl, int (&at)[2]) {
 // its conjugate mirror, G(q, K - c) = conj G(-q, c) (a real image).  Column 0
 // carries X(., 0) + i X(., K/2): its transform P gives grid column 0 as
 // (P(q) + conj P(-q)) / 2 and column K/2 as -i (P(q) - conj P(-q)) / 2.
+// One CTA per SM, spill-free (measured 22.3 against 24.6 us at K = 2048 for
+// two spilling CTAs per SM; the adjoint pass below measured slower that way,
+// 39.4 against 36.4 us, and keeps two).
 template <typename T, int LOGN, typename Src>
-__global__ void __launch_bounds__(ColThreads<T, LOGN>::value, ColThreads<T, LOGN>::value <= 512 ? 2 : 1)
+__global__ void __launch_bounds__(ColThreads<T, LOGN>::value, 1)
     k_col_fwd_h(Src src) {
   typedef typename cplx_t<T>::type C;
   decltype(auto) a = src.get();
