@@ -155,13 +155,15 @@ def algorithmic_bytes(kind: str, n: int, M: int, rsize: int = 4, levels: int = 4
         "col_inv": 4 * N * c + N * c,             # accumulator in, half-spectrum rows out
         "row_inv": N * c + 2 * N * rsize,         # half-spectrum rows in, image in/out (epilogue)
         # convolution form (real image, half spectra n x n complex), averaged
-        # over the cg + 1 launches of one CG: the first two forward passes
-        # read one image (x_hat, then p), the other cg - 1 apply the CG update
-        # (x, r, p, Ap in; x, r, p out); the first inverse pass forms r and p
-        # (b, x_hat in; r, p out), the other cg form Ap (p, r in; Ap out)
-        "row_fwd_h": (2 * (N * rsize + N * c) + (cg - 1) * (7 * N * rsize + N * c)) / (cg + 1),
+        # over the cg + 1 launches per SDMM iteration: the CG's first forward
+        # pass forms r = p = b - A x_hat (b, A x_hat in; r, p out), the other
+        # cg - 1 apply the CG update (x, r, p, Ap in; x, r, p out), and the
+        # pass of A x_hat for the next CG start reads x_hat; the cg inverse
+        # passes of the CG form Ap (p, r in; Ap out), the one of A x_hat
+        # reads x_hat and writes A x_hat
+        "row_fwd_h": ((4 * N * rsize + N * c) + (cg - 1) * (7 * N * rsize + N * c) + (N * rsize + N * c)) / (cg + 1),
         "col_conv": N * c + 2 * N * rsize + N * c,  # half-spectrum rows in, PSF half spectrum, rows out
-        "row_inv_h": ((N * c + 4 * N * rsize) + cg * (N * c + 3 * N * rsize)) / (cg + 1),
+        "row_inv_h": (cg * (N * c + 3 * N * rsize) + (N * c + 2 * N * rsize)) / (cg + 1),
     }
     return float(table.get(kind, 0))
 
@@ -622,15 +624,20 @@ def batch_study(count, iters, seed=4, server_arm=False, plain_arm=True):
                         [_snr_db(r["x"], x) for r, x in zip(reqs, xb)]) - np.array(snr_p)))), 6)})
         for o in ops64:
             o.close()
-    if server_arm:  # the request server with every instance admitted at once (one stream per solve)
-        srv = Server(int(150e9), count)
-        for n, (tile, chunk, _) in tuned.items():
-            srv.set_options(n, tile, chunk)
-        ids = [srv.submit(r["uv"], r["y"], r["n"], 3, r["eps"], nu=nu, gamma=g, **kw)
-               for r, nu, g in zip(reqs, nus, gammas)]
-        wall, _ = _drain(srv, ids)
-        srv.close()
-        out["server_all_admitted_solves_per_s"] = round(count / wall, 3)
+    if server_arm:  # the request server with every instance admitted at once
+        for batching, key in ((False, "server_all_admitted_solves_per_s"),
+                              (True, "server_all_admitted_iteration_batched_solves_per_s")):
+            srv = Server(int(150e9), count)
+            srv.set_batching(batching)
+            for n, (tile, chunk, _) in tuned.items():
+                srv.set_options(n, tile, chunk)
+            ids = [srv.submit(r["uv"], r["y"], r["n"], 3, r["eps"], nu=nu, gamma=g, **kw)
+                   for r, nu, g in zip(reqs, nus, gammas)]
+            wall, _ = _drain(srv, ids)
+            if batching:
+                out["server_batched_iteration_share"] = round(srv.counts()[0] / max(1, sum(srv.counts())), 4)
+            srv.close()
+            out[key] = round(count / wall, 3)
     return out
 
 
@@ -680,9 +687,16 @@ def serving_summary(count=12, seed=7, rate_mult=2.0):
     ids = [None] * count
     wall, res = _drain(srv, ids, list(arr), reqs, params)
     srv.close()
+    srv = Server(int(150e9), 16)
+    srv.set_batching(True)
+    wall_b, _ = _drain(srv, [None] * count, list(arr), reqs, params)
+    cnt = srv.counts()
+    srv.close()
     lat = np.array([r[2] for r in res])
     return {"requests": count, "one_at_a_time_solves_per_s": round(count / seq_wall, 3),
             "offered_rps": round(lam, 3), "solves_per_s": round(count / wall, 3),
+            "iteration_batched_solves_per_s": round(count / wall_b, 3),
+            "iteration_batched_share": round(cnt[0] / max(1, sum(cnt)), 4),
             "p50_s": round(float(np.percentile(lat, 50)), 4), "p99_s": round(float(np.percentile(lat, 99)), 4),
             "max_rel_diff_vs_alone": max(float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0]))
                                          for a, b in zip(res, seq_res)),

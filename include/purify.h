@@ -394,7 +394,14 @@ const char* purify_kernel_name(int kind);
  * that the solves' kernels overlap; a solve whose iteration has completed
  * gets its halting test and its next iteration in the next pass, while one
  * still running is left alone (no lock-step: a large image never holds back
- * a small one).  A finished solve frees its slot and memory at once.  The
+ * a small one).  A finished solve frees its slot and memory at once.
+ * Iteration-level batching (off by default, purify_server_set_batching): admitted solves that share
+ * image side, precision, CG steps and dictionary, use the convolution form of
+ * the CG operator (64 <= n <= 1024) and one visibility block advance together
+ * -- one SDMM iteration of all of them is one batched graph, each pass one
+ * launch over the group as in purify_batch_solve, cached while the group's
+ * membership is unchanged; a ready solve whose group is in flight joins it at
+ * the next iteration.  The
  * device memory of admitted solves comes from a stream-ordered memory pool
  * of the server that keeps up to `budget_bytes` mapped, so admitting and
  * releasing solves never synchronises the device; host inputs are staged
@@ -415,6 +422,10 @@ int purify_server_submit(purify_server* srv, const double* uv_host, const void* 
                          int dwt_levels, int precision, const purify_params* params, int* request_id);
 /* One scheduling pass; reports how many solves are active and queued after it. */
 int purify_server_step(purify_server* srv, int* n_active, int* n_queued);
+/* Iteration-level batching on (enable != 0) or off (0, the default). */
+int purify_server_set_batching(purify_server* srv, int enable);
+/* Solve-iterations launched so far in batched groups and on their own. */
+int purify_server_counts(purify_server* srv, int64_t* batched, int64_t* solo);
 /* Cancel a queued or running request: a queued one leaves the queue; a
  * running one is stopped between SDMM iterations (the call waits for the
  * iteration in flight on that solve's stream only) and its memory and slot

@@ -62,7 +62,8 @@ EXPORTS = ["purify_op_create", "purify_op_destroy", "purify_op_info", "purify_ph
            "purify_server_set_options", "purify_op_set_dictionary", "purify_op_dictionary",
            "purify_solve_begin", "purify_solve_step", "purify_solve_end", "purify_solve_state_bytes",
            "purify_solve_save", "purify_solve_load", "purify_set_wait_limit", "purify_wait_selftest",
-           "purify_server_cancel", "purify_op_set_prior", "purify_batch_solve"]
+           "purify_server_cancel", "purify_op_set_prior", "purify_batch_solve", "purify_server_set_batching",
+           "purify_server_counts"]
 KERNEL_KINDS = ["row_fwd", "col_fwd", "degrid", "grid", "gram", "col_inv", "row_inv", "sara_analysis",
                 "sara_synthesis", "vector", "memset", "col_conv", "row_fwd_h", "row_inv_h", "tv"]
 
@@ -121,6 +122,8 @@ def lib() -> ctypes.CDLL:
     L.purify_set_wait_limit.argtypes = [ctypes.c_uint32]
     L.purify_wait_selftest.argtypes = [ci, vp]
     L.purify_server_cancel.argtypes = [vp, ci]
+    L.purify_server_set_batching.argtypes = [vp, ci]
+    L.purify_server_counts.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.purify_op_set_prior.argtypes = [vp, ci, ci]
     L.purify_batch_solve.argtypes = [ci, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(purify_params),
                                      ctypes.POINTER(vp), ctypes.POINTER(purify_stats), vp]
@@ -527,6 +530,15 @@ class Server:
     def set_options(self, n: int, tile: int, chunk: int) -> None:
         o = purify_op_options(tile, chunk)
         _check(lib().purify_server_set_options(self.h, n, ctypes.byref(o)), "purify_server_set_options")
+
+    def set_batching(self, enable: bool) -> None:
+        _check(lib().purify_server_set_batching(self.h, int(enable)), "purify_server_set_batching")
+
+    def counts(self) -> tuple[int, int]:
+        """(solve-iterations launched in batched groups, on their own)."""
+        b, s = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().purify_server_counts(self.h, ctypes.byref(b), ctypes.byref(s)), "purify_server_counts")
+        return b.value, s.value
 
     def cancel(self, rid: int) -> None:
         _check(lib().purify_server_cancel(self.h, rid), "purify_server_cancel")

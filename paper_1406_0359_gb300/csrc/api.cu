@@ -187,7 +187,10 @@ template <typename T> class OpImpl : public purify_op {
   // composite operator by convolution (Section 3: precompute Phi^H Phi)
   double* uv_keep = nullptr;  // device copy of uv, for the PSF set-up
   T* khat = nullptr;          // real PSF half spectrum, launch_col_conv_h layout
+  T* axh = nullptr;           // (nu^2 Re Phi^H Phi + 2I) x_hat, for the next CG start
+  C* gridA2 = nullptr;        // half-spectrum rows of that product (beside the ball block's gridA)
   bool toep = false;          // current normal-operator mode
+  bool own_pending = false;   // work may be in flight on the own stream (begin, a solo iteration)
   // visibility blocks (Eq. 4-5)
   int nblocks = 1;
   std::vector<int64_t> block_sizes;
@@ -660,36 +663,52 @@ template <typename T> class OpImpl : public purify_op {
       if (e != cudaSuccess) return map_err(e, __LINE__);
       if (rc) return rc;
     }
+    if ((rc = alloc(&axh, N())) || (rc = alloc(&gridA2, size_t(g.n) * (g.K / 2)))) return rc;
     khat = khat_l;
     return PURIFY_OK;
   }
 
   // Front half of Re(Phi^H Phi) x: up to the half-spectrum rows in gridA, by the
   // NUFFT (G^H G per application) or by the precomputed convolution.
-  void normal_front(const RowPro<T>& pro, cudaStream_t s) {
+  // (The convolution form may run in the half-spectrum buffer `B` instead,
+  // beside a pass of Phi or Phi^H in gridA.)
+  void normal_front(const RowPro<T>& pro, cudaStream_t s, C* B = nullptr) {
+    if (!B) B = gridA;
     if (rec) {  // the batched solver takes the convolution form only
-      record(R_RF, s).rf = RowFwdArgs<T>{g, pro, nullptr, gridA, tw, row_pass_nseq(g)};
-      record(R_CC, s).cc = ColConvArgs<T>{g, gridA, khat, khat + size_t(g.K / 2) * g.K, tw, col_pass_width<T>()};
+      record(R_RF, s).rf = RowFwdArgs<T>{g, pro, nullptr, B, tw, row_pass_nseq(g)};
+      record(R_CC, s).cc = ColConvArgs<T>{g, B, khat, khat + size_t(g.K / 2) * g.K, tw, col_pass_width<T>()};
       return;
     }
     if (toep) {
-      PROF(KK_ROW_FWD_H, s, launch_row_fwd_h<T>(g, pro, nullptr, gridA, tw, s));
-      PROF(KK_COL_CONV, s, launch_col_conv_h<T>(g, gridA, khat, tw, s));
+      PROF(KK_ROW_FWD_H, s, launch_row_fwd_h<T>(g, pro, nullptr, B, tw, s));
+      PROF(KK_COL_CONV, s, launch_col_conv_h<T>(g, B, khat, tw, s));
     } else {
       gram_front(pro, s);
     }
   }
-  int normal_back(const RowEp<T>& ep_in, cudaStream_t s) {
+  int normal_back(const RowEp<T>& ep_in, cudaStream_t s, C* B = nullptr) {
     RowEp<T> ep = ep_in;
     if (!ep.err) ep.err = err;
+    if (!B) B = gridA;
     if (rec) {
-      record(R_RI, s).ri = RowInvArgs<T>{g, gridA, nullptr, ep, tw, row_pass_nseq(g), row_inv_blocks(g)};
+      record(R_RI, s).ri = RowInvArgs<T>{g, B, nullptr, ep, tw, row_pass_nseq(g), row_inv_blocks(g)};
       return row_inv_blocks(g);
     }
     int np = 0;
-    if (toep) PROF(KK_ROW_INV_H, s, np = launch_row_inv_h<T>(g, gridA, nullptr, ep, tw, s));
+    if (toep) PROF(KK_ROW_INV_H, s, np = launch_row_inv_h<T>(g, B, nullptr, ep, tw, s));
     else PROF(KK_ROW_INV, s, np = launch_row_inv_h<T>(g, gridA, deapod, ep, tw, s));
     return np;
+  }
+
+  // out = (nu2 Re Phi^H Phi + 2I) x
+  void normal_apply_qx(const T* x, T* out, double nu2, cudaStream_t s, C* B = nullptr) {
+    normal_front(plain(x), s, B);
+    RowEp<T> ep{};
+    ep.mode = EP_QX;
+    ep.out = out;
+    ep.p = x;
+    ep.nu2 = nu2;
+    normal_back(ep, s, B);
   }
 
   int gram(const void* x, void* out, int mode, cudaStream_t s) override {
@@ -886,9 +905,12 @@ template <typename T> class OpImpl : public purify_op {
     // last block of the inverse row pass sets <r,r> (initial residual), or
     // alpha and beta (CG step, from five inner products of the step's vectors);
     // the forward row pass of the next step applies x += alpha p,
-    // r -= alpha Ap, p = r + beta p on the fly.
-    normal_front(plain(xh), s);
-    {
+    // r -= alpha Ap, p = r + beta p on the fly.  With the convolution form the
+    // initial residual b - A x_hat needs no operator pass here: A x_hat was
+    // formed at the end of the previous iteration beside the ball block (or by
+    // the round set-up), and the first forward row pass takes r = p = b - A x_hat.
+    if (!toep) {
+      normal_front(plain(xh), s);
       RowEp<T> ep{};
       ep.mode = EP_CG_R0;
       ep.out = r;
@@ -904,7 +926,13 @@ template <typename T> class OpImpl : public purify_op {
     }
     for (int it = 0; it < cg_iters; ++it) {
       RowPro<T> pro = plain(p);
-      if (it > 0) {
+      if (it == 0 && toep) {
+        pro.mode = PRO_CG_START;
+        pro.x = xs;
+        pro.ap = axh;
+        pro.p = p;
+        pro.r = r;
+      } else if (it > 0) {
         pro.mode = PRO_CG_STEP;
         pro.p = p;
         pro.r = r;
@@ -1015,6 +1043,9 @@ template <typename T> class OpImpl : public purify_op {
       fin(partials, npo, FIN_OBJ, 0.0, s);
       PROF(KK_SARA_SYN, s, sara_synthesis_pos<T>(sara, xh, z2, xs, s));
     }
+    // A x_hat for the next iteration's CG start, on this branch (it has slack
+    // beside the ball block), in its own half-spectrum buffer
+    if (toep) normal_apply_qx(xh, axh, nu2, s, gridA2);
     // join: xs += nu Re Phi^H (2 r_3 - v_3)
     if (!rec && b3 != s) cudaStreamWaitEvent(s, ev_join, 0);
     RowEp<T> ep{};
@@ -1099,6 +1130,7 @@ template <typename T> class OpImpl : public purify_op {
     launch_fill<T>(w, D(), T(1), s);
     CK(cudaMemsetAsync(xh, 0, n2 * sizeof(T), s));
     run.active = true;
+    own_pending = true;
     return check(s, false);
   }
 
@@ -1118,6 +1150,32 @@ template <typename T> class OpImpl : public purify_op {
     ce = cudaGraphInstantiate(&run.gexec, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) return map_err(ce, __LINE__);
+    return PURIFY_OK;
+  }
+
+  // ---- iteration-level batching in the request server: the solves of one
+  // key (image side, precision, CG steps, dictionary) advance together
+  // through a batched graph; these hooks do each solve's part around it.
+  uint64_t batch_key() const override {
+    if (!run.active || !toep || prior != 0 || nblocks != 1 || g.n < 64 || g.n > 1024 || prof) return 0;
+    return uint64_t(g.n) | (uint64_t(sizeof(T) == 4 ? 1 : 2) << 12) | (uint64_t(run.P.cg_iters) << 16) |
+           (uint64_t(dictionary(nullptr)) << 32);
+  }
+  int prepare_iteration(cudaStream_t s) override {
+    if (!run.active) return PURIFY_ERR_INVALID;
+    if (own_pending) {  // work begin() or a solo iteration left on the own stream comes first
+      CK(cudaEventRecord(ev_in, own));
+      CK(cudaStreamWaitEvent(s, ev_in, 0));
+      own_pending = false;
+    }
+    return run.round_ready ? PURIFY_OK : start_round(s);
+  }
+  int finish_iteration(cudaStream_t s) override {
+    if (!run.active) return PURIFY_ERR_INVALID;
+    if (run.P.xi > 0) {
+      CK(cudaMemcpyAsync(h_sc, sc, kNumScalars * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaEventRecord(run.ev_sc, s));
+    }
     return PURIFY_OK;
   }
 
@@ -1224,6 +1282,9 @@ template <typename T> class OpImpl : public purify_op {
       int rc = capture_iteration(own);
       if (rc) return rc;
     }
+    // the CG start's A x_hat is not state: it is formed again from x_hat by
+    // the same passes as in the iteration
+    if (toep && run.round_ready) normal_apply_qx(xh, axh, run.nu * run.nu, own);
     return check(own, true);
   }
 
@@ -1253,16 +1314,12 @@ template <typename T> class OpImpl : public purify_op {
     cudaMemsetAsync(z3, 0, M * sizeof(C), s);
     if (run.round > 0 && P.warm_start) {
       // steps 1-3 with x_hat^(0) = previous solution: sum_i x_i = (Phi^H Phi + 2I) x_hat^(0)
-      normal_front(plain(xh), s);
-      RowEp<T> ep{};
-      ep.mode = EP_QX;
-      ep.out = xs;
-      ep.p = xh;
-      ep.nu2 = run.nu * run.nu;
-      normal_back(ep, s);
+      normal_apply_qx(xh, xs, run.nu * run.nu, s);
+      if (toep) cudaMemcpyAsync(axh, xs, n2 * sizeof(T), cudaMemcpyDeviceToDevice, s);  // the CG start's A x_hat
     } else {
       cudaMemsetAsync(xh, 0, n2 * sizeof(T), s);
       cudaMemsetAsync(xs, 0, n2 * sizeof(T), s);
+      if (toep) cudaMemsetAsync(axh, 0, n2 * sizeof(T), s);
     }
     run.t = 0;
     run.prev = -1.0;
@@ -1276,6 +1333,7 @@ template <typename T> class OpImpl : public purify_op {
     if (!run.active) return PURIFY_ERR_INVALID;
     cudaStream_t s = own;
     int rc;
+    own_pending = true;
     if (!run.round_ready && (rc = start_round(s))) return rc;
     if (run.gexec) {
       CK(cudaGraphLaunch(run.gexec, s));
@@ -1414,6 +1472,7 @@ template <typename T> class BatchImpl {
   };
   std::vector<OpImpl<T>*> ops;
   std::vector<Group> groups;
+  cudaMemPool_t pool = nullptr;  // tables from this pool (the request server's) when set
   cudaStream_t bs = nullptr;
   cudaEvent_t ev0 = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -1422,7 +1481,10 @@ template <typename T> class BatchImpl {
     if (bs) cudaStreamSynchronize(bs);
     if (gexec) cudaGraphExecDestroy(gexec);
     for (Group& gr : groups) {
-      if (gr.dev) cudaFree(gr.dev);
+      if (gr.dev) {
+        if (pool) cudaFreeAsync(gr.dev, bs);
+        else cudaFree(gr.dev);
+      }
       sara_batch_destroy(gr.sara);
       const cudaEvent_t evs[3] = {gr.fork, gr.join, gr.done};
       for (cudaEvent_t e : evs)
@@ -1431,6 +1493,7 @@ template <typename T> class BatchImpl {
       if (gr.aux) cudaStreamDestroy(gr.aux);
     }
     if (ev0) cudaEventDestroy(ev0);
+    if (bs) cudaStreamSynchronize(bs);
     if (bs) cudaStreamDestroy(bs);
   }
 
@@ -1498,11 +1561,17 @@ template <typename T> class BatchImpl {
             default: break;
           }
         }
-      CK(cudaMalloc(&gr.dev, host.size()));
-      CK(cudaMemcpy(gr.dev, host.data(), host.size(), cudaMemcpyHostToDevice));
+      if (pool) {
+        CK(cudaMallocFromPoolAsync(&gr.dev, host.size(), pool, bs));
+        CK(cudaMemcpyAsync(gr.dev, host.data(), host.size(), cudaMemcpyHostToDevice, bs));
+        CK(cudaStreamSynchronize(bs));
+      } else {
+        CK(cudaMalloc(&gr.dev, host.size()));
+        CK(cudaMemcpy(gr.dev, host.data(), host.size(), cudaMemcpyHostToDevice));
+      }
       if (!sara_in.empty()) {
         int np = 0;
-        const int rc = sara_batch_create<T>(sara_in, &gr.sara, &np);
+        const int rc = sara_batch_create<T>(sara_in, &gr.sara, &np, pool, bs);
         if (rc) return rc;
       }
       CK(cudaStreamCreateWithFlags(&gr.main, cudaStreamNonBlocking));
@@ -1594,6 +1663,27 @@ template <typename T> class BatchImpl {
   }
 };
 
+template <typename T> int batch_graph_build(purify_op* const* ops, int count, cudaMemPool_t pool, void** out) {
+  BatchImpl<T>* b = new (std::nothrow) BatchImpl<T>();
+  if (!b) return PURIFY_ERR_NOMEM;
+  b->pool = pool;
+  for (int i = 0; i < count; ++i) {
+    OpImpl<T>* o = dynamic_cast<OpImpl<T>*>(ops[i]);
+    if (!o) {
+      delete b;
+      return PURIFY_ERR_INVALID;
+    }
+    b->ops.push_back(o);
+  }
+  const int rc = b->build();
+  if (rc) {
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return PURIFY_OK;
+}
+
 // purify_batch_solve: begin every instance (nu, gamma, round 0 on its own
 // stream), record and capture the batched iteration, then run the rounds in
 // lock step -- the round set-ups per instance, the iterations as graph
@@ -1670,6 +1760,43 @@ int batch_solve(int count, purify_op* const* ops_in, const void* const* y, const
 }
 
 }  // namespace
+
+// The request server's batched iteration over solves of one key.
+struct BatchGraph {
+  int prec = 0;
+  void* impl = nullptr;
+};
+
+int batch_graph_create(purify_op* const* ops, int count, cudaMemPool_t pool, BatchGraph** out) {
+  if (!ops || count < 1 || !out) return PURIFY_ERR_INVALID;
+  int prec = 0;
+  ops[0]->info(nullptr, nullptr, nullptr, nullptr, nullptr, &prec, nullptr);
+  BatchGraph* g = new (std::nothrow) BatchGraph();
+  if (!g) return PURIFY_ERR_NOMEM;
+  g->prec = prec;
+  const int rc = prec == PURIFY_FP32 ? batch_graph_build<float>(ops, count, pool, &g->impl)
+                                     : batch_graph_build<double>(ops, count, pool, &g->impl);
+  if (rc) {
+    delete g;
+    return rc;
+  }
+  *out = g;
+  return PURIFY_OK;
+}
+
+int batch_graph_launch(BatchGraph* g, cudaStream_t s) {
+  cudaGraphExec_t ge = g->prec == PURIFY_FP32 ? static_cast<BatchImpl<float>*>(g->impl)->gexec
+                                              : static_cast<BatchImpl<double>*>(g->impl)->gexec;
+  const cudaError_t e = cudaGraphLaunch(ge, s);
+  return e == cudaSuccess ? PURIFY_OK : map_err(e, __LINE__);
+}
+
+void batch_graph_destroy(BatchGraph* g) {
+  if (!g) return;
+  if (g->prec == PURIFY_FP32) delete static_cast<BatchImpl<float>*>(g->impl);
+  else delete static_cast<BatchImpl<double>*>(g->impl);
+  delete g;
+}
 
 int create_pooled_op(const double* uv, int64_t M, int n, int levels, int precision, const purify_op_options* opt,
                      cudaMemPool_t pool, cudaStream_t s, purify_op** out) {

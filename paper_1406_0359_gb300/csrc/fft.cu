@@ -296,6 +296,26 @@ PD void row_prologue(const RowPro<T>& pro, const size_t (&row0)[NR], int t, T (&
         val[r][j] = fma(beta, pv, rn);
         pro.p[idx] = val[r][j];
       }
+  } else if (pro.mode == PRO_CG_START) {
+    // r = b - A x_hat, p = r (b in pro.x, A x_hat in pro.ap)
+    T bv[NR][E / 2], av[NR][E / 2];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int j = 0; j < E / 2; ++j) {
+        const size_t idx = row0[r] + i2[j];
+        bv[r][j] = pro.x[idx];
+        av[r][j] = pro.ap[idx];
+      }
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int j = 0; j < E / 2; ++j) {
+        const size_t idx = row0[r] + i2[j];
+        val[r][j] = bv[r][j] - av[r][j];
+        pro.r[idx] = val[r][j];
+        pro.p[idx] = val[r][j];
+      }
   } else {
     const T scl = pro.mode == PRO_SCALE ? T(pro.scalars[pro.idx]) : T(1);
 #pragma unroll

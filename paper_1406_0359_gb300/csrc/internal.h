@@ -84,7 +84,8 @@ template <typename T> struct RowEp {
 enum RowProMode : int {
   PRO_PLAIN = 0,    // src = x
   PRO_CG_STEP = 1,  // x += alpha p, r -= alpha Ap, p = r + beta p (scalars S_ALPHA, S_BETA); src = p
-  PRO_SCALE = 2     // src = x * scalars[scale_idx]   (power iteration normalisation)
+  PRO_SCALE = 2,    // src = x * scalars[scale_idx]   (power iteration normalisation)
+  PRO_CG_START = 3  // r = x - ap (b - A x_hat, A x_hat kept from the previous iteration), p = r; src = p
 };
 template <typename T> struct RowPro {
   int mode;
@@ -369,7 +370,10 @@ template <typename T> struct SaraBatchInst {
 template <typename T> struct SaraBatch;
 // Builds the device argument tables; *np receives the objective partials
 // each instance writes.
-template <typename T> int sara_batch_create(const std::vector<SaraBatchInst<T>>& in, SaraBatch<T>** out, int* np);
+// pool: take the tables from this stream-ordered pool on `s` (else cudaMalloc).
+template <typename T>
+int sara_batch_create(const std::vector<SaraBatchInst<T>>& in, SaraBatch<T>** out, int* np,
+                      cudaMemPool_t pool = nullptr, cudaStream_t s = nullptr);
 template <typename T> void sara_batch_launch(const SaraBatch<T>* b, cudaStream_t s);
 template <typename T> void sara_batch_destroy(SaraBatch<T>* b);
 // Objective partials the fused analysis of P writes.

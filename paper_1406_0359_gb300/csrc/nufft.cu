@@ -513,16 +513,19 @@ __global__ void __launch_bounds__(kThreads) k_degrid_w(Src src, KbPoly<T> kb, co
 // side by side so that one 16-byte shared access (two for FP64) moves both;
 // eight lanes updating eight consecutive cells of a row then touch 128
 // contiguous bytes, free of bank conflicts for any row pitch.
-template <typename T> struct __align__(4 * sizeof(T)) KCell { T sx, sy, cx, cy; };
-template <typename T> PD void kahan_cell_add(KCell<T>* cell, T vx, T vy) {
-  KCell<T> k = *cell;
-  const T yx = vx - k.cx, yy = vy - k.cy;
-  const T tx = k.sx + yx, ty = k.sy + yy;
-  k.cx = (tx - k.sx) - yx;
-  k.cy = (ty - k.sy) - yy;
-  k.sx = tx;
-  k.sy = ty;
+// A gridding accumulator cell (one complex value).  Rows of the per-warp
+// patch are padded so that the four quarter-warps of an update (four patch
+// rows, 8 consecutive cells each) fall in different banks where the row
+// length alone would put them on the same ones.
+template <typename T> struct __align__(2 * sizeof(T)) GCell { T x, y; };
+template <typename T> PD void cell_add(GCell<T>* cell, T vx, T vy) {
+  GCell<T> k = *cell;
+  k.x += vx;
+  k.y += vy;
   *cell = k;
+}
+template <typename T> __host__ __device__ constexpr int grid_row_stride(int pw) {
+  return (sizeof(T) == 4 && pw % 16 == 0) ? pw + 4 : pw;
 }
 
 template <typename T, typename Src>
@@ -543,10 +546,11 @@ __global__ void __launch_bounds__(kThreads) k_grid_w(Src src, KbPoly<T> kb) {
   const WorkItem it = items[item];
   const int tu = it.tile / g.ntile1d, tv = it.tile - tu * g.ntile1d;
   const int PW = g.TB + kJ;
-  // per warp: a PW x PW patch of Kahan cells, then the staging rows
-  KCell<T>* wacc = reinterpret_cast<KCell<T>*>(sm_raw) + warp * PW * PW;
-  T* wst = reinterpret_cast<T*>(reinterpret_cast<KCell<T>*>(sm_raw) + kWItems * PW * PW) + warp * 32 * kStage;
-  for (int e = lane; e < PW * PW; e += 32) wacc[e] = KCell<T>{T(0), T(0), T(0), T(0)};
+  // per warp: a PW x PW patch of cells (row stride PS), then the staging rows
+  const int PS = grid_row_stride<T>(PW);
+  GCell<T>* wacc = reinterpret_cast<GCell<T>*>(sm_raw) + warp * PW * PS;
+  T* wst = reinterpret_cast<T*>(reinterpret_cast<GCell<T>*>(sm_raw) + kWItems * PW * PS) + warp * 32 * kStage;
+  for (int e = lane; e < PW * PS; e += 32) wacc[e] = GCell<T>{T(0), T(0)};
   __syncwarp();
   T scale = 0;
   if (gpro.mode == GP_BALL) scale = T(gpro.block_scale ? gpro.block_scale[it.pad] : gpro.scalars[gpro.scale_idx]);
@@ -603,9 +607,9 @@ __global__ void __launch_bounds__(kThreads) k_grid_w(Src src, KbPoly<T> kb) {
       }
       if (cell != scell) {  // warp-uniform
         if (scell >= 0) {
-          const int o = ((scell >> 8) + ta) * PW + (scell & 255) + tc;
-          kahan_cell_add(wacc + o, s0.x, s0.y);
-          kahan_cell_add(wacc + o + 4 * PW, s1.x, s1.y);
+          const int o = ((scell >> 8) + ta) * PS + (scell & 255) + tc;
+          cell_add(wacc + o, s0.x, s0.y);
+          cell_add(wacc + o + 4 * PS, s1.x, s1.y);
           s0 = s1 = cz<C>();
         }
         scell = cell;
@@ -622,15 +626,15 @@ __global__ void __launch_bounds__(kThreads) k_grid_w(Src src, KbPoly<T> kb) {
     __syncwarp();
   }
   if (scell >= 0) {
-    const int o = ((scell >> 8) + ta) * PW + (scell & 255) + tc;
-    kahan_cell_add(wacc + o, s0.x, s0.y);
-    kahan_cell_add(wacc + o + 4 * PW, s1.x, s1.y);
+    const int o = ((scell >> 8) + ta) * PS + (scell & 255) + tc;
+    cell_add(wacc + o, s0.x, s0.y);
+    cell_add(wacc + o + 4 * PS, s1.x, s1.y);
   }
   __syncwarp();
   for (int e = lane; e < PW * PW; e += 32) {
     const int r = e / PW, c = e - r * PW;
-    const KCell<T> kc = wacc[e];
-    const C v = cmk<C>(kc.sx - kc.cx, kc.sy - kc.cy);
+    const GCell<T> kc = wacc[r * PS + c];
+    const C v = cmk<C>(kc.x, kc.y);
     if (v.x != 0 || v.y != 0) atomic_add_global(Q + size_t(tu * g.TB + r) * g.KP + (tv * g.TB + c), v);
   }
 }
@@ -1023,7 +1027,7 @@ void launch_grid(const Geometry& g, const WorkItem* items, int n_items, const Po
                  cudaStream_t s) {
   if (n_items <= 0) return;
   const size_t PW = size_t(g.TB + kJ);
-  const size_t sm = kWItems * (PW * PW * sizeof(KCell<T>) + 32 * kStage * sizeof(T));
+  const size_t sm = kWItems * (PW * size_t(grid_row_stride<T>(int(PW))) * sizeof(GCell<T>) + 32 * kStage * sizeof(T));
   ArgVal<GridArgs<T>> src{GridArgs<T>{g, items, n_items, pos, perm, pro, Q}};
   k_grid_w<T><<<(n_items + kWItems - 1) / kWItems, kThreads, sm, s>>>(src, kb);
 }
@@ -1033,7 +1037,7 @@ void launch_grid_batch(const GridArgs<T>* tab, int count, int max_items, int max
                        cudaStream_t s) {
   if (max_items <= 0 || count <= 0) return;
   const size_t PW = size_t(max_tb + kJ);
-  const size_t sm = kWItems * (PW * PW * sizeof(KCell<T>) + 32 * kStage * sizeof(T));
+  const size_t sm = kWItems * (PW * size_t(grid_row_stride<T>(int(PW))) * sizeof(GCell<T>) + 32 * kStage * sizeof(T));
   ArgTab<GridArgs<T>> src{tab};
   k_grid_w<T><<<dim3((max_items + kWItems - 1) / kWItems, count), kThreads, sm, s>>>(src, kb);
 }

@@ -28,6 +28,14 @@ struct purify_op {
   // Up to max_iters iterations of the resumable solve, then a synchronous
   // check of the device error flag; *done = 1 once the last round finished.
   virtual int run_steps(int max_iters, int* done) = 0;
+  // Iteration-level batching (request server): a non-zero key groups solves
+  // that can advance through one batched graph; the hooks run each solve's
+  // round set-up before it and its halting read-back after it, on `s`.  The
+  // caller sees the batched iteration complete (an event on `s`) before it
+  // makes the next call on the solve.
+  virtual uint64_t batch_key() const = 0;
+  virtual int prepare_iteration(cudaStream_t s) = 0;
+  virtual int finish_iteration(cudaStream_t s) = 0;
   // Solver state between iterations (checkpoint / resume).
   virtual int64_t state_bytes() const = 0;
   virtual int save_state(void* host, int64_t bytes) = 0;
@@ -102,4 +110,10 @@ int create_pooled_op(const double* uv, int64_t M, int n, int levels, int precisi
                      cudaMemPool_t pool, cudaStream_t s, purify_op** out);
 // Record the detail returned by purify_last_error() on this thread.
 void set_last_error(const char* msg);
+// One SDMM iteration of `count` active solves of one batch key as a batched
+// graph (one launch per pass over all of them), tables from `pool`.
+struct BatchGraph;
+int batch_graph_create(purify_op* const* ops, int count, cudaMemPool_t pool, BatchGraph** out);
+int batch_graph_launch(BatchGraph* g, cudaStream_t s);
+void batch_graph_destroy(BatchGraph* g);
 }  // namespace purify

@@ -616,6 +616,8 @@ void sara_synthesis_pos(const SaraPlan<T>& P, const T* xh, T* z2, T* xs, cudaStr
 // tables, instance in blockIdx.y / blockIdx.z).
 template <typename T> struct SaraBatch {
   void* dev = nullptr;
+  cudaMemPool_t pool = nullptr;  // dev from this pool (freed in stream order) when set
+  cudaStream_t pool_stream = nullptr;
   int count = 0, nf = 0, levels_a = 0, levels_s = 0, nb0 = 0;
   bool dirac = false, all = false;
   dim3 agrid[16], sgrid[16], fgrid;
@@ -627,7 +629,8 @@ template <typename T> struct SaraBatch {
 };
 
 template <typename T>
-int sara_batch_create(const std::vector<SaraBatchInst<T>>& in, SaraBatch<T>** out, int* np) {
+int sara_batch_create(const std::vector<SaraBatchInst<T>>& in, SaraBatch<T>** out, int* np, cudaMemPool_t pool,
+                      cudaStream_t s) {
   if (in.empty()) return PURIFY_ERR_INVALID;
   SaraBatch<T>* b = new (std::nothrow) SaraBatch<T>();
   if (!b) return PURIFY_ERR_NOMEM;
@@ -676,13 +679,16 @@ int sara_batch_create(const std::vector<SaraBatchInst<T>>& in, SaraBatch<T>** ou
   const size_t foff = off;
   b->fgrid = dim3(sp[0].fgrid.x, sp[0].fgrid.y, count);
   for (int i = 0; i < count; ++i) std::memcpy(&host[off + i * sizeof(SynArgs<T>)], &sp[i].fin, sizeof(SynArgs<T>));
-  if (cudaMalloc(&b->dev, total) != cudaSuccess) {
+  b->pool = pool;
+  b->pool_stream = s;
+  if ((pool ? cudaMallocFromPoolAsync(&b->dev, total, pool, s) : cudaMalloc(&b->dev, total)) != cudaSuccess) {
     delete b;
     return PURIFY_ERR_NOMEM;
   }
-  if (cudaMemcpy(b->dev, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
-    cudaFree(b->dev);
-    delete b;
+  const cudaError_t ce = pool ? cudaMemcpyAsync(b->dev, host.data(), total, cudaMemcpyHostToDevice, s)
+                              : cudaMemcpy(b->dev, host.data(), total, cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess || (pool && cudaStreamSynchronize(s) != cudaSuccess)) {
+    sara_batch_destroy(b);
     return PURIFY_ERR_CUDA;
   }
   unsigned char* d = static_cast<unsigned char*>(b->dev);
@@ -717,12 +723,16 @@ template <typename T> int sara_prox_partials(const SaraPlan<T>& P) {
 
 template <typename T> void sara_batch_destroy(SaraBatch<T>* b) {
   if (!b) return;
-  if (b->dev) cudaFree(b->dev);
+  if (b->dev) {
+    if (b->pool) cudaFreeAsync(b->dev, b->pool_stream);
+    else cudaFree(b->dev);
+  }
   delete b;
 }
 
 #define INST(T)                                                                                 \
-  template int sara_batch_create<T>(const std::vector<SaraBatchInst<T>>&, SaraBatch<T>**, int*);  \
+  template int sara_batch_create<T>(const std::vector<SaraBatchInst<T>>&, SaraBatch<T>**, int*,   \
+                                    cudaMemPool_t, cudaStream_t);                                 \
   template void sara_batch_launch<T>(const SaraBatch<T>*, cudaStream_t);                          \
   template void sara_batch_destroy<T>(SaraBatch<T>*);                                             \
   template int sara_prox_partials<T>(const SaraPlan<T>&);                                         \

@@ -1,6 +1,7 @@
 """Continuous-batching request server: results alone vs. in the mix (images
-from 64^2 to 2048^2), budget admission, cancellation, input checks, and the
-device-memory estimate."""
+from 64^2 to 2048^2), iteration-level batching of same-size solves on and
+off, budget admission, cancellation, input checks, and the device-memory
+estimate."""
 import math
 
 import numpy as np
@@ -31,11 +32,13 @@ def problem(n, M, seed):
     return uv, y, eps
 
 
-def run_server(reqs, slots, budget=int(40e9)):
+def run_server(reqs, slots, budget=int(40e9), batching=True, counts=None, **kw):
     from paper_1406_0359_gb300.binding import Server
 
     srv = Server(budget, slots)
-    ids = [srv.submit(uv, y, n, 3, eps, t_max=15, cg_iters=8, n_reweight=1) for (n, uv, y, eps) in reqs]
+    srv.set_batching(batching)
+    kw = dict(dict(t_max=15, cg_iters=8, n_reweight=1), **kw)
+    ids = [srv.submit(uv, y, n, 3, eps, **kw) for (n, uv, y, eps) in reqs]
     max_active = 0
     for _ in range(100000):
         a, q = srv.step()
@@ -43,6 +46,8 @@ def run_server(reqs, slots, budget=int(40e9)):
         if a == 0 and q == 0:
             break
     out = [srv.result(i) for i in ids]
+    if counts is not None:
+        counts.extend(srv.counts())
     srv.close()
     return out, max_active
 
@@ -61,6 +66,57 @@ def test_results_same_alone_and_in_mix():
         assert m[1]["iterations"] == a[1]["iterations"] == 30
         assert rel(m[0], a[0]) < 1e-5
         assert m[2] >= m[3] >= 0.0
+
+
+@pytest.mark.parametrize("xi", [0.0, 1e-3])
+def test_batched_groups_equal_solo_iterations(xi):
+    """Same-size solves advance in batched groups (one launch per pass over
+    the group); each result equals the same server's result with batching
+    off, with a fixed iteration count and with the halting test (solves of
+    one group stop at different iterations and the group re-forms)."""
+    need_gpu()
+    reqs = [(n, *problem(n, M, seed)) for n, M, seed in
+            [(128, 20000, 51), (128, 9000, 52), (64, 3000, 53), (128, 40000, 54), (64, 6000, 55), (256, 60000, 56)]]
+    kw = dict(t_max=40, xi=xi) if xi else {}
+    cb, cs = [], []
+    on, _ = run_server(reqs, 8, batching=True, counts=cb, **kw)
+    off, _ = run_server(reqs, 8, batching=False, counts=cs, **kw)
+    assert cb[0] > 0 and cs[0] == 0  # groups formed only with batching on
+    assert cb[0] + cb[1] == cs[1]  # the same solve-iterations in total
+    for a, b in zip(on, off):
+        assert a is not None and b is not None
+        assert a[1]["iterations"] == b[1]["iterations"]
+        if not xi:
+            assert a[1]["iterations"] == 30
+        assert rel(a[0], b[0]) < 1e-5
+
+
+def test_cancel_member_of_a_batched_group():
+    need_gpu()
+    from paper_1406_0359_gb300.binding import PurifyError, Server
+
+    reqs = [(128, *problem(128, M, s)) for M, s in ((20000, 61), (9000, 62), (30000, 63))]
+    alone, _ = run_server([reqs[2]], 1, t_max=40, n_reweight=0)
+    srv = Server(int(40e9), 4)
+    srv.set_batching(True)
+    ids = [srv.submit(uv, y, n, 3, eps, t_max=40, cg_iters=8, n_reweight=0) for (n, uv, y, eps) in reqs]
+    for _ in range(6):  # all three admitted, a few batched iterations in
+        srv.step()
+    assert srv.counts()[0] > 0
+    srv.cancel(ids[0])  # its iteration may be in flight in the group
+    for _ in range(100000):
+        a, q = srv.step()
+        if a == 0 and q == 0:
+            break
+    with pytest.raises(PurifyError) as e:
+        srv.result(ids[0])
+    assert e.value.code == -7
+    for rid in ids[1:]:
+        x, st, _, _ = srv.result(rid)
+        assert st["iterations"] == 40 and np.all(np.isfinite(x))
+    x, st, _, _ = srv.result(ids[2])
+    assert rel(x, alone[0][0]) < 1e-5
+    srv.close()
 
 
 def test_budget_limits_admission():
