@@ -418,7 +418,11 @@ template <typename T> class OpImpl : public purify_op {
     chunk = chunk_opt > 0 ? chunk_opt : 1024;
     if (!light) {  // a set-up operator runs only on the caller's stream
       CK(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
-      CK(cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking));
+      // the ball block is the longer branch of an iteration: its kernels'
+      // CTAs go first when both branches have work waiting
+      int lo = 0, hi = 0;
+      CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+      CK(cudaStreamCreateWithPriority(&aux, cudaStreamNonBlocking, hi));
       CK(cudaStreamCreateWithFlags(&aux2, cudaStreamNonBlocking));
       CK(cudaEventCreateWithFlags(&ev_zfork, cudaEventDisableTiming));
       CK(cudaEventCreateWithFlags(&ev_zjoin, cudaEventDisableTiming));
@@ -1575,7 +1579,9 @@ template <typename T> class BatchImpl {
         if (rc) return rc;
       }
       CK(cudaStreamCreateWithFlags(&gr.main, cudaStreamNonBlocking));
-      CK(cudaStreamCreateWithFlags(&gr.aux, cudaStreamNonBlocking));
+      int lo = 0, hi = 0;
+      CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+      CK(cudaStreamCreateWithPriority(&gr.aux, cudaStreamNonBlocking, hi));  // the ball block's branch first
       CK(cudaEventCreateWithFlags(&gr.fork, cudaEventDisableTiming));
       CK(cudaEventCreateWithFlags(&gr.join, cudaEventDisableTiming));
       CK(cudaEventCreateWithFlags(&gr.done, cudaEventDisableTiming));
