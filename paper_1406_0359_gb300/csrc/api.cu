@@ -28,13 +28,11 @@
 
 namespace purify {
 
-cudaError_t setup_alloc(void** p, size_t bytes, cudaStream_t s) {
+cudaMemPool_t library_pool() {
   static std::mutex mu;
   static cudaMemPool_t pools[64] = {};
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaMallocAsync(p, bytes, s);
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
   cudaMemPool_t pool = nullptr;
   {
     std::lock_guard<std::mutex> lk(mu);
@@ -51,13 +49,18 @@ cudaError_t setup_alloc(void** p, size_t bytes, cudaStream_t s) {
         pools[dev] = np;
       } else {
         cudaGetLastError();  // fall back to the device's default pool
-        e = cudaDeviceGetDefaultMemPool(&np, dev);
-        if (e != cudaSuccess) return e;
+        if (cudaDeviceGetDefaultMemPool(&np, dev) != cudaSuccess) return nullptr;
         pools[dev] = np;
       }
     }
     pool = pools[dev];
   }
+  return pool;
+}
+
+cudaError_t setup_alloc(void** p, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool = library_pool();
+  if (!pool) return cudaMallocAsync(p, bytes, s);
   return cudaMallocFromPoolAsync(p, bytes, pool, s);
 }
 
@@ -207,6 +210,7 @@ template <typename T> class OpImpl : public purify_op {
   // only stream that uses them; released in stream order.
   cudaStream_t pool_stream = nullptr;
   bool items_pooled = false;  // items from the set-up pool (refined operator)
+  cudaMemPool_t lib_pool = nullptr;  // the library's per-device pool (plain operators)
   // Operator of the request server: every allocation comes from the server's
   // stream-ordered pool on the operator's own stream and goes back to it in
   // stream order, so creating and releasing solves never synchronises the
@@ -289,7 +293,8 @@ template <typename T> class OpImpl : public purify_op {
     }
     WorkItem* new_items = nullptr;
     int new_n = 0;
-    const int rc = build_bins<T>(uv_keep, g.M, g, chunk, pos, perm, &new_items, &new_n, s, blocks, R, mem_pool);
+    const int rc =
+        build_bins<T>(uv_keep, g.M, g, chunk, pos, perm, &new_items, &new_n, s, blocks, R, mem_pool ? mem_pool : lib_pool);
     if (rc) {
       note_error("uv binning failed", __LINE__, cudaGetErrorName(cudaGetLastError()));
       return rc;
@@ -306,7 +311,7 @@ template <typename T> class OpImpl : public purify_op {
   void free_items() {
     if (!items) return;
     if (items_pooled) cudaFreeAsync(items, pool_stream);
-    else if (mem_pool) cudaFreeAsync(items, own);
+    else if (mem_pool || lib_pool) cudaFreeAsync(items, own);
     else cudaFree(items);
     items = nullptr;
   }
@@ -319,7 +324,7 @@ template <typename T> class OpImpl : public purify_op {
     free_items();
     if (pool_stream) {  // set-up operator: every use was on pool_stream
       for (void* a : allocs) cudaFreeAsync(a, pool_stream);
-    } else if (mem_pool) {  // server operator: both streams are idle
+    } else if (mem_pool || lib_pool) {  // both streams are idle
       for (void* a : allocs) cudaFreeAsync(a, own);
     } else {
       for (void* a : allocs) cudaFree(a);
@@ -342,9 +347,9 @@ template <typename T> class OpImpl : public purify_op {
     const size_t b = count * sizeof(U) > 0 ? count * sizeof(U) : 16;
     if (pool_stream) {
       CK(setup_alloc(&a, b, pool_stream));
-    } else if (mem_pool) {
+    } else if (mem_pool || lib_pool) {
       // complete before return, so that any stream may use it
-      CK(cudaMallocFromPoolAsync(&a, b, mem_pool, own));
+      CK(cudaMallocFromPoolAsync(&a, b, mem_pool ? mem_pool : lib_pool, own));
       CK(cudaStreamSynchronize(own));
     } else {
       CK(cudaMalloc(&a, b));
@@ -406,6 +411,11 @@ template <typename T> class OpImpl : public purify_op {
     light = light_only || refine;
     mem_pool = light ? nullptr : pool;
     if (light) pool_stream = s;
+    // An operator's own memory comes from the library's per-device pool,
+    // which keeps released memory mapped (up to kSetupPoolKeep), so that the
+    // next operator's creation reuses it instead of mapping new memory, and
+    // destroying an operator does not synchronise the device (cudaFree would).
+    if (!light && !mem_pool) lib_pool = library_pool();
     g.n = n;
     g.K = 2 * n;
     g.KP = g.K + kJ;
@@ -491,7 +501,7 @@ template <typename T> class OpImpl : public purify_op {
       CK(cudaMemcpyAsync(items, refine->items, size_t(n_items) * sizeof(WorkItem), cudaMemcpyDeviceToDevice, s));
       launch_encode_x2<T>(refine->uv_keep, refine->perm, M, refine->g.K, g.TB, pos, s);
     } else {
-      rc = build_bins<T>(uv, M, g, chunk, pos, perm, &items, &n_items, s, nullptr, 1, mem_pool);
+      rc = build_bins<T>(uv, M, g, chunk, pos, perm, &items, &n_items, s, nullptr, 1, mem_pool ? mem_pool : lib_pool);
     }
     if (rc) {
       note_error("uv binning failed", __LINE__, cudaGetErrorName(cudaGetLastError()));
