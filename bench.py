@@ -202,7 +202,10 @@ def run_ours(args, ws, rank, local):
     uv = torch.as_tensor(uv_h, device=dev)
     from paper_1406_0359_gb300.binding import purify_autotune
 
-    tile, chunk, tune_ms = purify_autotune(uv, n, L)
+    if args.tile and args.chunk:  # fixed work decomposition (reproducible profiles)
+        tile, chunk, tune_ms = args.tile, args.chunk, None
+    else:
+        tile, chunk, tune_ms = purify_autotune(uv, n, L)
     op = Operator(uv, n, L, "fp32", tile=tile, chunk=chunk)
     info = op.info()
     xt = torch.as_tensor(x_h, dtype=torch.float32, device=dev)
@@ -360,7 +363,8 @@ def run_ours(args, ws, rank, local):
                      "frac_of_hbm_peak": {k: round(v / hbm, 4) for k, v in pair_gbs.items()}},
         "plain_fp64_gpu_iters_per_s": None if plain is None else round(plain, 3),
         "precision_fp32_vs_fp64": precision,
-        "autotuned": {"tile": tile, "chunk": chunk, "phi_phiH_ms": round(tune_ms, 4)},
+        "autotuned": ({"tile": tile, "chunk": chunk, "phi_phiH_ms": round(tune_ms, 4)} if tune_ms is not None
+                      else {"tile": tile, "chunk": chunk, "fixed": True}),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
                      "unit": "GB/s", "frac": round(achieved / hbm, 4),
                      "traffic": MEASURED_TRAFFIC.get(dom) if args.workload == WORKLOAD else None,
@@ -773,6 +777,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-batch-summary", action="store_true")
+    ap.add_argument("--tile", type=int, default=0, help="with --chunk: skip the autotuner (8 or 16)")
+    ap.add_argument("--chunk", type=int, default=0, help="with --tile: visibilities per work item")
     ap.add_argument("--batch", action="store_true", help="64 uneven instances: batched vs one at a time")
     ap.add_argument("--batch-size", type=int, default=64)
     ap.add_argument("--batch-iters", type=int, default=50)

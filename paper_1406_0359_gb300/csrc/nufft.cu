@@ -514,9 +514,8 @@ __global__ void __launch_bounds__(kThreads) k_degrid_w(Src src, KbPoly<T> kb, co
 // eight lanes updating eight consecutive cells of a row then touch 128
 // contiguous bytes, free of bank conflicts for any row pitch.
 // A gridding accumulator cell (one complex value).  Rows of the per-warp
-// patch are padded so that the four quarter-warps of an update (four patch
-// rows, 8 consecutive cells each) fall in different banks where the row
-// length alone would put them on the same ones.
+// patch are padded so that the quarter-warps of an update (four patch rows,
+// 8 consecutive cells each) that share a half-warp fall in different banks.
 template <typename T> struct __align__(2 * sizeof(T)) GCell { T x, y; };
 template <typename T> PD void cell_add(GCell<T>* cell, T vx, T vy) {
   GCell<T> k = *cell;
@@ -524,8 +523,12 @@ template <typename T> PD void cell_add(GCell<T>* cell, T vx, T vy) {
   k.y += vy;
   *cell = k;
 }
+// FP32 cells are 8 bytes, and a warp's 8-byte accesses are served per
+// half-warp: its two quarter-warps (two patch rows) must fall on disjoint
+// banks, i.e. rows an odd multiple of 64 bytes apart (stride = 8 mod 16
+// cells).  FP64 cells (16 bytes) are served per quarter-warp and need none.
 template <typename T> __host__ __device__ constexpr int grid_row_stride(int pw) {
-  return (sizeof(T) == 4 && pw % 16 == 0) ? pw + 4 : pw;
+  return (sizeof(T) == 4 && pw % 16 == 0) ? pw + 8 : pw;
 }
 
 template <typename T, typename Src>
