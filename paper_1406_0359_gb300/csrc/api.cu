@@ -304,6 +304,7 @@ template <typename T> class OpImpl : public purify_op {
     items = new_items;
     n_items = new_n;
     nblocks = R;
+    ++struct_gen;
     block_sizes = sizes;
     return size_partials();
   }
@@ -318,6 +319,7 @@ template <typename T> class OpImpl : public purify_op {
 
   ~OpImpl() override {
     run_release();
+    if (gcache) cudaGraphExecDestroy(gcache);
     prof_release();
     if (own) cudaStreamSynchronize(own);
     if (aux) cudaStreamSynchronize(aux);
@@ -356,6 +358,7 @@ template <typename T> class OpImpl : public purify_op {
     }
     allocs.push_back(a);
     bytes += int64_t(b);
+    ++struct_gen;
     *ptr = static_cast<U*>(a);
     return PURIFY_OK;
   }
@@ -375,6 +378,7 @@ template <typename T> class OpImpl : public purify_op {
     }
     prior = pr;
     if (pr == 1) tv_iters = iters;
+    ++struct_gen;
     return PURIFY_OK;
   }
 
@@ -390,6 +394,7 @@ template <typename T> class OpImpl : public purify_op {
       return PURIFY_ERR_INVALID;
     }
     sara = p;
+    ++struct_gen;
     return PURIFY_OK;
   }
   unsigned dictionary(int* nbases) const override {
@@ -1086,7 +1091,6 @@ template <typename T> class OpImpl : public purify_op {
   } run;
 
   void run_release() {
-    if (run.gexec) cudaGraphExecDestroy(run.gexec);
     if (run.e0) cudaEventDestroy(run.e0);
     if (run.e1) cudaEventDestroy(run.e1);
     if (run.ev_sc) cudaEventDestroy(run.ev_sc);
@@ -1150,20 +1154,48 @@ template <typename T> class OpImpl : public purify_op {
 
   // One SDMM iteration captured as a CUDA graph (when the parameters ask for
   // replay), with the current nu and gamma baked into its kernel arguments.
-  int capture_iteration(cudaStream_t s) {
-    if (run.gexec) {
-      cudaGraphExecDestroy(run.gexec);
-      run.gexec = nullptr;
+  // The graph stays with the operator: a later solve with the same scalars,
+  // CG steps and pass structure (no buffer allocated, re-binned or
+  // re-planned since: struct_gen) replays it without capturing again.
+  struct GraphKey {
+    double nu, gamma, eps;
+    int cg, toep, prior, tv_iters, nblocks;
+    unsigned dict;
+    uint64_t gen;
+    bool operator==(const GraphKey& o) const {
+      return nu == o.nu && gamma == o.gamma && eps == o.eps && cg == o.cg && toep == o.toep && prior == o.prior &&
+             tv_iters == o.tv_iters && nblocks == o.nblocks && dict == o.dict && gen == o.gen;
     }
+  };
+  cudaGraphExec_t gcache = nullptr;
+  GraphKey gkey{};
+  uint64_t struct_gen = 0;
+  int capture_iteration(cudaStream_t s) {
+    run.gexec = nullptr;
     if (!run.P.use_graph || prof) return PURIFY_OK;
+    const GraphKey k{run.nu,   run.gamma, run.P.eps, run.P.cg_iters, toep ? 1 : 0, prior, tv_iters,
+                     nblocks,  dictionary(nullptr), struct_gen};
+    if (gcache && k == gkey) {
+      run.gexec = gcache;
+      return PURIFY_OK;
+    }
+    if (gcache) {
+      cudaGraphExecDestroy(gcache);
+      gcache = nullptr;
+    }
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     iteration(run.nu, run.gamma, run.P.eps, run.P.cg_iters, s);
     cudaError_t ce = cudaStreamEndCapture(s, &graph);
     if (ce != cudaSuccess) return map_err(ce, __LINE__);
-    ce = cudaGraphInstantiate(&run.gexec, graph, 0);
+    ce = cudaGraphInstantiate(&gcache, graph, 0);
     cudaGraphDestroy(graph);
-    if (ce != cudaSuccess) return map_err(ce, __LINE__);
+    if (ce != cudaSuccess) {
+      gcache = nullptr;
+      return map_err(ce, __LINE__);
+    }
+    gkey = k;
+    run.gexec = gcache;
     return PURIFY_OK;
   }
 
