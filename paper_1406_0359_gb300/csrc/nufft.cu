@@ -560,7 +560,8 @@ __global__ void __launch_bounds__(kThreads) k_grid_w(Src src, KbPoly<T> kb) {
   // lane (ta, tc) accumulates footprint cells (ta, tc) and (ta + 4, tc), so
   // each quarter-warp updates 8 consecutive cells of one patch row.
   const int ta = lane >> 3, tc = lane & 7;
-  int scell = -1;
+  const int lo = ta * PS + tc;  // the lane's first cell relative to a footprint's corner
+  int scell = -1;               // the current run's cell, as its footprint corner's offset in the patch
   C s0 = cz<C>(), s1 = cz<C>();
   for (int base = it.begin; base < it.end; base += 32) {
     const int i = base + lane;
@@ -591,7 +592,7 @@ __global__ void __launch_bounds__(kThreads) k_grid_w(Src src, KbPoly<T> kb) {
 #pragma unroll
         for (int a = 0; a < kJ; ++a) wu[a] = wv[a] = T(0);
       }
-      stage_store_grid(wst + lane * kStage, wu, wv, u.x, u.y, cu * 256 + cv);
+      stage_store_grid(wst + lane * kStage, wu, wv, u.x, u.y, cu * PS + cv);
     }
     __syncwarp();
     for (int j = 0; j < nv; ++j) {
@@ -610,7 +611,7 @@ __global__ void __launch_bounds__(kThreads) k_grid_w(Src src, KbPoly<T> kb) {
       }
       if (cell != scell) {  // warp-uniform
         if (scell >= 0) {
-          const int o = ((scell >> 8) + ta) * PS + (scell & 255) + tc;
+          const int o = scell + lo;
           cell_add(wacc + o, s0.x, s0.y);
           cell_add(wacc + o + 4 * PS, s1.x, s1.y);
           s0 = s1 = cz<C>();
@@ -629,7 +630,7 @@ __global__ void __launch_bounds__(kThreads) k_grid_w(Src src, KbPoly<T> kb) {
     __syncwarp();
   }
   if (scell >= 0) {
-    const int o = ((scell >> 8) + ta) * PS + (scell & 255) + tc;
+    const int o = scell + lo;
     cell_add(wacc + o, s0.x, s0.y);
     cell_add(wacc + o + 4 * PS, s1.x, s1.y);
   }
