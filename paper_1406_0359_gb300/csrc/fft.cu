@@ -228,13 +228,16 @@ template <typename T> struct EpAcc { Acc<T> a[5]; };
 template <int MODE, typename T>
 PD void row_ep_store(const RowEp<T>& ep, size_t idx, T val, EpOpd<T> opd, EpAcc<T>& part) {
   if constexpr (MODE == EP_CG_AP) {
+    // A thread's 16 terms are summed by plain FMAs (their rounding errors are
+    // independent across the ~10^5 threads and average out); the per-thread
+    // sums are then merged compensated.
     const T o = T(ep.nu2) * val + T(2) * opd.a;  // (A p)_i
     ep.out[idx] = o;
-    part.a[0].add_prod(opd.a, o);
-    part.a[1].add_prod(opd.b, o);
-    part.a[2].add_prod(o, o);
-    part.a[3].add_prod(opd.b, opd.a);
-    part.a[4].add_prod(opd.b, opd.b);
+    part.a[0].s = fma(opd.a, o, part.a[0].s);
+    part.a[1].s = fma(opd.b, o, part.a[1].s);
+    part.a[2].s = fma(o, o, part.a[2].s);
+    part.a[3].s = fma(opd.b, opd.a, part.a[3].s);
+    part.a[4].s = fma(opd.b, opd.b, part.a[4].s);
   } else if constexpr (MODE == EP_CG_R0) {
     const T o = opd.a - T(ep.nu2) * val;
     ep.out[idx] = o;
