@@ -290,11 +290,14 @@ def run_ours(args, ws, rank, local):
     uv_pin = torch.as_tensor(uv_h).pin_memory()
     y_pin = y.cpu().pin_memory()
     x_pin = torch.empty(n, n, dtype=torch.float32).pin_memory()
+    side = torch.cuda.Stream(dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     uv_d = uv_pin.to(dev, non_blocking=True)
-    y_d = y_pin.to(dev, non_blocking=True)
+    with torch.cuda.stream(side):  # y travels while the operator is built from uv
+        y_d = y_pin.to(dev, non_blocking=True)
     op2 = Op2(uv_d, n, L, "fp32")
+    torch.cuda.current_stream().wait_stream(side)
     r2 = op2.solve(y_d, eps, **kw)
     x_pin.copy_(r2.x, non_blocking=True)
     torch.cuda.synchronize()
@@ -303,7 +306,8 @@ def run_ours(args, ws, rank, local):
     e2e = {"value": round(K / e2e_s, 3), "unit": UNIT,
            "h2d_bytes_per_step": int((uv_pin.numel() * 8 + y_pin.numel() * 8) / K),
            "d2h_bytes_per_step": int(x_pin.numel() * 4 / K),
-           "includes": "H2D of uv and y, operator creation (uv binning), K SDMM iterations, D2H of x; per solve / K"}
+           "includes": "H2D of uv, then operator creation (uv binning) beside the H2D of y, K SDMM iterations, "
+                       "D2H of x; per solve / K"}
 
     # plain FP64 GPU solver (no graph), same problem; and the precision study:
     # FP32 (compensated gridding, FP64 reductions) against FP64 on the GPU,

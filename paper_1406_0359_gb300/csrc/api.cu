@@ -655,6 +655,10 @@ template <typename T> class OpImpl : public purify_op {
     int rc;
     T* khat_l = nullptr;
     if ((rc = alloc(&khat_l, size_t(g.K / 2 + 1) * g.K))) return rc;
+    if ((rc = alloc(&axh, N())) || (rc = alloc(&gridA2, size_t(g.n) * (g.K / 2)))) return rc;
+    // The spectrum is built on s and not waited for here: its temporaries
+    // return to the pool in stream order, and the caller's next work on s
+    // comes after it.
     {
       OpImpl<T> big;
       const bool reuse = g.TB == 8;  // this binning serves the 2n operator (tiles 16 on its grid)
@@ -678,11 +682,10 @@ template <typename T> class OpImpl : public purify_op {
       if (e == cudaSuccess && rc == 0) build_psf_spectrum<T>(psf, g.n, khat_l, X, tw, s);
       for (void* t : {static_cast<void*>(y1), static_cast<void*>(psf), static_cast<void*>(X)})
         if (t) cudaFreeAsync(t, s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e == cudaSuccess) e = cudaGetLastError();
       if (e != cudaSuccess) return map_err(e, __LINE__);
       if (rc) return rc;
     }
-    if ((rc = alloc(&axh, N())) || (rc = alloc(&gridA2, size_t(g.n) * (g.K / 2)))) return rc;
     khat = khat_l;
     return PURIFY_OK;
   }
@@ -1130,21 +1133,25 @@ template <typename T> class OpImpl : public purify_op {
     toep = gmode == 1;
     launch_gather<C>(static_cast<const C*>(y), perm, M, ys, s);
     launch_check_finite<T>(reinterpret_cast<const T*>(ys), 2 * M, err + 1, s);
+    run.nu = P->nu;
+    run.gamma = P->gamma;
+    run.decay = P->delta_decay > 0 ? P->delta_decay : 0.1;
+    // With nu and gamma given, the iteration graph is captured while the
+    // device still runs the set-up above (the PSF spectrum, the gather).
+    const bool early = run.nu > 0 && run.gamma > 0;
+    if (early && (rc = capture_iteration(s))) return rc;
     CK(cudaStreamSynchronize(s));
     if ((rc = take_input_flag("purify_sdmm_solve", "y holds a non-finite visibility"))) return rc;
-    run.nu = P->nu;
     if (!(run.nu > 0)) {
       double lam = 0;
       if ((rc = power_norm_sq(P->power_iters, &lam, s))) return rc;
       run.nu = lam > 0 ? 1.0 / std::sqrt(lam) : 1.0;
     }
-    run.gamma = P->gamma;
     if (!(run.gamma > 0)) {
       if ((rc = default_gamma(run.nu, &run.gamma, s))) return rc;
       if (!(run.gamma > 0)) run.gamma = 1e-12;
     }
-    run.decay = P->delta_decay > 0 ? P->delta_decay : 0.1;
-    if ((rc = capture_iteration(s))) return rc;
+    if (!early && (rc = capture_iteration(s))) return rc;
     launch_fill<T>(w, D(), T(1), s);
     CK(cudaMemsetAsync(xh, 0, n2 * sizeof(T), s));
     run.active = true;
