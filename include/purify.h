@@ -81,7 +81,8 @@ int purify_op_create(const double* uv, int64_t M, int n, int oversample, int J,
 /* Work decomposition of the gridding kernels (0 = default). */
 typedef struct {
   int tile;   /* uv tile side in grid cells: 8 (default) or 16 */
-  int chunk;  /* visibilities per work item, 64..8192 (default 1024) */
+  int chunk;  /* visibilities per work item, 64..8192 (default by M: 256 below 2^20,
+                 2048 from 2^21, 1024 between -- the autotuner's usual choices) */
 } purify_op_options;
 
 /* purify_op_create_ex -- purify_op_create with an explicit tile / chunk. */

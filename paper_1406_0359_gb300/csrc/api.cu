@@ -430,7 +430,9 @@ template <typename T> class OpImpl : public purify_op {
     g.ntile1d = g.K / g.TB;
     g.M = M;
     levels = L;
-    chunk = chunk_opt > 0 ? chunk_opt : 1024;
+    // default work-item length by M (what purify_autotune usually picks:
+    // many short items for small M, fewer long ones for large M)
+    chunk = chunk_opt > 0 ? chunk_opt : (M < (int64_t(1) << 20) ? 256 : M >= (int64_t(1) << 21) ? 2048 : 1024);
     if (!light) {  // a set-up operator runs only on the caller's stream
       CK(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
       // the ball block is the longer branch of an iteration: its kernels'

@@ -95,7 +95,7 @@ extern "C" int purify_estimate_bytes(int64_t M, int n, int dwt_levels, int preci
   b += double(n) * (K / 2) * c + 2 * KP * KP * c;  // half-spectrum rows, forward grid, gridding grid
   b += 2 * 8 * (N / 4) * r + 9 * N * r;      // wavelet scratch bands, prox output
   b += 6 * N * r + 18 * N * r + 2 * M * c;   // solver vectors, z1 and weights, z3 and sorted y
-  b += (M / 1024.0 + 4.0 * K * K / 256) * 16;  // work items (bound) and partial sums
+  b += (M / 256.0 + 4.0 * K * K / 256) * 16;  // work items (bound, chunks of >= 256) and partial sums
   b += M * (16 + c) + N * r;                 // the server's staging of uv and y, the result image
   if (n <= 1024) {
     // composite operator: spectrum kept; while it is built, a 2n operator,
