@@ -1030,8 +1030,7 @@ template <typename T> class OpImpl : public purify_op {
     gp.block_scale = scale_dev;
     grid(gp, b3);
     col_inv(b3);
-    if (rec) record(R_JOIN, s);
-    else if (b3 != s) cudaEventRecord(ev_join, b3);
+    if (!rec && b3 != s) cudaEventRecord(ev_join, b3);
     if (prior == 1) {
       // block 1 (weighted TV, L_1 = I) with block 2 (positivity) in its
       // epilogue: xs = x_1 + x_2
@@ -1070,8 +1069,10 @@ template <typename T> class OpImpl : public purify_op {
     // A x_hat for the next iteration's CG start, on this branch (it has slack
     // beside the ball block), in its own half-spectrum buffer
     if (toep) normal_apply_qx(xh, axh, nu2, s, gridA2);
-    // join: xs += nu Re Phi^H (2 r_3 - v_3)
-    if (!rec && b3 != s) cudaStreamWaitEvent(s, ev_join, 0);
+    // join: xs += nu Re Phi^H (2 r_3 - v_3) (the batched record joins here too,
+    // so that its l1 and positivity blocks also run beside the ball block)
+    if (rec) record(R_JOIN, s);
+    else if (b3 != s) cudaStreamWaitEvent(s, ev_join, 0);
     RowEp<T> ep{};
     ep.mode = EP_XS_ADD;
     ep.out = xs;
