@@ -128,7 +128,7 @@ template <typename T> cudaError_t configure_once() {
 // pages: creating an operator does not pay a pinned allocation.
 class PinnedSlots {
  public:
-  static constexpr size_t kSlot = 16;  // doubles per slot (>= kNumScalars)
+  static constexpr size_t kSlot = 32;  // doubles per slot (>= kNumScalars)
   double* get() {
     std::lock_guard<std::mutex> lk(mu_);
     if (free_.empty()) {
@@ -1157,6 +1157,7 @@ template <typename T> class OpImpl : public purify_op {
     if (!early && (rc = capture_iteration(s))) return rc;
     launch_fill<T>(w, D(), T(1), s);
     CK(cudaMemsetAsync(xh, 0, n2 * sizeof(T), s));
+    CK(cudaMemsetAsync(sc + S_CG0, 0, 5 * sizeof(double), s));  // the CG's accumulators start at zero
     run.active = true;
     own_pending = true;
     return check(s, false);

@@ -348,14 +348,39 @@ PD void row_ep_finish(const RowEp<T>& ep, EpAcc<T> part, double* red /*[5*32]*/,
     if (lane == 0) st[k * 32 + w] = part.a[k];
   }
   __syncthreads();
+  // CG step: the CTA's five sums go straight into FP64 accumulators (atomic
+  // adds as the CTAs finish), so that the last CTA only reads five values
+  const bool acc64 = ep.mode == EP_CG_AP && ep.ticket;
   if (w == 0) {
     for (int k = 0; k < nsum; ++k) {
       Acc<T> b = lane < nw ? st[k * 32 + lane] : Acc<T>();
       warp_merge(b);
-      if (lane == 0) P[size_t(k) * ep.pstride + bid] = b;
+      if (lane == 0) {
+        if (acc64) atomicAdd(ep.scalars + S_CG0 + k, b.value());
+        else P[size_t(k) * ep.pstride + bid] = b;
+      }
     }
   }
   if (!ep.ticket || !last_block_done_t0(ep.ticket, unsigned(nblocks))) return;
+  if (acc64) {
+    if (threadIdx.x != 0) return;
+    double sum[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      sum[k] = __ldcg(ep.scalars + S_CG0 + k);
+      ep.scalars[S_CG0 + k] = 0.0;  // ready for the next step
+    }
+    double* sc = ep.scalars;
+    const double rr = sum[4];
+    const double alpha = sum[0] > 0.0 ? sum[3] / sum[0] : 0.0;
+    double rr_new = rr - 2.0 * alpha * sum[1] + alpha * alpha * sum[2];
+    if (rr_new < 0.0) rr_new = 0.0;
+    sc[S_PAP] = sum[0];
+    sc[S_ALPHA] = alpha;
+    sc[S_BETA] = rr > 0.0 ? rr_new / rr : 0.0;
+    sc[S_RR] = rr_new;
+    return;
+  }
   // last block: merge all blocks' partials (fixed order), FP64 only at the end
   EpAcc<T> tot;
   int i = threadIdx.x;

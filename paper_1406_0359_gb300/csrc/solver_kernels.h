@@ -10,7 +10,9 @@ namespace purify {
 // Device scalar slots (double[kNumScalars]).
 enum ScalarSlot : int {
   S_RR = 0, S_ALPHA, S_BETA, S_PAP, S_BALLSCALE, S_BALLNORM, S_RESID, S_OBJ,
-  S_LAMBDA, S_INVNORM, S_MEAN, S_STD, S_MAXABS, S_FEAS, kNumScalars
+  S_LAMBDA, S_INVNORM, S_MEAN, S_STD, S_MAXABS, S_FEAS,
+  S_CG0,  // S_CG0 .. S_CG0 + 4: a CG step's five inner products, accumulated across CTAs (zero between steps)
+  kNumScalars = S_CG0 + 5
 };
 enum FinOp : int { FIN_OBJ = 0, FIN_NORM, FIN_MEAN, FIN_VAR };
 enum RedOp : int { RED_SQ = 0, RED_SUM, RED_VAR, RED_MAXABS };
