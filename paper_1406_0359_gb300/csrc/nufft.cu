@@ -507,13 +507,8 @@ __global__ void __launch_bounds__(kThreads) k_degrid_w(Src src, KbPoly<T> kb, co
   }
 }
 
-// Compensated (Kahan) accumulation of a run sum into a patch cell: the cell
-// keeps its running sum and the low-order part lost so far.
-// A gridding accumulator cell: the running sum and its Kahan compensation,
-// side by side so that one 16-byte shared access (two for FP64) moves both;
-// eight lanes updating eight consecutive cells of a row then touch 128
-// contiguous bytes, free of bank conflicts for any row pitch.
-// A gridding accumulator cell (one complex value).  Rows of the per-warp
+// A gridding accumulator cell (one complex value); a run sum is added into
+// it with one 8-byte (FP32) shared read-modify-write.  Rows of the per-warp
 // patch are padded so that the quarter-warps of an update (four patch rows,
 // 8 consecutive cells each) that share a half-warp fall in different banks.
 template <typename T> struct __align__(2 * sizeof(T)) GCell { T x, y; };
