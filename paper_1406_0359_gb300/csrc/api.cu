@@ -219,6 +219,8 @@ template <typename T> class OpImpl : public purify_op {
   cudaStream_t own = nullptr;  // solver stream (capturable, non-blocking)
   cudaStream_t aux = nullptr;  // second branch of an SDMM iteration (ball block)
   cudaStream_t aux2 = nullptr;  // zeroing of the gridding accumulator beside the ball block's first passes
+  cudaStream_t aux3 = nullptr;  // the A x_hat passes for the next CG start (lowest priority)
+  cudaEvent_t ev_axf = nullptr, ev_axj = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_zfork = nullptr, ev_zjoin = nullptr;
   double* bpart = nullptr;     // ball-block partials (2 per work item), apart from the l1 block's
@@ -339,6 +341,10 @@ template <typename T> class OpImpl : public purify_op {
     if (ev_zjoin) cudaEventDestroy(ev_zjoin);
     if (aux2) cudaStreamSynchronize(aux2);
     if (aux2) cudaStreamDestroy(aux2);
+    if (aux3) cudaStreamSynchronize(aux3);
+    if (aux3) cudaStreamDestroy(aux3);
+    if (ev_axf) cudaEventDestroy(ev_axf);
+    if (ev_axj) cudaEventDestroy(ev_axj);
     if (own) cudaStreamDestroy(own);
     if (aux) cudaStreamDestroy(aux);
     if (h_sc) pinned_slots().put(h_sc);
@@ -434,12 +440,16 @@ template <typename T> class OpImpl : public purify_op {
     // many short items for small M, fewer long ones for large M)
     chunk = chunk_opt > 0 ? chunk_opt : (M < (int64_t(1) << 20) ? 256 : M >= (int64_t(1) << 21) ? 2048 : 1024);
     if (!light) {  // a set-up operator runs only on the caller's stream
-      CK(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
       // the ball block is the longer branch of an iteration: its kernels'
-      // CTAs go first when both branches have work waiting
+      // CTAs go first when several branches have work waiting, then the
+      // l1 / positivity blocks (own stream), then the A x_hat passes
       int lo = 0, hi = 0;
       CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+      CK(cudaStreamCreateWithPriority(&own, cudaStreamNonBlocking, (lo + hi) / 2));
       CK(cudaStreamCreateWithPriority(&aux, cudaStreamNonBlocking, hi));
+      CK(cudaStreamCreateWithPriority(&aux3, cudaStreamNonBlocking, lo));
+      CK(cudaEventCreateWithFlags(&ev_axf, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ev_axj, cudaEventDisableTiming));
       CK(cudaStreamCreateWithFlags(&aux2, cudaStreamNonBlocking));
       CK(cudaEventCreateWithFlags(&ev_zfork, cudaEventDisableTiming));
       CK(cudaEventCreateWithFlags(&ev_zjoin, cudaEventDisableTiming));
@@ -998,6 +1008,12 @@ template <typename T> class OpImpl : public purify_op {
     // The gridding accumulator is zeroed on a third stream meanwhile (nothing
     // before the gridding pass touches it).
     const bool zpar = !rec && b3 != s;
+    if (zpar && toep) {  // A x_hat for the next CG start on its own, lowest-priority stream
+      cudaEventRecord(ev_axf, s);
+      cudaStreamWaitEvent(aux3, ev_axf, 0);
+      normal_apply_qx(xh, axh, nu2, aux3, gridA2);
+      cudaEventRecord(ev_axj, aux3);
+    }
     if (zpar) {
       cudaEventRecord(ev_zfork, b3);
       cudaStreamWaitEvent(aux2, ev_zfork, 0);
@@ -1066,9 +1082,10 @@ template <typename T> class OpImpl : public purify_op {
       fin(partials, npo, FIN_OBJ, 0.0, s);
       PROF(KK_SARA_SYN, s, sara_synthesis_pos<T>(sara, xh, z2, xs, s));
     }
-    // A x_hat for the next iteration's CG start, on this branch (it has slack
-    // beside the ball block), in its own half-spectrum buffer
-    if (toep) normal_apply_qx(xh, axh, nu2, s, gridA2);
+    // A x_hat for the next iteration's CG start (on the lowest-priority
+    // stream when the branches run side by side), in its own half-spectrum buffer
+    if (toep && !zpar) normal_apply_qx(xh, axh, nu2, s, gridA2);
+    if (toep && zpar) cudaStreamWaitEvent(s, ev_axj, 0);
     // join: xs += nu Re Phi^H (2 r_3 - v_3) (the batched record joins here too,
     // so that its l1 and positivity blocks also run beside the ball block)
     if (rec) record(R_JOIN, s);
