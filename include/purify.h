@@ -248,7 +248,9 @@ typedef struct {
   double delta_decay; /* delta_k = max(decay^(k-1) delta_1, delta_min); <= 0 selects 0.1 */
   int warm_start;     /* non-zero: each reweighted round starts from the previous solution */
   int power_iters;    /* power-iteration steps used when nu <= 0 (>= 1) */
-  int use_graph;      /* non-zero: replay one SDMM iteration as a captured CUDA graph */
+  int use_graph;      /* non-zero: replay one SDMM iteration as a captured CUDA graph (the operator
+                         keeps it for later solves with the same nu, gamma, eps, cg_iters,
+                         dictionary, prior and blocks) */
   int gram;           /* CG operator Re(Phi^H Phi): 0 NUFFT (G^H G each application), 1 precomputed
                          composite as a PSF convolution (Section 3), -1 the latter when n <= 1024 */
   const double* eps_blocks; /* host, one bound per visibility block (Eq. 5) when
